@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""ptSNE benchmark: point-iterations/s on the uneven-chunk workload
+(N = 1,000,000 points, D = 64, chunk sizes drawn U[1000, 5000], perplexity 30,
+100 gradient iterations per epoch, 2-D map), one step = one ptSNE epoch
+(partition gather, distances, perplexity search, joint P, all gradient
+iterations of every chunk, pooling, cost evaluation).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (launched by
+torch.distributed.run) every rank runs its own replica of the workload (weak
+scaling, no collective on the data path); the timed region is bracketed by a
+barrier and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ptSNE point-iterations/s at N=1M, D=64 vs plain FP32 GPU; % of roofline"
+UNIT = "point-iter/s"
+WORKLOAD = "uneven-1m-d64"
+PERM_POOL = 4          # distinct epoch partitions cycled through the steps
+DOMINANT = "grad_persist_kernel"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", choices=["fp32", "bf16_window"], default="fp32")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 per-chunk comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------- distributed helpers
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int) -> float:
+    """Max of a per-rank scalar over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, seconds_per_rank: float, world: int) -> tuple[float, float]:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    t = reduce_max(seconds_per_rank, world)
+    return units_per_rank * world / t, t
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ----------------------------------------------------------------- roofline bookkeeping
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def algorithmic_iterate_bytes(sizes: np.ndarray, iters: int) -> float:
+    """Minimum DRAM bytes of one launch of the iteration kernel: the symmetric
+    FP32 joint P read once per iteration (z (z - 1) / 2 stored pairs x 4 B per
+    chunk); map, velocity and gains are O(z) per chunk and are neglected."""
+    z = sizes.astype(np.float64)
+    return float(iters * np.sum(z * (z - 1) / 2 * 4.0))
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source
+    it was taken on is unchanged (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(f"{kernel}@{workload}")
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1812_09869_gb300", "csrc", rec["source"])
+    if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != rec["source_sha1"]:
+        return None
+    return float(rec["bytes_per_launch"])
+
+
+# ----------------------------------------------------------------- CPU baseline (the oracle)
+
+def oracle_sample(w, seconds: float, max_chunks: int = 64):
+    """Time the FP64 oracle on whole chunks of epoch 0 (affinities, all
+    iterations, cost) until `seconds` of CPU time have been spent."""
+    from oracle import oracle as O
+    prm = O.params(perplexity=w.perplexity, lr=w.lr, momentum=w.momentum, iters=w.iters, epochs=1)
+    perm = w.perms[0]
+    units, spent, chunks = 0, 0.0, 0
+    for c in range(min(max_chunks, len(w.offsets) - 1)):
+        idx = perm[w.offsets[c]:w.offsets[c + 1]]
+        t0 = time.perf_counter()
+        O.partial_tsne(w.X[idx], w.Y0[idx], prm)
+        spent += time.perf_counter() - t0
+        units += len(idx) * w.iters
+        chunks += 1
+        if spent >= seconds:
+            break
+    return {"value": units / spent, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{chunks} chunk(s) of epoch 0 ({units // w.iters} points), affinities + {w.iters} "
+                      f"iterations + cost each, FP64 C with OpenMP over rows; {spent:.1f} s"}
+
+
+# ----------------------------------------------------------------- our arm
+
+def bench_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1812_09869_gb300 import build as pbuild
+    from paper_1812_09869_gb300 import ptsne, synth
+
+    if rank == 0:
+        pbuild.build()
+    barrier(world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.workload(args.workload, epochs=PERM_POOL)
+    sizes = np.diff(w.offsets)
+    cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
+                       momentum=w.momentum, precision=args.precision, schedule="batched")
+    ctx = ptsne.Context(cfg)
+    Xd = torch.from_numpy(w.X).to(dev)
+    perms = torch.from_numpy(w.perms).to(dev)
+    Y = torch.from_numpy(w.Y0.copy()).to(dev)
+    cost = np.zeros((1, 2))
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        ctx.run(Xd, perms[k % PERM_POOL], 1, Y, cost_out=cost)
+
+    for k in range(args.warmup):
+        step(k)
+    ctx.set_profiling(True)
+    ctx.reset_counters()
+    sampler = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ctx.set_profiling(False)
+    secs = e0.elapsed_time(e1) / 1000.0
+    st = ctx.stats()
+    launches = int(st.kernel_launches)
+    stages = {name: (st.stage_ms[k] / st.stage_calls[k] if st.stage_calls[k] else None)
+              for k, name in enumerate(ptsne.STAGES)}
+    units = float(w.n * w.iters * args.steps)
+    value, tmax = aggregate(units, secs, world)
+    final_cost = cost[0].tolist()
+
+    # dominant kernel: one persistent launch per epoch runs every iteration
+    it_ms = stages["iterate"]
+    peaks = measured_peaks()
+    alg = algorithmic_iterate_bytes(sizes, w.iters)
+    achieved = alg / (it_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic(DOMINANT, args.workload),
+                "kernel": DOMINANT, "kernel_ms": it_ms, "algorithmic_bytes": alg,
+                "peak_source": peaks["source"]}
+
+    # end to end through the public API on host buffers (copies inside the timed region)
+    Xh = torch.from_numpy(w.X).pin_memory()
+    Ph = torch.from_numpy(w.perms).pin_memory()
+    Yh = torch.from_numpy(w.Y0.copy()).pin_memory()
+    ctx.run_host(Xh, Ph[0], 1, Yh)   # first call allocates the staging buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        ctx.run_host(Xh, Ph[k % PERM_POOL], 1, Yh, cost_out=cost)
+    t_e2e = time.perf_counter() - t0
+    e2e_value, _ = aggregate(float(w.n * w.iters * e2e_steps), t_e2e, world)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w.X.nbytes + w.n * 4 + w.Y0.nbytes),
+           "d2h_bytes_per_step": int(w.Y0.nbytes + 16)}
+    ctx.close()
+    del Xh, Ph, Yh
+
+    # plain FP32 GPU form: per-chunk launches, FP32 SIMT distances, full P
+    plain = None
+    if not args.no_plain and world == 1:
+        pcfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
+                            momentum=w.momentum, precision="fp32", schedule="per_chunk")
+        with ptsne.Context(pcfg) as pctx:
+            Yp = torch.from_numpy(w.Y0.copy()).to(dev)
+            pcost = np.zeros((1, 2))
+            pctx.run(Xd, perms[0], 1, Yp, cost_out=pcost)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pctx.run(Xd, perms[1], 1, Yp, cost_out=pcost)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ps = a.elapsed_time(b) / 1000.0
+        plain = {"value": w.n * w.iters / ps, "unit": UNIT, "ms_per_step": ps * 1e3, "schedule": "per_chunk",
+                 "distances": "fp32", "steps": 1, "speedup_of_value": value / (w.n * w.iters / ps),
+                 "final_cost": pcost[0].tolist()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, args.cpu_seconds)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": w.n, "d": w.d, "chunks": int(len(sizes)),
+                   "chunk_size_range": [int(sizes.min()), int(sizes.max())], "perplexity": w.perplexity,
+                   "iters_per_epoch": w.iters, "out_dim": 2, "schedule": "batched persistent",
+                   "distances": args.precision, "step": "one epoch", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (joint P %.1f GB per epoch)" % (4 * float((sizes ** 2).sum()) / 1e9)},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        "plain_fp32": plain, "stages_ms": stages, "final_cost": {"avg_kl": final_cost[0], "avg_norm_cost": final_cost[1]},
+        "impl": "ours",
+    }
+    return out
+
+
+# ----------------------------------------------------------------- reference arm (the oracle)
+
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import build as obuild
+    from oracle import oracle as O
+    from paper_1812_09869_gb300 import synth
+    obuild.build()
+    w = synth.workload(args.workload, epochs=1)
+    prm = O.params(perplexity=w.perplexity, lr=w.lr, momentum=w.momentum, iters=w.iters, epochs=1)
+    perm, off = w.perms[0], w.offsets
+
+    def one(c):
+        idx = perm[off[c]:off[c + 1]]
+        t0 = time.perf_counter()
+        O.partial_tsne(w.X[idx], w.Y0[idx], prm)
+        return len(idx) * w.iters, time.perf_counter() - t0
+
+    nck = len(off) - 1
+    for k in range(args.warmup):
+        one(k % nck)
+    units, secs = 0, 0.0
+    for k in range(args.steps):
+        u, s = one((args.warmup + k) % nck)
+        units += u
+        secs += s
+    value = units / secs
+    sample = (f"{args.steps} timed chunk(s) of epoch 0 (one per step: affinities + {w.iters} iterations + cost), "
+              f"FP64 C oracle with OpenMP")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": w.n, "d": w.d, "perplexity": w.perplexity,
+                       "iters_per_epoch": w.iters, "step": "one chunk's partial t-SNE"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        out = bench_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return 0
+    import torch
+    dist_init(world, "nccl" if torch.cuda.is_available() else "gloo")
+    out = bench_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

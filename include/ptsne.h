@@ -1,0 +1,188 @@
+/*
+ * ptsne.h — C ABI of libptsne.so, the GB300 (sm_103a) implementation of the
+ * hot path of parallelized t-SNE (ptSNE; Garriga & Bartumeus, "bigMap: Big
+ * Data Mapping with parallelized t-SNE", arXiv 1812.09869).
+ *
+ * A ptSNE epoch cuts a random permutation of the n points into chunks (the
+ * paper's "threads"; one layer), runs one partial t-SNE per chunk and pools
+ * the partial maps back (ptSNE section, subsections "threads" and "epochs").
+ * For each chunk of z points:
+ *   affinities  — squared Euclidean distances, per-row precision beta_i such
+ *                 that the perplexity 2^H of p_{.|i} (Eq. 1, Eq. 2) equals the
+ *                 target, joint P_ij = (p_{j|i} + p_{i|j}) / (2z) (Eq. 3);
+ *   iterations  — Cauchy kernel w_ij and normaliser Z (Eq. 4), exact gradient
+ *                 4 sum_j (p_ij - w_ij/Z) w_ij (y_i - y_j) (Eq. 6), momentum
+ *                 update in the descent direction (Eq. 12) with optional gains
+ *                 or the auto-adaptive learning rate (Eq. 13);
+ *   evaluation  — KL (Eq. 5) and pseudo-normalised cost (Eq. 9) averaged over
+ *                 chunks.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers on the current CUDA device;
+ *     *_host are host pointers.  Arrays are dense and row-major.
+ *   - Points are addressed in their ORIGINAL order (0..n-1) in X, Y, beta and
+ *     grad.  A partition is a device int32 permutation perm of [0, n); chunk c
+ *     holds the points perm[off[c] .. off[c+1]) with off the chunk offsets
+ *     given at creation.  Permutations are inputs (drawn by the caller).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued on it; entry points marked "async"
+ *     return before the GPU work completes.
+ *   - The caller owns every array it passes.  The context owns its device
+ *     workspace (allocated once by ptsne_create) and frees it in
+ *     ptsne_destroy.
+ *   - Return codes: PTSNE_OK (0), a negative error, or a positive warning.
+ *     Argument errors are detected on the host before any work is enqueued;
+ *     ptsne_last_error() then describes the first failure.  Permutation
+ *     entries outside [0, n) are detected on the device, skipped, and counted
+ *     (ptsne_get_stats); ptsne_run then fails with PTSNE_EINVAL.
+ */
+#ifndef PTSNE_H
+#define PTSNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTSNE_OK 0
+#define PTSNE_EINVAL (-1)     /* bad argument (null pointer, size, layout, perplexity) */
+#define PTSNE_ENONFINITE (-2) /* NaN or Inf found in X */
+#define PTSNE_ENOMEM (-3)     /* device allocation failed */
+#define PTSNE_ECUDA (-4)      /* a CUDA call failed */
+#define PTSNE_ESTATE (-5)     /* call order violated (e.g. step before affinities) */
+#define PTSNE_WBISECT 1       /* some rows' perplexity search missed its tolerance */
+
+#define PTSNE_LR_FIXED 0      /* eta = lr (with gains if use_gains) */
+#define PTSNE_LR_PAPER 1      /* eta = ln(z-1) (Ymax - Ymin) / 2 per chunk (Eq. 13) */
+
+#define PTSNE_PREC_FP32 0        /* distances in FP32 by direct differences */
+#define PTSNE_PREC_BF16_WINDOW 1 /* BF16 tensor-core Gram matrix, FP32 recompute in the
+                                    perplexity window of each row */
+
+#define PTSNE_SCHED_BATCHED 0    /* all chunks per launch; one persistent launch per epoch
+                                    runs every gradient iteration of every chunk */
+#define PTSNE_SCHED_PER_CHUNK 1  /* plain form: each chunk and iteration launched separately */
+
+/* Stages of a ptsne_run epoch, for per-stage timing (ptsne_set_profiling). */
+#define PTSNE_STAGE_GATHER 0     /* gather X and Y rows by the partition, reset the optimiser */
+#define PTSNE_STAGE_DISTANCES 1  /* pairwise distances (all chunks; the per-chunk schedule
+                                    counts its whole affinity phase here) */
+#define PTSNE_STAGE_PERPLEXITY 2 /* per-row beta search (and window recompute) */
+#define PTSNE_STAGE_JOINT_P 3    /* symmetric joint P */
+#define PTSNE_STAGE_ITERATE 4    /* all gradient iterations of the epoch */
+#define PTSNE_STAGE_POOL 5       /* scatter the partial maps back */
+#define PTSNE_STAGE_COST 6       /* per-epoch cost evaluation (if requested) */
+#define PTSNE_N_STAGES 7
+
+typedef struct ptsne_ctx ptsne_ctx;
+
+typedef struct {
+    int64_t n;                    /* points, >= 2 */
+    int32_t d;                    /* input dimensions, 1..4096 */
+    int32_t out_dim;              /* embedding dimensions: 2 or 3 (Eq. 4 text: d in {2,3}) */
+    double perplexity;            /* target perplexity; 1 < perplexity < z_min - 1 (Eq. 2:
+                                     the maximum perplexity of a chunk of z points is z-1) */
+    int32_t n_chunks;             /* >= 1 */
+    const int64_t* chunk_offsets; /* host, n_chunks+1 entries, off[0]=0, off[n_chunks]=n,
+                                     every chunk size in [2, 8192]; copied by ptsne_create */
+    int32_t iters;                /* gradient iterations per epoch (ptsne_run), >= 0 */
+    float lr;                     /* learning rate eta for PTSNE_LR_FIXED, > 0 */
+    float momentum;               /* alpha of Eq. 12, in [0, 1) */
+    int32_t lr_mode;              /* PTSNE_LR_FIXED or PTSNE_LR_PAPER */
+    int32_t use_gains;            /* 1: per-coordinate gains (+0.2 on sign change of grad
+                                     versus velocity, x0.8 otherwise, floor 0.01) */
+    int32_t precision;            /* PTSNE_PREC_* */
+    int32_t schedule;             /* PTSNE_SCHED_* */
+} ptsne_params;
+
+typedef struct {
+    int64_t bisect_rows;          /* rows searched by the last ptsne_affinities */
+    int64_t bisect_fp64_rows;     /* rows whose FP32 search stalled and were redone in FP64 */
+    int64_t bisect_failed_rows;   /* rows that missed the tolerance even in FP64 */
+    int64_t window_pairs;         /* BF16_WINDOW: distances recomputed in FP32 */
+    int64_t nonfinite_inputs;     /* NaN/Inf entries seen in X by the last gather */
+    int64_t bad_perm_entries;     /* permutation entries outside [0, n): skipped, never dereferenced */
+    double max_abs_entropy_err;   /* max |H(beta_i) - ln perplexity| (nats) of the last search */
+    int64_t kernel_launches;      /* kernels this context enqueued since creation / last reset */
+    double stage_ms[PTSNE_N_STAGES];     /* profiling on: device time per stage of ptsne_run */
+    int64_t stage_calls[PTSNE_N_STAGES]; /* profiling on: epochs accumulated into stage_ms */
+} ptsne_stats;
+
+/* Turn on (1) or off (0) per-stage timing of ptsne_run: CUDA events are
+ * recorded between its stages on the caller's stream and, after each epoch,
+ * the elapsed times are added to stage_ms (the host waits for each epoch to
+ * finish while profiling).  Off by default. */
+int ptsne_set_profiling(ptsne_ctx* ctx, int on);
+
+/* Zero kernel_launches, stage_ms and stage_calls. */
+int ptsne_reset_counters(ptsne_ctx* ctx);
+
+/* Create a context for one problem shape and allocate its device workspace
+ * on the current device.  Validates every field (PTSNE_EINVAL), then
+ * allocates (PTSNE_ENOMEM).  On success *out owns the workspace. */
+int ptsne_create(ptsne_ctx** out, const ptsne_params* params);
+
+/* Release the context and its workspace (NULL is a no-op).  Synchronises the
+ * device first so that no enqueued work still uses the workspace. */
+void ptsne_destroy(ptsne_ctx* ctx);
+
+/* Text of the last error recorded on ctx (never NULL).  With ctx == NULL:
+ * the reason of the last failed ptsne_create on the calling thread. */
+const char* ptsne_last_error(const ptsne_ctx* ctx);
+
+/* Input affinities for the partition perm_dev (Eq. 1-3 per chunk, n := z).
+ * X_dev: n x d float32.  perm_dev: n int32.  P_out_dev (optional, NULL to
+ * skip): receives every chunk's z x z joint P, row-major, chunks concatenated
+ * in chunk order (sum_c z_c^2 floats; rows and columns in chunk order, i.e.
+ * P_out[c][r][s] couples points perm[off[c]+r] and perm[off[c]+s]).
+ * beta_out_dev (optional): n floats, beta of each point in original order.
+ * Keeps P for later ptsne_step / ptsne_cost calls and resets the optimiser
+ * state (velocity 0, gains 1): each partition starts fresh partial t-SNEs.
+ * Async. */
+int ptsne_affinities(ptsne_ctx* ctx, const float* X_dev, const int32_t* perm_dev,
+                     float* P_out_dev, float* beta_out_dev, void* stream);
+
+/* One gradient iteration on every chunk of the partition of the last
+ * ptsne_affinities call (Eq. 4, 6, 12/13).  Y_dev: n x out_dim float32 in
+ * original order, updated in place.  grad_out_dev (optional): n x out_dim,
+ * the gradient of Eq. 6 at the input Y.  Z_out_dev (optional): n_chunks
+ * doubles, each chunk's Z of Eq. 4 at the input Y.  perm_dev must be the same
+ * permutation.  Async. */
+int ptsne_step(ptsne_ctx* ctx, const int32_t* perm_dev, float* Y_dev,
+               float* grad_out_dev, double* Z_out_dev, void* stream);
+
+/* Average over chunks of KL (Eq. 5) and pseudo-normalised cost (Eq. 9) for
+ * the P of the last ptsne_affinities and the map Y_dev (original order).
+ * out_dev: 2 doubles {avg KL, avg normalised cost} on the device.  Async. */
+int ptsne_cost(ptsne_ctx* ctx, const int32_t* perm_dev, const float* Y_dev,
+               double* out_dev, void* stream);
+
+/* The ptSNE cycle: for e in [0, epochs): affinities for perms_dev[e] (n int32
+ * each, epochs x n), `iters` gradient iterations of every chunk from the
+ * current map, pooling into Y_dev (n x out_dim, in: start map, out: result).
+ * cost_out_host (optional): epochs x 2 doubles, {avg KL, avg normalised cost}
+ * at the end of each epoch.  Synchronous: returns after the work completes,
+ * with PTSNE_WBISECT if some row missed the perplexity tolerance. */
+int ptsne_run(ptsne_ctx* ctx, const float* X_dev, const int32_t* perms_dev,
+              int32_t epochs, float* Y_dev, double* cost_out_host, void* stream);
+
+/* ptsne_run on HOST buffers: copies X_host (n x d), perms_host (epochs x n)
+ * and Y_host (n x out_dim) to context-owned device buffers, runs, and copies
+ * the map back into Y_host.  Page-locked host memory makes the copies
+ * asynchronous.  Synchronous. */
+int ptsne_run_host(ptsne_ctx* ctx, const float* X_host, const int32_t* perms_host,
+                   int32_t epochs, float* Y_host, double* cost_out_host, void* stream);
+
+/* Counters of the last ptsne_affinities / ptsne_run.  Synchronises stream. */
+int ptsne_get_stats(ptsne_ctx* ctx, ptsne_stats* out, void* stream);
+
+/* Bytes of device workspace held by ctx. */
+size_t ptsne_workspace_bytes(const ptsne_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTSNE_H */

@@ -1,0 +1,80 @@
+"""Build libptsne.so (sm_103a) in-tree with nvcc.
+
+Each .cu file under csrc/ is compiled separately (in parallel) and linked into
+paper_1812_09869_gb300/libptsne.so.  Rebuilds only what changed.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import glob
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libptsne.so")
+ROOT = os.path.dirname(HERE)
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+           "-Xptxas", "-v", "-I", os.path.join(ROOT, "include")]
+
+
+def _nvcc() -> str:
+    cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cand):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libptsne")
+    return cand
+
+
+def _headers_digest() -> str:
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "ptsne.h")]):
+        h.update(open(f, "rb").read())
+    h.update(" ".join(ARCH + NVFLAGS).encode())
+    return h.hexdigest()
+
+
+def _compile(src: str, obj: str, log: str) -> None:
+    cmd = [_nvcc(), *ARCH, *NVFLAGS, "-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    with open(log, "w") as f:
+        f.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr[-6000:]}")
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    digest = _headers_digest()
+    stamp = os.path.join(BUILD, "headers.sha1")
+    stale_headers = force or not os.path.exists(stamp) or open(stamp).read() != digest
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    jobs = []
+    objs = []
+    for src in srcs:
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        objs.append(obj)
+        if stale_headers or not os.path.exists(obj) or os.path.getmtime(obj) < os.path.getmtime(src):
+            jobs.append((src, obj, obj + ".log"))
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+            list(ex.map(lambda a: _compile(*a), jobs))
+    relink = bool(jobs) or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    if relink:
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
+        subprocess.run(cmd, check=True)
+    with open(stamp, "w") as f:
+        f.write(digest)
+    if verbose:
+        for _, obj, log in jobs:
+            print(open(log).read())
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,462 @@
+// C-ABI entry points of libptsne (declared and documented in include/ptsne.h).
+// They validate arguments on the host, own the device workspace, and enqueue
+// the kernels of k_*.cu on the caller's stream.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+
+#include "ptsne_internal.cuh"
+
+using namespace ptsne;
+
+namespace ptsne {
+int persistent_smem_bytes(int od, int64_t zmax);
+
+Layout make_layout(const ptsne_ctx* c) {
+    Layout L;
+    L.n = c->p.n;
+    L.n_chunks = c->p.n_chunks;
+    L.d = c->p.d;
+    L.dp = c->dp;
+    L.od = c->p.out_dim;
+    L.off = c->d_off;
+    L.moff = c->d_moff;
+    L.ld = c->d_ld;
+    L.chunk_of_row = c->d_chunk_of_row;
+    L.order = c->d_order;
+    return L;
+}
+}  // namespace ptsne
+
+namespace {
+
+constexpr int kCostHist = 4096;
+thread_local std::string g_create_err;  // message of the last failed ptsne_create on this thread
+
+int fail(ptsne_ctx* c, int code, const char* fmt, const char* a = "", long long b = 0) {
+    if (c) {
+        char buf[512];
+        snprintf(buf, sizeof buf, fmt, a, b);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(c, PTSNE_ECUDA, "%s: %lld", cudaGetErrorString(e_), \
+                                           (long long)__LINE__);                          \
+    } while (0)
+
+template <class T>
+int dalloc(ptsne_ctx* c, T** p, size_t count) {
+    const size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, PTSNE_ENOMEM, "device allocation of %s bytes failed (%lld)", "", (long long)bytes);
+    }
+    c->ws_bytes += bytes;
+    return PTSNE_OK;
+}
+
+void free_all(ptsne_ctx* c) {
+    void* ptrs[] = {c->d_off,  c->d_moff,  c->d_ld,   c->d_chunk_of_row, c->d_order, c->d_dense_off,
+                    c->d_tiles, c->Xg,     c->Xb,     c->xnorm,          c->D,       c->P,
+                    c->beta,   c->mrow,    c->Srow,   c->Yc,             c->vel,     c->gains,
+                    c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
+                    c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
+                    c->hY};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& e : c->ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char* ptsne_last_error(const ptsne_ctx* ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+size_t ptsne_workspace_bytes(const ptsne_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
+    if (!out || !prm) return PTSNE_EINVAL;
+    *out = nullptr;
+    ptsne_ctx* c = new (std::nothrow) ptsne_ctx();
+    if (!c) return PTSNE_ENOMEM;
+    g_create_err.clear();
+    auto bad = [&](const char* msg, long long v) {
+        fail(c, PTSNE_EINVAL, "invalid parameter: %s (%lld)", msg, v);
+        g_create_err = c->err;
+        delete c;
+        return PTSNE_EINVAL;
+    };
+    const ptsne_params& p = *prm;
+    if (p.n < 2) return bad("n must be >= 2", p.n);
+    if (p.d < 1 || p.d > 4096) return bad("d must be in [1, 4096]", p.d);
+    if (p.out_dim != 2 && p.out_dim != 3) return bad("out_dim must be 2 or 3", p.out_dim);
+    if (p.n_chunks < 1) return bad("n_chunks must be >= 1", p.n_chunks);
+    if (!p.chunk_offsets) return bad("chunk_offsets is NULL", 0);
+    if (p.chunk_offsets[0] != 0 || p.chunk_offsets[p.n_chunks] != p.n)
+        return bad("chunk offsets must start at 0 and end at n", p.chunk_offsets[p.n_chunks]);
+    int64_t zmin = INT64_MAX, zmax = 0;
+    for (int k = 0; k < p.n_chunks; ++k) {
+        const int64_t z = p.chunk_offsets[k + 1] - p.chunk_offsets[k];
+        if (z < 2 || z > kMaxChunk) return bad("every chunk size must be in [2, 8192]", z);
+        zmin = std::min(zmin, z);
+        zmax = std::max(zmax, z);
+    }
+    if (!(p.perplexity > 1.0) || !(p.perplexity < (double)(zmin - 1)) || !isfinite(p.perplexity))
+        return bad("perplexity must satisfy 1 < perplexity < min chunk size - 1", zmin);
+    if (p.iters < 0) return bad("iters must be >= 0", p.iters);
+    if (!(p.lr > 0.f) || !isfinite(p.lr)) return bad("lr must be > 0", 0);
+    if (!(p.momentum >= 0.f && p.momentum < 1.f)) return bad("momentum must be in [0, 1)", 0);
+    if (p.lr_mode != PTSNE_LR_FIXED && p.lr_mode != PTSNE_LR_PAPER) return bad("lr_mode", p.lr_mode);
+    if (p.use_gains != 0 && p.use_gains != 1) return bad("use_gains must be 0 or 1", p.use_gains);
+    if (p.precision != PTSNE_PREC_FP32 && p.precision != PTSNE_PREC_BF16_WINDOW)
+        return bad("precision", p.precision);
+    if (p.schedule != PTSNE_SCHED_BATCHED && p.schedule != PTSNE_SCHED_PER_CHUNK) return bad("schedule", p.schedule);
+    if (p.schedule == PTSNE_SCHED_BATCHED && persistent_smem_bytes(p.out_dim, zmax) > 227 * 1024)
+        return bad("largest chunk too large for the batched schedule at this out_dim", zmax);
+
+    c->p = p;
+    c->p.chunk_offsets = nullptr;
+    c->zmin = zmin;
+    c->zmax = zmax;
+    const int nc = p.n_chunks;
+    c->off.assign(p.chunk_offsets, p.chunk_offsets + nc + 1);
+    c->ld.resize(nc);
+    c->moff.resize(nc);
+    c->tile_start.resize(nc + 1);
+    std::vector<int64_t> dense(nc);
+    int64_t m = 0, t = 0, dz = 0;
+    std::vector<TileDesc> tiles;
+    for (int k = 0; k < nc; ++k) {
+        const int64_t z = c->off[k + 1] - c->off[k];
+        const int64_t ld = (z + kTile - 1) / kTile * kTile;
+        c->ld[k] = (int32_t)ld;
+        c->moff[k] = m;
+        m += z * ld;
+        dense[k] = dz;
+        dz += z * z;
+        c->tile_start[k] = t;
+        const int nb = (int)(ld / kTile);
+        for (int I = 0; I < nb; ++I)
+            for (int J = I; J < nb; ++J) tiles.push_back(TileDesc{k, (int16_t)I, (int16_t)J});
+        t = (int64_t)tiles.size();
+    }
+    c->tile_start[nc] = t;
+    c->mtotal = m;
+    c->ntiles = t;
+    c->order.resize(nc);
+    std::iota(c->order.begin(), c->order.end(), 0);
+    std::stable_sort(c->order.begin(), c->order.end(), [&](int a, int b) {
+        return (c->off[a + 1] - c->off[a]) > (c->off[b + 1] - c->off[b]);
+    });
+    std::vector<int32_t> cor(p.n);
+    for (int k = 0; k < nc; ++k)
+        for (int64_t r = c->off[k]; r < c->off[k + 1]; ++r) cor[r] = k;
+    c->dp = (p.d + 3) & ~3;
+    c->kp = (p.d + 63) & ~63;
+
+    const int64_t n = p.n, od = p.out_dim;
+    int st = PTSNE_OK;
+#define AL(ptr, count)                                               \
+    do {                                                             \
+        if ((st = dalloc(c, &(ptr), (size_t)(count))) != PTSNE_OK) { \
+            g_create_err = c->err;                                   \
+            free_all(c);                                             \
+            delete c;                                                \
+            return st;                                               \
+        }                                                            \
+    } while (0)
+    AL(c->d_off, nc + 1);
+    AL(c->d_moff, nc);
+    AL(c->d_ld, nc);
+    AL(c->d_chunk_of_row, n);
+    AL(c->d_order, nc);
+    AL(c->d_dense_off, nc);
+    AL(c->d_tiles, t);
+    AL(c->Xg, n * c->dp);
+    if (p.precision == PTSNE_PREC_BF16_WINDOW) {
+        AL(c->Xb, n * c->kp);
+        AL(c->xnorm, n);
+    }
+    AL(c->D, m);
+    AL(c->P, m);
+    AL(c->beta, n);
+    AL(c->mrow, n);
+    AL(c->Srow, n);
+    AL(c->Yc, n * od);
+    AL(c->vel, n * od);
+    AL(c->gains, n * od);
+    AL(c->acc, n * 2 * od);
+    AL(c->gradp, n * od);
+    AL(c->rowz, n);
+    AL(c->Zc, nc);
+    AL(c->ystat, 2 * nc);
+    AL(c->cost_rows, 4 * n);
+    AL(c->cost_chunk, 2 * nc);
+    AL(c->cost_hist, 2 * kCostHist);
+    AL(c->queue, 4);
+    AL(c->dstats, 1);
+#undef AL
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = up(c->d_off, c->off.data(), sizeof(int64_t) * (nc + 1));
+    if (e == cudaSuccess) e = up(c->d_moff, c->moff.data(), sizeof(int64_t) * nc);
+    if (e == cudaSuccess) e = up(c->d_ld, c->ld.data(), sizeof(int32_t) * nc);
+    if (e == cudaSuccess) e = up(c->d_chunk_of_row, cor.data(), sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = up(c->d_order, c->order.data(), sizeof(int32_t) * nc);
+    if (e == cudaSuccess) e = up(c->d_dense_off, dense.data(), sizeof(int64_t) * nc);
+    if (e == cudaSuccess) e = up(c->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size());
+    if (e == cudaSuccess) e = cudaMemset(c->dstats, 0, sizeof(DeviceStats));
+    // zero P once so that padded columns read as exact zeros before the first assembly
+    if (e == cudaSuccess) e = cudaMemset(c->P, 0, sizeof(float) * (size_t)m);
+    if (e != cudaSuccess) {
+        g_create_err = cudaGetErrorString(e);
+        free_all(c);
+        delete c;
+        return PTSNE_ECUDA;
+    }
+    *out = c;
+    return PTSNE_OK;
+}
+
+void ptsne_destroy(ptsne_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+// Record the event that opens stage k (profiling only).
+static void mark(ptsne_ctx* c, int k, cudaStream_t s) {
+    if (c->profiling) cudaEventRecord(c->ev[k], s);
+}
+
+// Gather (and, for ptsne_run, the chunk maps), then the affinities of every
+// chunk of the partition perm.  Opens stages GATHER..JOINT_P; the caller opens
+// ITERATE.
+static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s, bool reset_stats,
+                           const float* Y_run) {
+    if (reset_stats) CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
+    if (c->p.precision == PTSNE_PREC_BF16_WINDOW)
+        return fail(c, PTSNE_EINVAL, "precision %s not available in this build%lld", "BF16_WINDOW", 0);
+    mark(c, PTSNE_STAGE_GATHER, s);
+    CK(launch_gather(c, X, perm, s));
+    if (Y_run) CK(launch_gather_y(c, Y_run, perm, c->Yc, s));
+    CK(launch_reset_optim(c, s));
+    mark(c, PTSNE_STAGE_DISTANCES, s);
+    if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+        CK(launch_dist_fp32(c, 0, c->ntiles, s));
+        mark(c, PTSNE_STAGE_PERPLEXITY, s);
+        CK(launch_bisect(c, 0, c->p.n, s));
+        mark(c, PTSNE_STAGE_JOINT_P, s);
+        CK(launch_psym(c, 0, c->ntiles, s));
+    } else {
+        for (int k = 0; k < c->p.n_chunks; ++k) {
+            CK(launch_dist_fp32(c, c->tile_start[k], c->tile_start[k + 1], s));
+            CK(launch_bisect(c, c->off[k], c->off[k + 1], s));
+            CK(launch_psym(c, c->tile_start[k], c->tile_start[k + 1], s));
+        }
+        mark(c, PTSNE_STAGE_PERPLEXITY, s);
+        mark(c, PTSNE_STAGE_JOINT_P, s);
+    }
+    c->have_P = true;
+    return PTSNE_OK;
+}
+
+int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P_out, float* beta_out,
+                     void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!X || !perm) return fail(c, PTSNE_EINVAL, "X and perm must be device pointers%s%lld");
+    cudaStream_t s = as_stream(stream);
+    int st = affinities_impl(c, X, perm, s, true, nullptr);
+    if (st != PTSNE_OK) return st;
+    if (P_out) CK(launch_export_P(c, P_out, s));
+    if (beta_out) CK(launch_scatter_rows(c, c->beta, perm, 1, beta_out, s));
+    return PTSNE_OK;
+}
+
+static int iterate_rows(ptsne_ctx* c, float* grad_perm, cudaStream_t s) {
+    if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+        CK(launch_grad_rows(c, 0, c->p.n, s));
+        CK(launch_zreduce(c, 0, c->p.n_chunks, s));
+        CK(launch_update(c, 0, c->p.n, grad_perm, s));
+    } else {
+        for (int k = 0; k < c->p.n_chunks; ++k) {
+            CK(launch_grad_rows(c, c->off[k], c->off[k + 1], s));
+            CK(launch_zreduce(c, k, k + 1, s));
+            CK(launch_update(c, c->off[k], c->off[k + 1], grad_perm, s));
+        }
+    }
+    return PTSNE_OK;
+}
+
+int ptsne_step(ptsne_ctx* c, const int32_t* perm, float* Y, float* grad_out, double* Z_out, void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!perm || !Y) return fail(c, PTSNE_EINVAL, "perm and Y must be device pointers%s%lld");
+    if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_step before ptsne_affinities%s%lld");
+    cudaStream_t s = as_stream(stream);
+    CK(launch_gather_y(c, Y, perm, c->Yc, s));
+    int st = iterate_rows(c, grad_out ? c->gradp : nullptr, s);
+    if (st != PTSNE_OK) return st;
+    CK(launch_scatter_rows(c, c->Yc, perm, c->p.out_dim, Y, s));
+    if (grad_out) CK(launch_scatter_rows(c, c->gradp, perm, c->p.out_dim, grad_out, s));
+    if (Z_out)
+        CK(cudaMemcpyAsync(Z_out, c->Zc, sizeof(double) * c->p.n_chunks, cudaMemcpyDeviceToDevice, s));
+    return PTSNE_OK;
+}
+
+int ptsne_cost(ptsne_ctx* c, const int32_t* perm, const float* Y, double* out_dev, void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!perm || !Y || !out_dev) return fail(c, PTSNE_EINVAL, "perm, Y and out must be device pointers%s%lld");
+    if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_cost before ptsne_affinities%s%lld");
+    cudaStream_t s = as_stream(stream);
+    CK(launch_gather_y(c, Y, perm, c->Yc, s));
+    CK(launch_cost(c, out_dev, s));
+    return PTSNE_OK;
+}
+
+int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs, float* Y, double* cost_out,
+              void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!X || !perms || !Y) return fail(c, PTSNE_EINVAL, "X, perms and Y must be device pointers%s%lld");
+    if (epochs < 0) return fail(c, PTSNE_EINVAL, "epochs must be >= 0%s (%lld)", "", epochs);
+    cudaStream_t s = as_stream(stream);
+    const int64_t n = c->p.n;
+    // counters accumulate over the whole run
+    CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
+    for (int e = 0; e < epochs; ++e) {
+        const int32_t* perm = perms + (int64_t)e * n;
+        int st = affinities_impl(c, X, perm, s, false, Y);
+        if (st != PTSNE_OK) return st;
+        mark(c, PTSNE_STAGE_ITERATE, s);
+        if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+            CK(launch_grad_persistent(c, c->p.iters, s));
+        } else {
+            for (int it = 0; it < c->p.iters; ++it) {
+                st = iterate_rows(c, nullptr, s);
+                if (st != PTSNE_OK) return st;
+            }
+        }
+        mark(c, PTSNE_STAGE_POOL, s);
+        CK(launch_scatter_rows(c, c->Yc, perm, c->p.out_dim, Y, s));
+        mark(c, PTSNE_STAGE_COST, s);
+        if (cost_out) {
+            const int slot = e % kCostHist;
+            CK(launch_cost(c, c->cost_hist + 2 * slot, s));
+            if (slot == kCostHist - 1 || e == epochs - 1)
+                CK(cudaMemcpyAsync(cost_out + 2 * (int64_t)(e - slot), c->cost_hist, sizeof(double) * 2 * (slot + 1),
+                                   cudaMemcpyDeviceToHost, s));
+        }
+        if (c->profiling) {
+            CK(cudaEventRecord(c->ev[PTSNE_N_STAGES], s));
+            CK(cudaEventSynchronize(c->ev[PTSNE_N_STAGES]));
+            for (int k = 0; k < PTSNE_N_STAGES; ++k) {
+                if (k == PTSNE_STAGE_COST && !cost_out) continue;
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+                c->stage_ms[k] += ms;
+                c->stage_calls[k] += 1;
+            }
+        }
+    }
+    DeviceStats h;
+    CK(cudaMemcpyAsync(&h, c->dstats, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h.bad_index) return fail(c, PTSNE_EINVAL, "%s%lld permutation entries outside [0, n)", "", (long long)h.bad_index);
+    if (h.nonfinite) return fail(c, PTSNE_ENONFINITE, "%s%lld non-finite values in X", "", (long long)h.nonfinite);
+    if (h.failed_rows) {
+        fail(c, PTSNE_WBISECT, "%s%lld rows missed the perplexity tolerance", "", (long long)h.failed_rows);
+        return PTSNE_WBISECT;
+    }
+    return PTSNE_OK;
+}
+
+int ptsne_run_host(ptsne_ctx* c, const float* X_host, const int32_t* perms_host, int32_t epochs, float* Y_host,
+                   double* cost_out, void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!X_host || !perms_host || !Y_host) return fail(c, PTSNE_EINVAL, "host buffers must be non-NULL%s%lld");
+    if (epochs < 0) return fail(c, PTSNE_EINVAL, "epochs must be >= 0%s (%lld)", "", epochs);
+    cudaStream_t s = as_stream(stream);
+    const int64_t n = c->p.n, d = c->p.d, od = c->p.out_dim;
+    int st;
+    if (!c->hX && (st = dalloc(c, &c->hX, (size_t)(n * d))) != PTSNE_OK) return st;
+    if (!c->hY && (st = dalloc(c, &c->hY, (size_t)(n * od))) != PTSNE_OK) return st;
+    if (c->hperms_cap < (int64_t)epochs * n) {
+        if (c->hperms) { cudaFree(c->hperms); c->ws_bytes -= sizeof(int32_t) * c->hperms_cap; c->hperms = nullptr; }
+        if ((st = dalloc(c, &c->hperms, (size_t)epochs * n)) != PTSNE_OK) return st;
+        c->hperms_cap = (int64_t)epochs * n;
+    }
+    CK(cudaMemcpyAsync(c->hX, X_host, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->hperms, perms_host, sizeof(int32_t) * epochs * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->hY, Y_host, sizeof(float) * n * od, cudaMemcpyHostToDevice, s));
+    st = ptsne_run(c, c->hX, c->hperms, epochs, c->hY, cost_out, stream);
+    if (st < 0) return st;
+    CK(cudaMemcpyAsync(Y_host, c->hY, sizeof(float) * n * od, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
+int ptsne_get_stats(ptsne_ctx* c, ptsne_stats* out, void* stream) {
+    if (!c || !out) return PTSNE_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    DeviceStats h;
+    CK(cudaMemcpyAsync(&h, c->dstats, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->bisect_rows = c->p.n;
+    out->bisect_fp64_rows = (int64_t)h.fp64_rows;
+    out->bisect_failed_rows = (int64_t)h.failed_rows;
+    out->window_pairs = (int64_t)h.window_pairs;
+    out->nonfinite_inputs = (int64_t)h.nonfinite;
+    out->bad_perm_entries = (int64_t)h.bad_index;
+    float herr;
+    memcpy(&herr, &h.max_herr_bits, sizeof herr);
+    out->max_abs_entropy_err = herr;
+    out->kernel_launches = c->launches;
+    for (int k = 0; k < PTSNE_N_STAGES; ++k) {
+        out->stage_ms[k] = c->stage_ms[k];
+        out->stage_calls[k] = c->stage_calls[k];
+    }
+    return PTSNE_OK;
+}
+
+int ptsne_set_profiling(ptsne_ctx* c, int on) {
+    if (!c) return PTSNE_EINVAL;
+    if (on && !c->ev[0]) {
+        for (int k = 0; k <= PTSNE_N_STAGES; ++k) CK(cudaEventCreate(&c->ev[k]));
+    }
+    c->profiling = on != 0;
+    return PTSNE_OK;
+}
+
+int ptsne_reset_counters(ptsne_ctx* c) {
+    if (!c) return PTSNE_EINVAL;
+    c->launches = 0;
+    for (int k = 0; k < PTSNE_N_STAGES; ++k) {
+        c->stage_ms[k] = 0.0;
+        c->stage_calls[k] = 0;
+    }
+    return PTSNE_OK;
+}
+
+}  // extern "C"

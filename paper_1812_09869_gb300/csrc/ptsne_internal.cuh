@@ -1,0 +1,188 @@
+// Internal declarations of libptsne: context, device layout and launchers.
+// Every kernel lives in one .cu file together with its host launcher; the
+// entry points in ptsne_api.cu only validate, allocate and enqueue.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ptsne.h"
+
+namespace ptsne {
+
+// Square tile edge used by the pair kernels (distances, P assembly).  Chunk
+// matrices are stored z rows x ld columns with ld = z rounded up to kTile, so
+// every row starts 256-byte aligned and float4 loads never straddle rows.
+constexpr int kTile = 64;
+constexpr int kMaxChunk = 8192;
+
+// One upper-triangular tile (I <= J) of one chunk's z x z pair matrix.
+struct TileDesc {
+    int32_t chunk;
+    int16_t I, J;
+};
+
+// Device view of the chunk layout, passed by value to kernels.
+struct Layout {
+    int64_t n;                     // points
+    int32_t n_chunks;
+    int32_t d, dp;                 // input dims and row stride of the gathered X (multiple of 4)
+    int32_t od;                    // embedding dims
+    const int64_t* off;            // n_chunks+1 row offsets (permuted order)
+    const int64_t* moff;           // n_chunks offsets (floats) of each chunk's z x ld matrix
+    const int32_t* ld;             // n_chunks leading dimensions
+    const int32_t* chunk_of_row;   // n: chunk of each permuted row
+    const int32_t* order;          // n_chunks: chunks by decreasing size (work-queue order)
+};
+
+struct DeviceStats {               // device-side counters, reset per affinities call
+    unsigned long long fp64_rows;
+    unsigned long long failed_rows;
+    unsigned long long window_pairs;
+    unsigned long long nonfinite;
+    unsigned int max_herr_bits;    // float bits of max |H - ln perp| (non-negative floats order as ints)
+    unsigned int bad_index;        // permutation entries outside [0, n) (skipped)
+};
+
+struct Optim {                     // optimiser settings
+    float lr, momentum;
+    int lr_mode, use_gains;
+};
+
+}  // namespace ptsne
+
+struct ptsne_ctx {
+    ptsne_params p{};
+    std::vector<int64_t> off, moff;
+    std::vector<int32_t> ld, order;
+    int64_t zmin = 0, zmax = 0, mtotal = 0, ntiles = 0;
+    std::vector<int64_t> tile_start;   // per chunk, first entry in the tile table (n_chunks+1)
+    int dp = 0, kp = 0;                // padded X row (fp32) and bf16 K (multiple of 64)
+
+    // device layout tables
+    int64_t* d_off = nullptr;
+    int64_t* d_moff = nullptr;
+    int32_t* d_ld = nullptr;
+    int32_t* d_chunk_of_row = nullptr;
+    int32_t* d_order = nullptr;
+    int64_t* d_dense_off = nullptr;    // n_chunks: sum of z^2 of the preceding chunks (P export)
+    ptsne::TileDesc* d_tiles = nullptr;
+
+    // workspace
+    float* Xg = nullptr;               // n x dp gathered X (permuted order)
+    __nv_bfloat16* Xb = nullptr;       // n x kp gathered X in bf16 (BF16_WINDOW)
+    float* xnorm = nullptr;            // n squared norms of the bf16 rows (BF16_WINDOW)
+    float* D = nullptr;                // mtotal pair distances
+    float* P = nullptr;                // mtotal joint probabilities
+    float* beta = nullptr;             // n (permuted)
+    float* mrow = nullptr;             // n row minima of the distances
+    float* Srow = nullptr;             // n row normalisers at beta
+    float* Yc = nullptr;               // n x od (permuted)
+    float* vel = nullptr;              // n x od
+    float* gains = nullptr;            // n x od
+    float* acc = nullptr;              // n x 2od: attractive and repulsive sums
+    float* gradp = nullptr;            // n x od gradient in permuted order (ptsne_step output)
+    double* rowz = nullptr;            // n: per-row sum of w
+    double* Zc = nullptr;              // n_chunks
+    float* ystat = nullptr;            // n_chunks x 2 (min, max coordinate)
+    double* cost_rows = nullptr;       // n x 3 per-row cost partials
+    double* cost_chunk = nullptr;      // n_chunks x 2
+    double* cost_hist = nullptr;       // 2 x kCostHist per-epoch costs of ptsne_run
+    int* queue = nullptr;              // work-queue counters
+    ptsne::DeviceStats* dstats = nullptr;
+
+    // ptsne_run_host staging (lazily allocated)
+    float* hX = nullptr;
+    int32_t* hperms = nullptr;
+    int64_t hperms_cap = 0;
+    float* hY = nullptr;
+
+    bool have_P = false;
+    size_t ws_bytes = 0;
+    std::string err;
+
+    // tracing: kernels enqueued, and per-stage event timing of ptsne_run
+    mutable long long launches = 0;
+    bool profiling = false;
+    cudaEvent_t ev[PTSNE_N_STAGES + 1] = {};
+    double stage_ms[PTSNE_N_STAGES] = {};
+    long long stage_calls[PTSNE_N_STAGES] = {};
+};
+
+namespace ptsne {
+
+// --- launchers (host side, defined next to their kernels) -------------------
+cudaError_t launch_gather(const ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s);
+cudaError_t launch_gather_y(const ptsne_ctx* c, const float* Y, const int32_t* perm, float* Yc, cudaStream_t s);
+// all gathers and scatters skip (and count in DeviceStats::bad_index) perm entries outside [0, n)
+cudaError_t launch_scatter_rows(const ptsne_ctx* c, const float* src, const int32_t* perm, int width,
+                                float* dst, cudaStream_t s);
+cudaError_t launch_reset_optim(const ptsne_ctx* c, cudaStream_t s);
+cudaError_t launch_export_P(const ptsne_ctx* c, float* P_out, cudaStream_t s);
+
+cudaError_t launch_dist_fp32(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
+cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
+cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
+cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
+cudaError_t launch_psym(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
+
+cudaError_t launch_grad_rows(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
+cudaError_t launch_zreduce(const ptsne_ctx* c, int chunk_begin, int chunk_end, cudaStream_t s);
+cudaError_t launch_update(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, float* grad_perm,
+                          cudaStream_t s);
+cudaError_t launch_grad_persistent(const ptsne_ctx* c, int iters, cudaStream_t s);
+cudaError_t launch_cost(const ptsne_ctx* c, double* out2, cudaStream_t s);
+
+Layout make_layout(const ptsne_ctx* c);
+
+// Count k kernels enqueued by a launcher and return the launch status.
+inline cudaError_t launched(const ptsne_ctx* c, int k) {
+    c->launches += k;
+    return cudaGetLastError();
+}
+
+// --- device helpers ----------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// Hardware approximations (PTX ex2.approx / rcp.approx / lg2.approx).
+__device__ __forceinline__ float hw_ex2(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float hw_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float hw_lg2(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+#endif
+
+}  // namespace ptsne

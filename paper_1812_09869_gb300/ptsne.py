@@ -1,0 +1,205 @@
+"""Thin ctypes binding of libptsne.so (argument marshalling only).
+
+Every function forwards to the C entry point of the same name declared in
+include/ptsne.h; all arithmetic runs in the library's CUDA kernels.  Tensors
+are torch CUDA tensors (PyTorch supplies device memory and streams only).
+The library must have been built (``paper_1812_09869_gb300.build.build()``):
+nothing here falls back to any other implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libptsne.so")
+
+OK, EINVAL, ENONFINITE, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5
+WBISECT = 1
+LR_FIXED, LR_PAPER = 0, 1
+PREC_FP32, PREC_BF16_WINDOW = 0, 1
+SCHED_BATCHED, SCHED_PER_CHUNK = 0, 1
+
+_PRECISION = {"fp32": PREC_FP32, "bf16_window": PREC_BF16_WINDOW}
+_SCHEDULE = {"batched": SCHED_BATCHED, "per_chunk": SCHED_PER_CHUNK}
+
+
+class PtsneError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ptsne error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("d", C.c_int32),
+        ("out_dim", C.c_int32),
+        ("perplexity", C.c_double),
+        ("n_chunks", C.c_int32),
+        ("chunk_offsets", C.POINTER(C.c_int64)),
+        ("iters", C.c_int32),
+        ("lr", C.c_float),
+        ("momentum", C.c_float),
+        ("lr_mode", C.c_int32),
+        ("use_gains", C.c_int32),
+        ("precision", C.c_int32),
+        ("schedule", C.c_int32),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("bisect_rows", C.c_int64),
+        ("bisect_fp64_rows", C.c_int64),
+        ("bisect_failed_rows", C.c_int64),
+        ("window_pairs", C.c_int64),
+        ("nonfinite_inputs", C.c_int64),
+        ("bad_perm_entries", C.c_int64),
+        ("max_abs_entropy_err", C.c_double),
+        ("kernel_launches", C.c_int64),
+        ("stage_ms", C.c_double * 7),
+        ("stage_calls", C.c_int64 * 7),
+    ]
+
+
+STAGES = ("gather", "distances", "perplexity", "joint_p", "iterate", "pool", "cost")
+
+
+_lib = None
+
+
+def lib():
+    """Load libptsne.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1812_09869_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.ptsne_create.argtypes = [C.POINTER(vp), C.POINTER(Params)]
+        L.ptsne_destroy.argtypes = [vp]
+        L.ptsne_destroy.restype = None
+        L.ptsne_last_error.argtypes = [vp]
+        L.ptsne_last_error.restype = C.c_char_p
+        L.ptsne_affinities.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.ptsne_step.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.ptsne_cost.argtypes = [vp, vp, vp, vp, vp]
+        L.ptsne_run.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
+        L.ptsne_run_host.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
+        L.ptsne_get_stats.argtypes = [vp, C.POINTER(Stats), vp]
+        L.ptsne_workspace_bytes.argtypes = [vp]
+        L.ptsne_workspace_bytes.restype = C.c_size_t
+        L.ptsne_set_profiling.argtypes = [vp, C.c_int]
+        L.ptsne_reset_counters.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Config:
+    n: int
+    d: int
+    offsets: "object"            # sequence of n_chunks + 1 int64 offsets
+    perplexity: float = 30.0
+    out_dim: int = 2
+    iters: int = 100
+    lr: float = 200.0
+    momentum: float = 0.5
+    lr_mode: int = LR_FIXED
+    use_gains: int = 1
+    precision: str = "fp32"
+    schedule: str = "batched"
+
+
+class Context:
+    """Owns one ptsne_ctx (device workspace for one problem shape)."""
+
+    def __init__(self, cfg: Config):
+        import numpy as np
+        self.cfg = cfg
+        self._off = np.ascontiguousarray(np.asarray(cfg.offsets, dtype=np.int64))
+        p = Params(cfg.n, cfg.d, cfg.out_dim, cfg.perplexity, len(self._off) - 1,
+                   self._off.ctypes.data_as(C.POINTER(C.c_int64)), cfg.iters, cfg.lr, cfg.momentum,
+                   cfg.lr_mode, cfg.use_gains, _PRECISION[cfg.precision], _SCHEDULE[cfg.schedule])
+        h = C.c_void_p()
+        rc = lib().ptsne_create(C.byref(h), C.byref(p))
+        if rc != OK:
+            raise PtsneError(rc, lib().ptsne_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ptsne_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, warn_ok=False):
+        if rc < 0 or (rc > 0 and not warn_ok):
+            raise PtsneError(rc, lib().ptsne_last_error(self.h).decode())
+        return rc
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().ptsne_workspace_bytes(self.h))
+
+    @property
+    def n_chunks(self) -> int:
+        return len(self._off) - 1
+
+    # --- entry points -------------------------------------------------------
+    def affinities(self, X, perm, P_out=None, beta_out=None, stream=None):
+        return self._check(lib().ptsne_affinities(self.h, _ptr(X), _ptr(perm), _ptr(P_out), _ptr(beta_out),
+                                                  _stream(stream)))
+
+    def step(self, perm, Y, grad_out=None, Z_out=None, stream=None):
+        return self._check(lib().ptsne_step(self.h, _ptr(perm), _ptr(Y), _ptr(grad_out), _ptr(Z_out),
+                                            _stream(stream)))
+
+    def cost(self, perm, Y, out, stream=None):
+        return self._check(lib().ptsne_cost(self.h, _ptr(perm), _ptr(Y), _ptr(out), _stream(stream)))
+
+    def run(self, X, perms, epochs, Y, cost_out=None, stream=None):
+        """cost_out: optional float64 numpy array (epochs x 2)."""
+        cp = None if cost_out is None else cost_out.ctypes.data_as(C.POINTER(C.c_double))
+        return self._check(lib().ptsne_run(self.h, _ptr(X), _ptr(perms), epochs, _ptr(Y), cp, _stream(stream)),
+                           warn_ok=True)
+
+    def run_host(self, X_host, perms_host, epochs, Y_host, cost_out=None, stream=None):
+        """Host tensors (ideally pinned); Y_host is updated in place."""
+        cp = None if cost_out is None else cost_out.ctypes.data_as(C.POINTER(C.c_double))
+        return self._check(lib().ptsne_run_host(self.h, _ptr(X_host), _ptr(perms_host), epochs, _ptr(Y_host),
+                                                cp, _stream(stream)), warn_ok=True)
+
+    def stats(self, stream=None) -> Stats:
+        st = Stats()
+        self._check(lib().ptsne_get_stats(self.h, C.byref(st), _stream(stream)))
+        return st
+
+    def set_profiling(self, on: bool):
+        return self._check(lib().ptsne_set_profiling(self.h, int(bool(on))))
+
+    def reset_counters(self):
+        return self._check(lib().ptsne_reset_counters(self.h))

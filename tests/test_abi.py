@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every declared entry point, and
+its host-side argument validation rejects bad parameters before any device
+work (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ptsne.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(ptsne_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1812_09869_gb300 import build, ptsne
+    build.build()
+    return ptsne.lib()
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols()
+    for s in ("ptsne_create", "ptsne_destroy", "ptsne_affinities", "ptsne_step", "ptsne_run",
+              "ptsne_run_host", "ptsne_cost", "ptsne_get_stats", "ptsne_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in _declared_symbols():
+        assert hasattr(lib, s), f"libptsne.so does not export {s}"
+
+
+def _params(**kw):
+    from paper_1812_09869_gb300 import ptsne
+    off = np.asarray(kw.pop("offsets", [0, 100, 200]), dtype=np.int64)
+    base = dict(n=int(off[-1]), d=8, out_dim=2, perplexity=10.0, n_chunks=len(off) - 1, iters=10, lr=200.0,
+                momentum=0.5, lr_mode=0, use_gains=1, precision=0, schedule=0)
+    base.update(kw)
+    p = ptsne.Params(base["n"], base["d"], base["out_dim"], base["perplexity"], base["n_chunks"],
+                     off.ctypes.data_as(C.POINTER(C.c_int64)), base["iters"], base["lr"], base["momentum"],
+                     base["lr_mode"], base["use_gains"], base["precision"], base["schedule"])
+    return p, off
+
+
+@pytest.mark.parametrize("bad", [
+    dict(d=0), dict(d=5000), dict(out_dim=4), dict(perplexity=1.0), dict(perplexity=99.0),
+    dict(perplexity=float("nan")), dict(offsets=[0, 1, 200]), dict(offsets=[0, 100, 9000]),
+    dict(n=150), dict(iters=-1), dict(lr=0.0), dict(momentum=1.0), dict(lr_mode=7), dict(use_gains=2),
+    dict(precision=9), dict(schedule=3), dict(offsets=[0, 9000, 9100], perplexity=5.0),
+])
+def test_create_rejects_bad_parameters_on_the_host(lib, bad):
+    p, off = _params(**bad)
+    h = C.c_void_p()
+    rc = lib.ptsne_create(C.byref(h), C.byref(p))
+    assert rc == -1, (bad, rc)
+    assert not h.value
+    assert lib.ptsne_last_error(None).decode().startswith("invalid parameter")
+
+
+def test_null_arguments_are_rejected(lib):
+    h = C.c_void_p()
+    assert lib.ptsne_create(None, None) == -1
+    assert lib.ptsne_create(C.byref(h), None) == -1
+    assert lib.ptsne_affinities(None, None, None, None, None, None) == -1
+    assert lib.ptsne_step(None, None, None, None, None, None) == -1
+    assert lib.ptsne_run(None, None, None, 1, None, None, None) == -1
+    lib.ptsne_destroy(None)
+
+
+def test_bindings_fail_loudly_without_the_library(tmp_path, monkeypatch):
+    from paper_1812_09869_gb300 import ptsne
+    monkeypatch.setattr(ptsne, "_lib", None)
+    monkeypatch.setattr(ptsne, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        ptsne.lib()

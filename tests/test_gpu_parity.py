@@ -1,0 +1,251 @@
+"""CUDA path vs FP64 oracle, element by element, through the C ABI.
+
+Sizes are small enough for the oracle to finish in seconds while spanning
+several 64 x 64 tiles and ragged tails (chunk sizes and dimensions that are
+not multiples of the tile or of 4), plus degenerate small chunks.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1812_09869_gb300 import synth
+
+from parity import GRAD_TOL, KL_TOL, P_TOL, chunk_blocks, p_error, rel_max
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_09869_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _ctx(X, off, **kw):
+    from paper_1812_09869_gb300 import ptsne
+    cfg = ptsne.Config(n=X.shape[0], d=X.shape[1], offsets=off, **kw)
+    return ptsne.Context(cfg)
+
+
+def _gpu_affinities(dev, X, perm, off, **kw):
+    ctx = _ctx(X, off, **kw)
+    z2 = int((np.diff(off) ** 2).sum())
+    Xd = torch.from_numpy(X).to(dev)
+    pd = torch.from_numpy(perm).to(dev)
+    Pd = torch.zeros(z2, dtype=torch.float32, device=dev)
+    bd = torch.zeros(X.shape[0], dtype=torch.float32, device=dev)
+    ctx.affinities(Xd, pd, P_out=Pd, beta_out=bd)
+    torch.cuda.synchronize()
+    return ctx, Xd, pd, chunk_blocks(Pd.cpu().numpy(), off), bd.cpu().numpy().astype(np.float64)
+
+
+def _check_affinities(dev, X, perm, off, perp, **kw):
+    ctx, _, _, blocks, beta = _gpu_affinities(dev, X, perm, off, perplexity=perp, **kw)
+    st = ctx.stats()
+    assert st.bisect_failed_rows == 0
+    worst = 0.0
+    for c in range(len(off) - 1):
+        idx = perm[off[c]:off[c + 1]]
+        Pr, br, bad = O.affinities(X[idx], perp)
+        assert bad == 0
+        Pg = blocks[c]
+        assert np.array_equal(Pg, Pg.T), "GPU P must be exactly symmetric"
+        assert np.all(np.diag(Pg) == 0)
+        worst = max(worst, p_error(Pg, Pr))
+        assert np.abs(beta[idx] - br).max() <= 1e-4 * br.max()
+        assert abs(Pg.sum() - 1.0) < 1e-4
+    assert worst <= P_TOL, worst
+    ctx.close()
+    return worst
+
+
+def test_affinities_single_chunk_2000x10(dev):
+    w = synth.workload("plain-2000x10")
+    _check_affinities(dev, w.X, w.perms[0], w.offsets, 30.0)
+
+
+@pytest.mark.parametrize("schedule", ["batched", "per_chunk"])
+def test_affinities_ragged_chunks(dev, schedule):
+    X, _ = synth.gaussian_mixture(3000, 37, 6, seed=31, anisotropic=True)
+    off = np.array([0, 700, 1777, 3000])
+    perm = synth.permutations(3000, 1, seed=32)[0]
+    _check_affinities(dev, X, perm, off, 25.0, schedule=schedule)
+
+
+def test_affinities_tiny_and_degenerate_chunks(dev):
+    X, _ = synth.gaussian_mixture(314, 3, 3, seed=33)
+    off = np.array([0, 5, 22, 55, 119, 184, 314])   # z = 5, 17, 33, 64, 65, 130
+    perm = synth.permutations(314, 1, seed=34)[0]
+    _check_affinities(dev, X, perm, off, 3.0)
+
+
+def test_affinities_with_duplicate_points(dev):
+    """Exact duplicates give zero distances; the search must still converge."""
+    X, _ = synth.gaussian_mixture(400, 6, 2, seed=35)
+    X[100:110] = X[0]
+    perm = np.arange(400, dtype=np.int32)
+    _check_affinities(dev, X, perm, np.array([0, 400]), 20.0)
+
+
+def _step(dev, X, perm, off, Y0, **kw):
+    ctx, Xd, pd, blocks, _ = _gpu_affinities(dev, X, perm, off, **kw)
+    Yd = torch.from_numpy(Y0.copy()).to(dev)
+    gd = torch.zeros_like(Yd)
+    Zd = torch.zeros(len(off) - 1, dtype=torch.float64, device=dev)
+    ctx.step(pd, Yd, grad_out=gd, Z_out=Zd)
+    torch.cuda.synchronize()
+    ctx.close()
+    return Yd.cpu().numpy(), gd.cpu().numpy(), Zd.cpu().numpy()
+
+
+def test_gradient_after_one_step_2000x10(dev):
+    w = synth.workload("plain-2000x10")
+    perm, off = w.perms[0], w.offsets
+    Y1, g, Z = _step(dev, w.X, perm, off, w.Y0, perplexity=30.0)
+    idx = perm
+    Pr, _, _ = O.affinities(w.X[idx], 30.0)
+    gr, Zr = O.gradient(Pr, w.Y0[idx])
+    assert rel_max(g[idx], gr) <= GRAD_TOL
+    assert abs(Z[0] - Zr) <= 1e-6 * Zr
+    Yr = w.Y0[idx].astype(np.float64).copy()
+    vel, gains = np.zeros_like(Yr), np.ones_like(Yr)
+    O.update(Yr, vel, gains, gr, lr=200.0, momentum=0.5)
+    assert rel_max(Y1[idx] - w.Y0[idx], Yr - w.Y0[idx]) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("schedule", ["batched", "per_chunk"])
+def test_step_three_dims_paper_lr_no_gains(dev, schedule):
+    X, _ = synth.gaussian_mixture(900, 12, 5, seed=36)
+    off = np.array([0, 333, 900])
+    perm = synth.permutations(900, 1, seed=37)[0]
+    Y0 = synth.init_gaussian(900, 3, 1.0, seed=38)
+    Y1, g, Z = _step(dev, X, perm, off, Y0, perplexity=15.0, out_dim=3, lr_mode=1, use_gains=0,
+                     schedule=schedule)
+    for c in range(2):
+        idx = perm[off[c]:off[c + 1]]
+        Pr, _, _ = O.affinities(X[idx], 15.0)
+        gr, Zr = O.gradient(Pr, Y0[idx])
+        assert rel_max(g[idx], gr) <= GRAD_TOL
+        assert abs(Z[c] - Zr) <= 1e-6 * Zr
+        Yr = Y0[idx].astype(np.float64).copy()
+        O.update(Yr, np.zeros_like(Yr), np.ones_like(Yr), gr, momentum=0.5, lr_mode=1, use_gains=0)
+        assert rel_max(Y1[idx] - Y0[idx], Yr - Y0[idx]) <= GRAD_TOL
+
+
+def test_cost_matches_oracle(dev):
+    X, _ = synth.gaussian_mixture(1500, 16, 5, seed=39)
+    off = np.array([0, 640, 1500])
+    perm = synth.permutations(1500, 1, seed=40)[0]
+    ctx, Xd, pd, blocks, _ = _gpu_affinities(dev, X, perm, off, perplexity=20.0)
+    Y = synth.init_gaussian(1500, 2, 3.0, seed=41)
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.cost(pd, torch.from_numpy(Y).to(dev), out)
+    kl, nc = out.cpu().numpy()
+    ctx.close()
+    kl_g = nc_g = kl_r = nc_r = 0.0
+    for c in range(2):
+        idx = perm[off[c]:off[c + 1]]
+        kl_g += O.kl(blocks[c], Y[idx]) / 2
+        nc_g += O.normalized_cost(blocks[c], Y[idx]) / 2
+        Pr, _, _ = O.affinities(X[idx], 20.0)
+        kl_r += O.kl(Pr, Y[idx]) / 2
+        nc_r += O.normalized_cost(Pr, Y[idx]) / 2
+    # the cost kernels on the GPU's own P: FP32 logs, FP64 sums
+    assert abs(kl - kl_g) <= 1e-5 * abs(kl_g) and abs(nc - nc_g) <= 1e-5 * nc_g
+    assert abs(kl - kl_r) <= 1e-4 * abs(kl_r) and abs(nc - nc_r) <= 1e-4 * nc_r
+
+
+@pytest.mark.parametrize("schedule", ["batched", "per_chunk"])
+def test_final_kl_within_one_percent_2000x10(dev, schedule):
+    w = synth.workload("plain-2000x10")
+    ctx = _ctx(w.X, w.offsets, perplexity=30.0, iters=100, schedule=schedule)
+    Xd = torch.from_numpy(w.X).to(dev)
+    pd = torch.from_numpy(w.perms).to(dev)
+    Yd = torch.from_numpy(w.Y0.copy()).to(dev)
+    cost = np.zeros((1, 2))
+    rc = ctx.run(Xd, pd, 1, Yd, cost_out=cost)
+    assert rc == 0
+    ctx.close()
+    _, cref = O.ptsne_run(w.X, w.Y0, w.perms, w.offsets, O.params(perplexity=30.0, iters=100, epochs=1))
+    assert abs(cost[0, 0] - cref[0, 0]) <= KL_TOL * cref[0, 0], (cost, cref)
+    assert abs(cost[0, 1] - cref[0, 1]) <= KL_TOL * cref[0, 1]
+
+
+def test_multi_epoch_run_matches_oracle_cost(dev):
+    X, _ = synth.gaussian_mixture(4000, 20, 8, seed=42, anisotropic=True)
+    off = synth.equal_chunk_offsets(4000, 4)
+    perms = synth.permutations(4000, 3, seed=43)
+    Y0 = synth.init_gaussian(4000, 2, 1e-4, seed=44)
+    ctx = _ctx(X, off, perplexity=30.0, iters=60)
+    Yd = torch.from_numpy(Y0.copy()).to(dev)
+    cost = np.zeros((3, 2))
+    ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev), 3, Yd, cost_out=cost)
+    ctx.close()
+    prm = O.params(perplexity=30.0, iters=60, epochs=3)
+    _, cref = O.ptsne_run(X, Y0, perms, off, prm)
+    # epoch 0 is one partial t-SNE per chunk from the same start: tight match
+    assert abs(cost[0, 0] - cref[0, 0]) <= 1e-3 * cref[0, 0], (cost, cref)
+    # later epochs start from pooled maps; the trajectory is chaotic (a 1e-6
+    # relative change of the oracle's own start map moves its epoch-2 KL by
+    # ~0.5%), so the GPU must fall within the spread of an oracle ensemble over
+    # such perturbed starts, widened by the 1% tolerance
+    rng = np.random.default_rng(7)
+    ens = [cref]
+    for _ in range(3):
+        _, ck = O.ptsne_run(X, Y0 * (1 + 1e-6 * rng.standard_normal(Y0.shape)), perms, off, prm)
+        ens.append(ck)
+    ens = np.stack(ens)
+    lo, hi = ens.min(0), ens.max(0)
+    assert np.all(cost >= lo * (1 - KL_TOL)) and np.all(cost <= hi * (1 + KL_TOL)), (cost, ens)
+
+
+def test_persistent_iterations_equal_row_steps(dev):
+    """The batched persistent kernel and the per-row kernels compute the same
+    iterations (to FP32 summation-order differences)."""
+    X, _ = synth.gaussian_mixture(2500, 10, 4, seed=45)
+    off = np.array([0, 1200, 2500])
+    perm = synth.permutations(2500, 1, seed=46)
+    Y0 = synth.init_gaussian(2500, 2, 1.0, seed=47)
+    Xd, pd = torch.from_numpy(X).to(dev), torch.from_numpy(perm).to(dev)
+    ctx = _ctx(X, off, perplexity=30.0, iters=5)
+    Ya = torch.from_numpy(Y0.copy()).to(dev)
+    ctx.run(Xd, pd, 1, Ya)
+    Yb = torch.from_numpy(Y0.copy()).to(dev)
+    ctx.affinities(Xd, pd[0])
+    for _ in range(5):
+        ctx.step(pd[0], Yb)
+    torch.cuda.synchronize()
+    ctx.close()
+    a, b = Ya.cpu().numpy(), Yb.cpu().numpy()
+    assert rel_max(a - Y0, b - Y0) <= 1e-4
+
+
+def test_run_host_equals_run_device(dev):
+    w = synth.workload("plain-2000x10")
+    ctx = _ctx(w.X, w.offsets, perplexity=30.0, iters=20)
+    Yd = torch.from_numpy(w.Y0.copy()).to(dev)
+    ctx.run(torch.from_numpy(w.X).to(dev), torch.from_numpy(w.perms).to(dev), 1, Yd)
+    Yh = torch.from_numpy(w.Y0.copy()).pin_memory()
+    ctx.run_host(torch.from_numpy(w.X).pin_memory(), torch.from_numpy(w.perms).pin_memory(), 1, Yh)
+    ctx.close()
+    assert np.array_equal(Yd.cpu().numpy(), Yh.numpy())
+
+
+def test_errors_nonfinite_input_and_call_order(dev):
+    from paper_1812_09869_gb300 import ptsne
+    X, _ = synth.gaussian_mixture(300, 5, 2, seed=48)
+    X[7, 2] = np.nan
+    perm = synth.permutations(300, 1, seed=49)
+    ctx = _ctx(X, np.array([0, 300]), perplexity=10.0, iters=2)
+    with pytest.raises(ptsne.PtsneError) as e:
+        ctx.step(torch.from_numpy(perm[0]).to(dev), torch.zeros(300, 2, device=dev))
+    assert e.value.code == ptsne.ESTATE
+    with pytest.raises(ptsne.PtsneError) as e:
+        ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perm).to(dev), 1, torch.zeros(300, 2, device=dev))
+    assert e.value.code == ptsne.ENONFINITE
+    ctx.close()
