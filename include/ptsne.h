@@ -52,6 +52,7 @@ extern "C" {
 #define PTSNE_ENOMEM (-3)     /* device allocation failed */
 #define PTSNE_ECUDA (-4)      /* a CUDA call failed */
 #define PTSNE_ESTATE (-5)     /* call order violated (e.g. step before affinities) */
+#define PTSNE_ETIMEOUT (-6)   /* a bounded wait inside a kernel ran out (results invalid) */
 #define PTSNE_WBISECT 1       /* some rows' perplexity search missed its tolerance */
 
 #define PTSNE_LR_FIXED 0      /* eta = lr (with gains if use_gains) */
@@ -104,6 +105,7 @@ typedef struct {
     int64_t window_pairs;         /* BF16_WINDOW: distances recomputed in FP32 */
     int64_t nonfinite_inputs;     /* NaN/Inf entries seen in X by the last gather */
     int64_t bad_perm_entries;     /* permutation entries outside [0, n): skipped, never dereferenced */
+    int64_t wait_timeouts;        /* bounded in-kernel waits that ran out (PTSNE_ETIMEOUT) */
     double max_abs_entropy_err;   /* max |H(beta_i) - ln perplexity| (nats) of the last search */
     int64_t kernel_launches;      /* kernels this context enqueued since creation / last reset */
     double stage_ms[PTSNE_N_STAGES];     /* profiling on: device time per stage of ptsne_run */
@@ -118,6 +120,41 @@ int ptsne_set_profiling(ptsne_ctx* ctx, int on);
 
 /* Zero kernel_launches, stage_ms and stage_calls. */
 int ptsne_reset_counters(ptsne_ctx* ctx);
+
+/* Launch shape of the batched iteration kernel (no effect on results beyond
+ * FP32 summation order).  cluster: thread blocks sharing one chunk through
+ * distributed shared memory (1, 2 or 4); group: consumer warps that split
+ * each P tile (2 or 4); consumer_warps: per block, a multiple of group in
+ * [group, 16].  Defaults {1, 2, 16}; ptsne_autotune picks by timing. */
+typedef struct {
+    int32_t cluster;
+    int32_t group;
+    int32_t consumer_warps;
+} ptsne_tuning;
+
+int ptsne_set_tuning(ptsne_ctx* ctx, const ptsne_tuning* tuning);
+int ptsne_get_tuning(const ptsne_ctx* ctx, ptsne_tuning* tuning);
+
+typedef struct {
+    ptsne_tuning tuning;
+    double ms_per_iter;           /* device time per gradient iteration (all chunks) */
+} ptsne_tune_trial;
+
+/* Autotuner of the batched iteration kernel's launch shape (no counterpart in
+ * the paper, whose kernels are CPU threads).  Computes the affinities of the
+ * partition perm_dev, then times `iters` gradient iterations from the map
+ * Y_dev (n x out_dim, not modified) for every candidate shape with CUDA
+ * events (best of two), restoring the optimiser state between trials, and
+ * applies the fastest to ctx.  cache_path (optional): a text file of one
+ * record per line, keyed by device name, SM count, out_dim and the chunk-size
+ * layout; a matching record is applied without timing, a new result is
+ * appended.  trials_out (optional, host, capacity max_trials) receives every
+ * timed trial; *n_trials_out their count (0 on a cache hit).  Leaves the
+ * affinities of perm_dev in ctx with a reset optimiser state.  Synchronous.
+ * Per-chunk schedule: PTSNE_EINVAL (nothing to tune). */
+int ptsne_autotune(ptsne_ctx* ctx, const float* X_dev, const int32_t* perm_dev, const float* Y_dev, int32_t iters,
+                   const char* cache_path, ptsne_tune_trial* trials_out, int32_t max_trials,
+                   int32_t* n_trials_out, void* stream);
 
 /* Create a context for one problem shape and allocate its device workspace
  * on the current device.  Validates every field (PTSNE_EINVAL), then

@@ -1,0 +1,190 @@
+// Autotuner of the batched iteration kernel's launch shape: times every
+// candidate (blocks per chunk x warps per tile x consumer warps) on the
+// caller's chunk layout and keeps the fastest; results persist in a small text
+// cache keyed by device and layout.
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "ptsne_internal.cuh"
+
+using namespace ptsne;
+
+namespace ptsne {
+cudaError_t launch_gather_y(const ptsne_ctx* c, const float* Y, const int32_t* perm, float* Yc, cudaStream_t s);
+}
+
+namespace {
+
+// Key of a tuning record: the device and everything of the layout that the
+// kernel's speed depends on.
+std::string tune_key(const ptsne_ctx* c) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) prop.name[0] = 0;
+    long double z2 = 0;
+    for (int k = 0; k < c->p.n_chunks; ++k) {
+        const long double z = (long double)(c->off[k + 1] - c->off[k]);
+        z2 += z * z;
+    }
+    char buf[512];
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (ch == ' ' || ch == '|') ch = '_';
+    snprintf(buf, sizeof buf, "%s|sm%d|od%d|chunks%d|zmin%lld|zmax%lld|z2_%.4Le", name.c_str(), sms, c->p.out_dim,
+             c->p.n_chunks, (long long)c->zmin, (long long)c->zmax, z2);
+    return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, IterTune* out) {
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char k[600];
+        int cl = 0, g = 0, w = 0;
+        if (sscanf(line, "%599s %d %d %d", k, &cl, &g, &w) == 4 && key == k) {
+            out->cluster = cl;
+            out->group = g;
+            out->consumer_warps = w;
+            found = true;  // the last matching record wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_append(const char* path, const std::string& key, const IterTune& t, double ms) {
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), t.cluster, t.group, t.consumer_warps, ms);
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P_out, float* beta_out,
+                                void* stream);
+
+extern "C" int ptsne_autotune(ptsne_ctx* c, const float* X, const int32_t* perm, const float* Y, int32_t iters,
+                              const char* cache_path, ptsne_tune_trial* trials, int32_t max_trials, int32_t* n_trials,
+                              void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (n_trials) *n_trials = 0;
+    if (!X || !perm || !Y || iters < 1) {
+        c->err = "autotune: X, perm, Y must be device pointers and iters >= 1";
+        return PTSNE_EINVAL;
+    }
+    if (c->p.schedule != PTSNE_SCHED_BATCHED) {
+        c->err = "autotune: only the batched schedule has launch shapes to tune";
+        return PTSNE_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const std::string key = tune_key(c);
+    IterTune cached;
+    if (cache_path && cache_lookup(cache_path, key, &cached)) {
+        c->tune = cached;
+        return ptsne_affinities(c, X, perm, nullptr, nullptr, stream);
+    }
+    int st = ptsne_affinities(c, X, perm, nullptr, nullptr, stream);
+    if (st != PTSNE_OK) return st;
+    const size_t m = (size_t)c->p.n * c->p.out_dim;
+    float *y0 = nullptr, *v0 = nullptr, *g0 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (y0) cudaFree(y0);
+        if (v0) cudaFree(v0);
+        if (g0) cudaFree(g0);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    auto cuda_fail = [&](cudaError_t e) {
+        c->err = std::string("autotune: ") + cudaGetErrorString(e);
+        cleanup();
+        return PTSNE_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&y0, m * sizeof(float))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&v0, m * sizeof(float))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMalloc(&g0, m * sizeof(float))) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_gather_y(c, Y, perm, c->Yc, s)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(y0, c->Yc, m * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(v0, c->vel, m * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(g0, c->gains, m * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e);
+    auto restore = [&]() {
+        cudaMemcpyAsync(c->Yc, y0, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(c->vel, v0, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(c->gains, g0, m * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    };
+
+    const IterTune keep = c->tune;
+    IterTune best = keep;
+    double best_ms = 1e300;
+    int nt = 0;
+    const int clusters[] = {1, 2, 4}, groups[] = {2, 4}, warps[] = {8, 12, 16};
+    for (int cl : clusters)
+        for (int g : groups)
+            for (int w : warps) {
+                if (w % g) continue;
+                c->tune = IterTune{cl, g, w};
+                double ms = 1e300;
+                for (int rep = 0; rep < 2; ++rep) {
+                    restore();
+                    cudaEventRecord(e0, s);
+                    e = launch_iterate(c, iters, 0, nullptr, nullptr, nullptr, s);
+                    cudaEventRecord(e1, s);
+                    if (e != cudaSuccess) break;
+                    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms = t / iters < ms ? t / iters : ms;
+                }
+                if (e != cudaSuccess) {
+                    // a shape that cannot launch here (e.g. cluster occupancy) is skipped
+                    cudaGetLastError();
+                    continue;
+                }
+                if (trials && nt < max_trials) {
+                    trials[nt].tuning.cluster = cl;
+                    trials[nt].tuning.group = g;
+                    trials[nt].tuning.consumer_warps = w;
+                    trials[nt].ms_per_iter = ms;
+                }
+                ++nt;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c->tune;
+                }
+            }
+    restore();
+    cudaStreamSynchronize(s);
+    DeviceStats h;
+    cudaMemcpy(&h, c->dstats, sizeof h, cudaMemcpyDeviceToHost);
+    cleanup();
+    if (h.timeouts) {
+        c->tune = keep;
+        c->err = "autotune: a bounded device wait ran out";
+        return PTSNE_ETIMEOUT;
+    }
+    if (nt == 0) {
+        c->tune = keep;
+        c->err = "autotune: no launch shape could run";
+        return PTSNE_ECUDA;
+    }
+    c->tune = best;
+    if (n_trials) *n_trials = nt;
+    if (cache_path) cache_append(cache_path, key, best, best_ms);
+    // leave a fresh optimiser state for the caller's next step / run
+    cudaError_t er = launch_reset_optim(c, s);
+    return er == cudaSuccess ? PTSNE_OK : PTSNE_ECUDA;
+}

@@ -1,5 +1,6 @@
-// Gradient iterations of every chunk (Eq. 4, Eq. 6, Eq. 12/13) and the cost
-// evaluation (Eq. 5, Eq. 9).
+// Gradient iterations on the dense z x ld P of the plain per-chunk schedule
+// (Eq. 4, Eq. 6, Eq. 12/13) and its cost evaluation (Eq. 5, Eq. 9).  The
+// batched schedule uses the packed symmetric P of k_iter.cu instead.
 //
 // One pass per iteration: for each row i the warp accumulates
 //   A_i = sum_j p_ij w_ij (y_i - y_j),  R_i = sum_j w_ij^2 (y_i - y_j),
@@ -15,8 +16,6 @@ namespace ptsne {
 
 namespace {
 constexpr int kRowWarps = 8;
-constexpr int kPersistThreads = 1024;
-constexpr float kPadCoord = 1e18f;  // coordinate of padding points: w ~ 1e-36, p = 0
 }
 
 template <int OD>
@@ -134,35 +133,6 @@ zreduce_kernel(const double* __restrict__ rowz, const float* __restrict__ Yc, La
     }
 }
 
-// Position update, Eq. 12 in the descent direction, with gains or Eq. 13:
-//   g = 4 (A - R / Z);  gains (+0.2 if sign(g) != sign(vel), else x0.8, >= 0.01)
-//   vel = momentum * vel - eta * gains * g;  y += vel.
-template <int OD>
-__device__ __forceinline__ void update_point(float* y, float* vel, float* gains, const float* A,
-                                             const float* R, float invZ, float eta, const Optim& opt,
-                                             float* gout) {
-#pragma unroll
-    for (int k = 0; k < OD; ++k) {
-        const float g = 4.0f * (A[k] - R[k] * invZ);
-        if (gout) gout[k] = g;
-        float v = vel[k];
-        float gm = 1.0f;
-        if (opt.use_gains) {
-            float gn = ((g > 0.f) != (v > 0.f)) ? gains[k] + 0.2f : gains[k] * 0.8f;
-            gn = fmaxf(gn, 0.01f);
-            gains[k] = gn;
-            gm = gn;
-        }
-        v = opt.momentum * v - eta * gm * g;
-        vel[k] = v;
-        y[k] += v;
-    }
-}
-
-__device__ __forceinline__ float step_eta(const Optim& opt, int z, float ymin, float ymax) {
-    return opt.lr_mode == PTSNE_LR_PAPER ? logf((float)(z - 1)) * (ymax - ymin) * 0.5f : opt.lr;
-}
-
 template <int OD>
 __global__ void __launch_bounds__(256)
 update_kernel(float* __restrict__ Yc, float* __restrict__ vel, float* __restrict__ gains,
@@ -176,140 +146,6 @@ update_kernel(float* __restrict__ Yc, float* __restrict__ vel, float* __restrict
         const float eta = step_eta(opt, z, ystat[2 * c], ystat[2 * c + 1]);
         update_point<OD>(Yc + r * OD, vel + r * OD, gains + r * OD, acc + r * 2 * OD, acc + r * 2 * OD + OD,
                          invZ, eta, opt, grad_perm ? grad_perm + r * OD : nullptr);
-    }
-}
-
-// ---------------------------------------------------------------- persistent form
-// One block per chunk at a time (chunks pulled from a queue in decreasing size
-// order), every iteration of the epoch inside the block: the chunk's map lives
-// in shared memory, Z is reduced by the block, so no grid-wide synchronisation
-// is ever needed.  P rows stream from HBM once per iteration.
-
-template <int OD>
-struct SmemY {
-    static constexpr int kStride = OD == 2 ? 2 : 4;  // floats per point in shared memory
-};
-
-template <int OD>
-__global__ void __launch_bounds__(kPersistThreads, 1)
-grad_persist_kernel(const float* __restrict__ P, float* __restrict__ Yc, float* __restrict__ vel,
-                    float* __restrict__ gains, Layout L, int zcap, int iters, Optim opt, int* queue) {
-    extern __shared__ __align__(16) float smem[];
-    constexpr int YS = SmemY<OD>::kStride;
-    constexpr int AS = 2 * OD;
-    float* ys = smem;                     // zcap x YS
-    float* accs = smem + (size_t)zcap * YS;  // zcap x AS
-    __shared__ double red[kPersistThreads / 32];
-    __shared__ float rmin[kPersistThreads / 32], rmax[kPersistThreads / 32];
-    __shared__ int s_item;
-    __shared__ double s_Z;
-    __shared__ float s_eta;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kWarps = kPersistThreads / 32;
-
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = atomicAdd(queue, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= L.n_chunks) return;
-        const int c = L.order[item];
-        const int64_t off = L.off[c];
-        const int z = (int)(L.off[c + 1] - off);
-        const int zr = (z + 3) & ~3;
-        const int ld = L.ld[c];
-        const float* Pc = P + L.moff[c];
-
-        for (int t = tid; t < zr; t += kPersistThreads) {
-#pragma unroll
-            for (int k = 0; k < YS; ++k)
-                ys[t * YS + k] = (k < OD) ? (t < z ? Yc[(off + t) * OD + k] : kPadCoord) : 0.f;
-        }
-        __syncthreads();
-
-        for (int it = 0; it < iters; ++it) {
-            if (opt.lr_mode == PTSNE_LR_PAPER) {
-                float mn = FLT_MAX, mx = -FLT_MAX;
-                for (int t = tid; t < z; t += kPersistThreads)
-#pragma unroll
-                    for (int k = 0; k < OD; ++k) {
-                        mn = fminf(mn, ys[t * YS + k]);
-                        mx = fmaxf(mx, ys[t * YS + k]);
-                    }
-                mn = warp_min(mn);
-                mx = warp_max(mx);
-                if (lane == 0) { rmin[warp] = mn; rmax[warp] = mx; }
-                __syncthreads();
-                if (tid == 0) {
-                    float a = FLT_MAX, b = -FLT_MAX;
-                    for (int w = 0; w < kWarps; ++w) { a = fminf(a, rmin[w]); b = fmaxf(b, rmax[w]); }
-                    s_eta = step_eta(opt, z, a, b);
-                }
-            }
-            // gradient pass: warp per row
-            double zw = 0.0;
-            for (int i = warp; i < z; i += kWarps) {
-                float yi[OD];
-#pragma unroll
-                for (int k = 0; k < OD; ++k) yi[k] = ys[i * YS + k];
-                const float* prow = Pc + (int64_t)i * ld;
-                PairAcc<OD> s;
-                s.clear();
-                int j0 = lane * 4;
-                for (; j0 + 128 < zr; j0 += 256) {
-                    const float4 pa = __ldg(reinterpret_cast<const float4*>(prow + j0));
-                    const float4 pb = __ldg(reinterpret_cast<const float4*>(prow + j0 + 128));
-                    const float pva[4] = {pa.x, pa.y, pa.z, pa.w}, pvb[4] = {pb.x, pb.y, pb.z, pb.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) s.add(yi, ys + (j0 + e) * YS, pva[e]);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) s.add(yi, ys + (j0 + 128 + e) * YS, pvb[e]);
-                }
-                for (; j0 < zr; j0 += 128) {
-                    const float4 pa = __ldg(reinterpret_cast<const float4*>(prow + j0));
-                    const float pva[4] = {pa.x, pa.y, pa.z, pa.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) s.add(yi, ys + (j0 + e) * YS, pva[e]);
-                }
-#pragma unroll
-                for (int k = 0; k < OD; ++k) {
-                    s.a[k] = warp_sum(s.a[k]);
-                    s.r[k] = warp_sum(s.r[k]);
-                }
-                const double zrow = warp_sum((double)s.z) - 1.0;
-                if (lane == 0) {
-#pragma unroll
-                    for (int k = 0; k < OD; ++k) {
-                        accs[i * AS + k] = s.a[k];
-                        accs[i * AS + OD + k] = s.r[k];
-                    }
-                    zw += zrow;
-                }
-            }
-            if (lane == 0) red[warp] = zw;
-            __syncthreads();
-            if (tid == 0) {
-                double Z = 0.0;
-                for (int w = 0; w < kWarps; ++w) Z += red[w];
-                s_Z = Z;
-            }
-            __syncthreads();
-            const float invZ = (float)(1.0 / s_Z);
-            const float eta = opt.lr_mode == PTSNE_LR_PAPER ? s_eta : opt.lr;
-            for (int i = tid; i < z; i += kPersistThreads) {
-                float y[OD];
-#pragma unroll
-                for (int k = 0; k < OD; ++k) y[k] = ys[i * YS + k];
-                update_point<OD>(y, vel + (off + i) * OD, gains + (off + i) * OD, accs + i * AS,
-                                 accs + i * AS + OD, invZ, eta, opt, nullptr);
-#pragma unroll
-                for (int k = 0; k < OD; ++k) ys[i * YS + k] = y[k];
-            }
-            __syncthreads();
-        }
-        for (int t = tid; t < z; t += kPersistThreads)
-#pragma unroll
-            for (int k = 0; k < OD; ++k) Yc[(off + t) * OD + k] = ys[t * YS + k];
     }
 }
 
@@ -450,35 +286,6 @@ cudaError_t launch_update(const ptsne_ctx* c, int64_t row_begin, int64_t row_end
     return launched(c, 1);
 }
 
-int persistent_smem_bytes(int od, int64_t zmax) {
-    const int zcap = (int)((zmax + 3) & ~3LL);
-    const int ys = od == 2 ? 2 : 4;
-    return zcap * (ys + 2 * od) * (int)sizeof(float);
-}
-
-cudaError_t launch_grad_persistent(const ptsne_ctx* c, int iters, cudaStream_t s) {
-    if (iters <= 0) return cudaSuccess;
-    const int zcap = (int)((c->zmax + 3) & ~3LL);
-    const size_t smem = (size_t)persistent_smem_bytes(c->p.out_dim, c->zmax);
-    cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = c->p.n_chunks < sms ? c->p.n_chunks : sms;
-    const Layout L = make_layout(c);
-    if (c->p.out_dim == 2) {
-        cudaFuncSetAttribute(grad_persist_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        grad_persist_kernel<2><<<grid, kPersistThreads, smem, s>>>(c->P, c->Yc, c->vel, c->gains, L, zcap, iters,
-                                                                  optim_of(c), c->queue);
-    } else {
-        cudaFuncSetAttribute(grad_persist_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        grad_persist_kernel<3><<<grid, kPersistThreads, smem, s>>>(c->P, c->Yc, c->vel, c->gains, L, zcap, iters,
-                                                                  optim_of(c), c->queue);
-    }
-    return launched(c, 1);
-}
-
 cudaError_t launch_cost(const ptsne_ctx* c, double* out2, cudaStream_t s) {
     const Layout L = make_layout(c);
     const unsigned g = row_blocks(c->p.n, kRowWarps);
@@ -489,6 +296,11 @@ cudaError_t launch_cost(const ptsne_ctx* c, double* out2, cudaStream_t s) {
     cost_chunk_kernel<<<c->p.n_chunks, 256, 0, s>>>(c->cost_rows, L, c->cost_chunk);
     cost_final_kernel<<<1, 32, 0, s>>>(c->cost_chunk, c->p.n_chunks, out2);
     return launched(c, 3);
+}
+
+cudaError_t launch_cost_final(const ptsne_ctx* c, double* out2, cudaStream_t s) {
+    cost_final_kernel<<<1, 32, 0, s>>>(c->cost_chunk, c->p.n_chunks, out2);
+    return launched(c, 1);
 }
 
 }  // namespace ptsne

@@ -1,0 +1,783 @@
+// Batched gradient iterations on the packed symmetric P (Eq. 4, Eq. 6,
+// Eq. 12/13) and the per-chunk cost (Eq. 5, Eq. 9) — the ptSNE hot loop.
+//
+// One persistent launch runs every iteration of every chunk of an epoch.  A
+// chunk is owned by a cluster of K blocks (K = 1, 2 or 4); the chunk's map
+// lives in every block's shared memory and each block takes every K-th round
+// of the chunk's tile tournament.  Within a block:
+//   - one producer lane streams the block's P tiles (4 KB each, stored once
+//     per unordered pair of 32-row blocks) from HBM into a ring of shared
+//     buffers with cp.async.bulk, completion tracked by mbarriers;
+//   - consumer warps take the tiles in stream order, G = 2 or 4 warps per
+//     tile: a tile (rows a, columns b) serves both directions — rows of a
+//     against columns of b (the tile read row-wise) and rows of b against
+//     columns of a (read column-wise) — so every ordered pair (i, j) is
+//     evaluated once per iteration and P is read once per unordered pair
+//     (2 bytes per ordered pair).  Each warp copies its share of the tile into
+//     registers and releases the buffer before computing;
+//   - per ordered pair: w = 1 / (1 + |y_i - y_j|^2), and the row sums
+//     A_i += p_ij w (y_i - y_j), R_i += w^2 (y_i - y_j), Z_i += w (two pairs at
+//     a time per lane with packed f32x2 arithmetic for 2-D maps), merged into
+//     shared-memory accumulators with atomic adds;
+//   - then Z = sum_i Z_i (FP64, over the cluster through distributed shared
+//     memory), dC/dy_i = 4 (A_i - R_i / Z) (Eq. 6), and the update of each
+//     block's slice of rows, broadcast to every block's copy of the map.
+// Every mbarrier wait is bounded in time; a wait that runs out is counted in
+// DeviceStats::timeouts (the host then reports PTSNE_ETIMEOUT) and the kernel
+// runs to completion without blocking.
+#include <float.h>
+
+#include "ptsne_internal.cuh"
+
+namespace ptsne {
+
+namespace {
+constexpr float kPad = 1e18f;                  // map coordinate of padding rows: w ~ 1e-36, p = 0
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
+constexpr float kLn2f = 0.69314718055994531f;
+constexpr int kTileBytes = kPTileStride * 4;    // P tile + trailer, one bulk copy
+}  // namespace
+
+struct IterArgs {
+    const float* P2;            // packed tiles of all chunks
+    const int64_t* ptile_off;   // n_chunks: first tile of each chunk
+    Layout L;
+    float* Yc;                  // n x od map, permuted order (in/out)
+    float* vel;
+    float* gains;
+    float* gradp;               // optional: gradient at the input map (permuted order)
+    double* Zc;                 // optional: Z of the last gradient pass, per chunk
+    double* cost_chunk;         // cost pass: {KL, normalised cost} per chunk
+    int iters;                  // gradient passes
+    int cost_pass;              // 1: one cost pass after the gradient passes
+    Optim opt;
+    int* queue;                 // chunk work queue (zeroed before launch)
+    unsigned int* timeouts;
+    int zcap;                   // rows of the shared map / accumulators (multiple of 32)
+    int ring;                   // ring buffers: a multiple of the consumer slots (see below)
+    int group;                  // consumer warps per tile (2 or 4)
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity; false if it did not complete within
+// kWaitNs, or at once when an earlier wait of the launch already ran out (so a
+// failed launch drains quickly instead of timing out on every tile).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const unsigned int* timeouts) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(bar, parity)) {
+        if (*(volatile const unsigned int*)timeouts != 0u) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cl_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// block barrier, or cluster barrier when the chunk is shared by several blocks
+__device__ __forceinline__ void sync_owner(uint32_t K) {
+    if (K > 1) cl_barrier();
+    else __syncthreads();
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float ld_cl_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_cl_f64(uint32_t a) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_cl_s32(uint32_t a) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_cl_f32(uint32_t a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+// packed FP32 pairs (f32x2 arithmetic, round to nearest like the scalar ops)
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ---------------------------------------------------------------- per-pair arithmetic
+// The shared map is structure-of-arrays: coordinate k of row i at map[k * zcap + i].
+
+// Gradient sums of one lane's row (own) against n partner rows pbase..pbase+n-1
+// with P values pv, 2-D maps, two pairs per packed instruction.
+template <int N>
+__device__ __forceinline__ void grad_task_2d(const float* map, int zcap, int own, int pbase, const float (&pv)[N],
+                                             float (&a)[2], float (&r)[2], float& z) {
+    const float* xs = map;
+    const float* ys = map + zcap;
+    const float ox = xs[own], oy = ys[own];
+    const f2 OX = pk(ox, ox), OY = pk(oy, oy), NEG = pk(-1.f, -1.f), ONE = pk(1.f, 1.f);
+    // one accumulator set: a second set shortens the dependency chains but costs
+    // the registers that let the compiler overlap the steps (measured slower)
+    f2 AX = 0, AY = 0, RX = 0, RY = 0, Z = 0;
+#pragma unroll
+    for (int m = 0; m < N / 4; ++m) {
+        const float4 x4 = *reinterpret_cast<const float4*>(xs + pbase + 4 * m);
+        const float4 y4 = *reinterpret_cast<const float4*>(ys + pbase + 4 * m);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const f2 X = h ? pk(x4.z, x4.w) : pk(x4.x, x4.y);
+            const f2 Yv = h ? pk(y4.z, y4.w) : pk(y4.x, y4.y);
+            const f2 Pp = pk(pv[4 * m + 2 * h], pv[4 * m + 2 * h + 1]);
+            const f2 DX = fma2(X, NEG, OX);     // own - other
+            const f2 DY = fma2(Yv, NEG, OY);
+            f2 Q = fma2(DX, DX, ONE);
+            Q = fma2(DY, DY, Q);
+            float q0, q1;
+            upk(Q, q0, q1);
+            const f2 W = pk(hw_rcp(q0), hw_rcp(q1));
+            Z = add2(Z, W);
+            const f2 PW = mul2(Pp, W), WW = mul2(W, W);
+            AX = fma2(PW, DX, AX);
+            AY = fma2(PW, DY, AY);
+            RX = fma2(WW, DX, RX);
+            RY = fma2(WW, DY, RY);
+        }
+    }
+    float l, h;
+    upk(AX, l, h); a[0] = l + h;
+    upk(AY, l, h); a[1] = l + h;
+    upk(RX, l, h); r[0] = l + h;
+    upk(RY, l, h); r[1] = l + h;
+    upk(Z, l, h); z = l + h;
+}
+
+// Same sums for 3-D maps (scalar arithmetic).
+template <int N>
+__device__ __forceinline__ void grad_task_3d(const float* map, int zcap, int own, int pbase, const float (&pv)[N],
+                                             float (&a)[3], float (&r)[3], float& z) {
+    float o[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { o[k] = map[k * zcap + own]; a[k] = 0.f; r[k] = 0.f; }
+    z = 0.f;
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        float d[3], q = 1.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d[k] = o[k] - map[k * zcap + pbase + t];
+            q = fmaf(d[k], d[k], q);
+        }
+        const float w = hw_rcp(q);
+        z += w;
+        const float pw = pv[t] * w, w2 = w * w;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a[k] = fmaf(pw, d[k], a[k]);
+            r[k] = fmaf(w2, d[k], r[k]);
+        }
+    }
+}
+
+// Cost sums of one lane's row: sum p ln p, sum p ln w, sum p, sum w (Eq. 5, Eq. 9).
+template <int OD, int N>
+__device__ __forceinline__ void cost_task(const float* map, int zcap, int own, int pbase, const float (&pv)[N],
+                                          float (&c)[4]) {
+    float o[OD];
+#pragma unroll
+    for (int k = 0; k < OD; ++k) o[k] = map[k * zcap + own];
+    c[0] = c[1] = c[2] = c[3] = 0.f;
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        float q = 1.0f;
+#pragma unroll
+        for (int k = 0; k < OD; ++k) {
+            const float d = o[k] - map[k * zcap + pbase + t];
+            q = fmaf(d, d, q);
+        }
+        c[3] += hw_rcp(q);
+        const float p = pv[t];
+        if (p >= FLT_MIN) {
+            c[0] += p * (hw_lg2(p) * kLn2f);
+            c[1] -= p * (hw_lg2(q) * kLn2f);
+            c[2] += p;
+        }
+    }
+}
+
+// Copy a warp's share of a staged tile into registers:
+// row-wise (lane = tile row) for tile columns [c0, c0 + N), or
+// column-wise (lane = tile column) for tile rows [r0, r0 + N).
+template <int N>
+__device__ __forceinline__ void tile_row_share(const float* tile, int lane, int c0, float (&pv)[N]) {
+    const float* trow = tile + lane * kPT;
+    const int l7 = lane & 7;
+#pragma unroll
+    for (int m = 0; m < N / 4; ++m) {
+        const int c4 = (c0 >> 2) + m;
+        const float4 v = *reinterpret_cast<const float4*>(trow + ((c4 ^ l7) << 2));
+        pv[4 * m] = v.x; pv[4 * m + 1] = v.y; pv[4 * m + 2] = v.z; pv[4 * m + 3] = v.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void tile_col_share(const float* tile, int lane, int r0, float (&pv)[N]) {
+    const int hi = lane >> 2, lo = lane & 3;
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        const int r = r0 + t;
+        pv[t] = tile[r * kPT + (((hi ^ (r & 7)) << 2) | lo)];
+    }
+}
+
+// Tile stream of one block of the cluster: the rounds r = rank, rank + K, ...
+// of the chunk's tournament, every tile of each round in storage order (the
+// pair rounds first, then, for an even block count, the diagonal round).
+struct Stream {
+    TourSched T;
+    int jd;      // pair rounds owned by this block
+    int nq;      // tiles per pass
+    __device__ Stream(int nb, uint32_t rank, uint32_t K) : T(nb) {
+        jd = (int)rank < T.M ? (T.M - 1 - (int)rank) / (int)K + 1 : 0;
+        nq = jd * T.tpr;
+        if (!(nb & 1) && (nb - 1) % (int)K == (int)rank) nq += nb;  // the diagonal round
+    }
+};
+
+// Position in a stream, advanced by additions only: ring buffer and phase of
+// the stream index q, and (j, p) = (j-th round of this block, tile in round)
+// of the index s within the current pass.
+struct Cursor {
+    unsigned long long q;
+    uint32_t buf, ph;
+    int s, j, p;
+    __device__ __forceinline__ void advance_ring(uint32_t delta, uint32_t ring) {
+        q += delta;
+        buf += delta;
+        while (buf >= ring) { buf -= ring; ph ^= 1u; }
+    }
+    // set s and normalise (j, p) for a stream of jd pair rounds of tpr tiles
+    __device__ __forceinline__ void seek(int s_, int jd, int tpr) {
+        s = s_; j = 0; p = s_;
+        while (j < jd && p >= tpr) { p -= tpr; ++j; }
+    }
+    __device__ __forceinline__ void step(int delta, int jd, int tpr) {
+        s += delta; p += delta;
+        while (j < jd && p >= tpr) { p -= tpr; ++j; }
+    }
+    // round of the current tile (the diagonal round after the pair rounds)
+    __device__ __forceinline__ int round(uint32_t rank, uint32_t K, int jd, int nb) const {
+        return j < jd ? (int)rank + j * (int)K : nb - 1;
+    }
+};
+
+// Compensated FP32 running sum (per lane; combined in FP64 at the end of a pass).
+struct KSum {
+    float s, c;
+    __device__ __forceinline__ void clear() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// One warp's share of a tile.  G = 2: one warp takes rows of a (tile
+// row-wise), the other rows of b (tile column-wise); G = 4 halves each.  A
+// diagonal tile (a == b) is read row-wise only, its columns split G ways.
+template <int OD, int N>
+__device__ __forceinline__ void consume_share(const float* tile, const float* map, int zcap, int z, int a, int b,
+                                              int lane, int colwise, int start, bool cost, float* acc,
+                                              uint32_t empty_bar, KSum (&part)[4], bool diag_owner) {
+    float pv[N];
+    if (colwise) tile_col_share<N>(tile, lane, start, pv);
+    else tile_row_share<N>(tile, lane, start, pv);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty_bar);   // the buffer is free again
+    const int own = (colwise ? b : a) * kPT + lane;
+    const int pbase = (colwise ? a : b) * kPT + start;
+    if (own >= z) return;
+    if (!cost) {
+        float av[OD], rv[OD], w;
+        if constexpr (OD == 2) grad_task_2d<N>(map, zcap, own, pbase, pv, av, rv, w);
+        else grad_task_3d<N>(map, zcap, own, pbase, pv, av, rv, w);
+#pragma unroll
+        for (int k = 0; k < OD; ++k) {
+            atomicAdd(acc + k * zcap + own, av[k]);
+            atomicAdd(acc + (OD + k) * zcap + own, rv[k]);
+        }
+        part[0].add(diag_owner ? w - 1.0f : w);   // drop the w_ii = 1 term of this row
+    } else {
+        float cs[4];
+        cost_task<OD, N>(map, zcap, own, pbase, pv, cs);
+        part[0].add(diag_owner ? cs[3] - 1.0f : cs[3]);
+        part[1].add(cs[0]);
+        part[2].add(cs[1]);
+        part[3].add(cs[2]);
+    }
+}
+
+template <int OD>
+// At most 16 consumer warps + 1 producer warp: 96 registers per thread hold a
+// warp's register copy of its tile share without spilling.
+__global__ void __launch_bounds__(544, 1) iterate_kernel(IterArgs A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthreads = blockDim.x;
+    const int Wc = (nthreads >> 5) - 1;            // consumer warps; the last warp produces
+    const bool is_producer = warp == Wc;
+    const int G = A.group;
+    const int sub = warp % G;                       // this warp's share of each of its tiles
+    const int slot = warp / G, nslots = Wc / G;     // tiles q with q % nslots == slot
+    const uint32_t ring_n = (uint32_t)A.ring;
+    const int zcap = A.zcap;
+
+    float* ring = reinterpret_cast<float*>(smem_raw);
+    uint64_t* fullb = reinterpret_cast<uint64_t*>(smem_raw + (size_t)A.ring * kTileBytes);
+    uint64_t* emptyb = fullb + A.ring;
+    float* map = reinterpret_cast<float*>(emptyb + A.ring);   // OD arrays of zcap floats
+    float* acc = map + (size_t)OD * zcap;                     // 2*OD arrays: A_0.., R_0..
+
+    __shared__ double s_red[32][4];
+    __shared__ double s_part[4];                    // this block's Z (and cost) partial sums
+    __shared__ int s_item;
+    __shared__ float s_mn[32], s_mx[32];
+    __shared__ float s_eta;
+
+    const uint32_t K = cl_size(), rank = cl_rank();
+    const uint32_t ring_a = smem_u32(ring), full_a = smem_u32(fullb), empty_a = smem_u32(emptyb);
+    if (tid == 0) {
+        for (int b = 0; b < A.ring; ++b) {
+            mbar_init(full_a + 8 * b, 1);
+            mbar_init(empty_a + 8 * b, (uint32_t)G);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    // stream cursors: the producer visits every q, a consumer slot q = slot + k * nslots
+    Cursor cur;
+    cur.q = is_producer ? 0ull : (unsigned long long)slot;
+    cur.buf = is_producer ? 0u : (uint32_t)slot;   // slot < nslots <= ring
+    cur.ph = 0u;
+    unsigned long long q0 = 0;  // first stream index of the current pass (same in every thread)
+    for (;;) {
+        if (rank == 0 && tid == 0) s_item = atomicAdd(A.queue, 1);
+        sync_owner(K);
+        const int item = (K > 1) ? ld_cl_s32(map_rank(smem_u32(&s_item), 0)) : s_item;
+        sync_owner(K);
+        if (item >= A.L.n_chunks) break;
+
+        const int c = A.L.order[item];
+        const int64_t off = A.L.off[c];
+        const int z = (int)(A.L.off[c + 1] - off);
+        const int nb = (z + kPT - 1) / kPT;
+        const int zr = nb * kPT;
+        const Stream S(nb, rank, K);
+        const float* P2c = A.P2 + A.ptile_off[c] * kPTileStride;
+        const int slice = (z + (int)K - 1) / (int)K;           // rows updated by this block
+        const int ulo = (int)rank * slice, uhi = min(z, ulo + slice);
+
+        for (int i = tid; i < zr; i += nthreads) {
+#pragma unroll
+            for (int k = 0; k < OD; ++k) map[k * zcap + i] = i < z ? A.Yc[(off + i) * OD + k] : kPad;
+        }
+        for (int i = tid; i < 2 * OD * zcap; i += nthreads) acc[i] = 0.f;
+        __syncthreads();
+
+        const int npass = A.iters + (A.cost_pass ? 1 : 0);
+        for (int it = 0; it < npass; ++it) {
+            const bool cost = it == A.iters;
+            if (!cost && A.opt.lr_mode == PTSNE_LR_PAPER) {
+                float mn = FLT_MAX, mx = -FLT_MAX;
+                for (int i = tid; i < z; i += nthreads)
+#pragma unroll
+                    for (int k = 0; k < OD; ++k) {
+                        mn = fminf(mn, map[k * zcap + i]);
+                        mx = fmaxf(mx, map[k * zcap + i]);
+                    }
+                mn = warp_min(mn);
+                mx = warp_max(mx);
+                if (lane == 0) { s_mn[warp] = mn; s_mx[warp] = mx; }
+                __syncthreads();
+                if (tid == 0) {
+                    float a = FLT_MAX, b = -FLT_MAX;
+                    for (int w = 0; w < (nthreads >> 5); ++w) { a = fminf(a, s_mn[w]); b = fmaxf(b, s_mx[w]); }
+                    s_eta = step_eta(A.opt, z, a, b);
+                }
+            }
+
+            KSum part[4];                              // Z, sum p ln p, sum p ln w, sum p
+#pragma unroll
+            for (int k = 0; k < 4; ++k) part[k].clear();
+            const unsigned long long qend = q0 + (unsigned long long)S.nq;
+            if (is_producer) {
+                // Lane l issues tile s = base + l of each batch.  A batch spans at most
+                // `ring` tiles, so it uses every buffer at most once, and the warp ends
+                // batch k before starting batch k + 1: each buffer's uses stay in
+                // stream order, one phase at a time.
+                const int batch = A.ring < 32 ? A.ring : 32;
+                const uint32_t q0r = (uint32_t)(q0 % ring_n), q0ph = (uint32_t)(q0 / ring_n) & 1u;
+                for (int base = 0; base < S.nq; base += batch) {
+                    const int s = base + lane;
+                    if (lane < batch && s < S.nq) {
+                        const uint32_t t = q0r + (uint32_t)s;
+                        const uint32_t buf = t % ring_n, ph = q0ph ^ ((t / ring_n) & 1u);
+                        if (!mbar_wait(empty_a + 8 * buf, ph ^ 1u, A.timeouts)) atomicAdd(A.timeouts, 1u);
+                        int r, p;
+                        if (s < S.jd * S.T.tpr) {
+                            const int j = s / S.T.tpr;
+                            p = s - j * S.T.tpr;
+                            r = (int)rank + j * (int)K;
+                        } else {
+                            r = nb - 1;
+                            p = s - S.jd * S.T.tpr;
+                        }
+                        const float* src = P2c + (S.T.round_base(r) + p) * kPTileStride;
+                        mbar_expect_tx(full_a + 8 * buf, kTileBytes);
+                        bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
+                    }
+                    __syncwarp();
+                }
+            } else {
+                int kth = 0;    // tiles this warp has taken in the pass (alternates the roles)
+                for (; cur.q < qend; cur.advance_ring((uint32_t)nslots, ring_n), ++kth) {
+                    // The ring holds a whole number of consumer slots, so tile q - ring
+                    // (this buffer's previous use) belonged to this same slot and was
+                    // waited for before: the barrier is at most one phase behind, and
+                    // the parity test cannot mistake an older phase for this one.
+                    if (!mbar_wait(full_a + 8 * cur.buf, cur.ph, A.timeouts) && lane == 0) atomicAdd(A.timeouts, 1u);
+                    __syncwarp();
+                    const float* tile = ring + (size_t)cur.buf * kPTileStride;
+                    const int a = __float_as_int(tile[kPTileFloats]), b = __float_as_int(tile[kPTileFloats + 1]);
+                    const uint32_t ebar = empty_a + 8 * cur.buf;
+                    if (a == b) {
+                        // diagonal: rows of a against columns split G ways; the owner
+                        // of column `lane` drops that row's w_ii = 1
+                        const int w = kPT / G, c0 = sub * w;
+                        const bool own_diag = lane >= c0 && lane < c0 + w;
+                        if (G == 2) consume_share<OD, 16>(tile, map, zcap, z, a, b, lane, 0, c0, cost, acc, ebar, part, own_diag);
+                        else consume_share<OD, 8>(tile, map, zcap, z, a, b, lane, 0, c0, cost, acc, ebar, part, own_diag);
+                    } else {
+                        // the slot's warps swap directions on alternate tiles, so the
+                        // slower column-wise read is shared evenly between them
+                        const int h = G / 2;                        // warps per direction
+                        const int colwise = (sub >= h) ^ (kth & 1), start = (sub % h) * (kPT / h);
+                        if (G == 2) consume_share<OD, 32>(tile, map, zcap, z, a, b, lane, colwise, start, cost, acc, ebar, part, false);
+                        else consume_share<OD, 16>(tile, map, zcap, z, a, b, lane, colwise, start, cost, acc, ebar, part, false);
+                    }
+                }
+            }
+            // block partials (fixed order), then the cluster total
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double v = warp_sum(part[k].value());
+                if (lane == 0) s_red[warp][k] = v;
+            }
+            __syncthreads();
+            if (tid < 4) {
+                double v = 0.0;
+                for (int w = 0; w < Wc; ++w) v += s_red[w][tid];
+                s_part[tid] = v;
+            }
+            sync_owner(K);
+            double tot[4] = {0.0, 0.0, 0.0, 0.0};
+            for (uint32_t rr = 0; rr < K; ++rr)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tot[k] += K > 1 ? ld_cl_f64(map_rank(smem_u32(&s_part[k]), rr)) : s_part[k];
+            if (cost) {
+                if (rank == 0 && tid == 0) {
+                    const double lnZ = log(tot[0]);
+                    A.cost_chunk[2 * c] = tot[1] - tot[2] + tot[3] * lnZ;
+                    A.cost_chunk[2 * c + 1] = (-tot[2] + tot[3] * lnZ) / (log((double)z) + log((double)(z - 1)));
+                }
+            } else {
+                if (rank == 0 && tid == 0 && A.Zc) A.Zc[c] = tot[0];
+                const float invZ = (float)(1.0 / tot[0]);
+                const float eta = A.opt.lr_mode == PTSNE_LR_PAPER ? s_eta : A.opt.lr;
+                for (int i = ulo + tid; i < uhi; i += nthreads) {
+                    float Av[OD], Rv[OD], y[OD];
+#pragma unroll
+                    for (int k = 0; k < OD; ++k) { Av[k] = 0.f; Rv[k] = 0.f; y[k] = map[k * zcap + i]; }
+                    for (uint32_t rr = 0; rr < K; ++rr) {
+#pragma unroll
+                        for (int k = 0; k < OD; ++k) {
+                            if (K > 1) {
+                                Av[k] += ld_cl_f32(map_rank(smem_u32(acc + k * zcap + i), rr));
+                                Rv[k] += ld_cl_f32(map_rank(smem_u32(acc + (OD + k) * zcap + i), rr));
+                            } else {
+                                Av[k] += acc[k * zcap + i];
+                                Rv[k] += acc[(OD + k) * zcap + i];
+                            }
+                        }
+                    }
+                    const int64_t gi = (off + i) * OD;
+                    update_point<OD>(y, A.vel + gi, A.gains + gi, Av, Rv, invZ, eta, A.opt,
+                                     A.gradp ? A.gradp + gi : nullptr);
+                    for (uint32_t rr = 0; rr < K; ++rr)
+#pragma unroll
+                        for (int k = 0; k < OD; ++k) {
+                            if (K > 1) st_cl_f32(map_rank(smem_u32(map + k * zcap + i), rr), y[k]);
+                            else map[k * zcap + i] = y[k];
+                        }
+                }
+            }
+            sync_owner(K);   // new map everywhere; remote reads of acc are done
+            for (int i = tid; i < 2 * OD * zcap; i += nthreads) acc[i] = 0.f;
+            __syncthreads();
+            q0 = qend;
+        }
+        for (int i = ulo + tid; i < uhi; i += nthreads)
+#pragma unroll
+            for (int k = 0; k < OD; ++k) A.Yc[(off + i) * OD + k] = map[k * zcap + i];
+        __syncthreads();
+    }
+    // every issued copy has been waited for by a consumer; if a wait ran out,
+    // wait (bounded) for the copies still in flight before the block exits
+    if (is_producer && lane == 0) {
+        const unsigned long long n = q0 < (unsigned long long)A.ring ? q0 : (unsigned long long)A.ring;
+        uint32_t buf = (uint32_t)((q0 - n) % ring_n), ph = (uint32_t)((q0 - n) / ring_n) & 1u;
+        for (unsigned long long q = q0 - n; q < q0; ++q) {
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try(full_a + 8 * buf, ph))
+                if (global_ns() - t0 > kWaitNs) break;
+            if (++buf == ring_n) { buf = 0; ph ^= 1u; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- packed P assembly and export
+
+// Joint P (Eq. 3) of one stored 32 x 32 tile, written packed and swizzled.
+// D is symmetric (z x ld rows), so d_ji is d_ij:
+//   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ij - m_j)) / S_j) / (2z),
+// zero on the diagonal and outside the chunk.
+__global__ void __launch_bounds__(256)
+psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
+                   const TileDesc2* __restrict__ tiles, int64_t t0, const float* __restrict__ beta,
+                   const float* __restrict__ mrow, const float* __restrict__ Srow) {
+    constexpr float kLog2e = 1.4426950408889634f;
+    const TileDesc2 td = tiles[t0 + blockIdx.x];
+    const int c = td.chunk;
+    const int64_t off = L.off[c];
+    const int z = (int)(L.off[c + 1] - off);
+    const int ld = L.ld[c];
+    const int tid = threadIdx.x, r = tid >> 3, c4 = tid & 7;
+    const int i = td.a * kPT + r;
+    const int j0 = td.b * kPT + c4 * 4;
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < z) {
+        const float4 dv = *reinterpret_cast<const float4*>(D + L.moff[c] + (int64_t)i * ld + j0);
+        const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
+        const float bi = beta[off + i] * kLog2e, mi = mrow[off + i], si = 1.0f / Srow[off + i];
+        const float inv2z = 1.0f / (2.0f * (float)z);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = j0 + e;
+            if (j < z && j != i) {
+                const float bj = beta[off + j] * kLog2e, mj = mrow[off + j], sj = 1.0f / Srow[off + j];
+                const float cij = __fmul_rn(hw_ex2(-bi * (d4[e] - mi)), si);
+                const float cji = __fmul_rn(hw_ex2(-bj * (d4[e] - mj)), sj);
+                out[e] = __fmul_rn(__fadd_rn(cij, cji), inv2z);
+            }
+        }
+    }
+    float* dst = P2 + (ptile_off[c] + td.pos) * kPTileStride;
+    *reinterpret_cast<float4*>(dst + packed_index(r, c4 * 4)) = make_float4(out[0], out[1], out[2], out[3]);
+    if (tid == 0)   // trailer: the tile's row and column blocks
+        *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, 0, 0);
+}
+
+// Packed tiles -> dense z x z per chunk (chunks concatenated), both halves.
+__global__ void __launch_bounds__(256)
+export_packed_kernel(const float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
+                     const TileDesc2* __restrict__ tiles, const int64_t* __restrict__ dense_off, float* __restrict__ out) {
+    const TileDesc2 td = tiles[blockIdx.x];
+    const int c = td.chunk;
+    const int z = (int)(L.off[c + 1] - L.off[c]);
+    const float* src = P2 + (ptile_off[c] + td.pos) * kPTileStride;
+    float* dst = out + dense_off[c];
+    for (int e = threadIdx.x; e < kPTileFloats; e += blockDim.x) {
+        const int r = e >> 5, cc = e & 31;
+        const int i = td.a * kPT + r, j = td.b * kPT + cc;
+        if (i < z && j < z) {
+            const float v = src[packed_index(r, cc)];
+            dst[(int64_t)i * z + j] = v;
+            dst[(int64_t)j * z + i] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+int iterate_smem_bytes(int od, int64_t zmax, int ring) {
+    const int zcap = (int)((zmax + kPT - 1) / kPT * kPT);
+    const int per_row = 3 * od * 4;   // map + A + R, structure-of-arrays
+    // tiles (with trailers), full + empty barriers, map and accumulators
+    return ring * (kTileBytes + 16) + zcap * per_row;
+}
+
+// Ring size for `slots` consumer slots: a whole number of buffers per slot
+// (at most 4, at most 48 buffers) next to the map in 227 KB; 0 if not even
+// one buffer per slot fits.
+int iterate_ring(int od, int64_t zmax, int slots) {
+    const int avail = 227 * 1024 - 2048 - iterate_smem_bytes(od, zmax, 0);
+    const int fit = avail > 0 ? avail / (kTileBytes + 16) : 0;
+    int m = fit / slots;
+    if (m > 4) m = 4;
+    if (m * slots > 48) m = 48 / slots;
+    return m >= 1 ? m * slots : 0;
+}
+
+cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s) {
+    if (c->ntiles2 <= 0) return cudaSuccess;
+    int k = 0;
+    for (int64_t b = 0; b < c->ntiles2; b += 2147483647LL, ++k) {
+        const int64_t cnt = (c->ntiles2 - b) < 2147483647LL ? (c->ntiles2 - b) : 2147483647LL;
+        psym_packed_kernel<<<(unsigned)cnt, 256, 0, s>>>(c->D, c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2, b,
+                                                         c->beta, c->mrow, c->Srow);
+    }
+    return launched(c, k);
+}
+
+cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t s) {
+    export_packed_kernel<<<(unsigned)c->ntiles2, 256, 0, s>>>(c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2,
+                                                              c->d_dense_off, P_out);
+    return launched(c, 1);
+}
+
+cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc, double* cost_chunk,
+                           cudaStream_t s) {
+    if (iters <= 0 && !cost_pass) return cudaSuccess;
+    const int K = c->tune.cluster, G = c->tune.group;
+    if (G != 2 && G != 4) return cudaErrorInvalidValue;
+    int Wc = c->tune.consumer_warps;
+    int ring = iterate_ring(c->p.out_dim, c->zmax, Wc / G);
+    while (ring == 0 && Wc > G) {   // very large chunks: fewer consumer slots
+        Wc -= G;
+        ring = iterate_ring(c->p.out_dim, c->zmax, Wc / G);
+    }
+    if (ring == 0) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, ring);
+    cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    IterArgs a;
+    a.P2 = c->P2;
+    a.ptile_off = c->d_ptile_off;
+    a.L = make_layout(c);
+    a.Yc = c->Yc;
+    a.vel = c->vel;
+    a.gains = c->gains;
+    a.gradp = gradp;
+    a.Zc = Zc;
+    a.cost_chunk = cost_chunk;
+    a.iters = iters;
+    a.cost_pass = cost_pass;
+    a.opt = Optim{c->p.lr, c->p.momentum, c->p.lr_mode, c->p.use_gains};
+    a.queue = c->queue;
+    a.timeouts = &c->dstats->timeouts;
+    a.zcap = (int)((c->zmax + kPT - 1) / kPT * kPT);
+    a.ring = ring;
+    a.group = G;
+
+    void (*kern)(IterArgs) = c->p.out_dim == 2 ? iterate_kernel<2> : iterate_kernel<3>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3((unsigned)((Wc + 1) * 32), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    int clusters = sms / K;
+    if (K > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)K;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3((unsigned)K, 1, 1);
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0) clusters = active;
+        cudaGetLastError();
+    }
+    if (clusters > c->p.n_chunks) clusters = c->p.n_chunks;
+    if (clusters < 1) clusters = 1;
+    cfg.gridDim = dim3((unsigned)(clusters * K), 1, 1);
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e != cudaSuccess) return e;
+    return launched(c, 1);
+}
+
+}  // namespace ptsne

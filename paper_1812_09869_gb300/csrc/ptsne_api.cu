@@ -13,7 +13,6 @@
 using namespace ptsne;
 
 namespace ptsne {
-int persistent_smem_bytes(int od, int64_t zmax);
 
 Layout make_layout(const ptsne_ctx* c) {
     Layout L;
@@ -71,7 +70,7 @@ void free_all(ptsne_ctx* c) {
                     c->beta,   c->mrow,    c->Srow,   c->Yc,             c->vel,     c->gains,
                     c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
-                    c->hY};
+                    c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -131,7 +130,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (p.precision != PTSNE_PREC_FP32 && p.precision != PTSNE_PREC_BF16_WINDOW)
         return bad("precision", p.precision);
     if (p.schedule != PTSNE_SCHED_BATCHED && p.schedule != PTSNE_SCHED_PER_CHUNK) return bad("schedule", p.schedule);
-    if (p.schedule == PTSNE_SCHED_BATCHED && persistent_smem_bytes(p.out_dim, zmax) > 227 * 1024)
+    if (p.schedule == PTSNE_SCHED_BATCHED && iterate_ring(p.out_dim, zmax, 1) < 1)
         return bad("largest chunk too large for the batched schedule at this out_dim", zmax);
 
     c->p = p;
@@ -163,6 +162,25 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     c->tile_start[nc] = t;
     c->mtotal = m;
     c->ntiles = t;
+    // packed symmetric P: 32 x 32 tiles of each chunk in tournament order
+    std::vector<TileDesc2> tiles2;
+    std::vector<int64_t> ptoff(nc);
+    if (p.schedule == PTSNE_SCHED_BATCHED) {
+        int64_t acc2 = 0;
+        for (int k = 0; k < nc; ++k) {
+            const int nb = (int)((c->off[k + 1] - c->off[k] + kPT - 1) / kPT);
+            const TourSched T(nb);
+            ptoff[k] = acc2;
+            for (int r = 0; r < T.rounds(); ++r)
+                for (int q = 0; q < T.tiles_in_round(r); ++q) {
+                    int a, b;
+                    T.pair(r, q, a, b);
+                    tiles2.push_back(TileDesc2{k, (int16_t)a, (int16_t)b, (int32_t)(T.round_base(r) + q)});
+                }
+            acc2 += T.total_tiles();
+        }
+        c->ntiles2 = acc2;
+    }
     c->order.resize(nc);
     std::iota(c->order.begin(), c->order.end(), 0);
     std::stable_sort(c->order.begin(), c->order.end(), [&](int a, int b) {
@@ -198,7 +216,13 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         AL(c->xnorm, n);
     }
     AL(c->D, m);
-    AL(c->P, m);
+    if (p.schedule == PTSNE_SCHED_BATCHED) {
+        AL(c->P2, c->ntiles2 * kPTileStride);
+        AL(c->d_ptile_off, nc);
+        AL(c->d_tiles2, c->ntiles2);
+    } else {
+        AL(c->P, m);
+    }
     AL(c->beta, n);
     AL(c->mrow, n);
     AL(c->Srow, n);
@@ -227,9 +251,13 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (e == cudaSuccess) e = up(c->d_order, c->order.data(), sizeof(int32_t) * nc);
     if (e == cudaSuccess) e = up(c->d_dense_off, dense.data(), sizeof(int64_t) * nc);
     if (e == cudaSuccess) e = up(c->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size());
+    if (e == cudaSuccess && c->ntiles2) {
+        e = up(c->d_ptile_off, ptoff.data(), sizeof(int64_t) * nc);
+        if (e == cudaSuccess) e = up(c->d_tiles2, tiles2.data(), sizeof(TileDesc2) * tiles2.size());
+    }
     if (e == cudaSuccess) e = cudaMemset(c->dstats, 0, sizeof(DeviceStats));
     // zero P once so that padded columns read as exact zeros before the first assembly
-    if (e == cudaSuccess) e = cudaMemset(c->P, 0, sizeof(float) * (size_t)m);
+    if (e == cudaSuccess && c->P) e = cudaMemset(c->P, 0, sizeof(float) * (size_t)m);
     if (e != cudaSuccess) {
         g_create_err = cudaGetErrorString(e);
         free_all(c);
@@ -270,7 +298,7 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cu
         mark(c, PTSNE_STAGE_PERPLEXITY, s);
         CK(launch_bisect(c, 0, c->p.n, s));
         mark(c, PTSNE_STAGE_JOINT_P, s);
-        CK(launch_psym(c, 0, c->ntiles, s));
+        CK(launch_psym_packed(c, s));
     } else {
         for (int k = 0; k < c->p.n_chunks; ++k) {
             CK(launch_dist_fp32(c, c->tile_start[k], c->tile_start[k + 1], s));
@@ -291,7 +319,7 @@ int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P
     cudaStream_t s = as_stream(stream);
     int st = affinities_impl(c, X, perm, s, true, nullptr);
     if (st != PTSNE_OK) return st;
-    if (P_out) CK(launch_export_P(c, P_out, s));
+    if (P_out) CK(c->P2 ? launch_export_packed(c, P_out, s) : launch_export_P(c, P_out, s));
     if (beta_out) CK(launch_scatter_rows(c, c->beta, perm, 1, beta_out, s));
     return PTSNE_OK;
 }
@@ -317,8 +345,12 @@ int ptsne_step(ptsne_ctx* c, const int32_t* perm, float* Y, float* grad_out, dou
     if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_step before ptsne_affinities%s%lld");
     cudaStream_t s = as_stream(stream);
     CK(launch_gather_y(c, Y, perm, c->Yc, s));
-    int st = iterate_rows(c, grad_out ? c->gradp : nullptr, s);
-    if (st != PTSNE_OK) return st;
+    if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+        CK(launch_iterate(c, 1, 0, grad_out ? c->gradp : nullptr, c->Zc, nullptr, s));
+    } else {
+        int st = iterate_rows(c, grad_out ? c->gradp : nullptr, s);
+        if (st != PTSNE_OK) return st;
+    }
     CK(launch_scatter_rows(c, c->Yc, perm, c->p.out_dim, Y, s));
     if (grad_out) CK(launch_scatter_rows(c, c->gradp, perm, c->p.out_dim, grad_out, s));
     if (Z_out)
@@ -332,7 +364,12 @@ int ptsne_cost(ptsne_ctx* c, const int32_t* perm, const float* Y, double* out_de
     if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_cost before ptsne_affinities%s%lld");
     cudaStream_t s = as_stream(stream);
     CK(launch_gather_y(c, Y, perm, c->Yc, s));
-    CK(launch_cost(c, out_dev, s));
+    if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+        CK(launch_iterate(c, 0, 1, nullptr, nullptr, c->cost_chunk, s));
+        CK(launch_cost_final(c, out_dev, s));
+    } else {
+        CK(launch_cost(c, out_dev, s));
+    }
     return PTSNE_OK;
 }
 
@@ -351,7 +388,8 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
         if (st != PTSNE_OK) return st;
         mark(c, PTSNE_STAGE_ITERATE, s);
         if (c->p.schedule == PTSNE_SCHED_BATCHED) {
-            CK(launch_grad_persistent(c, c->p.iters, s));
+            // every iteration of every chunk, then (if requested) one cost pass, in one launch
+            CK(launch_iterate(c, c->p.iters, cost_out ? 1 : 0, nullptr, nullptr, c->cost_chunk, s));
         } else {
             for (int it = 0; it < c->p.iters; ++it) {
                 st = iterate_rows(c, nullptr, s);
@@ -363,7 +401,8 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
         mark(c, PTSNE_STAGE_COST, s);
         if (cost_out) {
             const int slot = e % kCostHist;
-            CK(launch_cost(c, c->cost_hist + 2 * slot, s));
+            if (c->p.schedule == PTSNE_SCHED_BATCHED) CK(launch_cost_final(c, c->cost_hist + 2 * slot, s));
+            else CK(launch_cost(c, c->cost_hist + 2 * slot, s));
             if (slot == kCostHist - 1 || e == epochs - 1)
                 CK(cudaMemcpyAsync(cost_out + 2 * (int64_t)(e - slot), c->cost_hist, sizeof(double) * 2 * (slot + 1),
                                    cudaMemcpyDeviceToHost, s));
@@ -383,6 +422,7 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
     DeviceStats h;
     CK(cudaMemcpyAsync(&h, c->dstats, sizeof h, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (h.timeouts) return fail(c, PTSNE_ETIMEOUT, "%s%lld bounded device waits ran out", "", (long long)h.timeouts);
     if (h.bad_index) return fail(c, PTSNE_EINVAL, "%s%lld permutation entries outside [0, n)", "", (long long)h.bad_index);
     if (h.nonfinite) return fail(c, PTSNE_ENONFINITE, "%s%lld non-finite values in X", "", (long long)h.nonfinite);
     if (h.failed_rows) {
@@ -429,6 +469,7 @@ int ptsne_get_stats(ptsne_ctx* c, ptsne_stats* out, void* stream) {
     out->window_pairs = (int64_t)h.window_pairs;
     out->nonfinite_inputs = (int64_t)h.nonfinite;
     out->bad_perm_entries = (int64_t)h.bad_index;
+    out->wait_timeouts = (int64_t)h.timeouts;
     float herr;
     memcpy(&herr, &h.max_herr_bits, sizeof herr);
     out->max_abs_entropy_err = herr;
@@ -446,6 +487,27 @@ int ptsne_set_profiling(ptsne_ctx* c, int on) {
         for (int k = 0; k <= PTSNE_N_STAGES; ++k) CK(cudaEventCreate(&c->ev[k]));
     }
     c->profiling = on != 0;
+    return PTSNE_OK;
+}
+
+int ptsne_set_tuning(ptsne_ctx* c, const ptsne_tuning* t) {
+    if (!c || !t) return PTSNE_EINVAL;
+    const bool ok_k = t->cluster == 1 || t->cluster == 2 || t->cluster == 4;
+    const bool ok_g = t->group == 2 || t->group == 4;
+    if (!ok_k || !ok_g || t->consumer_warps < t->group || t->consumer_warps > 16 ||
+        t->consumer_warps % t->group != 0)
+        return fail(c, PTSNE_EINVAL, "invalid tuning%s (cluster %lld)", "", t->cluster);
+    c->tune.cluster = t->cluster;
+    c->tune.group = t->group;
+    c->tune.consumer_warps = t->consumer_warps;
+    return PTSNE_OK;
+}
+
+int ptsne_get_tuning(const ptsne_ctx* c, ptsne_tuning* t) {
+    if (!c || !t) return PTSNE_EINVAL;
+    t->cluster = c->tune.cluster;
+    t->group = c->tune.group;
+    t->consumer_warps = c->tune.consumer_warps;
     return PTSNE_OK;
 }
 

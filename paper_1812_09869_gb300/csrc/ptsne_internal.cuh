@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ptsne.h"
+#include "ptsne.h"   // include/ptsne.h (the build passes -I include)
 
 namespace ptsne {
 
@@ -25,6 +25,59 @@ struct TileDesc {
     int32_t chunk;
     int16_t I, J;
 };
+
+// ---- packed symmetric P for the batched iteration kernel ---------------------
+// Each chunk's joint P is stored once per unordered pair of 32-row blocks as
+// 32 x 32 FP32 tiles (row block a <= column block b), in the order of a
+// round-robin tournament over the chunk's nb row blocks: in every round each
+// block meets exactly one partner (or its own diagonal tile), so one pass over
+// the tiles in storage order touches every block once per round.  Inside a
+// tile, element (r, c) sits at r*32 + (((c >> 2) ^ (r & 7)) << 2 | (c & 3))
+// (16-byte chunks XOR-swizzled by row), which makes both a row-wise float4
+// read (lane = r) and a column read (lane = c) free of bank conflicts.
+constexpr int kPT = 32;                      // packed tile edge
+constexpr int kPTileFloats = kPT * kPT;      // 1024 floats = 4 KB of P
+// Stored tile: the 4 KB of P followed by a 16-byte trailer {a, b, 0, 0} (int
+// bits) naming its row and column blocks, so a consumer learns the pair from
+// the tile itself.
+constexpr int kPTileStride = kPTileFloats + 4;
+
+struct TileDesc2 {
+    int32_t chunk;
+    int16_t a, b;      // row block a <= column block b
+    int32_t pos;       // tile index inside the chunk's packed block
+};
+
+// Tournament schedule of nb row blocks (circle method).  For odd nb a dummy
+// player makes nb + 1 players: nb rounds of (nb + 1) / 2 tiles, the block
+// paired with the dummy taking its diagonal tile.  For even nb: nb - 1 pair
+// rounds of nb / 2 tiles, then one round of the nb diagonal tiles.
+struct TourSched {
+    int nb, M, tpr;    // M = pair rounds' modulus (odd), tpr = tiles per pair round
+    __host__ __device__ explicit TourSched(int nb_) : nb(nb_) {
+        M = (nb & 1) ? nb : nb - 1;
+        tpr = (nb + 1) / 2;
+    }
+    __host__ __device__ int rounds() const { return nb; }
+    __host__ __device__ bool diag_round(int r) const { return !(nb & 1) && r == nb - 1; }
+    __host__ __device__ int tiles_in_round(int r) const { return diag_round(r) ? nb : tpr; }
+    __host__ __device__ long long round_base(int r) const { return (long long)r * tpr; }
+    __host__ __device__ long long total_tiles() const { return (long long)nb * (nb + 1) / 2; }
+    // blocks (a <= b) of tile p of round r; a == b for a diagonal tile
+    __host__ __device__ void pair(int r, int p, int& a, int& b) const {
+        if (diag_round(r)) { a = b = p; return; }
+        int u, v;
+        if (p == 0) { u = M; v = r; }
+        else { u = (r + p) % M; v = (r - p + M) % M; }
+        if ((nb & 1) && u == M) { a = b = v; return; }   // bye: the diagonal tile
+        a = u < v ? u : v;
+        b = u < v ? v : u;
+    }
+};
+
+__host__ __device__ inline int packed_index(int r, int c) {
+    return r * kPT + ((((c >> 2) ^ (r & 7)) << 2) | (c & 3));
+}
 
 // Device view of the chunk layout, passed by value to kernels.
 struct Layout {
@@ -46,11 +99,20 @@ struct DeviceStats {               // device-side counters, reset per affinities
     unsigned long long nonfinite;
     unsigned int max_herr_bits;    // float bits of max |H - ln perp| (non-negative floats order as ints)
     unsigned int bad_index;        // permutation entries outside [0, n) (skipped)
+    unsigned int timeouts;         // bounded device waits that ran out
+    unsigned int pad;
 };
 
 struct Optim {                     // optimiser settings
     float lr, momentum;
     int lr_mode, use_gains;
+};
+
+// Launch shape of the batched iteration kernel (chosen by the autotuner).
+struct IterTune {
+    int cluster = 1;               // blocks sharing one chunk (1, 2 or 4)
+    int group = 2;                 // consumer warps per tile (2 or 4)
+    int consumer_warps = 16;       // consumer warps per block (multiple of group, <= 16)
 };
 
 }  // namespace ptsne
@@ -71,6 +133,12 @@ struct ptsne_ctx {
     int32_t* d_order = nullptr;
     int64_t* d_dense_off = nullptr;    // n_chunks: sum of z^2 of the preceding chunks (P export)
     ptsne::TileDesc* d_tiles = nullptr;
+    // packed symmetric P (batched schedule)
+    int64_t ntiles2 = 0;               // stored 32 x 32 tiles over all chunks
+    int64_t* d_ptile_off = nullptr;    // n_chunks: first packed tile of each chunk
+    ptsne::TileDesc2* d_tiles2 = nullptr;
+    float* P2 = nullptr;               // ntiles2 x 1024 floats
+    ptsne::IterTune tune;
 
     // workspace
     float* Xg = nullptr;               // n x dp gathered X (permuted order)
@@ -134,8 +202,16 @@ cudaError_t launch_grad_rows(const ptsne_ctx* c, int64_t row_begin, int64_t row_
 cudaError_t launch_zreduce(const ptsne_ctx* c, int chunk_begin, int chunk_end, cudaStream_t s);
 cudaError_t launch_update(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, float* grad_perm,
                           cudaStream_t s);
-cudaError_t launch_grad_persistent(const ptsne_ctx* c, int iters, cudaStream_t s);
 cudaError_t launch_cost(const ptsne_ctx* c, double* out2, cudaStream_t s);
+cudaError_t launch_cost_final(const ptsne_ctx* c, double* out2, cudaStream_t s);
+
+// batched schedule (packed symmetric P)
+cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s);
+cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t s);
+cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc,
+                           double* cost_chunk, cudaStream_t s);
+int iterate_ring(int od, int64_t zmax, int slots); // 0 if the map does not fit in shared memory
+int iterate_smem_bytes(int od, int64_t zmax, int ring);
 
 Layout make_layout(const ptsne_ctx* c);
 
@@ -182,6 +258,35 @@ __device__ __forceinline__ float hw_lg2(float x) {
     float r;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Position update, Eq. 12 in the descent direction, with gains or Eq. 13:
+//   g = 4 (A - R / Z);  gains (+0.2 if sign(g) != sign(vel), else x0.8, >= 0.01)
+//   vel = momentum * vel - eta * gains * g;  y += vel.
+template <int OD>
+__device__ __forceinline__ void update_point(float* y, float* vel, float* gains, const float* A, const float* R,
+                                             float invZ, float eta, const Optim& opt, float* gout) {
+#pragma unroll
+    for (int k = 0; k < OD; ++k) {
+        const float g = 4.0f * (A[k] - R[k] * invZ);
+        if (gout) gout[k] = g;
+        float v = vel[k];
+        float gm = 1.0f;
+        if (opt.use_gains) {
+            float gn = ((g > 0.f) != (v > 0.f)) ? gains[k] + 0.2f : gains[k] * 0.8f;
+            gn = fmaxf(gn, 0.01f);
+            gains[k] = gn;
+            gm = gn;
+        }
+        v = opt.momentum * v - eta * gm * g;
+        vel[k] = v;
+        y[k] += v;
+    }
+}
+
+// Learning rate: fixed, or Eq. 13 from the extent [ymin, ymax] of the chunk's map.
+__device__ __forceinline__ float step_eta(const Optim& opt, int z, float ymin, float ymax) {
+    return opt.lr_mode == PTSNE_LR_PAPER ? logf((float)(z - 1)) * (ymax - ymin) * 0.5f : opt.lr;
 }
 #endif
 

@@ -15,7 +15,7 @@ from dataclasses import dataclass
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libptsne.so")
 
-OK, EINVAL, ENONFINITE, ENOMEM, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENONFINITE, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 WBISECT = 1
 LR_FIXED, LR_PAPER = 0, 1
 PREC_FP32, PREC_BF16_WINDOW = 0, 1
@@ -57,6 +57,7 @@ class Stats(C.Structure):
         ("window_pairs", C.c_int64),
         ("nonfinite_inputs", C.c_int64),
         ("bad_perm_entries", C.c_int64),
+        ("wait_timeouts", C.c_int64),
         ("max_abs_entropy_err", C.c_double),
         ("kernel_launches", C.c_int64),
         ("stage_ms", C.c_double * 7),
@@ -65,6 +66,14 @@ class Stats(C.Structure):
 
 
 STAGES = ("gather", "distances", "perplexity", "joint_p", "iterate", "pool", "cost")
+
+
+class Tuning(C.Structure):
+    _fields_ = [("cluster", C.c_int32), ("group", C.c_int32), ("consumer_warps", C.c_int32)]
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("tuning", Tuning), ("ms_per_iter", C.c_double)]
 
 
 _lib = None
@@ -93,6 +102,10 @@ def lib():
         L.ptsne_workspace_bytes.restype = C.c_size_t
         L.ptsne_set_profiling.argtypes = [vp, C.c_int]
         L.ptsne_reset_counters.argtypes = [vp]
+        L.ptsne_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.ptsne_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.ptsne_autotune.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_char_p, C.POINTER(TuneTrial), C.c_int32,
+                                     C.POINTER(C.c_int32), vp]
         _lib = L
     return _lib
 
@@ -203,3 +216,23 @@ class Context:
 
     def reset_counters(self):
         return self._check(lib().ptsne_reset_counters(self.h))
+
+    def set_tuning(self, cluster: int, group: int, consumer_warps: int):
+        t = Tuning(cluster, group, consumer_warps)
+        return self._check(lib().ptsne_set_tuning(self.h, C.byref(t)))
+
+    def tuning(self) -> tuple:
+        t = Tuning()
+        self._check(lib().ptsne_get_tuning(self.h, C.byref(t)))
+        return (t.cluster, t.group, t.consumer_warps)
+
+    def autotune(self, X, perm, Y, iters=3, cache_path=None, stream=None):
+        """Returns [((cluster, group, consumer_warps), ms_per_iter), ...] of the timed trials."""
+        cap = 64
+        arr = (TuneTrial * cap)()
+        n = C.c_int32(0)
+        cp = None if cache_path is None else os.fsencode(cache_path)
+        self._check(lib().ptsne_autotune(self.h, _ptr(X), _ptr(perm), _ptr(Y), iters, cp, arr, cap, C.byref(n),
+                                         _stream(stream)))
+        return [((t.tuning.cluster, t.tuning.group, t.tuning.consumer_warps), t.ms_per_iter)
+                for t in arr[:n.value]]
