@@ -43,7 +43,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", choices=["fp32", "bf16_window"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16_window"], default=None,
+                    help="distance precision (default: the workload's own)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 per-chunk comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
@@ -214,8 +215,9 @@ def bench_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = synth.workload(args.workload, epochs=PERM_POOL)
     sizes = np.diff(w.offsets)
+    precision = args.precision or w.precision
     cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
-                       momentum=w.momentum, precision=args.precision, schedule="batched")
+                       momentum=w.momentum, precision=precision, schedule="batched")
     ctx = ptsne.Context(cfg)
     Xd = torch.from_numpy(w.X).to(dev)
     perms = torch.from_numpy(w.perms).to(dev)
@@ -255,6 +257,10 @@ def bench_ours(args, rank, world, local_rank):
     launches = int(st.kernel_launches)
     stages = {name: (st.stage_ms[k] / st.stage_calls[k] if st.stage_calls[k] else None)
               for k, name in enumerate(ptsne.STAGES)}
+    # counters of the last epoch's affinities (reset by each search)
+    search = {"evals_per_row": st.bisect_evals / w.n, "fp64_rows": int(st.bisect_fp64_rows),
+              "failed_rows": int(st.bisect_failed_rows), "window_pairs": int(st.window_pairs),
+              "max_abs_entropy_err": st.max_abs_entropy_err}
     units = float(w.n * w.iters * args.steps)
     value, tmax = aggregate(units, secs, world)
     final_cost = cost[0].tolist()
@@ -317,12 +323,14 @@ def bench_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "n": w.n, "d": w.d, "chunks": int(len(sizes)),
                    "chunk_size_range": [int(sizes.min()), int(sizes.max())], "perplexity": w.perplexity,
                    "iters_per_epoch": w.iters, "out_dim": 2, "schedule": "batched persistent",
-                   "distances": args.precision, "step": "one epoch", "parallelism": f"replicas{world}",
+                   "distances": {"fp32": "fp32 direct differences",
+                                 "bf16_window": "bf16 tcgen05 Gram + fp32 window recompute"}[precision],
+                   "step": "one epoch", "parallelism": f"replicas{world}",
                    "tuning": {"cluster": tuning[0], "group": tuning[1], "consumer_warps": tuning[2]},
                    "autotune_ms_per_iter": {f"{t[0]}x{t[1]}x{t[2]}": round(ms, 4) for t, ms in trials},
                    "l2": "inputs larger than L2 (joint P %.1f GB per epoch)" % (4 * float((sizes ** 2).sum()) / 1e9)},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-        "plain_fp32": plain, "stages_ms": stages, "final_cost": {"avg_kl": final_cost[0], "avg_norm_cost": final_cost[1]},
+        "plain_fp32": plain, "stages_ms": stages, "perplexity_search": search, "final_cost": {"avg_kl": final_cost[0], "avg_norm_cost": final_cost[1]},
         "impl": "ours",
     }
     return out

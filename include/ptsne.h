@@ -110,6 +110,7 @@ typedef struct {
     int64_t kernel_launches;      /* kernels this context enqueued since creation / last reset */
     double stage_ms[PTSNE_N_STAGES];     /* profiling on: device time per stage of ptsne_run */
     int64_t stage_calls[PTSNE_N_STAGES]; /* profiling on: epochs accumulated into stage_ms */
+    int64_t bisect_evals;         /* entropy evaluations (FP32 and FP64) of the last search, all rows */
 } ptsne_stats;
 
 /* Turn on (1) or off (0) per-stage timing of ptsne_run: CUDA events are
@@ -180,6 +181,16 @@ const char* ptsne_last_error(const ptsne_ctx* ctx);
  * Async. */
 int ptsne_affinities(ptsne_ctx* ctx, const float* X_dev, const int32_t* perm_dev,
                      float* P_out_dev, float* beta_out_dev, void* stream);
+
+/* Pairwise squared distances of every chunk of the partition perm_dev, at
+ * the context's precision and before any window recompute: FP32 direct
+ * differences (PTSNE_PREC_FP32), or |x~_i|^2 + |x~_j|^2 - 2 x~_i . x~_j from
+ * the BF16-rounded rows on the tensor cores (PTSNE_PREC_BF16_WINDOW).
+ * D_out_dev: sum_c z_c^2 floats, dense z x z per chunk in chunk order (as
+ * P_out of ptsne_affinities; diagonal entries unspecified).  Does not change
+ * the affinities kept by the context.  Async. */
+int ptsne_distances(ptsne_ctx* ctx, const float* X_dev, const int32_t* perm_dev, float* D_out_dev,
+                    void* stream);
 
 /* One gradient iteration on every chunk of the partition of the last
  * ptsne_affinities call (Eq. 4, 6, 12/13).  Y_dev: n x out_dim float32 in

@@ -1,16 +1,16 @@
 // Input affinities of each chunk: per-row precision search (Eq. 1, Eq. 2) and
 // the symmetric joint P (Eq. 3, with n := z, the chunk size).
 //
-// Row search: one warp per row, the row staged once in shared memory as
+// Row search: a group of 128 threads per row holds the row in registers as
 // t_j = d_ij - m_i (m_i = min_{j!=i} d_ij; the shift cancels in Eq. 1).  The
 // entropy H(beta) = ln S + beta T1 / S with S = sum e_j, T1 = sum t_j e_j,
 // e_j = exp(-beta t_j), is non-increasing in beta, so the root of
 // H(beta) = ln(perplexity) is bracketed and found by bisection on beta,
 // accelerated by Newton steps in ln(beta) (dH/dln(beta) = -beta^2 Var_p(t))
-// whenever the Newton point falls inside the bracket.  Sums are FP32 per lane
-// (compensated once the root is near) and reduced across the warp in FP64.  A
-// row whose FP32 search stalls (bracket collapsed, or 64 evaluations) is
-// redone in FP64 by the same warp.
+// whenever the Newton point falls inside the bracket.  Sums are FP32 per
+// thread (compensated once the root is near) and combined across the group
+// with error-free two-sums.  A row whose FP32 search stalls (bracket
+// collapsed, or 64 evaluations) is redone in FP64 by the same group.
 #include <float.h>
 
 #include "ptsne_internal.cuh"
@@ -18,7 +18,7 @@
 namespace ptsne {
 
 namespace {
-constexpr int kBisectWarpsMax = 8;
+constexpr int kGroup = 128;            // threads per row
 constexpr float kBig = 1e37f;          // stands for "excluded" (diagonal, tail padding)
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTolFine = 1e-6f;      // |H - ln perp| (nats) accepted from the FP32 search
@@ -28,128 +28,157 @@ constexpr int kMaxEval32 = 64;
 constexpr int kMaxEval64 = 200;
 }  // namespace
 
-struct RowSums {
-    float S, T1, T2;
-};
+// s + v with the rounding error carried in c (error-free two-sum)
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v, float cv) {
+    const float t = s + v;
+    const float bb = t - s;
+    const float e = (s - (t - bb)) + (v - bb);
+    s = t;
+    c = c + cv + e;
+}
 
-// Warp sum of per-lane values s + c (c a compensation term), combining lanes
-// with an error-free two-sum at every level, so the result keeps FP32
-// accuracy independently of the tree.
-__device__ __forceinline__ float warp_sum_comp(float s, float c) {
+// Sum over the 128-thread group of per-thread (s, c) pairs, FP32 accuracy
+// independently of the order; every thread receives the same value.
+__device__ __forceinline__ float group_sum_comp(float s, float c, float (*red)[2]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float so = __shfl_xor_sync(0xffffffffu, s, o);
         const float co = __shfl_xor_sync(0xffffffffu, c, o);
-        const float t = s + so;
-        const float bb = t - s;
-        const float e = (s - (t - bb)) + (so - bb);
-        s = t;
-        c = c + co + e;
+        two_sum_add(s, c, so, co);
     }
-    return s + c;
+    if (lane == 0) { red[warp][0] = s; red[warp][1] = c; }
+    __syncthreads();
+    float a = red[0][0], ac = red[0][1];
+#pragma unroll
+    for (int w = 1; w < kGroup / 32; ++w) two_sum_add(a, ac, red[w][0], red[w][1]);
+    __syncthreads();
+    return a + ac;
+}
+__device__ __forceinline__ float group_sum(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float a = red[0];
+#pragma unroll
+    for (int w = 1; w < kGroup / 32; ++w) a += red[w];
+    __syncthreads();
+    return a;
+}
+__device__ __forceinline__ double group_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double a = red[0];
+#pragma unroll
+    for (int w = 1; w < kGroup / 32; ++w) a += red[w];
+    __syncthreads();
+    return a;
+}
+__device__ __forceinline__ float group_min(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_min(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float a = red[0];
+#pragma unroll
+    for (int w = 1; w < kGroup / 32; ++w) a = fminf(a, red[w]);
+    __syncthreads();
+    return a;
 }
 
-// S, T1, T2 of the staged row at precision beta.  `fine` selects compensated
-// (Kahan) per-lane sums and a compensated cross-lane reduction of S and T1.
-__device__ __forceinline__ RowSums row_sums(const float* __restrict__ row, int zr, float beta, bool fine) {
-    const int lane = threadIdx.x & 31;
+struct RowSums {
+    float S, T1, T2;
+};
+
+// S, T1, T2 of the row held in registers (excluded entries are kBig: e = 0).
+template <int VPT>
+__device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, bool fine, float (*red2)[2],
+                                            float* red) {
     const float b2 = beta * kLog2e;
-    const float4* r4 = reinterpret_cast<const float4*>(row);
-    const int nq = zr >> 2;  // zr is a multiple of 4 (tail padded with kBig)
-    float S = 0.f, T1 = 0.f, T2 = 0.f;
     RowSums out;
     if (!fine) {
-        float S2 = 0.f, T12 = 0.f, T22 = 0.f;
-        int q = lane;
-        for (; q + 32 < nq; q += 64) {
-            const float4 a = r4[q], b = r4[q + 32];
-            const float ta[4] = {a.x, a.y, a.z, a.w}, tb[4] = {b.x, b.y, b.z, b.w};
+        float S = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float ea = hw_ex2(-b2 * ta[e]), eb = hw_ex2(-b2 * tb[e]);
-                const float tea = ta[e] * ea, teb = tb[e] * eb;
-                S += ea; T1 += tea; T2 = fmaf(tea, ta[e], T2);
-                S2 += eb; T12 += teb; T22 = fmaf(teb, tb[e], T22);
-            }
+        for (int k = 0; k < VPT; ++k) {
+            const float e = hw_ex2(-b2 * t[k]);
+            const float te = t[k] * e;
+            S += e;
+            T1 += te;
+            T2 = fmaf(te, t[k], T2);
         }
-        for (; q < nq; q += 32) {
-            const float4 a = r4[q];
-            const float ta[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float ea = hw_ex2(-b2 * ta[e]);
-                const float tea = ta[e] * ea;
-                S += ea; T1 += tea; T2 = fmaf(tea, ta[e], T2);
-            }
-        }
-        out.S = warp_sum(S + S2);
-        out.T1 = warp_sum(T1 + T12);
-        out.T2 = warp_sum(T2 + T22);
+        out.S = group_sum(S, red);
+        out.T1 = group_sum(T1, red);
+        out.T2 = group_sum(T2, red);
         return out;
     }
-    float cS = 0.f, cT = 0.f;  // Kahan compensations (true sum = S - cS)
-    for (int q = lane; q < nq; q += 32) {
-        const float4 a = r4[q];
-        const float ta[4] = {a.x, a.y, a.z, a.w};
+    float S = 0.f, cS = 0.f, T1 = 0.f, cT = 0.f, T2 = 0.f;   // Kahan: true sum = S - cS
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float ea = hw_ex2(-b2 * ta[e]);
-            const float tea = ta[e] * ea;
-            float y = ea - cS, t = S + y;
-            cS = (t - S) - y; S = t;
-            y = tea - cT; t = T1 + y;
-            cT = (t - T1) - y; T1 = t;
-            T2 = fmaf(tea, ta[e], T2);
-        }
+    for (int k = 0; k < VPT; ++k) {
+        const float e = hw_ex2(-b2 * t[k]);
+        const float te = t[k] * e;
+        float y = e - cS, s2 = S + y;
+        cS = (s2 - S) - y; S = s2;
+        y = te - cT; s2 = T1 + y;
+        cT = (s2 - T1) - y; T1 = s2;
+        T2 = fmaf(te, t[k], T2);
     }
-    out.S = warp_sum_comp(S, -cS);
-    out.T1 = warp_sum_comp(T1, -cT);
-    out.T2 = warp_sum(T2);
+    out.S = group_sum_comp(S, -cS, red2);
+    out.T1 = group_sum_comp(T1, -cT, red2);
+    out.T2 = group_sum(T2, red);
     return out;
 }
 
-__global__ void __launch_bounds__(kBisectWarpsMax * 32)
-bisect_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, int ldmax, double ln_perp_d,
-              float* __restrict__ beta_out, float* __restrict__ m_out, float* __restrict__ S_out,
-              DeviceStats* st) {
-    extern __shared__ __align__(16) float smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float* row = smem + (size_t)warp * ldmax;
+// One row per 128-thread block; thread `tid` holds entries j = 4 tid + 512 q + e.
+template <int VPT>
+__global__ void __launch_bounds__(kGroup, VPT >= 48 ? 3 : (VPT >= 24 ? 4 : 6))
+bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, double ln_perp_d,
+                    float* __restrict__ beta_out, float* __restrict__ m_out, float* __restrict__ S_out,
+                    DeviceStats* st, const float* beta_init) {
+    __shared__ float red[kGroup / 32];
+    __shared__ float red2[kGroup / 32][2];
+    __shared__ double redd[kGroup / 32];
+    const int tid = threadIdx.x;
     const float ln_perp = (float)ln_perp_d;
-    for (int64_t r = r0 + (int64_t)blockIdx.x * nw + warp; r < r1; r += (int64_t)gridDim.x * nw) {
+    for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const int c = L.chunk_of_row[r];
         const int64_t off = L.off[c];
         const int z = (int)(L.off[c + 1] - off);
         const int i = (int)(r - off);
         const int ld = L.ld[c];
-        const int zr = (z + 3) & ~3;
         const float* src = D + L.moff[c] + (int64_t)i * ld;
 
-        // stage the row, excluding the diagonal and the padded tail
+        float t[VPT];
         float mn = FLT_MAX;
-        for (int j = lane * 4; j < zr; j += 128) {
-            float4 v = *reinterpret_cast<const float4*>(src + j);
-            float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < VPT / 4; ++q) {
+            const int j0 = 4 * tid + 4 * kGroup * q;
+            float4 v = make_float4(kBig, kBig, kBig, kBig);
+            if (j0 < z) v = *reinterpret_cast<const float4*>(src + j0);   // j0 + 3 < ld
+            const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                if (j + e >= z || j + e == i) vv[e] = kBig;
-                else mn = fminf(mn, vv[e]);
+                const int j = j0 + e;
+                const float x = (j < z && j != i) ? vv[e] : kBig;
+                t[4 * q + e] = x;
+                if (x < kBig) mn = fminf(mn, x);
             }
-            *reinterpret_cast<float4*>(row + j) = make_float4(vv[0], vv[1], vv[2], vv[3]);
         }
-        mn = warp_min(mn);
-        __syncwarp();
+        mn = group_min(mn, red);
         float tsum = 0.f;
-        for (int j = lane; j < zr; j += 32) {
-            const float v = row[j];
-            const float t = v >= kBig ? kBig : v - mn;
-            row[j] = t;
-            if (t < kBig) tsum += t;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            if (t[k] < kBig) {
+                t[k] -= mn;
+                tsum += t[k];
+            }
         }
-        tsum = warp_sum(tsum);
-        __syncwarp();
+        tsum = group_sum(tsum, red);
 
         float beta, S, herr;
+        int evals = 0;
         bool fp64 = false, failed = false;
         if (!(tsum > 0.f)) {
             // every neighbour at the same distance: p_{j|i} = 1/(z-1) for every beta
@@ -161,11 +190,16 @@ bisect_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, int
             float lo = 0.f, hi = INFINITY;
             beta = (float)(z - 1) / tsum;
             float f = INFINITY;
+            if (beta_init) {   // warm start: expected near the root, so evaluate compensated at once
+                const float b0 = beta_init[r];
+                if (b0 > 0.f && isfinite(b0)) { beta = b0; f = 0.f; }
+            }
             bool conv = false;
             RowSums s{};
             for (int it = 0; it < kMaxEval32; ++it) {
                 const bool fine = fabsf(f) < kTolCoarse;
-                s = row_sums(row, zr, beta, fine);
+                s = row_sums<VPT>(t, beta, fine, red2, red);
+                ++evals;
                 // H in nats; logf and the division are correctly rounded to ~1 ulp
                 f = (logf(s.S) + beta * (s.T1 / s.S)) - ln_perp;
                 // accept only from a compensated evaluation
@@ -184,18 +218,21 @@ bisect_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, int
             S = s.S;
             herr = fabsf(f);
             if (!conv) {
-                // FP64 redo of the same search on the staged (FP32) row
+                // FP64 redo of the same search on the held (FP32) row
                 fp64 = true;
                 double b = beta, blo = 0.0, bhi = INFINITY, fd = INFINITY, Sd = 0.0;
                 for (int it = 0; it < kMaxEval64; ++it) {
                     double sS = 0.0, sT1 = 0.0, sT2 = 0.0;
-                    for (int j = lane; j < zr; j += 32) {
-                        const float t = row[j];
-                        if (t >= kBig) continue;
-                        const double e = exp(-b * (double)t);
-                        sS += e; sT1 += (double)t * e; sT2 += (double)t * t * e;
+#pragma unroll
+                    for (int k = 0; k < VPT; ++k) {
+                        if (t[k] >= kBig) continue;
+                        const double e = exp(-b * (double)t[k]);
+                        sS += e; sT1 += (double)t[k] * e; sT2 += (double)t[k] * t[k] * e;
                     }
-                    sS = warp_sum(sS); sT1 = warp_sum(sT1); sT2 = warp_sum(sT2);
+                    sS = group_sum(sS, redd);
+                    sT1 = group_sum(sT1, redd);
+                    sT2 = group_sum(sT2, redd);
+                    ++evals;
                     Sd = sS;
                     fd = log(sS) + b * sT1 / sS - ln_perp_d;
                     if (fabs(fd) <= kTol64) break;
@@ -215,27 +252,30 @@ bisect_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, int
                 failed = herr > kTolFine;
             }
         }
-        if (lane == 0) {
+        if (tid == 0) {
             beta_out[r] = beta;
             m_out[r] = mn;
             S_out[r] = S;
             if (fp64) atomicAdd(&st->fp64_rows, 1ull);
             if (failed) atomicAdd(&st->failed_rows, 1ull);
+            atomicAdd(&st->bisect_evals, (unsigned long long)evals);
             atomicMax(&st->max_herr_bits, __float_as_uint(herr));
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
-// Joint P of Eq. 3 on one 64 x 64 upper tile (I <= J), written to the tile and
-// its transpose.  D is symmetric, so d_ji is read from the same tile:
-//   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ij - m_j)) / S_j) / (2z).
+// Joint P of Eq. 3 on one 64 x 64 upper tile (I <= J) of the dense layout,
+// written to the tile and its transpose; the (J, I) tile of D is staged
+// transposed in shared memory so that each conditional uses its own row:
+//   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ji - m_j)) / S_j) / (2z).
 // The padded columns [z, ld) of every row are set to 0.
 __global__ void __launch_bounds__(256)
 psym_kernel(const float* __restrict__ D, float* __restrict__ P, Layout L, const TileDesc* __restrict__ tiles,
             int64_t t0, const float* __restrict__ beta, const float* __restrict__ mrow,
             const float* __restrict__ Srow) {
     __shared__ float pb[2][kTile], pm[2][kTile], ps[2][kTile];
+    __shared__ float dT[kTile][kTile + 1];   // dT[jj][ii] = d_{j i}
     const TileDesc td = tiles[t0 + blockIdx.x];
     const int c = td.chunk;
     const int64_t off = L.off[c];
@@ -254,9 +294,17 @@ psym_kernel(const float* __restrict__ D, float* __restrict__ P, Layout L, const 
             pb[side][k] = 0.f; pm[side][k] = 0.f; ps[side][k] = 0.f;
         }
     }
+    const float* dbase = D + L.moff[c];
+    // rows j0.. of D at columns i0..: coalesced float4 reads
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int jj = ty * 4 + r, j = j0 + jj;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < z) v = *reinterpret_cast<const float4*>(dbase + (int64_t)j * ld + i0 + tx * 4);
+        dT[jj][tx * 4 + 0] = v.x; dT[jj][tx * 4 + 1] = v.y; dT[jj][tx * 4 + 2] = v.z; dT[jj][tx * 4 + 3] = v.w;
+    }
     __syncthreads();
     const float inv2z = 1.0f / (2.0f * (float)z);
-    const float* dbase = D + L.moff[c];
     float* pbase = P + L.moff[c];
     float out[4][4];
 #pragma unroll
@@ -270,10 +318,10 @@ psym_kernel(const float* __restrict__ D, float* __restrict__ P, Layout L, const 
             const int lj = tx * 4 + q, j = j0 + lj;
             float p = 0.f;
             if (i < z && j < z && i != j) {
-                // explicitly rounded products and sum: no FMA contraction, so the
-                // (i, j) and (j, i) threads of a diagonal tile round identically
+                // explicitly rounded products and sum: no FMA contraction, so the two
+                // halves of a diagonal tile round identically
                 const float cij = __fmul_rn(hw_ex2(-pb[0][li] * (d4[q] - pm[0][li])), ps[0][li]);
-                const float cji = __fmul_rn(hw_ex2(-pb[1][lj] * (d4[q] - pm[1][lj])), ps[1][lj]);
+                const float cji = __fmul_rn(hw_ex2(-pb[1][lj] * (dT[lj][li] - pm[1][lj])), ps[1][lj]);
                 p = __fmul_rn(__fadd_rn(cij, cji), inv2z);
             }
             out[r][q] = p;
@@ -293,20 +341,26 @@ psym_kernel(const float* __restrict__ D, float* __restrict__ P, Layout L, const 
     }
 }
 
-cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s) {
-    const int64_t rows = row_end - row_begin;
-    if (rows <= 0) return cudaSuccess;
-    const int ldmax = (int)((c->zmax + kTile - 1) / kTile * kTile);
-    // one staged row per warp: as many warps as 227 KB of shared memory holds (<= 8)
-    int warps = (int)((227 * 1024) / ((size_t)ldmax * sizeof(float)));
-    warps = warps > kBisectWarpsMax ? kBisectWarpsMax : (warps < 1 ? 1 : warps);
-    const size_t smem = (size_t)warps * ldmax * sizeof(float);
-    cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int64_t blocks = (rows + warps - 1) / warps;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    bisect_kernel<<<(unsigned)blocks, warps * 32, smem, s>>>(
-        c->D, make_layout(c), row_begin, row_end, ldmax, log(c->p.perplexity), c->beta, c->mrow,
-        c->Srow, c->dstats);
+template <int VPT>
+static void launch_group(const ptsne_ctx* c, int64_t r0, int64_t r1, cudaStream_t s, const float* beta_init) {
+    int64_t blocks = r1 - r0;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    bisect_group_kernel<VPT><<<(unsigned)blocks, kGroup, 0, s>>>(c->D, make_layout(c), r0, r1,
+                                                                   log(c->p.perplexity), c->beta, c->mrow, c->Srow,
+                                                                   c->dstats, beta_init);
+}
+
+cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
+                          const float* beta_init) {
+    if (row_end <= row_begin) return cudaSuccess;
+    const int64_t per = (c->zmax + 4 * kGroup - 1) / (4 * kGroup) * 4;   // values per thread
+    if (per <= 8) launch_group<8>(c, row_begin, row_end, s, beta_init);
+    else if (per <= 16) launch_group<16>(c, row_begin, row_end, s, beta_init);
+    else if (per <= 24) launch_group<24>(c, row_begin, row_end, s, beta_init);
+    else if (per <= 32) launch_group<32>(c, row_begin, row_end, s, beta_init);
+    else if (per <= 40) launch_group<40>(c, row_begin, row_end, s, beta_init);
+    else if (per <= 48) launch_group<48>(c, row_begin, row_end, s, beta_init);
+    else launch_group<64>(c, row_begin, row_end, s, beta_init);
     return launched(c, 1);
 }
 

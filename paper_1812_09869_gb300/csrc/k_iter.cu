@@ -616,10 +616,10 @@ __global__ void __launch_bounds__(544, 1) iterate_kernel(IterArgs A) {
 
 // ---------------------------------------------------------------- packed P assembly and export
 
-// Joint P (Eq. 3) of one stored 32 x 32 tile, written packed and swizzled.
-// D is symmetric (z x ld rows), so d_ji is d_ij:
-//   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ij - m_j)) / S_j) / (2z),
-// zero on the diagonal and outside the chunk.
+// Joint P (Eq. 3) of one stored 32 x 32 tile, written packed and swizzled:
+//   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ji - m_j)) / S_j) / (2z),
+// zero on the diagonal and outside the chunk.  D need not be symmetric: after
+// the window recompute each row holds its own exact entries.
 __global__ void __launch_bounds__(256)
 psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
                    const TileDesc2* __restrict__ tiles, int64_t t0, const float* __restrict__ beta,
@@ -633,6 +633,16 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
     const int tid = threadIdx.x, r = tid >> 3, c4 = tid & 7;
     const int i = td.a * kPT + r;
     const int j0 = td.b * kPT + c4 * 4;
+    // the (b, a) block of D, transposed: dT[jj][ii] = d_{j i}, so that each
+    // conditional of Eq. 3 is taken from its own row of D
+    __shared__ float dT[kPT][kPT + 1];
+    {
+        const int jr = td.b * kPT + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jr < z) v = *reinterpret_cast<const float4*>(D + L.moff[c] + (int64_t)jr * ld + td.a * kPT + c4 * 4);
+        dT[r][c4 * 4 + 0] = v.x; dT[r][c4 * 4 + 1] = v.y; dT[r][c4 * 4 + 2] = v.z; dT[r][c4 * 4 + 3] = v.w;
+    }
+    __syncthreads();
     float out[4] = {0.f, 0.f, 0.f, 0.f};
     if (i < z) {
         const float4 dv = *reinterpret_cast<const float4*>(D + L.moff[c] + (int64_t)i * ld + j0);
@@ -644,8 +654,9 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
             const int j = j0 + e;
             if (j < z && j != i) {
                 const float bj = beta[off + j] * kLog2e, mj = mrow[off + j], sj = 1.0f / Srow[off + j];
+                // explicitly rounded: the two halves of a diagonal tile round identically
                 const float cij = __fmul_rn(hw_ex2(-bi * (d4[e] - mi)), si);
-                const float cji = __fmul_rn(hw_ex2(-bj * (d4[e] - mj)), sj);
+                const float cji = __fmul_rn(hw_ex2(-bj * (dT[c4 * 4 + e][r] - mj)), sj);
                 out[e] = __fmul_rn(__fadd_rn(cij, cji), inv2z);
             }
         }

@@ -121,10 +121,14 @@ cudaError_t launch_reset_optim(const ptsne_ctx* c, cudaStream_t s) {
     return launched(c, 1);
 }
 
-cudaError_t launch_export_P(const ptsne_ctx* c, float* P_out, cudaStream_t s) {
+cudaError_t launch_export_dense(const ptsne_ctx* c, const float* src, float* out, cudaStream_t s) {
     dim3 grid(64, c->p.n_chunks);
-    export_P_kernel<<<grid, 256, 0, s>>>(c->P, make_layout(c), c->d_dense_off, P_out);
+    export_P_kernel<<<grid, 256, 0, s>>>(src, make_layout(c), c->d_dense_off, out);
     return launched(c, 1);
+}
+
+cudaError_t launch_export_P(const ptsne_ctx* c, float* P_out, cudaStream_t s) {
+    return launch_export_dense(c, c->P, P_out, s);
 }
 
 }  // namespace ptsne

@@ -70,7 +70,7 @@ void free_all(ptsne_ctx* c) {
                     c->beta,   c->mrow,    c->Srow,   c->Yc,             c->vel,     c->gains,
                     c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
-                    c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2};
+                    c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -162,6 +162,19 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     c->tile_start[nc] = t;
     c->mtotal = m;
     c->ntiles = t;
+    // BF16 Gram matrix: 128 x 128 upper tiles of each chunk
+    std::vector<TileDesc> tiles128;
+    if (p.precision == PTSNE_PREC_BF16_WINDOW) {
+        c->tile_start128.resize(nc + 1);
+        for (int k = 0; k < nc; ++k) {
+            c->tile_start128[k] = (int64_t)tiles128.size();
+            const int nb = (int)((c->off[k + 1] - c->off[k] + 127) / 128);
+            for (int I = 0; I < nb; ++I)
+                for (int J = I; J < nb; ++J) tiles128.push_back(TileDesc{k, (int16_t)I, (int16_t)J});
+        }
+        c->tile_start128[nc] = (int64_t)tiles128.size();
+        c->ntiles128 = (int64_t)tiles128.size();
+    }
     // packed symmetric P: 32 x 32 tiles of each chunk in tournament order
     std::vector<TileDesc2> tiles2;
     std::vector<int64_t> ptoff(nc);
@@ -214,6 +227,8 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (p.precision == PTSNE_PREC_BF16_WINDOW) {
         AL(c->Xb, n * c->kp);
         AL(c->xnorm, n);
+        AL(c->d_tiles128, c->ntiles128);
+        AL(c->maxnorm, 1);
     }
     AL(c->D, m);
     if (p.schedule == PTSNE_SCHED_BATCHED) {
@@ -251,6 +266,8 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (e == cudaSuccess) e = up(c->d_order, c->order.data(), sizeof(int32_t) * nc);
     if (e == cudaSuccess) e = up(c->d_dense_off, dense.data(), sizeof(int64_t) * nc);
     if (e == cudaSuccess) e = up(c->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size());
+    if (e == cudaSuccess && c->ntiles128)
+        e = up(c->d_tiles128, tiles128.data(), sizeof(TileDesc) * tiles128.size());
     if (e == cudaSuccess && c->ntiles2) {
         e = up(c->d_ptile_off, ptoff.data(), sizeof(int64_t) * nc);
         if (e == cudaSuccess) e = up(c->d_tiles2, tiles2.data(), sizeof(TileDesc2) * tiles2.size());
@@ -286,23 +303,34 @@ static void mark(ptsne_ctx* c, int k, cudaStream_t s) {
 static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s, bool reset_stats,
                            const float* Y_run) {
     if (reset_stats) CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
-    if (c->p.precision == PTSNE_PREC_BF16_WINDOW)
-        return fail(c, PTSNE_EINVAL, "precision %s not available in this build%lld", "BF16_WINDOW", 0);
+    const bool mixed = c->p.precision == PTSNE_PREC_BF16_WINDOW;
     mark(c, PTSNE_STAGE_GATHER, s);
     CK(launch_gather(c, X, perm, s));
+    if (mixed) CK(launch_gather_bf16(c, s));
     if (Y_run) CK(launch_gather_y(c, Y_run, perm, c->Yc, s));
     CK(launch_reset_optim(c, s));
     mark(c, PTSNE_STAGE_DISTANCES, s);
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
-        CK(launch_dist_fp32(c, 0, c->ntiles, s));
+        if (mixed) CK(launch_dist_bf16(c, 0, c->ntiles128, s));
+        else CK(launch_dist_fp32(c, 0, c->ntiles, s));
         mark(c, PTSNE_STAGE_PERPLEXITY, s);
         CK(launch_bisect(c, 0, c->p.n, s));
+        if (mixed) {
+            // FP32 distances inside each row's window, then the search again from beta~
+            CK(launch_window_recompute(c, 0, c->p.n, s));
+            CK(launch_bisect(c, 0, c->p.n, s, c->beta));
+        }
         mark(c, PTSNE_STAGE_JOINT_P, s);
         CK(launch_psym_packed(c, s));
     } else {
         for (int k = 0; k < c->p.n_chunks; ++k) {
-            CK(launch_dist_fp32(c, c->tile_start[k], c->tile_start[k + 1], s));
+            if (mixed) CK(launch_dist_bf16(c, c->tile_start128[k], c->tile_start128[k + 1], s));
+            else CK(launch_dist_fp32(c, c->tile_start[k], c->tile_start[k + 1], s));
             CK(launch_bisect(c, c->off[k], c->off[k + 1], s));
+            if (mixed) {
+                CK(launch_window_recompute(c, c->off[k], c->off[k + 1], s));
+                CK(launch_bisect(c, c->off[k], c->off[k + 1], s, c->beta));
+            }
             CK(launch_psym(c, c->tile_start[k], c->tile_start[k + 1], s));
         }
         mark(c, PTSNE_STAGE_PERPLEXITY, s);
@@ -321,6 +349,21 @@ int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P
     if (st != PTSNE_OK) return st;
     if (P_out) CK(c->P2 ? launch_export_packed(c, P_out, s) : launch_export_P(c, P_out, s));
     if (beta_out) CK(launch_scatter_rows(c, c->beta, perm, 1, beta_out, s));
+    return PTSNE_OK;
+}
+
+int ptsne_distances(ptsne_ctx* c, const float* X, const int32_t* perm, float* D_out, void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!X || !perm || !D_out) return fail(c, PTSNE_EINVAL, "X, perm and D_out must be device pointers%s%lld");
+    cudaStream_t s = as_stream(stream);
+    CK(launch_gather(c, X, perm, s));
+    if (c->p.precision == PTSNE_PREC_BF16_WINDOW) {
+        CK(launch_gather_bf16(c, s));
+        CK(launch_dist_bf16(c, 0, c->ntiles128, s));
+    } else {
+        CK(launch_dist_fp32(c, 0, c->ntiles, s));
+    }
+    CK(launch_export_dense(c, c->D, D_out, s));
     return PTSNE_OK;
 }
 
@@ -470,6 +513,7 @@ int ptsne_get_stats(ptsne_ctx* c, ptsne_stats* out, void* stream) {
     out->nonfinite_inputs = (int64_t)h.nonfinite;
     out->bad_perm_entries = (int64_t)h.bad_index;
     out->wait_timeouts = (int64_t)h.timeouts;
+    out->bisect_evals = (int64_t)h.bisect_evals;
     float herr;
     memcpy(&herr, &h.max_herr_bits, sizeof herr);
     out->max_abs_entropy_err = herr;

@@ -97,6 +97,7 @@ struct DeviceStats {               // device-side counters, reset per affinities
     unsigned long long failed_rows;
     unsigned long long window_pairs;
     unsigned long long nonfinite;
+    unsigned long long bisect_evals;  // entropy evaluations, all rows
     unsigned int max_herr_bits;    // float bits of max |H - ln perp| (non-negative floats order as ints)
     unsigned int bad_index;        // permutation entries outside [0, n) (skipped)
     unsigned int timeouts;         // bounded device waits that ran out
@@ -137,8 +138,13 @@ struct ptsne_ctx {
     int64_t ntiles2 = 0;               // stored 32 x 32 tiles over all chunks
     int64_t* d_ptile_off = nullptr;    // n_chunks: first packed tile of each chunk
     ptsne::TileDesc2* d_tiles2 = nullptr;
-    float* P2 = nullptr;               // ntiles2 x 1024 floats
+    float* P2 = nullptr;               // ntiles2 x kPTileStride floats
     ptsne::IterTune tune;
+    // BF16 Gram matrix (PTSNE_PREC_BF16_WINDOW): 128 x 128 upper tiles per chunk
+    int64_t ntiles128 = 0;
+    std::vector<int64_t> tile_start128;
+    ptsne::TileDesc* d_tiles128 = nullptr;
+    unsigned int* maxnorm = nullptr;   // largest |x~| (float bits), for the window bound
 
     // workspace
     float* Xg = nullptr;               // n x dp gathered X (permuted order)
@@ -191,11 +197,16 @@ cudaError_t launch_scatter_rows(const ptsne_ctx* c, const float* src, const int3
                                 float* dst, cudaStream_t s);
 cudaError_t launch_reset_optim(const ptsne_ctx* c, cudaStream_t s);
 cudaError_t launch_export_P(const ptsne_ctx* c, float* P_out, cudaStream_t s);
+// z x ld chunk matrices (src) -> dense z x z per chunk, chunks concatenated
+cudaError_t launch_export_dense(const ptsne_ctx* c, const float* src, float* out, cudaStream_t s);
 
 cudaError_t launch_dist_fp32(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
-cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
+// beta_init (optional): start each row's search from this beta instead of 1 / mean(d - m)
+cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
+                          const float* beta_init = nullptr);
+cudaError_t launch_gather_bf16(const ptsne_ctx* c, cudaStream_t s);
 cudaError_t launch_psym(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 
 cudaError_t launch_grad_rows(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);

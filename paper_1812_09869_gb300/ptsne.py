@@ -62,6 +62,7 @@ class Stats(C.Structure):
         ("kernel_launches", C.c_int64),
         ("stage_ms", C.c_double * 7),
         ("stage_calls", C.c_int64 * 7),
+        ("bisect_evals", C.c_int64),
     ]
 
 
@@ -94,6 +95,7 @@ def lib():
         L.ptsne_last_error.restype = C.c_char_p
         L.ptsne_affinities.argtypes = [vp, vp, vp, vp, vp, vp]
         L.ptsne_step.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.ptsne_distances.argtypes = [vp, vp, vp, vp, vp]
         L.ptsne_cost.argtypes = [vp, vp, vp, vp, vp]
         L.ptsne_run.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
         L.ptsne_run_host.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
@@ -186,6 +188,9 @@ class Context:
     def affinities(self, X, perm, P_out=None, beta_out=None, stream=None):
         return self._check(lib().ptsne_affinities(self.h, _ptr(X), _ptr(perm), _ptr(P_out), _ptr(beta_out),
                                                   _stream(stream)))
+
+    def distances(self, X, perm, D_out, stream=None):
+        return self._check(lib().ptsne_distances(self.h, _ptr(X), _ptr(perm), _ptr(D_out), _stream(stream)))
 
     def step(self, perm, Y, grad_out=None, Z_out=None, stream=None):
         return self._check(lib().ptsne_step(self.h, _ptr(perm), _ptr(Y), _ptr(grad_out), _ptr(Z_out),
