@@ -167,7 +167,8 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* params);
 void ptsne_destroy(ptsne_ctx* ctx);
 
 /* Text of the last error recorded on ctx (never NULL).  With ctx == NULL:
- * the reason of the last failed ptsne_create on the calling thread. */
+ * the reason of the last failed ptsne_create or ptsne_gradient_static on the
+ * calling thread. */
 const char* ptsne_last_error(const ptsne_ctx* ctx);
 
 /* Input affinities for the partition perm_dev (Eq. 1-3 per chunk, n := z).
@@ -228,6 +229,31 @@ int ptsne_get_stats(ptsne_ctx* ctx, ptsne_stats* out, void* stream);
 
 /* Bytes of device workspace held by ctx. */
 size_t ptsne_workspace_bytes(const ptsne_ctx* ctx);
+
+/* Largest chunk ptsne_gradient_static accepts. */
+#define PTSNE_STATIC_MAX_ROWS 32768
+
+/* The exact gradient of one chunk WITHOUT any device allocation and without a
+ * context.  The paper has no counterpart: it exists for callers that cannot
+ * call cudaMalloc (a host framework that owns the whole device memory pool,
+ * code running under an active stream capture in global or thread-local
+ * mode, callers that must not block on an allocation).
+ *   P_dev:    z rows of ld floats (ld >= z), the symmetric joint P of the
+ *             chunk (e.g. one block of ptsne_affinities' P_out, ld = z);
+ *             the diagonal is ignored.
+ *   Y_dev:    z x out_dim floats, the chunk's map in the same row order.
+ *   grad_out_dev: z x out_dim floats, dC/dy_i = 4 (A_i - R_i / Z) as ptsne_step
+ *             computes it.
+ *   Z_out_dev (optional): 1 double, Z of the chunk.
+ * z in [2, PTSNE_STATIC_MAX_ROWS], out_dim 2 or 3; anything else returns
+ * PTSNE_EINVAL before any work, with the reason in ptsne_last_error(NULL).
+ * Scratch (1 MiB of per-row sums) is a fixed array in the library's device
+ * memory, shared by every call on a device: calls that can overlap on the GPU
+ * race on it; calls ordered on one stream are safe, and nothing needs
+ * clearing between them.  The first call on each device looks up the array's
+ * address and may load the module: make it before any stream capture.  Async. */
+int ptsne_gradient_static(const float* P_dev, int64_t ld, const float* Y_dev, int32_t z, int32_t out_dim,
+                          float* grad_out_dev, double* Z_out_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -84,6 +84,8 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+void ptsne::set_last_error(const char* msg) { g_create_err = msg; }
+
 extern "C" {
 
 const char* ptsne_last_error(const ptsne_ctx* ctx) {

@@ -92,6 +92,9 @@ struct Layout {
     const int32_t* order;          // n_chunks: chunks by decreasing size (work-queue order)
 };
 
+// Records the message that ptsne_last_error(NULL) returns on the calling thread.
+void set_last_error(const char* msg);
+
 struct DeviceStats {               // device-side counters, reset per affinities call
     unsigned long long fp64_rows;
     unsigned long long failed_rows;

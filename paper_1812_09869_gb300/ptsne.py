@@ -108,6 +108,7 @@ def lib():
         L.ptsne_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.ptsne_autotune.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_char_p, C.POINTER(TuneTrial), C.c_int32,
                                      C.POINTER(C.c_int32), vp]
+        L.ptsne_gradient_static.argtypes = [vp, C.c_int64, vp, C.c_int32, C.c_int32, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -241,3 +242,15 @@ class Context:
                                          _stream(stream)))
         return [((t.tuning.cluster, t.tuning.group, t.tuning.consumer_warps), t.ms_per_iter)
                 for t in arr[:n.value]]
+
+
+def gradient_static(P, Y, grad_out, Z_out=None, ld=None, stream=None):
+    """ptsne_gradient_static: the gradient of one chunk with no device
+    allocation (fixed library scratch).  P: z x ld float32, Y and grad_out:
+    z x out_dim float32, Z_out: optional 1-element float64 tensor."""
+    z, od = int(Y.shape[0]), int(Y.shape[1])
+    ld = int(P.shape[-1]) if ld is None else int(ld)
+    rc = lib().ptsne_gradient_static(_ptr(P), ld, _ptr(Y), z, od, _ptr(grad_out), _ptr(Z_out), _stream(stream))
+    if rc != OK:
+        raise PtsneError(rc, lib().ptsne_last_error(None).decode())
+    return rc
