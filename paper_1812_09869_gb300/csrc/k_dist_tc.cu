@@ -16,7 +16,9 @@
 // so j can carry weight exp(-beta (d_ij - m_i)) >= exp(-T) only if
 //   d~_ij - E(d~_ij) <= m~_i + E(m~_i) + T / beta~_i.
 // Those distances are recomputed in FP32 by direct differences and written to
-// (i, j) and (j, i); the perplexity search then runs again from beta~.
+// row i only (each row owns its entries; the joint-P assembly reads d_ij for
+// p_{j|i} and d_ji for p_{i|j}); the perplexity search then runs again from
+// beta~.
 #include <float.h>
 
 #include "ptsne_internal.cuh"

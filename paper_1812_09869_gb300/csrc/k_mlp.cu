@@ -1,0 +1,852 @@
+// Learned out-of-sample mapper: MLP d_in -> 256 -> 256 -> out_dim with exact
+// GELU, BF16 weights and activations, FP32 accumulation on the tensor cores.
+// No counterpart in the paper (it maps new points by re-running ptSNE); the
+// network is trained on ptSNE's own maps and used to place held-out points
+// and to warm-start ptsne_run.
+//
+// One GEMM kernel serves every contraction: C = A B^T with A (M x K) and
+// B (N x K) BF16, both K-major, staged by TMA (128-byte swizzle, 3-stage ring),
+// one elected thread issuing tcgen05.mma (M = 128, N = NT, K = 16) into an
+// FP32 accumulator of NT columns in tensor memory, and four warps reading it
+// back (tcgen05.ld, one accumulator row per thread) for a fused epilogue:
+//
+//   FWD        u = acc + b; U = u (FP32), H = g(u) (BF16), H^T (BF16)
+//   HEAD_INFER h = g(acc + b2); y = W3 h + b3 per row (the whole hidden row is
+//              in the thread's accumulator lane); Y = y * std + mean
+//   HEAD_TRAIN as HEAD_INFER, then r = (y - t) / B, loss += |y - t|^2 / (2B),
+//              dL/dW3 += r h^T, dL/db3 += r, and, re-reading the accumulator,
+//              dA2 = (W3^T r) * g'(u2) (BF16, and transposed), dL/db2 += dA2
+//   DGELU      dA1 = acc * g'(U1) (transposed, BF16), dL/db1 += dA1
+//   ATOMIC     C += acc (FP32 atomics; split-K weight gradients)
+//
+// A training step (batch B rows):
+//   gather    X[rows] -> Xb (B x 64, BF16, zero-padded), Xb^T; T[rows] -> t
+//   FWD       Xb  x W1b^T   -> U1, H1, H1^T                (K = 64)
+//   HEAD_TRAIN H1 x W2b^T   -> loss, dW3, db3, dA2, dA2^T, db2  (K = 256)
+//   ATOMIC    dA2^T x H1^T  -> dW2 (256 x 256)              (K = B, split)
+//   DGELU     dA2 x W2^T    -> dA1^T, db1                   (K = 256)
+//   ATOMIC    dA1^T x Xb^T  -> dW1 (256 x d_in)             (K = B, split)
+//   AdamW on the FP32 master parameters, rewriting the BF16 copies.
+#include <float.h>
+#include <math.h>
+
+#include <mutex>
+#include <string>
+
+#include "ptsne_internal.cuh"
+#include "ptsne_mlp.h"
+#include "tc_common.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace ptsne {
+namespace mlp {
+
+constexpr int kH = PTSNE_MLP_HIDDEN;   // 256
+constexpr int kKin = 64;               // input features padded to one K block
+constexpr int kStages = 3;
+
+enum Epi { EPI_FWD = 0, EPI_HEAD_INFER = 1, EPI_HEAD_TRAIN = 2, EPI_DGELU = 3, EPI_ATOMIC = 4 };
+
+struct GemmArgs {
+    int M;               // valid rows of A (rows >= M are computed but not stored)
+    int kblocks;         // K / 64
+    int kb_per_split;    // K blocks per CTA along gridDim.y
+    const float* bias;   // FWD, HEAD_*: [NT]
+    float* U;            // FWD: pre-activation [M][NT] (optional)
+    bf16* H;             // FWD: activation [M][NT] (optional); HEAD_TRAIN: dA2 [M][NT]
+    bf16* HT;            // FWD: activation^T; HEAD_TRAIN: dA2^T; DGELU: dA1^T  ([NT][ldT])
+    int64_t ldT;
+    const float* Uin;    // DGELU: pre-activation [M][NT]
+    float* colsum;       // DGELU: db1; HEAD_TRAIN: db2  ([NT])
+    float* C;            // ATOMIC: [M][ldc]
+    int ldc, ncols;
+    const bf16* W3;      // HEAD_*: [OD][NT]
+    const float* b3;     // HEAD_*: [OD]
+    const float* T;      // HEAD_TRAIN: standardised targets [M][OD]
+    float invB;          // HEAD_TRAIN
+    double* loss;        // HEAD_TRAIN: accumulates sum |y - t|^2 / (2B)
+    float* gW3;          // HEAD_TRAIN: [OD][NT]
+    float* gb3;          // HEAD_TRAIN: [OD]
+    const double* scaler;   // HEAD_INFER: mean[OD], std[OD]
+    float* Y;            // HEAD_INFER: [M][OD]
+    unsigned int* timeouts;
+};
+
+__device__ __forceinline__ float gelu(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float u) {
+    return 0.5f * (1.0f + erff(u * 0.70710678118654752f)) + u * expf(-0.5f * u * u) * 0.39894228040143268f;
+}
+
+// v[32] on each lane -> on lane l, the sum over the warp's lanes of v[l]
+// (recursive halving: 31 shuffles for 32 columns).  Destroys v.
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ void store_bf16x32(bf16* dst, const float (&v)[32]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint4 pk;
+        uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+            w[e] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        reinterpret_cast<uint4*>(dst)[q] = pk;
+    }
+}
+
+template <int NT, int EPI, int OD>
+__global__ void __launch_bounds__(128, 1)
+mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a) {
+    constexpr int kBRows = NT < 128 ? 128 : NT;
+    constexpr uint32_t kABytes = tc::kTileBytes;
+    constexpr uint32_t kBBytes = (uint32_t)kBRows * 128u;
+    constexpr uint32_t kStageBytes = kABytes + kBBytes;
+    constexpr bool kHead = EPI == EPI_HEAD_INFER || EPI == EPI_HEAD_TRAIN;
+    extern __shared__ unsigned char dsmem[];
+    __shared__ uint64_t full_bar[kStages], done_bar[kStages];
+    __shared__ uint32_t tmem_base;
+    __shared__ float sb[NT];
+    __shared__ float sw3[kHead ? OD : 1][NT];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t sbase = (tc::smem_addr(dsmem) + 1023u) & ~1023u;
+    const int m0 = blockIdx.x * 128;
+    const int kb0 = blockIdx.y * a.kb_per_split;
+    const int kb1 = min(kb0 + a.kb_per_split, a.kblocks);
+    const int nkb = kb1 - kb0;   // >= 1 (the launcher sizes gridDim.y)
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem_base), NT < 32 ? 32 : NT);
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(tc::smem_addr(&full_bar[s]), 1);
+            tc::mbar_init(tc::smem_addr(&done_bar[s]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (EPI == EPI_FWD || kHead)
+        for (int n = tid; n < NT; n += 128) sb[n] = a.bias[n];
+    if (kHead)
+        for (int idx = tid; idx < OD * NT; idx += 128) sw3[idx / NT][idx % NT] = __bfloat162float(a.W3[idx]);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(128, NT);
+        bool ok = true;
+        auto issue = [&](int i) {
+            const int s = i % kStages;
+            const uint32_t fb = tc::smem_addr(&full_bar[s]);
+            const uint32_t sa = sbase + (uint32_t)s * kStageBytes, sbb = sa + kABytes;
+            tc::mbar_expect_tx(fb, kStageBytes);
+            const int col = (kb0 + i) * tc::kTileK;
+            tc::tma_load_2d(sa, &tmA, col, m0, fb);
+#pragma unroll
+            for (int r = 0; r < kBRows / 128; ++r) tc::tma_load_2d(sbb + (uint32_t)r * tc::kTileBytes, &tmB, col, r * 128, fb);
+        };
+        for (int i = 0; i < kStages && i < nkb; ++i) issue(i);
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % kStages;
+            const uint32_t par = (uint32_t)(i / kStages) & 1u;
+            ok = tc::mbar_wait(tc::smem_addr(&full_bar[s]), par) && ok;
+            tc::tc_fence_after();
+            const uint32_t sa = sbase + (uint32_t)s * kStageBytes, sbb = sa + kABytes;
+            const uint64_t da = tc::sw128_desc(sa), db = tc::sw128_desc(sbb);
+#pragma unroll
+            for (int k16 = 0; k16 < tc::kTileK / 16; ++k16)
+                tc::mma_bf16(tmem, da + 2 * k16, db + 2 * k16, idesc, (i > 0 || k16 > 0) ? 1u : 0u);
+            tc::mma_commit(tc::smem_addr(&done_bar[s]));
+            if (i + kStages < nkb) {   // stage s is free once these MMAs are done
+                ok = tc::mbar_wait(tc::smem_addr(&done_bar[s]), par) && ok;
+                issue(i + kStages);
+            }
+        }
+        const int last = nkb - 1;
+        ok = tc::mbar_wait(tc::smem_addr(&done_bar[last % kStages]), (uint32_t)(last / kStages) & 1u) && ok;
+        if (!ok) atomicAdd(a.timeouts, 1u);
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+
+    const int row = warp * 32 + lane;
+    const int m = m0 + row;
+    const bool valid = m < a.M;
+    const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+
+    if constexpr (EPI == EPI_FWD) {
+        for (int c = 0; c < NT / 32; ++c) {
+            float v[32];
+            tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] += sb[c * 32 + e];
+            if (valid && a.U) {
+                float4* up = reinterpret_cast<float4*>(a.U + (int64_t)m * NT + c * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) up[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = gelu(v[e]);
+            if (valid && a.H) store_bf16x32(a.H + (int64_t)m * NT + c * 32, v);
+            if (valid && a.HT) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) a.HT[(int64_t)(c * 32 + e) * a.ldT + m] = __float2bfloat16_rn(v[e]);
+            }
+        }
+    } else if constexpr (kHead) {
+        float y[OD];
+#pragma unroll
+        for (int k = 0; k < OD; ++k) y[k] = 0.f;
+        for (int c = 0; c < NT / 32; ++c) {
+            float v[32];
+            tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const float h = gelu(v[e] + sb[c * 32 + e]);
+#pragma unroll
+                for (int k = 0; k < OD; ++k) y[k] = fmaf(h, sw3[k][c * 32 + e], y[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < OD; ++k) y[k] += a.b3[k];
+        if constexpr (EPI == EPI_HEAD_INFER) {
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < OD; ++k)
+                    a.Y[(int64_t)m * OD + k] = (float)((double)y[k] * a.scaler[OD + k] + a.scaler[k]);
+            }
+        } else {
+            float r[OD];
+            float l2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < OD; ++k) {
+                const float diff = valid ? y[k] - a.T[(int64_t)m * OD + k] : 0.f;
+                l2 = fmaf(diff, diff, l2);
+                r[k] = diff * a.invB;
+            }
+            const double lw = warp_sum((double)l2);
+            if (lane == 0) atomicAdd(a.loss, lw * 0.5 * (double)a.invB);
+#pragma unroll
+            for (int k = 0; k < OD; ++k) {
+                const float rs = warp_sum(r[k]);
+                if (lane == 0) atomicAdd(&a.gb3[k], rs);
+            }
+            // second pass over the accumulator: dW3, dA2 and db2
+            for (int c = 0; c < NT / 32; ++c) {
+                float v[32], g[32], t[32];
+                tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const float u = v[e] + sb[c * 32 + e];
+                    g[e] = gelu(u);
+                    v[e] = gelu_grad(u);
+                }
+#pragma unroll
+                for (int k = 0; k < OD; ++k) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) t[e] = r[k] * g[e];
+                    const float s = warp_transpose_sum(t, lane);
+                    atomicAdd(&a.gW3[k * NT + c * 32 + lane], s);
+                }
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    float dh = 0.f;
+#pragma unroll
+                    for (int k = 0; k < OD; ++k) dh = fmaf(r[k], sw3[k][c * 32 + e], dh);
+                    t[e] = dh * v[e];
+                }
+                if (valid) {
+                    store_bf16x32(a.H + (int64_t)m * NT + c * 32, t);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) a.HT[(int64_t)(c * 32 + e) * a.ldT + m] = __float2bfloat16_rn(t[e]);
+                }
+                const float s = warp_transpose_sum(t, lane);
+                atomicAdd(&a.colsum[c * 32 + lane], s);
+            }
+        }
+    } else if constexpr (EPI == EPI_DGELU) {
+        for (int c = 0; c < NT / 32; ++c) {
+            float v[32];
+            tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
+            if (valid) {
+                const float4* up = reinterpret_cast<const float4*>(a.Uin + (int64_t)m * NT + c * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 u = up[q];
+                    v[4 * q] *= gelu_grad(u.x);
+                    v[4 * q + 1] *= gelu_grad(u.y);
+                    v[4 * q + 2] *= gelu_grad(u.z);
+                    v[4 * q + 3] *= gelu_grad(u.w);
+                }
+#pragma unroll
+                for (int e = 0; e < 32; ++e) a.HT[(int64_t)(c * 32 + e) * a.ldT + m] = __float2bfloat16_rn(v[e]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] = 0.f;
+            }
+            const float s = warp_transpose_sum(v, lane);
+            atomicAdd(&a.colsum[c * 32 + lane], s);
+        }
+    } else {   // EPI_ATOMIC
+        for (int c = 0; c < NT / 32; ++c) {
+            float v[32];
+            tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
+            if (valid) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const int n = c * 32 + e;
+                    if (n < a.ncols) atomicAdd(&a.C[(int64_t)m * a.ldc + n], v[e]);
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NT < 32 ? 32 : NT);
+}
+
+// Batch gather: rows of X (FP32, n x din) -> Xb (B x 64 BF16, zero-padded) and
+// Xb^T (64 x B), targets -> standardised t (B x OD).  64 rows per block.
+__global__ void __launch_bounds__(256)
+gather_batch_kernel(const float* __restrict__ X, const float* __restrict__ T, int64_t n, int din, int od,
+                    const int32_t* __restrict__ rows, int B, const double* __restrict__ scaler, bf16* __restrict__ Xb,
+                    bf16* __restrict__ XbT, float* __restrict__ t, unsigned int* bad) {
+    __shared__ bf16 tile[64][kKin + 8];
+    const int b0 = blockIdx.x * 64;
+    for (int idx = threadIdx.x; idx < 64 * kKin; idx += 256) {
+        const int s = idx / kKin, k = idx % kKin;
+        const int32_t r = rows[b0 + s];
+        const bool ok = r >= 0 && r < n;
+        if (!ok && k == 0) atomicAdd(bad, 1u);
+        const float v = (ok && k < din) ? X[(int64_t)r * din + k] : 0.f;
+        const bf16 bv = __float2bfloat16_rn(v);
+        Xb[(int64_t)(b0 + s) * kKin + k] = bv;
+        tile[s][k] = bv;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 64 * kKin; idx += 256) {
+        const int k = idx / 64, s = idx % 64;
+        XbT[(int64_t)k * B + b0 + s] = tile[s][k];
+    }
+    for (int idx = threadIdx.x; idx < 64 * od; idx += 256) {
+        const int s = idx / od, k = idx % od;
+        const int32_t r = rows[b0 + s];
+        const double v = (r >= 0 && r < n) ? (double)T[(int64_t)r * od + k] : scaler[k];
+        t[(int64_t)(b0 + s) * od + k] = (float)((v - scaler[k]) / scaler[od + k]);
+    }
+}
+
+// Inference input: X rows [r0, r0 + M) -> Xs (M x 64 BF16, zero-padded).
+__global__ void convert_rows_kernel(const float* __restrict__ X, int64_t r0, int M, int din, bf16* __restrict__ Xs) {
+    const int64_t total = (int64_t)M * kKin;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = idx / kKin;
+        const int k = (int)(idx % kKin);
+        Xs[idx] = __float2bfloat16_rn(k < din ? X[(r0 + s) * din + k] : 0.f);
+    }
+}
+
+struct Offsets {
+    int64_t W1, b1, W2, b2, W3, b3, n;
+};
+
+__host__ __device__ inline Offsets param_offsets(int din, int od) {
+    Offsets o;
+    o.W1 = 0;
+    o.b1 = o.W1 + (int64_t)kH * din;
+    o.W2 = o.b1 + kH;
+    o.b2 = o.W2 + (int64_t)kH * kH;
+    o.W3 = o.b2 + kH;
+    o.b3 = o.W3 + (int64_t)od * kH;
+    o.n = o.b3 + od;
+    return o;
+}
+
+struct Bf16Copies {
+    bf16 *W1b, *W2b, *W2Tb, *W3b;
+};
+
+__device__ __forceinline__ void write_copy(int64_t idx, float w, const Offsets& o, int din, const Bf16Copies& cp) {
+    const bf16 b = __float2bfloat16_rn(w);
+    if (idx < o.b1) {
+        const int64_t h = idx / din, k = idx % din;
+        cp.W1b[h * kKin + k] = b;
+    } else if (idx >= o.W2 && idx < o.b2) {
+        const int64_t q = idx - o.W2, oo = q / kH, i = q % kH;
+        cp.W2b[oo * kH + i] = b;
+        cp.W2Tb[i * kH + oo] = b;
+    } else if (idx >= o.W3 && idx < o.b3) {
+        cp.W3b[idx - o.W3] = b;
+    }
+}
+
+__global__ void sync_copies_kernel(const float* __restrict__ W, Offsets o, int din, Bf16Copies cp) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < o.n; idx += (int64_t)gridDim.x * blockDim.x)
+        write_copy(idx, W[idx], o, din, cp);
+}
+
+// AdamW (decoupled decay on W1, W2, W3) on the FP32 master parameters; the
+// BF16 working copies are rewritten from the updated values.
+__global__ void adamw_kernel(float* __restrict__ W, float* __restrict__ m1, float* __restrict__ m2,
+                             const float* __restrict__ g, Offsets o, int din, Bf16Copies cp, float lr, float b1,
+                             float b2, float eps, float wd, float bc1, float bc2) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < o.n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[idx];
+        const float mi = b1 * m1[idx] + (1.0f - b1) * gi;
+        const float vi = b2 * m2[idx] + (1.0f - b2) * gi * gi;
+        m1[idx] = mi;
+        m2[idx] = vi;
+        const bool is_w = idx < o.b1 || (idx >= o.W2 && idx < o.b2) || (idx >= o.W3 && idx < o.b3);
+        float w = W[idx];
+        const float upd = (mi * bc1) / (sqrtf(vi * bc2) + eps) + (is_w ? wd * w : 0.f);
+        w -= lr * upd;
+        W[idx] = w;
+        write_copy(idx, w, o, din, cp);
+    }
+}
+
+// Scaler: mean (pass 1) and population standard deviation (pass 2) of each
+// output coordinate, FP64.  acc holds [sum[od], ssq[od]].
+__global__ void scaler_sum_kernel(const float* __restrict__ T, int64_t n, int od, const double* __restrict__ acc,
+                                  double* __restrict__ out, int pass) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < od; ++k) {
+            const double v = T[i * od + k];
+            if (pass == 0) s[k] += v;
+            else {
+                const double d = v - acc[k] / (double)n;
+                s[k] += d * d;
+            }
+        }
+    }
+    for (int k = 0; k < od; ++k) {
+        const double w = warp_sum(s[k]);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&out[k], w);
+    }
+}
+__global__ void scaler_final_kernel(const double* __restrict__ acc, int64_t n, int od, double* __restrict__ scaler) {
+    const int k = threadIdx.x;
+    if (k < od) {
+        scaler[k] = acc[k] / (double)n;
+        const double sd = sqrt(acc[od + k] / (double)n);
+        scaler[od + k] = sd > 0.0 ? sd : 1.0;
+    }
+}
+
+}  // namespace mlp
+}  // namespace ptsne
+
+using namespace ptsne;
+using namespace ptsne::mlp;
+
+struct ptsne_mlp {
+    ptsne_mlp_params p{};
+    int din = 0, od = 0, B = 0;
+    int64_t slab = 0;
+    Offsets off{};
+    float *W = nullptr, *m1 = nullptr, *m2 = nullptr, *grad = nullptr;
+    int64_t step = 0;
+    Bf16Copies cp{};
+    double* scaler = nullptr;     // mean[od], std[od]
+    double* sacc = nullptr;       // sum[od], ssq[od]
+    bf16 *Xb = nullptr, *XbT = nullptr, *H1 = nullptr, *H1T = nullptr, *dA2 = nullptr, *dA2T = nullptr,
+         *dA1T = nullptr;
+    float *U1 = nullptr, *tb = nullptr;
+    double* loss = nullptr;       // [1 + max epochs tracked per train call]
+    int loss_cap = 0;
+    bf16 *Xs = nullptr, *H1s = nullptr;
+    unsigned int* dflags = nullptr;   // [0] timeouts, [1] bad rows
+    CUtensorMap tmXb, tmW1b, tmH1, tmW2b, tmdA2T, tmH1T, tmdA2, tmW2Tb, tmdA1T, tmXbT, tmXs, tmH1s;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_mlp_create_err;
+
+int mfail(ptsne_mlp* m, int code, const char* msg) {
+    if (m) m->err = msg;
+    return code;
+}
+
+#define MCK(call)                                                          \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return mfail(m, PTSNE_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+cudaError_t malloc_zero(T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    return cudaMemset(*p, 0, sizeof(T) * (count ? count : 1));
+}
+
+void free_mlp(ptsne_mlp* m) {
+    void* ptrs[] = {m->W,   m->m1,  m->m2,   m->grad, m->cp.W1b, m->cp.W2b, m->cp.W2Tb, m->cp.W3b,
+                    m->scaler, m->sacc, m->Xb, m->XbT, m->H1, m->H1T, m->dA2, m->dA2T, m->dA1T,
+                    m->U1,  m->tb,  m->loss, m->Xs, m->H1s, m->dflags};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+size_t gemm_smem(int nt) {
+    const size_t brows = nt < 128 ? 128 : nt;
+    return (size_t)kStages * (tc::kTileBytes + brows * 128) + 1024;
+}
+
+template <int NT, int EPI, int OD>
+cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const GemmArgs& a, int mtiles, int splits,
+                        cudaStream_t s) {
+    auto kern = mlp_gemm_kernel<NT, EPI, OD>;
+    const size_t smem = gemm_smem(NT);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3((unsigned)mtiles, (unsigned)splits), 128, smem, s>>>(A, B, a);
+    return cudaGetLastError();
+}
+
+GemmArgs base_args(ptsne_mlp* m) {
+    GemmArgs a{};
+    a.timeouts = m->dflags;
+    return a;
+}
+
+// split-K shape of a K = B contraction: (K blocks per CTA, CTAs along K)
+void split_k(int kblocks, int* per, int* splits) {
+    int sp = kblocks < 16 ? kblocks : 16;
+    *per = (kblocks + sp - 1) / sp;
+    *splits = (kblocks + *per - 1) / *per;
+}
+
+template <int OD>
+cudaError_t run_grad_od(ptsne_mlp* m, const float* X, const float* T, int64_t n, const int32_t* rows, double* loss,
+                        cudaStream_t s) {
+    const int B = m->B;
+    cudaError_t e = cudaMemsetAsync(m->grad, 0, sizeof(float) * m->off.n, s);
+    if (e != cudaSuccess) return e;
+    gather_batch_kernel<<<B / 64, 256, 0, s>>>(X, T, n, m->din, OD, rows, B, m->scaler, m->Xb, m->XbT, m->tb,
+                                               m->dflags + 1);
+    // layer 1
+    GemmArgs a = base_args(m);
+    a.M = B;
+    a.kblocks = 1;
+    a.kb_per_split = 1;
+    a.bias = m->W + m->off.b1;
+    a.U = m->U1;
+    a.H = m->H1;
+    a.HT = m->H1T;
+    a.ldT = B;
+    if ((e = launch_gemm<kH, EPI_FWD, OD>(m->tmXb, m->tmW1b, a, B / 128, 1, s)) != cudaSuccess) return e;
+    // layer 2 + head + loss + dW3 + dA2
+    a = base_args(m);
+    a.M = B;
+    a.kblocks = kH / 64;
+    a.kb_per_split = a.kblocks;
+    a.bias = m->W + m->off.b2;
+    a.H = m->dA2;
+    a.HT = m->dA2T;
+    a.ldT = B;
+    a.colsum = m->grad + m->off.b2;
+    a.W3 = m->cp.W3b;
+    a.b3 = m->W + m->off.b3;
+    a.T = m->tb;
+    a.invB = 1.0f / (float)B;
+    a.loss = loss;
+    a.gW3 = m->grad + m->off.W3;
+    a.gb3 = m->grad + m->off.b3;
+    if ((e = launch_gemm<kH, EPI_HEAD_TRAIN, OD>(m->tmH1, m->tmW2b, a, B / 128, 1, s)) != cudaSuccess) return e;
+    // dW2 = dA2^T H1
+    int per, sp;
+    split_k(B / 64, &per, &sp);
+    a = base_args(m);
+    a.M = kH;
+    a.kblocks = B / 64;
+    a.kb_per_split = per;
+    a.C = m->grad + m->off.W2;
+    a.ldc = kH;
+    a.ncols = kH;
+    if ((e = launch_gemm<kH, EPI_ATOMIC, OD>(m->tmdA2T, m->tmH1T, a, kH / 128, sp, s)) != cudaSuccess) return e;
+    // dA1 = (dA2 W2) * g'(U1)
+    a = base_args(m);
+    a.M = B;
+    a.kblocks = kH / 64;
+    a.kb_per_split = a.kblocks;
+    a.HT = m->dA1T;
+    a.ldT = B;
+    a.Uin = m->U1;
+    a.colsum = m->grad + m->off.b1;
+    if ((e = launch_gemm<kH, EPI_DGELU, OD>(m->tmdA2, m->tmW2Tb, a, B / 128, 1, s)) != cudaSuccess) return e;
+    // dW1 = dA1^T Xb
+    a = base_args(m);
+    a.M = kH;
+    a.kblocks = B / 64;
+    a.kb_per_split = per;
+    a.C = m->grad + m->off.W1;
+    a.ldc = m->din;
+    a.ncols = m->din;
+    if ((e = launch_gemm<64, EPI_ATOMIC, OD>(m->tmdA1T, m->tmXbT, a, kH / 128, sp, s)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t run_grad(ptsne_mlp* m, const float* X, const float* T, int64_t n, const int32_t* rows, double* loss,
+                     cudaStream_t s) {
+    return m->od == 2 ? run_grad_od<2>(m, X, T, n, rows, loss, s) : run_grad_od<3>(m, X, T, n, rows, loss, s);
+}
+
+cudaError_t run_adamw(ptsne_mlp* m, cudaStream_t s) {
+    m->step += 1;
+    const ptsne_mlp_params& p = m->p;
+    const float bc1 = (float)(1.0 / (1.0 - pow((double)p.beta1, (double)m->step)));
+    const float bc2 = (float)(1.0 / (1.0 - pow((double)p.beta2, (double)m->step)));
+    adamw_kernel<<<152 * 4, 256, 0, s>>>(m->W, m->m1, m->m2, m->grad, m->off, m->din, m->cp, p.lr, p.beta1, p.beta2,
+                                         p.eps, p.weight_decay, bc1, bc2);
+    return cudaGetLastError();
+}
+
+template <int OD>
+cudaError_t run_infer_od(ptsne_mlp* m, const float* X, int64_t n, float* Y, cudaStream_t s) {
+    for (int64_t r0 = 0; r0 < n; r0 += m->slab) {
+        const int M = (int)((n - r0) < m->slab ? (n - r0) : m->slab);
+        int64_t g = ((int64_t)M * kKin + 255) / 256;
+        if (g > 152 * 16) g = 152 * 16;
+        convert_rows_kernel<<<(unsigned)g, 256, 0, s>>>(X, r0, M, m->din, m->Xs);
+        const int mt = (M + 127) / 128;
+        GemmArgs a = base_args(m);
+        a.M = M;
+        a.kblocks = 1;
+        a.kb_per_split = 1;
+        a.bias = m->W + m->off.b1;
+        a.H = m->H1s;
+        cudaError_t e = launch_gemm<kH, EPI_FWD, OD>(m->tmXs, m->tmW1b, a, mt, 1, s);
+        if (e != cudaSuccess) return e;
+        a = base_args(m);
+        a.M = M;
+        a.kblocks = kH / 64;
+        a.kb_per_split = a.kblocks;
+        a.bias = m->W + m->off.b2;
+        a.W3 = m->cp.W3b;
+        a.b3 = m->W + m->off.b3;
+        a.scaler = m->scaler;
+        a.Y = Y + r0 * OD;
+        e = launch_gemm<kH, EPI_HEAD_INFER, OD>(m->tmH1s, m->tmW2b, a, mt, 1, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+bool valid_params(const ptsne_mlp_params* p, const char** why) {
+    if (p->d_in < 1 || p->d_in > 64) return *why = "d_in must be in [1, 64]", false;
+    if (p->out_dim != 2 && p->out_dim != 3) return *why = "out_dim must be 2 or 3", false;
+    if (p->batch < 128 || p->batch > 65536 || p->batch % 128) return *why = "batch must be a multiple of 128 in [128, 65536]", false;
+    if (p->infer_rows < 128 || p->infer_rows % 128 || p->infer_rows > (1 << 24))
+        return *why = "infer_rows must be a multiple of 128 in [128, 2^24]", false;
+    if (!(p->lr > 0.f) || !(p->beta1 >= 0.f && p->beta1 < 1.f) || !(p->beta2 >= 0.f && p->beta2 < 1.f) ||
+        !(p->eps > 0.f) || !(p->weight_decay >= 0.f))
+        return *why = "AdamW settings out of range (lr > 0, 0 <= beta < 1, eps > 0, weight_decay >= 0)", false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ptsne_mlp_last_error(const ptsne_mlp* m) { return m ? m->err.c_str() : g_mlp_create_err.c_str(); }
+
+int ptsne_mlp_create(ptsne_mlp** out, const ptsne_mlp_params* prm, const float* init_host) {
+    if (!out || !prm || !init_host) {
+        g_mlp_create_err = "out, params and init_host must be non-NULL";
+        return PTSNE_EINVAL;
+    }
+    *out = nullptr;
+    const char* why = nullptr;
+    if (!valid_params(prm, &why)) {
+        g_mlp_create_err = std::string("invalid parameter: ") + why;
+        return PTSNE_EINVAL;
+    }
+    ptsne_mlp* m = new (std::nothrow) ptsne_mlp();
+    if (!m) return PTSNE_ENOMEM;
+    m->p = *prm;
+    m->din = prm->d_in;
+    m->od = prm->out_dim;
+    m->B = prm->batch;
+    m->slab = prm->infer_rows;
+    m->off = param_offsets(m->din, m->od);
+    const int64_t B = m->B, S = m->slab;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    A(malloc_zero(&m->W, m->off.n));
+    A(malloc_zero(&m->m1, m->off.n));
+    A(malloc_zero(&m->m2, m->off.n));
+    A(malloc_zero(&m->grad, m->off.n));
+    A(malloc_zero(&m->cp.W1b, (size_t)kH * kKin));
+    A(malloc_zero(&m->cp.W2b, (size_t)kH * kH));
+    A(malloc_zero(&m->cp.W2Tb, (size_t)kH * kH));
+    A(malloc_zero(&m->cp.W3b, (size_t)m->od * kH));
+    A(malloc_zero(&m->scaler, 2 * (size_t)m->od));
+    A(malloc_zero(&m->sacc, 2 * (size_t)m->od));
+    A(malloc_zero(&m->Xb, (size_t)B * kKin));
+    A(malloc_zero(&m->XbT, (size_t)128 * B));   // rows 64..127 stay zero (the 128-row TMA box)
+    A(malloc_zero(&m->H1, (size_t)B * kH));
+    A(malloc_zero(&m->H1T, (size_t)kH * B));
+    A(malloc_zero(&m->dA2, (size_t)B * kH));
+    A(malloc_zero(&m->dA2T, (size_t)kH * B));
+    A(malloc_zero(&m->dA1T, (size_t)kH * B));
+    A(malloc_zero(&m->U1, (size_t)B * kH));
+    A(malloc_zero(&m->tb, (size_t)B * m->od));
+    m->loss_cap = 1024;
+    A(malloc_zero(&m->loss, (size_t)m->loss_cap + 1));
+    A(malloc_zero(&m->Xs, (size_t)S * kKin));
+    A(malloc_zero(&m->H1s, (size_t)S * kH));
+    A(malloc_zero(&m->dflags, 2));
+    if (e == cudaSuccess) e = cudaMemcpy(m->W, init_host, sizeof(float) * m->off.n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<double> sc(2 * m->od, 0.0);
+        for (int k = 0; k < m->od; ++k) sc[m->od + k] = 1.0;
+        e = cudaMemcpy(m->scaler, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {
+        sync_copies_kernel<<<152, 256>>>(m->W, m->off, m->din, m->cp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_mlp_create_err = std::string("device setup failed: ") + cudaGetErrorString(e);
+        free_mlp(m);
+        delete m;
+        return e == cudaErrorMemoryAllocation ? PTSNE_ENOMEM : PTSNE_ECUDA;
+    }
+    bool ok = tc::make_bf16_tmap(&m->tmXb, m->Xb, B, kKin) && tc::make_bf16_tmap(&m->tmW1b, m->cp.W1b, kH, kKin) &&
+              tc::make_bf16_tmap(&m->tmH1, m->H1, B, kH) && tc::make_bf16_tmap(&m->tmW2b, m->cp.W2b, kH, kH) &&
+              tc::make_bf16_tmap(&m->tmdA2T, m->dA2T, kH, B) && tc::make_bf16_tmap(&m->tmH1T, m->H1T, kH, B) &&
+              tc::make_bf16_tmap(&m->tmdA2, m->dA2, B, kH) && tc::make_bf16_tmap(&m->tmW2Tb, m->cp.W2Tb, kH, kH) &&
+              tc::make_bf16_tmap(&m->tmdA1T, m->dA1T, kH, B) && tc::make_bf16_tmap(&m->tmXbT, m->XbT, 128, B) &&
+              tc::make_bf16_tmap(&m->tmXs, m->Xs, S, kKin) && tc::make_bf16_tmap(&m->tmH1s, m->H1s, S, kH);
+    if (!ok) {
+        g_mlp_create_err = "the driver refused a TMA tensor map";
+        free_mlp(m);
+        delete m;
+        return PTSNE_ECUDA;
+    }
+    *out = m;
+    return PTSNE_OK;
+}
+
+void ptsne_mlp_destroy(ptsne_mlp* m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    free_mlp(m);
+    delete m;
+}
+
+int ptsne_mlp_get_params(ptsne_mlp* m, float* out_host, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!out_host) return mfail(m, PTSNE_EINVAL, "out_host must be non-NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MCK(cudaMemcpyAsync(out_host, m->W, sizeof(float) * m->off.n, cudaMemcpyDeviceToHost, s));
+    MCK(cudaStreamSynchronize(s));
+    return PTSNE_OK;
+}
+
+int ptsne_mlp_fit_scaler(ptsne_mlp* m, const float* T, int64_t n, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!T || n < 1) return mfail(m, PTSNE_EINVAL, "T must be a device pointer and n >= 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MCK(cudaMemsetAsync(m->sacc, 0, sizeof(double) * 2 * m->od, s));
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    scaler_sum_kernel<<<(unsigned)g, 256, 0, s>>>(T, n, m->od, m->sacc, m->sacc, 0);
+    scaler_sum_kernel<<<(unsigned)g, 256, 0, s>>>(T, n, m->od, m->sacc, m->sacc + m->od, 1);
+    scaler_final_kernel<<<1, 32, 0, s>>>(m->sacc, n, m->od, m->scaler);
+    MCK(cudaGetLastError());
+    return PTSNE_OK;
+}
+
+int ptsne_mlp_grad(ptsne_mlp* m, const float* X, const float* T, int64_t n, const int32_t* rows, float* grad_out,
+                   double* loss_out, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!X || !T || !rows || n < 1) return mfail(m, PTSNE_EINVAL, "X, T and rows must be device pointers, n >= 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MCK(cudaMemsetAsync(m->loss, 0, sizeof(double), s));
+    MCK(run_grad(m, X, T, n, rows, m->loss, s));
+    if (grad_out) MCK(cudaMemcpyAsync(grad_out, m->grad, sizeof(float) * m->off.n, cudaMemcpyDeviceToDevice, s));
+    if (loss_out) MCK(cudaMemcpyAsync(loss_out, m->loss, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return PTSNE_OK;
+}
+
+int ptsne_mlp_train_step(ptsne_mlp* m, const float* X, const float* T, int64_t n, const int32_t* rows,
+                         double* loss_out, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!X || !T || !rows || n < 1) return mfail(m, PTSNE_EINVAL, "X, T and rows must be device pointers, n >= 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MCK(cudaMemsetAsync(m->loss, 0, sizeof(double), s));
+    MCK(run_grad(m, X, T, n, rows, m->loss, s));
+    MCK(run_adamw(m, s));
+    if (loss_out) MCK(cudaMemcpyAsync(loss_out, m->loss, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return PTSNE_OK;
+}
+
+int ptsne_mlp_train(ptsne_mlp* m, const float* X, const float* T, int64_t n, const int32_t* orders, int32_t epochs,
+                    double* loss_out_host, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!X || !T || !orders) return mfail(m, PTSNE_EINVAL, "X, T and orders must be device pointers");
+    if (epochs < 0) return mfail(m, PTSNE_EINVAL, "epochs must be >= 0");
+    if (n < m->B) return mfail(m, PTSNE_EINVAL, "n must be at least one batch");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t steps = n / m->B;
+    MCK(cudaMemsetAsync(m->dflags + 1, 0, sizeof(unsigned int), s));
+    std::vector<double> host;
+    for (int32_t e0 = 0; e0 < epochs; e0 += m->loss_cap) {
+        const int ne = (epochs - e0) < m->loss_cap ? (epochs - e0) : m->loss_cap;
+        MCK(cudaMemsetAsync(m->loss + 1, 0, sizeof(double) * ne, s));
+        for (int e = 0; e < ne; ++e) {
+            const int32_t* ord = orders + (int64_t)(e0 + e) * n;
+            for (int64_t b = 0; b < steps; ++b) {
+                MCK(run_grad(m, X, T, n, ord + b * m->B, m->loss + 1 + e, s));
+                MCK(run_adamw(m, s));
+            }
+        }
+        host.resize(ne);
+        MCK(cudaMemcpyAsync(host.data(), m->loss + 1, sizeof(double) * ne, cudaMemcpyDeviceToHost, s));
+        MCK(cudaStreamSynchronize(s));
+        if (loss_out_host)
+            for (int e = 0; e < ne; ++e) loss_out_host[e0 + e] = host[e] / (double)steps;
+    }
+    unsigned int flags[2];
+    MCK(cudaMemcpyAsync(flags, m->dflags, sizeof flags, cudaMemcpyDeviceToHost, s));
+    MCK(cudaStreamSynchronize(s));
+    if (flags[0]) return mfail(m, PTSNE_ETIMEOUT, "a bounded wait inside a GEMM ran out");
+    if (flags[1]) return mfail(m, PTSNE_EINVAL, "orders holds entries outside [0, n)");
+    return PTSNE_OK;
+}
+
+int ptsne_mlp_infer(ptsne_mlp* m, const float* X, int64_t n, float* Y, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!X || !Y || n < 1) return mfail(m, PTSNE_EINVAL, "X and Y must be device pointers, n >= 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MCK(m->od == 2 ? run_infer_od<2>(m, X, n, Y, s) : run_infer_od<3>(m, X, n, Y, s));
+    return PTSNE_OK;
+}
+
+}  // extern "C"

@@ -25,6 +25,7 @@ __all__ = [
     "permutations",
     "init_gaussian",
     "init_disk",
+    "mlp_init",
     "Workload",
     "workload",
     "WORKLOADS",
@@ -176,6 +177,20 @@ def init_disk(n: int, seed: int) -> np.ndarray:
     r = np.sqrt(rng.uniform(0.0, 1.0, size=n))
     t = rng.uniform(0.0, 2.0 * np.pi, size=n)
     return np.stack([r * np.cos(t), r * np.sin(t)], axis=1).astype(np.float32)
+
+
+def mlp_init(d_in: int, out_dim: int, seed: int, hidden: int = 256) -> dict:
+    """Initial mapper parameters: weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)),
+    biases zero, float32 (W1 hidden x d_in, W2 hidden x hidden, W3 out x hidden)."""
+    rng = _rng(seed)
+
+    def u(rows, cols):
+        a = 1.0 / np.sqrt(cols)
+        return rng.uniform(-a, a, size=(rows, cols)).astype(np.float32)
+
+    return {"W1": u(hidden, d_in), "b1": np.zeros(hidden, np.float32),
+            "W2": u(hidden, hidden), "b2": np.zeros(hidden, np.float32),
+            "W3": u(out_dim, hidden), "b3": np.zeros(out_dim, np.float32)}
 
 
 @dataclasses.dataclass

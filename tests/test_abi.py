@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared_symbols():
-    text = open(os.path.join(ROOT, "include", "ptsne.h")).read()
+    import glob
+    text = "".join(open(f).read() for f in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(ptsne_\w+)\s*\(", text, re.M)))
 
 
@@ -26,7 +27,8 @@ def lib():
 def test_header_declares_the_boundary():
     syms = _declared_symbols()
     for s in ("ptsne_create", "ptsne_destroy", "ptsne_affinities", "ptsne_step", "ptsne_run",
-              "ptsne_run_host", "ptsne_cost", "ptsne_get_stats", "ptsne_last_error"):
+              "ptsne_run_host", "ptsne_cost", "ptsne_get_stats", "ptsne_last_error", "ptsne_gradient_static",
+              "ptsne_mlp_create", "ptsne_mlp_train", "ptsne_mlp_grad", "ptsne_mlp_infer"):
         assert s in syms
 
 
@@ -78,3 +80,30 @@ def test_bindings_fail_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(ptsne, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         ptsne.lib()
+
+
+@pytest.mark.parametrize("field,value", [("d_in", 65), ("d_in", 0), ("out_dim", 4), ("batch", 100),
+                                         ("batch", 0), ("infer_rows", 1000), ("lr", 0.0), ("beta2", 1.0)])
+def test_mapper_create_rejects_bad_parameters(lib, field, value):
+    """Checked on the host before any device allocation."""
+    from paper_1812_09869_gb300 import mapper as M
+    from paper_1812_09869_gb300 import ptsne
+    L = M.lib()
+    p = M.MlpParams(50, 2, 4096, 1 << 16, 1e-3, 0.9, 0.999, 1e-8, 1e-4)
+    setattr(p, field, value)
+    init = np.zeros(M.n_params(50, 2), np.float32)
+    h = C.c_void_p()
+    assert L.ptsne_mlp_create(C.byref(h), C.byref(p), init.ctypes.data_as(C.c_void_p)) == ptsne.EINVAL
+    assert not h.value
+    assert "invalid parameter" in L.ptsne_mlp_last_error(None).decode()
+
+
+def test_mapper_pack_roundtrip():
+    from paper_1812_09869_gb300 import mapper as M
+    from paper_1812_09869_gb300 import synth
+    W = synth.mlp_init(50, 3, seed=5)
+    flat = M.pack(W)
+    assert flat.size == M.n_params(50, 3) == 256 * 50 + 256 + 256 * 256 + 256 + 3 * 256 + 3
+    back = M.unpack(flat, 50, 3)
+    for k in M.PARAM_ORDER:
+        assert np.array_equal(back[k], W[k])

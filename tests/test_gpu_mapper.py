@@ -1,0 +1,192 @@
+"""Learned mapper: the tcgen05 forward and backward passes and the AdamW step
+against the FP64 numpy oracle, and what a trained mapper gains as a warm
+start of ptSNE over plain ptSNE from a random start."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1812_09869_gb300 import synth
+
+from parity import rel_max
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# The GPU keeps hidden activations in BF16 between layers (relative rounding
+# <= 2^-9 per entry) and accumulates in FP32; the oracle runs the same
+# BF16-valued weights and inputs in FP64.  Over two hidden layers the
+# rounding stays below a few 1e-3 of the largest output or gradient entry.
+FWD_TOL = 1e-2
+MLP_GRAD_TOL = 2e-2
+
+
+def _bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).bfloat16().float().numpy()
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_09869_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _weights(d_in, od, seed):
+    """BF16-valued weights (so the FP32 master copy equals what the kernels
+    use) and small non-zero biases."""
+    W = synth.mlp_init(d_in, od, seed)
+    rng = np.random.default_rng(seed + 7)
+    for k in ("b1", "b2", "b3"):
+        W[k] = rng.uniform(-0.1, 0.1, size=W[k].shape).astype(np.float32)
+    return {k: (_bf16(v) if k.startswith("W") else v) for k, v in W.items()}
+
+
+def _f64(W):
+    return {k: np.asarray(v, dtype=np.float64) for k, v in W.items()}
+
+
+def test_forward_with_scaler_matches_oracle(dev):
+    from paper_1812_09869_gb300.mapper import Mapper
+    n, d_in = 1000, 50                     # 3 inference slabs of 256 rows and a ragged one of 232
+    X, _ = synth.gaussian_mixture(n, d_in, 5, seed=70)
+    X = _bf16(X)
+    W = _weights(d_in, 2, 71)
+    rng = np.random.default_rng(72)
+    T = (rng.standard_normal((n, 2)) * np.array([2.0, 0.5]) + np.array([3.0, -2.0])).astype(np.float32)
+    with Mapper(d_in, W, infer_rows=256) as m:
+        Xd = torch.from_numpy(X).to(dev)
+        m.fit_scaler(torch.from_numpy(T).to(dev))
+        Yd = torch.zeros((n, 2), dtype=torch.float32, device=dev)
+        m.infer(Xd, Yd)
+        torch.cuda.synchronize()
+        y = Yd.cpu().numpy().astype(np.float64)
+    mean, std = T.astype(np.float64).mean(0), T.astype(np.float64).std(0)
+    y_ref, _ = O.mlp_forward(_f64(W), X.astype(np.float64))
+    assert rel_max((y - mean) / std, y_ref) <= FWD_TOL
+
+
+@pytest.mark.parametrize("batch", [128, 512])
+def test_gradient_matches_oracle(dev, batch):
+    from paper_1812_09869_gb300 import mapper as M
+    n, d_in = 3000, 50
+    X, _ = synth.gaussian_mixture(n, d_in, 6, seed=73)
+    X = _bf16(X)
+    rng = np.random.default_rng(74)
+    T = rng.standard_normal((n, 2)).astype(np.float32)
+    rows = synth.permutations(n, 1, seed=75)[0][:batch].copy()
+    W = _weights(d_in, 2, 76)
+    with M.Mapper(d_in, W, batch=batch) as m:
+        g = torch.zeros(M.n_params(d_in, 2), dtype=torch.float32, device=dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        m.grad(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(rows).to(dev), g, loss)
+        torch.cuda.synchronize()
+        G = M.unpack(g.cpu().numpy(), d_in, 2)
+        L = loss.item()
+    L_ref, G_ref = O.mlp_loss_grad(_f64(W), X[rows], T[rows])
+    assert abs(L - L_ref) <= 1e-2 * L_ref
+    for k in M.PARAM_ORDER:
+        assert rel_max(G[k], G_ref[k]) <= MLP_GRAD_TOL, (k, rel_max(G[k], G_ref[k]))
+
+
+def test_first_adamw_step_matches_oracle(dev):
+    """Step 1 of AdamW moves each parameter by lr (g / (|g| + eps) + wd w):
+    entries whose gradient is not tiny must land where the oracle puts them."""
+    from paper_1812_09869_gb300 import mapper as M
+    n, d_in, batch, lr, wd = 2000, 50, 256, 1e-3, 1e-4
+    X, _ = synth.gaussian_mixture(n, d_in, 6, seed=77)
+    X = _bf16(X)
+    T = np.random.default_rng(78).standard_normal((n, 2)).astype(np.float32)
+    rows = synth.permutations(n, 1, seed=79)[0][:batch].copy()
+    W = _weights(d_in, 2, 80)
+    with M.Mapper(d_in, W, batch=batch, lr=lr, weight_decay=wd) as m:
+        m.train_step(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(rows).to(dev))
+        torch.cuda.synchronize()
+        W1 = m.params()
+    Wr = _f64(W)
+    _, g = O.mlp_loss_grad(Wr, X[rows], T[rows])
+    m1 = {k: np.zeros_like(v) for k, v in Wr.items()}
+    m2 = {k: np.zeros_like(v) for k, v in Wr.items()}
+    O.adamw_step(Wr, g, m1, m2, 1, lr=lr, wd=wd)
+    for k in M.PARAM_ORDER:
+        robust = np.abs(g[k]) > 1e-2 * np.abs(g[k]).max()
+        diff = np.abs(W1[k] - Wr[k])
+        assert diff[robust].max() <= 1e-6, k
+        assert diff.max() <= 2.1 * lr, k
+
+
+def test_training_fits_a_smooth_map(dev):
+    from paper_1812_09869_gb300 import mapper as M
+    n, d_in = 8192, 50
+    X, _ = synth.gaussian_mixture(n, d_in, 10, seed=81)
+    R = np.random.default_rng(82).standard_normal((d_in, 2)) / np.sqrt(d_in) / 3.0
+    T = np.tanh(X.astype(np.float64) @ R).astype(np.float32) * 5.0
+    orders = synth.permutations(n, 20, seed=83)
+    with M.Mapper(d_in, synth.mlp_init(d_in, 2, 84), batch=512) as m:
+        Xd, Td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
+        m.fit_scaler(Td)
+        loss = m.train(Xd, Td, torch.from_numpy(orders).to(dev), 20)
+        Yd = torch.zeros((n, 2), dtype=torch.float32, device=dev)
+        m.infer(Xd, Yd)
+        torch.cuda.synchronize()
+    assert np.all(np.isfinite(loss))
+    assert loss[-1] < 0.05 * loss[0], loss
+    resid = Yd.cpu().numpy() - T
+    assert np.sqrt((resid ** 2).mean()) < 0.1 * T.std()
+
+
+def test_warm_start_gains_over_plain_ptsne(dev):
+    """Train ptSNE on one half of a mixture, fit the mapper to its map, place
+    the other half with the mapper, and run ptSNE on that half from the
+    mapper's placement and from the usual random start with the same short
+    schedule: the warm start reaches a lower KL (Eq. 5), and the mapper's own
+    placement keeps 10-nearest-neighbour structure well above chance."""
+    from paper_1812_09869_gb300 import mapper as M
+    from paper_1812_09869_gb300 import ptsne
+    half, d_in = 16384, 50
+    X, _ = synth.gaussian_mixture(2 * half, d_in, 20, seed=85, anisotropic=True)
+    Xtr, Xte = X[:half], X[half:]
+    off = synth.equal_chunk_offsets(half, 8)
+    Xtr_d, Xte_d = torch.from_numpy(Xtr).to(dev), torch.from_numpy(Xte).to(dev)
+
+    def run(Xd, Y0, epochs, iters, seed):
+        cfg = ptsne.Config(n=half, d=d_in, offsets=off, perplexity=30.0, iters=iters)
+        with ptsne.Context(cfg) as ctx:
+            Yd = torch.from_numpy(np.ascontiguousarray(Y0, dtype=np.float32)).to(dev)
+            cost = np.zeros((epochs, 2))
+            ctx.run(Xd, torch.from_numpy(synth.permutations(half, epochs, seed)).to(dev), epochs, Yd, cost_out=cost)
+            torch.cuda.synchronize()
+            return Yd.cpu().numpy(), cost[-1, 0]
+
+    Ytr, kl_tr = run(Xtr_d, synth.init_gaussian(half, 2, 1e-4, seed=86), 4, 100, 87)
+    with M.Mapper(d_in, synth.mlp_init(d_in, 2, 88), batch=1024) as m:
+        Ttr = torch.from_numpy(Ytr).to(dev)
+        m.fit_scaler(Ttr)
+        loss = m.train(Xtr_d, Ttr, torch.from_numpy(synth.permutations(half, 40, seed=89)).to(dev), 40)
+        Ymap_d = torch.zeros((half, 2), dtype=torch.float32, device=dev)
+        m.infer(Xte_d, Ymap_d)
+        torch.cuda.synchronize()
+        Ymap = Ymap_d.cpu().numpy()
+    assert loss[-1] < 0.2 * loss[0], loss
+
+    short = 30
+    Y_cold, kl_cold = run(Xte_d, synth.init_gaussian(half, 2, 1e-4, seed=90), 1, short, 91)
+    Y_warm, kl_warm = run(Xte_d, Ymap, 1, short, 91)
+    Y_full, kl_full = run(Xte_d, synth.init_gaussian(half, 2, 1e-4, seed=90), 4, 100, 92)
+    q = np.arange(1000)
+    pres = {name: O.knn_preservation(Xte[q], Xte, Y[q], Y, k=10)
+            for name, Y in (("map", Ymap), ("cold", Y_cold), ("warm", Y_warm), ("full", Y_full))}
+    print(f"\nKL train {kl_tr:.4f}  cold@{short} {kl_cold:.4f}  warm@{short} {kl_warm:.4f}  "
+          f"full(4x100) {kl_full:.4f}; 10-NN preservation {pres}")
+    # the gain: at equal iterations the warm start ends at a clearly lower KL,
+    # below even a 4-epoch x 100-iteration run from the random start
+    assert kl_warm < 0.8 * kl_cold
+    assert kl_warm < kl_full
+    # neighbourhoods: 10-NN within 50-d Gaussian blobs are mostly noise, so
+    # every map keeps a few percent of them; the mapper's placement alone keeps
+    # far more than chance (10 / n) and the warm start loses little to the cold one
+    chance = 10.0 / half
+    assert pres["map"] > 10 * chance
+    assert pres["warm"] >= 0.75 * pres["cold"]
