@@ -297,7 +297,7 @@ def bench_ours(args, rank, world, local_rank):
     plain = None
     if not args.no_plain and world == 1:
         pcfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
-                            momentum=w.momentum, precision="fp32", schedule="per_chunk")
+                            momentum=w.momentum, precision="fp32", schedule="per_chunk", use_graph=0)
         with ptsne.Context(pcfg) as pctx:
             Yp = torch.from_numpy(w.Y0.copy()).to(dev)
             pcost = np.zeros((1, 2))
@@ -308,7 +308,8 @@ def bench_ours(args, rank, world, local_rank):
             b.record(stream)
             torch.cuda.synchronize()
             ps = a.elapsed_time(b) / 1000.0
-        plain = {"value": w.n * w.iters / ps, "unit": UNIT, "ms_per_step": ps * 1e3, "schedule": "per_chunk",
+        plain = {"value": w.n * w.iters / ps, "unit": UNIT, "ms_per_step": ps * 1e3,
+                 "schedule": "per_chunk, plain launches",
                  "distances": "fp32", "steps": 1, "speedup_of_value": value / (w.n * w.iters / ps),
                  "final_cost": pcost[0].tolist()}
 
@@ -322,7 +323,7 @@ def bench_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "n": w.n, "d": w.d, "chunks": int(len(sizes)),
                    "chunk_size_range": [int(sizes.min()), int(sizes.max())], "perplexity": w.perplexity,
-                   "iters_per_epoch": w.iters, "out_dim": 2, "schedule": "batched persistent",
+                   "iters_per_epoch": w.iters, "out_dim": 2, "schedule": "batched persistent, graph-captured epoch",
                    "distances": {"fp32": "fp32 direct differences",
                                  "bf16_window": "bf16 tcgen05 Gram + fp32 window recompute"}[precision],
                    "step": "one epoch", "parallelism": f"replicas{world}",

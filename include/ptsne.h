@@ -96,6 +96,10 @@ typedef struct {
                                      versus velocity, x0.8 otherwise, floor 0.01) */
     int32_t precision;            /* PTSNE_PREC_* */
     int32_t schedule;             /* PTSNE_SCHED_* */
+    int32_t use_graph;            /* 1: ptsne_run replays each epoch from one captured CUDA
+                                     graph (captured on the first call, and again whenever
+                                     X, Y, the tuning or the cost request change); 0: plain
+                                     launches.  Off while profiling is on. */
 } ptsne_params;
 
 typedef struct {

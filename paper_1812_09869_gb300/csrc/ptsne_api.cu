@@ -70,9 +70,14 @@ void free_all(ptsne_ctx* c) {
                     c->beta,   c->mrow,    c->Srow,   c->Yc,             c->vel,     c->gains,
                     c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
-                    c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm};
+                    c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
+                    c->perm_cur, c->cost_cur};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->graph = nullptr;
+    c->cap_stream = nullptr;
     for (auto& e : c->ev)
         if (e) {
             cudaEventDestroy(e);
@@ -132,6 +137,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (p.precision != PTSNE_PREC_FP32 && p.precision != PTSNE_PREC_BF16_WINDOW)
         return bad("precision", p.precision);
     if (p.schedule != PTSNE_SCHED_BATCHED && p.schedule != PTSNE_SCHED_PER_CHUNK) return bad("schedule", p.schedule);
+    if (p.use_graph != 0 && p.use_graph != 1) return bad("use_graph must be 0 or 1", p.use_graph);
     if (p.schedule == PTSNE_SCHED_BATCHED && iterate_ring(p.out_dim, zmax, 1) < 1)
         return bad("largest chunk too large for the batched schedule at this out_dim", zmax);
 
@@ -256,6 +262,8 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     AL(c->cost_hist, 2 * kCostHist);
     AL(c->queue, 4);
     AL(c->dstats, 1);
+    AL(c->perm_cur, n);
+    AL(c->cost_cur, 2);
 #undef AL
     auto up = [&](void* dst, const void* src, size_t bytes) {
         return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -342,6 +350,73 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cu
     return PTSNE_OK;
 }
 
+static int iterate_rows(ptsne_ctx* c, float* grad_perm, cudaStream_t s);
+
+// One epoch of ptsne_run on the partition perm: affinities, every gradient
+// iteration of every chunk, the pool back into Y and, if want_cost, the
+// epoch's average cost into cost_dst (2 doubles).
+static int run_epoch(ptsne_ctx* c, const float* X, const int32_t* perm, float* Y, bool want_cost, double* cost_dst,
+                     cudaStream_t s) {
+    int st = affinities_impl(c, X, perm, s, false, Y);
+    if (st != PTSNE_OK) return st;
+    mark(c, PTSNE_STAGE_ITERATE, s);
+    if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+        // every iteration of every chunk, then (if requested) one cost pass, in one launch
+        CK(launch_iterate(c, c->p.iters, want_cost ? 1 : 0, nullptr, nullptr, c->cost_chunk, s));
+    } else {
+        for (int it = 0; it < c->p.iters; ++it) {
+            st = iterate_rows(c, nullptr, s);
+            if (st != PTSNE_OK) return st;
+        }
+    }
+    mark(c, PTSNE_STAGE_POOL, s);
+    CK(launch_scatter_rows(c, c->Yc, perm, c->p.out_dim, Y, s));
+    mark(c, PTSNE_STAGE_COST, s);
+    if (want_cost) {
+        if (c->p.schedule == PTSNE_SCHED_BATCHED) CK(launch_cost_final(c, cost_dst, s));
+        else CK(launch_cost(c, cost_dst, s));
+    }
+    return PTSNE_OK;
+}
+
+static bool same_tune(const IterTune& a, const IterTune& b) {
+    return a.cluster == b.cluster && a.group == b.group && a.consumer_warps == b.consumer_warps;
+}
+
+// Capture one epoch (partition read from perm_cur, cost left in cost_cur) on
+// the context's private stream and instantiate it; replays then run on the
+// caller's stream, which may be the legacy default stream.
+static int capture_epoch(ptsne_ctx* c, const float* X, float* Y, bool want_cost) {
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+    const int st = run_epoch(c, X, c->perm_cur, Y, want_cost, c->cost_cur, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    if (st != PTSNE_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != PTSNE_OK ? st : fail(c, PTSNE_ECUDA, "epoch capture failed (%s, line %lld)", cudaGetErrorString(e), __LINE__);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        c->graph = nullptr;
+        return fail(c, PTSNE_ECUDA, "epoch graph instantiation failed (%s, line %lld)", cudaGetErrorString(ei), __LINE__);
+    }
+    c->graph_X = X;
+    c->graph_Y = Y;
+    c->graph_cost = want_cost ? 1 : 0;
+    c->graph_tune = c->tune;
+    return PTSNE_OK;
+}
+
 int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P_out, float* beta_out,
                      void* stream) {
     if (!c) return PTSNE_EINVAL;
@@ -425,38 +500,37 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
     if (epochs < 0) return fail(c, PTSNE_EINVAL, "epochs must be >= 0%s (%lld)", "", epochs);
     cudaStream_t s = as_stream(stream);
     const int64_t n = c->p.n;
+    const bool want_cost = cost_out != nullptr;
+    const bool use_graph = c->p.use_graph && !c->profiling;
+    if (use_graph && (!c->graph || c->graph_X != X || c->graph_Y != Y || c->graph_cost != (int)want_cost ||
+                      !same_tune(c->graph_tune, c->tune))) {
+        const int st = capture_epoch(c, X, Y, want_cost);
+        if (st != PTSNE_OK) return st;
+    }
     // counters accumulate over the whole run
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
     for (int e = 0; e < epochs; ++e) {
         const int32_t* perm = perms + (int64_t)e * n;
-        int st = affinities_impl(c, X, perm, s, false, Y);
-        if (st != PTSNE_OK) return st;
-        mark(c, PTSNE_STAGE_ITERATE, s);
-        if (c->p.schedule == PTSNE_SCHED_BATCHED) {
-            // every iteration of every chunk, then (if requested) one cost pass, in one launch
-            CK(launch_iterate(c, c->p.iters, cost_out ? 1 : 0, nullptr, nullptr, c->cost_chunk, s));
+        const int slot = e % kCostHist;
+        if (use_graph) {
+            CK(cudaMemcpyAsync(c->perm_cur, perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            CK(cudaGraphLaunch(c->graph, s));
+            c->launches += c->graph_launches;
+            if (want_cost)
+                CK(cudaMemcpyAsync(c->cost_hist + 2 * slot, c->cost_cur, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   s));
         } else {
-            for (int it = 0; it < c->p.iters; ++it) {
-                st = iterate_rows(c, nullptr, s);
-                if (st != PTSNE_OK) return st;
-            }
+            const int st = run_epoch(c, X, perm, Y, want_cost, c->cost_hist + 2 * slot, s);
+            if (st != PTSNE_OK) return st;
         }
-        mark(c, PTSNE_STAGE_POOL, s);
-        CK(launch_scatter_rows(c, c->Yc, perm, c->p.out_dim, Y, s));
-        mark(c, PTSNE_STAGE_COST, s);
-        if (cost_out) {
-            const int slot = e % kCostHist;
-            if (c->p.schedule == PTSNE_SCHED_BATCHED) CK(launch_cost_final(c, c->cost_hist + 2 * slot, s));
-            else CK(launch_cost(c, c->cost_hist + 2 * slot, s));
-            if (slot == kCostHist - 1 || e == epochs - 1)
-                CK(cudaMemcpyAsync(cost_out + 2 * (int64_t)(e - slot), c->cost_hist, sizeof(double) * 2 * (slot + 1),
-                                   cudaMemcpyDeviceToHost, s));
-        }
+        if (want_cost && (slot == kCostHist - 1 || e == epochs - 1))
+            CK(cudaMemcpyAsync(cost_out + 2 * (int64_t)(e - slot), c->cost_hist, sizeof(double) * 2 * (slot + 1),
+                               cudaMemcpyDeviceToHost, s));
         if (c->profiling) {
             CK(cudaEventRecord(c->ev[PTSNE_N_STAGES], s));
             CK(cudaEventSynchronize(c->ev[PTSNE_N_STAGES]));
             for (int k = 0; k < PTSNE_N_STAGES; ++k) {
-                if (k == PTSNE_STAGE_COST && !cost_out) continue;
+                if (k == PTSNE_STAGE_COST && !want_cost) continue;
                 float ms = 0.f;
                 CK(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
                 c->stage_ms[k] += ms;

@@ -182,6 +182,18 @@ struct ptsne_ctx {
     size_t ws_bytes = 0;
     std::string err;
 
+    // graph-captured epoch of ptsne_run: it reads the partition from perm_cur
+    // and leaves the epoch's cost in cost_cur, so one graph serves every epoch
+    int32_t* perm_cur = nullptr;       // n
+    double* cost_cur = nullptr;        // 2
+    cudaStream_t cap_stream = nullptr; // private stream the epoch is captured on
+    cudaGraphExec_t graph = nullptr;
+    const float* graph_X = nullptr;
+    const float* graph_Y = nullptr;
+    int graph_cost = -1;
+    ptsne::IterTune graph_tune{};
+    long long graph_launches = 0;      // kernels per replay
+
     // tracing: kernels enqueued, and per-stage event timing of ptsne_run
     mutable long long launches = 0;
     bool profiling = false;

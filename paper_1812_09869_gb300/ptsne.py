@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("use_gains", C.c_int32),
         ("precision", C.c_int32),
         ("schedule", C.c_int32),
+        ("use_graph", C.c_int32),
     ]
 
 
@@ -137,6 +138,7 @@ class Config:
     use_gains: int = 1
     precision: str = "fp32"
     schedule: str = "batched"
+    use_graph: int = 1
 
 
 class Context:
@@ -148,7 +150,7 @@ class Context:
         self._off = np.ascontiguousarray(np.asarray(cfg.offsets, dtype=np.int64))
         p = Params(cfg.n, cfg.d, cfg.out_dim, cfg.perplexity, len(self._off) - 1,
                    self._off.ctypes.data_as(C.POINTER(C.c_int64)), cfg.iters, cfg.lr, cfg.momentum,
-                   cfg.lr_mode, cfg.use_gains, _PRECISION[cfg.precision], _SCHEDULE[cfg.schedule])
+                   cfg.lr_mode, cfg.use_gains, _PRECISION[cfg.precision], _SCHEDULE[cfg.schedule], cfg.use_graph)
         h = C.c_void_p()
         rc = lib().ptsne_create(C.byref(h), C.byref(p))
         if rc != OK:

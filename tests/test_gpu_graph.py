@@ -1,0 +1,75 @@
+"""The graph-captured epoch of ptsne_run against plain launches: same maps,
+same costs, same kernel count, and a new capture whenever an input that the
+graph holds (X, Y, tuning, cost request) changes."""
+import numpy as np
+import pytest
+
+from paper_1812_09869_gb300 import synth
+
+from parity import rel_max
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_09869_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _setup(n=12000, d=24, chunks=7, epochs=2):
+    X, _ = synth.gaussian_mixture(n, d, 9, seed=95, anisotropic=True)
+    off = synth.uniform_chunk_offsets(n, 1000, 2500, seed=96)
+    perms = synth.permutations(n, epochs, seed=97)
+    Y0 = synth.init_gaussian(n, 2, 1e-4, seed=98)
+    return X, off, perms, Y0
+
+
+def _run(dev, X, off, perms, Y0, use_graph, schedule="batched", precision="fp32", Yd=None, tuning=None):
+    from paper_1812_09869_gb300 import ptsne
+    cfg = ptsne.Config(n=X.shape[0], d=X.shape[1], offsets=off, perplexity=30.0, iters=5, schedule=schedule,
+                       precision=precision, use_graph=use_graph)
+    with ptsne.Context(cfg) as ctx:
+        if tuning:
+            ctx.set_tuning(*tuning)
+        Yd = torch.from_numpy(Y0.copy()).to(dev) if Yd is None else Yd
+        cost = np.zeros((perms.shape[0], 2))
+        ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev), perms.shape[0], Yd, cost_out=cost)
+        torch.cuda.synchronize()
+        return Yd.cpu().numpy(), cost, ctx.stats().kernel_launches
+
+
+@pytest.mark.parametrize("schedule,precision", [("batched", "fp32"), ("batched", "bf16_window"),
+                                                ("per_chunk", "fp32")])
+def test_graph_epochs_match_plain_launches(dev, schedule, precision):
+    X, off, perms, Y0 = _setup()
+    Yg, cg, lg = _run(dev, X, off, perms, Y0, 1, schedule, precision)
+    Ye, ce, le = _run(dev, X, off, perms, Y0, 0, schedule, precision)
+    assert rel_max(Yg - Y0, Ye - Y0) <= 1e-4
+    assert np.abs(cg - ce).max() <= 1e-5 * np.abs(ce).max()
+    assert lg == le > 0
+
+
+def test_graph_is_recaptured_when_its_inputs_change(dev):
+    from paper_1812_09869_gb300 import ptsne
+    X, off, perms, Y0 = _setup(epochs=1)
+    cfg = ptsne.Config(n=X.shape[0], d=X.shape[1], offsets=off, perplexity=30.0, iters=5, use_graph=1)
+    Xd, Pd = torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev)
+    with ptsne.Context(cfg) as ctx:
+        outs = []
+        for k, tun in enumerate([None, None, (1, 4, 16)]):
+            if tun:
+                ctx.set_tuning(*tun)
+            Yd = torch.from_numpy(Y0.copy()).to(dev)      # a new Y buffer each time
+            cost = np.zeros((1, 2)) if k != 1 else None    # cost request toggles too
+            ctx.run(Xd, Pd, 1, Yd, cost_out=cost)
+            torch.cuda.synchronize()
+            outs.append(Yd.cpu().numpy())
+    Ye, _, _ = _run(dev, X, off, perms, Y0, 0)
+    for Y in outs:
+        assert rel_max(Y - Y0, Ye - Y0) <= 1e-4
