@@ -98,8 +98,9 @@ typedef struct {
     int32_t schedule;             /* PTSNE_SCHED_* */
     int32_t use_graph;            /* 1: ptsne_run replays each epoch from one captured CUDA
                                      graph (captured on the first call, and again whenever
-                                     X, Y, the tuning or the cost request change); 0: plain
-                                     launches.  Off while profiling is on. */
+                                     X, Y, the tuning, profiling or the cost request
+                                     change); 0: plain launches.  Profiling marks are
+                                     captured as event nodes of the graph. */
 } ptsne_params;
 
 typedef struct {

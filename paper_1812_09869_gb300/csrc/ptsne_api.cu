@@ -304,7 +304,10 @@ void ptsne_destroy(ptsne_ctx* c) {
 
 // Record the event that opens stage k (profiling only).
 static void mark(ptsne_ctx* c, int k, cudaStream_t s) {
-    if (c->profiling) cudaEventRecord(c->ev[k], s);
+    if (!c->profiling) return;
+    // inside an epoch capture the record becomes an event node of the graph
+    if (c->capturing) cudaEventRecordWithFlags(c->ev[k], s, cudaEventRecordExternal);
+    else cudaEventRecord(c->ev[k], s);
 }
 
 // Gather (and, for ptsne_run, the chunk maps), then the affinities of every
@@ -394,7 +397,9 @@ static int capture_epoch(ptsne_ctx* c, const float* X, float* Y, bool want_cost)
     if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     const long long l0 = c->launches;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+    c->capturing = true;
     const int st = run_epoch(c, X, c->perm_cur, Y, want_cost, c->cost_cur, c->cap_stream);
+    c->capturing = false;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     c->graph_launches = c->launches - l0;
@@ -414,6 +419,7 @@ static int capture_epoch(ptsne_ctx* c, const float* X, float* Y, bool want_cost)
     c->graph_Y = Y;
     c->graph_cost = want_cost ? 1 : 0;
     c->graph_tune = c->tune;
+    c->graph_prof = c->profiling ? 1 : 0;
     return PTSNE_OK;
 }
 
@@ -501,9 +507,9 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
     cudaStream_t s = as_stream(stream);
     const int64_t n = c->p.n;
     const bool want_cost = cost_out != nullptr;
-    const bool use_graph = c->p.use_graph && !c->profiling;
+    const bool use_graph = c->p.use_graph != 0;
     if (use_graph && (!c->graph || c->graph_X != X || c->graph_Y != Y || c->graph_cost != (int)want_cost ||
-                      !same_tune(c->graph_tune, c->tune))) {
+                      c->graph_prof != (c->profiling ? 1 : 0) || !same_tune(c->graph_tune, c->tune))) {
         const int st = capture_epoch(c, X, Y, want_cost);
         if (st != PTSNE_OK) return st;
     }

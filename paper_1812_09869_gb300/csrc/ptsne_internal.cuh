@@ -191,6 +191,8 @@ struct ptsne_ctx {
     const float* graph_X = nullptr;
     const float* graph_Y = nullptr;
     int graph_cost = -1;
+    int graph_prof = -1;               // profiling marks captured as event nodes
+    bool capturing = false;
     ptsne::IterTune graph_tune{};
     long long graph_launches = 0;      // kernels per replay
 

@@ -73,3 +73,22 @@ def test_graph_is_recaptured_when_its_inputs_change(dev):
     Ye, _, _ = _run(dev, X, off, perms, Y0, 0)
     for Y in outs:
         assert rel_max(Y - Y0, Ye - Y0) <= 1e-4
+
+
+def test_profiled_graph_records_stage_times(dev):
+    from paper_1812_09869_gb300 import ptsne
+    X, off, perms, Y0 = _setup(epochs=2)
+    cfg = ptsne.Config(n=X.shape[0], d=X.shape[1], offsets=off, perplexity=30.0, iters=5, use_graph=1)
+    with ptsne.Context(cfg) as ctx:
+        ctx.set_profiling(True)
+        Yd = torch.from_numpy(Y0.copy()).to(dev)
+        cost = np.zeros((2, 2))
+        ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev), 2, Yd, cost_out=cost)
+        torch.cuda.synchronize()
+        st = ctx.stats()
+    ms = dict(zip(ptsne.STAGES, st.stage_ms))
+    calls = dict(zip(ptsne.STAGES, st.stage_calls))
+    assert calls["iterate"] == 2 and ms["iterate"] > 0 and ms["distances"] > 0 and ms["perplexity"] > 0
+    Ye, ce, _ = _run(dev, X, off, perms, Y0, 0)
+    assert rel_max(Yd.cpu().numpy() - Y0, Ye - Y0) <= 1e-4
+    assert np.abs(cost - ce).max() <= 1e-5 * np.abs(ce).max()
