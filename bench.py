@@ -45,7 +45,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", choices=["fp32", "bf16_window"], default=None,
                     help="distance precision (default: the workload's own)")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 per-chunk comparison")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the comparison of forms (plain FP32, batched, mixed precision, learned)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--tuning", default=None,
@@ -201,6 +202,119 @@ def oracle_sample(w, seconds: float, max_chunks: int = 64):
                       f"iterations + cost each, FP64 C with OpenMP over rows; {spent:.1f} s"}
 
 
+# ----------------------------------------------------------------- forms of the method
+
+def _timed_epochs(ctx, Xd, perm_rows, Y, stream):
+    """Run one epoch per partition row, timing all of them with CUDA events;
+    returns (seconds, avg KL after each epoch)."""
+    import torch
+    kls = []
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    secs = 0.0
+    for pr in perm_rows:
+        cost = np.zeros((1, 2))
+        a.record(stream)
+        ctx.run(Xd, pr, 1, Y, cost_out=cost)
+        b.record(stream)
+        torch.cuda.synchronize()
+        secs += a.elapsed_time(b) / 1000.0
+        kls.append(float(cost[0, 0]))
+    return secs, kls
+
+
+def compare_forms(w, Xd, perms, dev, stream, tuning):
+    """Plain FP32 (per-chunk launches, FP32 SIMT distances, dense P), batched
+    FP32 and batched mixed precision, each running the same two epochs
+    (partitions 0 and 1) from the same start map; the second epoch is timed
+    and the final KL compared."""
+    import torch
+    from paper_1812_09869_gb300 import ptsne
+    kinds = {"plain_fp32": dict(precision="fp32", schedule="per_chunk", use_graph=0),
+             "batched_fp32": dict(precision="fp32", schedule="batched", use_graph=1),
+             "batched_bf16_window": dict(precision="bf16_window", schedule="batched", use_graph=1)}
+    out = {}
+    for name, kw in kinds.items():
+        cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
+                           momentum=w.momentum, **kw)
+        with ptsne.Context(cfg) as c:
+            if kw["schedule"] == "batched":
+                c.set_tuning(*tuning)
+            Y = torch.from_numpy(w.Y0.copy()).to(dev)
+            _timed_epochs(c, Xd, [perms[0]], Y, stream)
+            secs, kls = _timed_epochs(c, Xd, [perms[1]], Y, stream)
+        out[name] = {"value": w.n * w.iters / secs, "unit": UNIT, "ms_per_epoch": secs * 1e3,
+                     "final_kl_after_2_epochs": kls[-1], **kw}
+    base = out["plain_fp32"]
+    for name, r in out.items():
+        r["speedup_vs_plain"] = r["value"] / base["value"]
+        r["kl_rel_diff_vs_plain"] = abs(r["final_kl_after_2_epochs"] - base["final_kl_after_2_epochs"]) / \
+            base["final_kl_after_2_epochs"]
+    return out
+
+
+def learned_form(dev, stream, train_epochs=10, mapper_epochs=20, warm_iters=25, max_warm_epochs=16):
+    """The learned form on the 1M + 1M, D = 50 mixture: ptSNE maps the training
+    half, the mapper is trained on that map and places the held-out half, and
+    ptSNE on the held-out half is run from that placement until it reaches the
+    KL that the full schedule (train_epochs x 100 iterations) from the random
+    start reaches."""
+    import torch
+    from paper_1812_09869_gb300 import mapper as M
+    from paper_1812_09869_gb300 import ptsne, synth
+    w = synth.workload("mapper-1m+1m-d50", epochs=train_epochs)
+    half = w.n // 2
+    Xtr = torch.from_numpy(np.ascontiguousarray(w.X[:half])).to(dev)
+    Xte = torch.from_numpy(np.ascontiguousarray(w.X[half:])).to(dev)
+    perms_tr = torch.from_numpy(w.perms).to(dev)
+    perms_te = torch.from_numpy(synth.permutations(half, max(max_warm_epochs, train_epochs), seed=405)).to(dev)
+
+    def ctx(iters):
+        return ptsne.Context(ptsne.Config(n=half, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=iters,
+                                          lr=w.lr, momentum=w.momentum))
+
+    with ctx(w.iters) as c:
+        Ytr = torch.from_numpy(w.Y0.copy()).to(dev)
+        t_ptsne_tr, kl_tr = _timed_epochs(c, Xtr, [perms_tr[e] for e in range(train_epochs)], Ytr, stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with M.Mapper(w.d, synth.mlp_init(w.d, 2, seed=505), batch=4096) as m:
+        orders = torch.from_numpy(synth.permutations(half, mapper_epochs, seed=605)).to(dev)
+        t0 = time.perf_counter()
+        m.fit_scaler(Ytr)
+        loss = m.train(Xtr, Ytr, orders, mapper_epochs)
+        t_train = time.perf_counter() - t0
+        Ymap = torch.zeros((half, 2), dtype=torch.float32, device=dev)
+        m.infer(Xte, Ymap)   # warm-up
+        a.record(stream)
+        m.infer(Xte, Ymap)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_infer = a.elapsed_time(b) / 1000.0
+    with ctx(w.iters) as c:
+        Yc = torch.from_numpy(synth.init_gaussian(half, 2, 1e-4, seed=705)).to(dev)
+        t_cold, kl_cold = _timed_epochs(c, Xte, [perms_te[e] for e in range(train_epochs)], Yc, stream)
+    target = kl_cold[-1]
+    with ctx(warm_iters) as c:
+        Yw = Ymap.clone()
+        t_warm, kls = 0.0, []
+        for e in range(max_warm_epochs):
+            t, k = _timed_epochs(c, Xte, [perms_te[e]], Yw, stream)
+            t_warm += t
+            kls += k
+            if k[-1] <= target:
+                break
+    reached = kls[-1] <= target
+    return {"workload": "mapper-1m+1m-d50", "mlp": "50-256-256-2 GELU, BF16 tcgen05, AdamW",
+            "train_ptsne": {"epochs": train_epochs, "iters": train_epochs * w.iters, "seconds": t_ptsne_tr,
+                            "final_kl": kl_tr[-1]},
+            "mapper_train": {"epochs": mapper_epochs, "batch": 4096, "seconds": t_train,
+                             "loss_first_last": [float(loss[0]), float(loss[-1])]},
+            "mapper_infer": {"points": half, "seconds": t_infer, "points_per_s": half / t_infer},
+            "cold": {"iters": train_epochs * w.iters, "seconds": t_cold, "final_kl": target},
+            "warm": {"iters": warm_iters * len(kls), "seconds_incl_infer": t_warm + t_infer,
+                     "kl_per_epoch": kls, "reached_cold_kl": reached},
+            "speedup_at_equal_kl": (t_cold / (t_warm + t_infer)) if reached else None}
+
+
 # ----------------------------------------------------------------- our arm
 
 def bench_ours(args, rank, world, local_rank):
@@ -295,25 +409,12 @@ def bench_ours(args, rank, world, local_rank):
     ctx.close()
     del Xh, Ph, Yh
 
-    # plain FP32 GPU form: per-chunk launches, FP32 SIMT distances, full P
-    plain = None
+    # the forms of the method at equal work: same partitions, same start map
+    forms = learned = None
     if not args.no_plain and world == 1:
-        pcfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
-                            momentum=w.momentum, precision="fp32", schedule="per_chunk", use_graph=0)
-        with ptsne.Context(pcfg) as pctx:
-            Yp = torch.from_numpy(w.Y0.copy()).to(dev)
-            pcost = np.zeros((1, 2))
-            pctx.run(Xd, perms[0], 1, Yp, cost_out=pcost)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pctx.run(Xd, perms[1], 1, Yp, cost_out=pcost)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ps = a.elapsed_time(b) / 1000.0
-        plain = {"value": w.n * w.iters / ps, "unit": UNIT, "ms_per_step": ps * 1e3,
-                 "schedule": "per_chunk, plain launches",
-                 "distances": "fp32", "steps": 1, "speedup_of_value": value / (w.n * w.iters / ps),
-                 "final_cost": pcost[0].tolist()}
+        forms = compare_forms(w, Xd, perms, dev, stream, tuning)
+        learned = learned_form(dev, stream)
+    plain = forms["plain_fp32"] if forms else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -333,7 +434,7 @@ def bench_ours(args, rank, world, local_rank):
                    "autotune_ms_per_iter": {f"{t[0]}x{t[1]}x{t[2]}": round(ms, 4) for t, ms in trials},
                    "l2": "inputs larger than L2 (joint P %.1f GB per epoch)" % (4 * float((sizes ** 2).sum()) / 1e9)},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-        "plain_fp32": plain, "stages_ms": stages, "perplexity_search": search, "final_cost": {"avg_kl": final_cost[0], "avg_norm_cost": final_cost[1]},
+        "plain_fp32": plain, "forms": forms, "learned": learned, "stages_ms": stages, "perplexity_search": search, "final_cost": {"avg_kl": final_cost[0], "avg_norm_cost": final_cost[1]},
         "impl": "ours",
     }
     return out

@@ -23,6 +23,10 @@ constexpr float kBig = 1e37f;          // stands for "excluded" (diagonal, tail 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTolFine = 1e-6f;      // |H - ln perp| (nats) accepted from the FP32 search
 constexpr float kTolCoarse = 1e-3f;    // switch to compensated sums below this
+// accepted when the FP32 bracket has collapsed: one ulp of beta then moves H
+// by beta^2 Var(t) 6e-8, so sharp rows cannot get closer in FP32, and the FP64
+// result would round to the same FP32 beta
+constexpr float kTolResolved = 2e-5f;
 constexpr double kTol64 = 1e-9;        // FP64 fallback tolerance
 constexpr int kMaxEval32 = 64;
 constexpr int kMaxEval64 = 200;
@@ -133,10 +137,10 @@ __device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, b
 
 // One row per 128-thread block; thread `tid` holds entries j = 4 tid + 512 q + e.
 template <int VPT>
-__global__ void __launch_bounds__(kGroup, VPT >= 48 ? 3 : (VPT >= 24 ? 4 : 6))
+__global__ void __launch_bounds__(kGroup, VPT >= 48 ? 3 : (VPT >= 16 ? 4 : 6))
 bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, double ln_perp_d,
                     float* __restrict__ beta_out, float* __restrict__ m_out, float* __restrict__ S_out,
-                    DeviceStats* st, const float* beta_init) {
+                    DeviceStats* st, const float* beta_init, int coarse) {
     __shared__ float red[kGroup / 32];
     __shared__ float red2[kGroup / 32][2];
     __shared__ double redd[kGroup / 32];
@@ -196,27 +200,38 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
             }
             bool conv = false;
             RowSums s{};
+            // best compensated evaluation, and the H step one ulp of beta makes there
+            float best_f = INFINITY, best_beta = beta, best_S = 0.f, best_ulp_h = 0.f;
             for (int it = 0; it < kMaxEval32; ++it) {
-                const bool fine = fabsf(f) < kTolCoarse;
+                const bool fine = !coarse && fabsf(f) < kTolCoarse;
                 s = row_sums<VPT>(t, beta, fine, red2, red);
                 ++evals;
                 // H in nats; logf and the division are correctly rounded to ~1 ulp
                 f = (logf(s.S) + beta * (s.T1 / s.S)) - ln_perp;
-                // accept only from a compensated evaluation
-                if (fine && fabsf(f) <= kTolFine) { conv = true; break; }
-                if (f > 0.f) lo = beta; else hi = beta;
                 const float mean = s.T1 / s.S;
                 const float var = fmaxf(s.T2 / s.S - mean * mean, 0.f);
-                const float denom = beta * beta * var;
+                const float denom = beta * beta * var;   // -dH / d ln(beta)
+                if (fine && fabsf(f) < best_f) {
+                    best_f = fabsf(f); best_beta = beta; best_S = s.S; best_ulp_h = denom * 6e-8f;
+                }
+                // accept only from a compensated evaluation (coarse: from any, to 1e-3 nats)
+                if (coarse ? fabsf(f) <= kTolCoarse : (fine && fabsf(f) <= kTolFine)) { conv = true; break; }
+                if (f > 0.f) lo = beta; else hi = beta;
                 float step = denom > 0.f ? f / denom : 0.f;
                 step = fminf(fmaxf(step, -3.f), 3.f);
                 float nb = beta * expf(step);
                 if (!(nb > lo && nb < hi)) nb = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
-                if (nb == beta || (hi - lo) <= 4e-7f * beta) break;  // FP32 stall
+                if (nb == beta || (hi - lo) <= 4e-7f * beta) {   // FP32 bracket collapsed
+                    if (best_f <= fmaxf(kTolResolved, 4.f * best_ulp_h)) {
+                        beta = best_beta; s.S = best_S; f = best_f; conv = true;
+                    }
+                    break;
+                }
                 beta = nb;
             }
             S = s.S;
             herr = fabsf(f);
+            if (coarse) conv = true;   // only brackets the window; never redone in FP64
             if (!conv) {
                 // FP64 redo of the same search on the held (FP32) row
                 fp64 = true;
@@ -259,7 +274,7 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
             if (fp64) atomicAdd(&st->fp64_rows, 1ull);
             if (failed) atomicAdd(&st->failed_rows, 1ull);
             atomicAdd(&st->bisect_evals, (unsigned long long)evals);
-            atomicMax(&st->max_herr_bits, __float_as_uint(herr));
+            if (!coarse) atomicMax(&st->max_herr_bits, __float_as_uint(herr));
         }
         __syncthreads();
     }
@@ -342,25 +357,26 @@ psym_kernel(const float* __restrict__ D, float* __restrict__ P, Layout L, const 
 }
 
 template <int VPT>
-static void launch_group(const ptsne_ctx* c, int64_t r0, int64_t r1, cudaStream_t s, const float* beta_init) {
+static void launch_group(const ptsne_ctx* c, int64_t r0, int64_t r1, cudaStream_t s, const float* beta_init,
+                         int coarse) {
     int64_t blocks = r1 - r0;
     if (blocks > 152 * 32) blocks = 152 * 32;
     bisect_group_kernel<VPT><<<(unsigned)blocks, kGroup, 0, s>>>(c->D, make_layout(c), r0, r1,
                                                                    log(c->p.perplexity), c->beta, c->mrow, c->Srow,
-                                                                   c->dstats, beta_init);
+                                                                   c->dstats, beta_init, coarse);
 }
 
 cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
-                          const float* beta_init) {
+                          const float* beta_init, int coarse) {
     if (row_end <= row_begin) return cudaSuccess;
     const int64_t per = (c->zmax + 4 * kGroup - 1) / (4 * kGroup) * 4;   // values per thread
-    if (per <= 8) launch_group<8>(c, row_begin, row_end, s, beta_init);
-    else if (per <= 16) launch_group<16>(c, row_begin, row_end, s, beta_init);
-    else if (per <= 24) launch_group<24>(c, row_begin, row_end, s, beta_init);
-    else if (per <= 32) launch_group<32>(c, row_begin, row_end, s, beta_init);
-    else if (per <= 40) launch_group<40>(c, row_begin, row_end, s, beta_init);
-    else if (per <= 48) launch_group<48>(c, row_begin, row_end, s, beta_init);
-    else launch_group<64>(c, row_begin, row_end, s, beta_init);
+    if (per <= 8) launch_group<8>(c, row_begin, row_end, s, beta_init, coarse);
+    else if (per <= 16) launch_group<16>(c, row_begin, row_end, s, beta_init, coarse);
+    else if (per <= 24) launch_group<24>(c, row_begin, row_end, s, beta_init, coarse);
+    else if (per <= 32) launch_group<32>(c, row_begin, row_end, s, beta_init, coarse);
+    else if (per <= 40) launch_group<40>(c, row_begin, row_end, s, beta_init, coarse);
+    else if (per <= 48) launch_group<48>(c, row_begin, row_end, s, beta_init, coarse);
+    else launch_group<64>(c, row_begin, row_end, s, beta_init, coarse);
     return launched(c, 1);
 }
 

@@ -188,14 +188,16 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xi, const fl
 // data; the joint-P assembly takes each conditional from its own row.
 //
 // Candidate test.  With E(d) = 4 e sqrt(d) + 4 e^2 + s the bound on |d~ - d|,
-// entry j is a candidate when d~ - E(d~) <= lim_i = T / beta_i + m_i + E(m_i).
+// entry j is a candidate when d~ - E(d~) <= lim_i = T / (0.8 beta~_i) + m_i + E(m_i)
+// (beta~_i from a coarse search on d~, |H - ln perp| <= 1e-3 nats; the 1/0.8
+// widening covers its error).
 // In u = sqrt(d~) this is u^2 - 4 e u - (4 e^2 + s + lim_i) <= 0, i.e.
 // d~ <= (2 e + sqrt(8 e^2 + s + lim_i))^2, one threshold per row (widened by
 // 1e-6 relative to cover its own rounding).
 __global__ void __launch_bounds__(256)
 window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int64_t r0, int64_t r1,
               const float* __restrict__ beta, const float* __restrict__ mrow, const unsigned int* maxnorm,
-              unsigned long long* pairs) {
+              unsigned long long* pairs, int32_t* __restrict__ dense_rows, int* __restrict__ dense_cnt) {
     extern __shared__ float wsm[];   // per warp: one staged row of Xg (dp floats) + 64 candidate slots
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int dp = L.dp;
@@ -219,9 +221,22 @@ window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int
         float dmax = FLT_MAX;
         if (b > 0.f) {
             const float Em = 4.0f * e * sqrtf(fmaxf(m, 0.f)) + 4.0f * e * e + acc_slack;
-            const float lim = kWindowT / b + m + Em;
+            // beta~ comes from a coarse search (|H - ln perp| <= 1e-3): widen by 1/0.8
+            const float lim = kWindowT / (0.8f * b) + m + Em;
             const float u = 2.0f * e + sqrtf(8.0f * e * e + acc_slack + lim);
             dmax = u * u * (1.0f + 1e-6f);
+        }
+        // rows whose window covers at least 1/16 of the chunk go to the tiled
+        // kernel, which recomputes the whole row at a far higher rate
+        int ncand = 0;
+        for (int j0 = 0; j0 < z; j0 += 32) {
+            const int j = j0 + lane;
+            ncand += __popc(__ballot_sync(0xffffffffu, j < z && j != i && Drow[j] <= dmax));
+        }
+        if (ncand * 16 >= z) {
+            if (lane == 0) dense_rows[off + atomicAdd(&dense_cnt[c], 1)] = i;
+            count += (lane == 0) ? (unsigned long long)(z - 1) : 0ull;
+            continue;
         }
         int nbuf = 0;
         for (int j0 = 0; j0 < z; j0 += 32) {
@@ -255,6 +270,85 @@ window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int
     if (lane == 0 && count) atomicAdd(pairs, count);
 }
 
+// Dense window rows: one block per (chunk, 128-column block).  The block's
+// columns x_j are staged transposed in shared memory (all of K when it fits,
+// else 64 dimensions at a time) and every dense row of the chunk is run
+// against them, 8 rows at a time, by direct differences in the same order as
+// exact_d2.  Writes D[i][j] of the dense rows only.
+template <bool kFull>
+__global__ void __launch_bounds__(128)
+window_dense_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, const TileDesc* __restrict__ colblk,
+                    const int32_t* __restrict__ dense_rows, const int* __restrict__ dense_cnt) {
+    extern __shared__ float dsm[];
+    const TileDesc td = colblk[blockIdx.x];
+    const int c = td.chunk;
+    const int cnt = dense_cnt[c];
+    if (cnt == 0) return;
+    const int64_t off = L.off[c];
+    const int z = (int)(L.off[c + 1] - off);
+    const int ld = L.ld[c];
+    const int dp = L.dp;
+    const int tid = threadIdx.x;
+    const int j = td.J * 128 + tid;
+    const bool jv = j < z;
+    const int kc_max = kFull ? dp : 64;
+    float* xjT = dsm;                       // [kc_max][128]
+    float* xi = dsm + (size_t)kc_max * 128; // [8][kc_max]
+    const float* xj_row = Xg + (off + (jv ? j : 0)) * dp;
+    float* Dc = D + L.moff[c];
+    if (kFull) {
+        for (int k = 0; k < dp; k += 4) {
+            const float4 v = jv ? *reinterpret_cast<const float4*>(xj_row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xjT[(k + 0) * 128 + tid] = v.x;
+            xjT[(k + 1) * 128 + tid] = v.y;
+            xjT[(k + 2) * 128 + tid] = v.z;
+            xjT[(k + 3) * 128 + tid] = v.w;
+        }
+    }
+    for (int rg = 0; rg < cnt; rg += 8) {
+        const int R = min(8, cnt - rg);
+        float acc[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+        for (int k0 = 0; k0 < dp; k0 += kc_max) {
+            const int kc = min(kc_max, dp - k0);
+            __syncthreads();   // previous users of xi / xjT are done
+            if (!kFull) {
+                for (int k = 0; k < kc; k += 4) {
+                    const float4 v =
+                        jv ? *reinterpret_cast<const float4*>(xj_row + k0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    xjT[(k + 0) * 128 + tid] = v.x;
+                    xjT[(k + 1) * 128 + tid] = v.y;
+                    xjT[(k + 2) * 128 + tid] = v.z;
+                    xjT[(k + 3) * 128 + tid] = v.w;
+                }
+            }
+            for (int idx = tid; idx < 8 * kc; idx += 128) {
+                const int r = idx / kc, k = idx % kc;
+                xi[r * kc_max + k] = r < R ? Xg[(off + dense_rows[off + rg + r]) * dp + k0 + k] : 0.f;
+            }
+            __syncthreads();
+            for (int k = 0; k < kc; ++k) {
+                const float xv = xjT[k * 128 + tid];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const float t = xi[r * kc_max + k] - xv;
+                    acc[r] = fmaf(t, t, acc[r]);
+                }
+            }
+        }
+        if (jv) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                if (r < R) {
+                    const int i = dense_rows[off + rg + r];
+                    if (i != j) Dc[(int64_t)i * ld + j] = acc[r];
+                }
+            }
+        }
+    }
+}
+
 cudaError_t launch_gather_bf16(const ptsne_ctx* c, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->maxnorm, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
@@ -285,9 +379,26 @@ cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64
     if (e != cudaSuccess) return e;
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    e = cudaMemsetAsync(c->dense_cnt, 0, sizeof(int) * c->p.n_chunks, s);
+    if (e != cudaSuccess) return e;
     window_kernel<<<(unsigned)blocks, 256, smem, s>>>(c->D, c->Xg, make_layout(c), row_begin, row_end, c->beta,
-                                                      c->mrow, c->maxnorm, &c->dstats->window_pairs);
-    return launched(c, 1);
+                                                      c->mrow, c->maxnorm, &c->dstats->window_pairs, c->dense_rows,
+                                                      c->dense_cnt);
+    // column blocks of the chunks these rows belong to
+    const int c0 = c->chunk_of(row_begin), c1 = c->chunk_of(row_end - 1);
+    const int64_t b0 = c->colblk_start[c0], b1 = c->colblk_start[c1 + 1];
+    const bool full = c->dp <= 256;
+    const size_t dsm = full ? (size_t)c->dp * (128 + 8) * sizeof(float) : (size_t)64 * (128 + 8) * sizeof(float);
+    if (full) {
+        e = cudaFuncSetAttribute(window_dense_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        if (e != cudaSuccess) return e;
+        window_dense_kernel<true><<<(unsigned)(b1 - b0), 128, dsm, s>>>(c->D, c->Xg, make_layout(c),
+                                                                        c->d_colblk + b0, c->dense_rows, c->dense_cnt);
+    } else {
+        window_dense_kernel<false><<<(unsigned)(b1 - b0), 128, dsm, s>>>(c->D, c->Xg, make_layout(c),
+                                                                         c->d_colblk + b0, c->dense_rows, c->dense_cnt);
+    }
+    return launched(c, 2);
 }
 
 }  // namespace ptsne

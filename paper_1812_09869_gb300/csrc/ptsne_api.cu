@@ -71,7 +71,7 @@ void free_all(ptsne_ctx* c) {
                     c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
-                    c->perm_cur, c->cost_cur};
+                    c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -183,6 +183,17 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         c->tile_start128[nc] = (int64_t)tiles128.size();
         c->ntiles128 = (int64_t)tiles128.size();
     }
+    // 128-column blocks of each chunk (dense window rows)
+    std::vector<TileDesc> colblk;
+    if (p.precision == PTSNE_PREC_BF16_WINDOW) {
+        c->colblk_start.resize(nc + 1);
+        for (int k = 0; k < nc; ++k) {
+            c->colblk_start[k] = (int64_t)colblk.size();
+            const int nb = (int)((c->off[k + 1] - c->off[k] + 127) / 128);
+            for (int J = 0; J < nb; ++J) colblk.push_back(TileDesc{k, (int16_t)0, (int16_t)J});
+        }
+        c->colblk_start[nc] = (int64_t)colblk.size();
+    }
     // packed symmetric P: 32 x 32 tiles of each chunk in tournament order
     std::vector<TileDesc2> tiles2;
     std::vector<int64_t> ptoff(nc);
@@ -237,6 +248,9 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         AL(c->xnorm, n);
         AL(c->d_tiles128, c->ntiles128);
         AL(c->maxnorm, 1);
+        AL(c->dense_rows, n);
+        AL(c->dense_cnt, nc);
+        AL(c->d_colblk, (int64_t)colblk.size());
     }
     AL(c->D, m);
     if (p.schedule == PTSNE_SCHED_BATCHED) {
@@ -278,6 +292,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (e == cudaSuccess) e = up(c->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size());
     if (e == cudaSuccess && c->ntiles128)
         e = up(c->d_tiles128, tiles128.data(), sizeof(TileDesc) * tiles128.size());
+    if (e == cudaSuccess && !colblk.empty()) e = up(c->d_colblk, colblk.data(), sizeof(TileDesc) * colblk.size());
     if (e == cudaSuccess && c->ntiles2) {
         e = up(c->d_ptile_off, ptoff.data(), sizeof(int64_t) * nc);
         if (e == cudaSuccess) e = up(c->d_tiles2, tiles2.data(), sizeof(TileDesc2) * tiles2.size());
@@ -327,7 +342,8 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cu
         if (mixed) CK(launch_dist_bf16(c, 0, c->ntiles128, s));
         else CK(launch_dist_fp32(c, 0, c->ntiles, s));
         mark(c, PTSNE_STAGE_PERPLEXITY, s);
-        CK(launch_bisect(c, 0, c->p.n, s));
+        // mixed precision: a coarse search on d~ only places the windows
+        CK(launch_bisect(c, 0, c->p.n, s, nullptr, mixed ? 1 : 0));
         if (mixed) {
             // FP32 distances inside each row's window, then the search again from beta~
             CK(launch_window_recompute(c, 0, c->p.n, s));
@@ -339,7 +355,7 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cu
         for (int k = 0; k < c->p.n_chunks; ++k) {
             if (mixed) CK(launch_dist_bf16(c, c->tile_start128[k], c->tile_start128[k + 1], s));
             else CK(launch_dist_fp32(c, c->tile_start[k], c->tile_start[k + 1], s));
-            CK(launch_bisect(c, c->off[k], c->off[k + 1], s));
+            CK(launch_bisect(c, c->off[k], c->off[k + 1], s, nullptr, mixed ? 1 : 0));
             if (mixed) {
                 CK(launch_window_recompute(c, c->off[k], c->off[k + 1], s));
                 CK(launch_bisect(c, c->off[k], c->off[k + 1], s, c->beta));

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -148,6 +149,15 @@ struct ptsne_ctx {
     std::vector<int64_t> tile_start128;
     ptsne::TileDesc* d_tiles128 = nullptr;
     unsigned int* maxnorm = nullptr;   // largest |x~| (float bits), for the window bound
+    // window rows recomputed whole: per chunk, a list of rows and its length,
+    // and the chunks' 128-column blocks (TileDesc{chunk, 0, block})
+    int32_t* dense_rows = nullptr;     // n (chunk c's list starts at off[c])
+    int* dense_cnt = nullptr;          // n_chunks
+    ptsne::TileDesc* d_colblk = nullptr;
+    std::vector<int64_t> colblk_start; // n_chunks + 1
+    int chunk_of(int64_t r) const {     // chunk holding row r (off is sorted)
+        return (int)(std::upper_bound(off.begin(), off.end(), r) - off.begin()) - 1;
+    }
 
     // workspace
     float* Xg = nullptr;               // n x dp gathered X (permuted order)
@@ -222,7 +232,7 @@ cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t til
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
 // beta_init (optional): start each row's search from this beta instead of 1 / mean(d - m)
 cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
-                          const float* beta_init = nullptr);
+                          const float* beta_init = nullptr, int coarse = 0);
 cudaError_t launch_gather_bf16(const ptsne_ctx* c, cudaStream_t s);
 cudaError_t launch_psym(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 
