@@ -140,7 +140,8 @@ template <int VPT>
 __global__ void __launch_bounds__(kGroup, VPT >= 48 ? 3 : (VPT >= 16 ? 4 : 6))
 bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, double ln_perp_d,
                     float* __restrict__ beta_out, float* __restrict__ m_out, float* __restrict__ S_out,
-                    DeviceStats* st, const float* beta_init, int coarse) {
+                    DeviceStats* st, const float* beta_init, int coarse, const unsigned int* maxnorm,
+                    int32_t* __restrict__ dense_rows, int* __restrict__ dense_cnt, uint8_t* __restrict__ row_dense) {
     __shared__ float red[kGroup / 32];
     __shared__ float red2[kGroup / 32][2];
     __shared__ double redd[kGroup / 32];
@@ -267,6 +268,20 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                 failed = herr > kTolFine;
             }
         }
+        if (coarse) {
+            // window placement for the mixed-precision recompute: rows whose
+            // window covers >= 1/16 of the chunk are listed for the tiled kernel
+            const float dmax = window_dmax(beta, mn, __uint_as_float(*maxnorm), L.dp);
+            float ncand = 0.f;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) ncand += (t[k] < kBig && t[k] + mn <= dmax) ? 1.f : 0.f;
+            ncand = group_sum(ncand, red);
+            if (tid == 0) {
+                const bool dense = ncand * 16.f >= (float)z;
+                if (dense) dense_rows[off + atomicAdd(&dense_cnt[c], 1)] = i;
+                row_dense[r] = dense ? 1 : 0;
+            }
+        }
         if (tid == 0) {
             beta_out[r] = beta;
             m_out[r] = mn;
@@ -363,12 +378,19 @@ static void launch_group(const ptsne_ctx* c, int64_t r0, int64_t r1, cudaStream_
     if (blocks > 152 * 32) blocks = 152 * 32;
     bisect_group_kernel<VPT><<<(unsigned)blocks, kGroup, 0, s>>>(c->D, make_layout(c), r0, r1,
                                                                    log(c->p.perplexity), c->beta, c->mrow, c->Srow,
-                                                                   c->dstats, beta_init, coarse);
+                                                                   c->dstats, beta_init, coarse, c->maxnorm,
+                                                                   c->dense_rows, c->dense_cnt, c->row_dense);
 }
 
 cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
                           const float* beta_init, int coarse) {
     if (row_end <= row_begin) return cudaSuccess;
+    if (coarse) {   // the coarse search lists the dense window rows of its chunks
+        if (!c->dense_cnt) return cudaErrorInvalidValue;
+        const int c0 = c->chunk_of(row_begin), c1 = c->chunk_of(row_end - 1);
+        const cudaError_t e = cudaMemsetAsync(c->dense_cnt + c0, 0, sizeof(int) * (size_t)(c1 - c0 + 1), s);
+        if (e != cudaSuccess) return e;
+    }
     const int64_t per = (c->zmax + 4 * kGroup - 1) / (4 * kGroup) * 4;   // values per thread
     if (per <= 8) launch_group<8>(c, row_begin, row_end, s, beta_init, coarse);
     else if (per <= 16) launch_group<16>(c, row_begin, row_end, s, beta_init, coarse);

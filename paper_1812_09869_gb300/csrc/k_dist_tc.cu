@@ -48,10 +48,6 @@ bool make_bf16_tmap(CUtensorMap* out, const void* base, uint64_t rows, uint64_t 
 }
 }  // namespace tc
 
-namespace {
-constexpr float kWindowT = 25.0f;      // e^-25 ~ 1.4e-11 of the row's largest weight
-constexpr float kBf16U = 0.00390625f;  // 2^-8
-}
 
 // Xg (FP32, permuted) -> Xb (BF16, K padded to kp with zeros) and |x~|^2;
 // also the largest |x~| (as float bits) for the window bound.
@@ -182,62 +178,36 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xi, const fl
     return s;
 }
 
-// Window recompute: one warp per row; candidates are compacted with a ballot
-// into a per-warp list and recomputed 32 at a time, one per lane.  Only the
-// row's own entries (i, j) are rewritten, so rows never write each other's
-// data; the joint-P assembly takes each conditional from its own row.
-//
-// Candidate test.  With E(d) = 4 e sqrt(d) + 4 e^2 + s the bound on |d~ - d|,
-// entry j is a candidate when d~ - E(d~) <= lim_i = T / (0.8 beta~_i) + m_i + E(m_i)
-// (beta~_i from a coarse search on d~, |H - ln perp| <= 1e-3 nats; the 1/0.8
-// widening covers its error).
-// In u = sqrt(d~) this is u^2 - 4 e u - (4 e^2 + s + lim_i) <= 0, i.e.
-// d~ <= (2 e + sqrt(8 e^2 + s + lim_i))^2, one threshold per row (widened by
-// 1e-6 relative to cover its own rounding).
+// Window recompute of the sparse rows (the coarse search has listed the rows
+// whose window covers >= 1/16 of the chunk for the tiled kernel below): one
+// warp per row; candidates d~_ij <= window_dmax(...) are compacted with a
+// ballot into a per-warp list and recomputed 32 at a time, one per lane, by
+// direct differences.  Only the row's own entries (i, j) are rewritten.
 __global__ void __launch_bounds__(256)
 window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int64_t r0, int64_t r1,
               const float* __restrict__ beta, const float* __restrict__ mrow, const unsigned int* maxnorm,
-              unsigned long long* pairs, int32_t* __restrict__ dense_rows, int* __restrict__ dense_cnt) {
+              unsigned long long* pairs, const uint8_t* __restrict__ row_dense) {
     extern __shared__ float wsm[];   // per warp: one staged row of Xg (dp floats) + 64 candidate slots
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int dp = L.dp;
     float* xi = wsm + (size_t)warp * (dp + 64);
     int* cand = reinterpret_cast<int*>(xi + dp);
     const float xmax = __uint_as_float(*maxnorm);
-    const float e = kBf16U * xmax * 1.01f;
-    // FP32 accumulation of the Gram entries and norms: ~dp * 2^-24 of |x|^2, times 4 for margin
-    const float acc_slack = 4.0f * (float)dp * 6.0e-8f * xmax * xmax;
     unsigned long long count = 0;
     for (int64_t r = r0 + (int64_t)blockIdx.x * nw + warp; r < r1; r += (int64_t)gridDim.x * nw) {
         const int c = L.chunk_of_row[r];
         const int64_t off = L.off[c];
         const int z = (int)(L.off[c + 1] - off);
+        if (row_dense[r]) {   // recomputed whole by window_dense_kernel
+            count += (lane == 0) ? (unsigned long long)(z - 1) : 0ull;
+            continue;
+        }
         const int i = (int)(r - off);
         const int ld = L.ld[c];
         float* Drow = D + L.moff[c] + (int64_t)i * ld;
         for (int k = lane; k < dp; k += 32) xi[k] = Xg[r * dp + k];
         __syncwarp();
-        const float b = beta[r], m = mrow[r];
-        float dmax = FLT_MAX;
-        if (b > 0.f) {
-            const float Em = 4.0f * e * sqrtf(fmaxf(m, 0.f)) + 4.0f * e * e + acc_slack;
-            // beta~ comes from a coarse search (|H - ln perp| <= 1e-3): widen by 1/0.8
-            const float lim = kWindowT / (0.8f * b) + m + Em;
-            const float u = 2.0f * e + sqrtf(8.0f * e * e + acc_slack + lim);
-            dmax = u * u * (1.0f + 1e-6f);
-        }
-        // rows whose window covers at least 1/16 of the chunk go to the tiled
-        // kernel, which recomputes the whole row at a far higher rate
-        int ncand = 0;
-        for (int j0 = 0; j0 < z; j0 += 32) {
-            const int j = j0 + lane;
-            ncand += __popc(__ballot_sync(0xffffffffu, j < z && j != i && Drow[j] <= dmax));
-        }
-        if (ncand * 16 >= z) {
-            if (lane == 0) dense_rows[off + atomicAdd(&dense_cnt[c], 1)] = i;
-            count += (lane == 0) ? (unsigned long long)(z - 1) : 0ull;
-            continue;
-        }
+        const float dmax = window_dmax(beta[r], mrow[r], xmax, dp);
         int nbuf = 0;
         for (int j0 = 0; j0 < z; j0 += 32) {
             const int j = j0 + lane;
@@ -268,6 +238,94 @@ window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int
     }
     count = __reduce_add_sync(0xffffffffu, (unsigned)count);
     if (lane == 0 && count) atomicAdd(pairs, count);
+}
+
+// Dense window rows, D <= KR (padded) dimensions: as window_dense_kernel, with
+// the block's column x_j held in registers and 8 dense rows staged k-major in
+// shared memory, two rows per packed f32x2 instruction (IEEE per lane, the
+// same operation order as exact_d2, so the results are identical).
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2x v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2x fma2x(f2x a, f2x b, f2x c) {
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2x sub2x(f2x a, f2x b) {
+    f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <int KR>
+__global__ void __launch_bounds__(128)
+window_dense_reg_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L,
+                        const TileDesc* __restrict__ colblk, const int32_t* __restrict__ dense_rows,
+                        const int* __restrict__ dense_cnt) {
+    __shared__ __align__(16) float xiT[KR][8];
+    const TileDesc td = colblk[blockIdx.x];
+    const int c = td.chunk;
+    const int cnt = dense_cnt[c];
+    if (cnt == 0) return;
+    const int64_t off = L.off[c];
+    const int z = (int)(L.off[c + 1] - off);
+    const int ld = L.ld[c];
+    const int dp = L.dp;
+    const int tid = threadIdx.x;
+    const int j = td.J * 128 + tid;
+    const bool jv = j < z;
+    float xj[KR];
+    const float* xj_row = Xg + (off + (jv ? j : 0)) * dp;
+#pragma unroll
+    for (int k = 0; k < KR; k += 4) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jv && k < dp) v = *reinterpret_cast<const float4*>(xj_row + k);
+        xj[k] = v.x; xj[k + 1] = v.y; xj[k + 2] = v.z; xj[k + 3] = v.w;
+    }
+    float* Dc = D + L.moff[c];
+    for (int rg = 0; rg < cnt; rg += 8) {
+        const int R = min(8, cnt - rg);
+        __syncthreads();   // previous group's reads of xiT are done
+        for (int idx = tid; idx < 8 * KR; idx += 128) {
+            const int r = idx & 7, k = idx >> 3;
+            xiT[k][r] = (r < R && k < dp) ? Xg[(off + dense_rows[off + rg + r]) * dp + k] : 0.f;
+        }
+        __syncthreads();
+        f2x acc[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(&xiT[k][0]);
+            const float4 b = *reinterpret_cast<const float4*>(&xiT[k][4]);
+            const f2x XJ = pk2(xj[k], xj[k]);
+            f2x t = sub2x(pk2(a.x, a.y), XJ);
+            acc[0] = fma2x(t, t, acc[0]);
+            t = sub2x(pk2(a.z, a.w), XJ);
+            acc[1] = fma2x(t, t, acc[1]);
+            t = sub2x(pk2(b.x, b.y), XJ);
+            acc[2] = fma2x(t, t, acc[2]);
+            t = sub2x(pk2(b.z, b.w), XJ);
+            acc[3] = fma2x(t, t, acc[3]);
+        }
+        if (jv) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) upk2(acc[q], v[2 * q], v[2 * q + 1]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                if (r < R) {
+                    const int i = dense_rows[off + rg + r];
+                    if (i != j) Dc[(int64_t)i * ld + j] = v[r];
+                }
+            }
+        }
+    }
 }
 
 // Dense window rows: one block per (chunk, 128-column block).  The block's
@@ -374,29 +432,30 @@ cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t til
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s) {
     const int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
+    // sparse rows (the coarse search has listed the dense ones)
     const size_t smem = (size_t)8 * (c->dp + 64) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    e = cudaMemsetAsync(c->dense_cnt, 0, sizeof(int) * c->p.n_chunks, s);
-    if (e != cudaSuccess) return e;
     window_kernel<<<(unsigned)blocks, 256, smem, s>>>(c->D, c->Xg, make_layout(c), row_begin, row_end, c->beta,
-                                                      c->mrow, c->maxnorm, &c->dstats->window_pairs, c->dense_rows,
-                                                      c->dense_cnt);
-    // column blocks of the chunks these rows belong to
+                                                      c->mrow, c->maxnorm, &c->dstats->window_pairs, c->row_dense);
+    // dense rows: the column blocks of the chunks these rows belong to
     const int c0 = c->chunk_of(row_begin), c1 = c->chunk_of(row_end - 1);
     const int64_t b0 = c->colblk_start[c0], b1 = c->colblk_start[c1 + 1];
-    const bool full = c->dp <= 256;
-    const size_t dsm = full ? (size_t)c->dp * (128 + 8) * sizeof(float) : (size_t)64 * (128 + 8) * sizeof(float);
-    if (full) {
+    const unsigned nb = (unsigned)(b1 - b0);
+    const Layout L = make_layout(c);
+    if (c->dp <= 16) window_dense_reg_kernel<16><<<nb, 128, 0, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
+    else if (c->dp <= 32) window_dense_reg_kernel<32><<<nb, 128, 0, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
+    else if (c->dp <= 64) window_dense_reg_kernel<64><<<nb, 128, 0, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
+    else if (c->dp <= 256) {
+        const size_t dsm = (size_t)c->dp * (128 + 8) * sizeof(float);
         e = cudaFuncSetAttribute(window_dense_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
         if (e != cudaSuccess) return e;
-        window_dense_kernel<true><<<(unsigned)(b1 - b0), 128, dsm, s>>>(c->D, c->Xg, make_layout(c),
-                                                                        c->d_colblk + b0, c->dense_rows, c->dense_cnt);
+        window_dense_kernel<true><<<nb, 128, dsm, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
     } else {
-        window_dense_kernel<false><<<(unsigned)(b1 - b0), 128, dsm, s>>>(c->D, c->Xg, make_layout(c),
-                                                                         c->d_colblk + b0, c->dense_rows, c->dense_cnt);
+        const size_t dsm = (size_t)64 * (128 + 8) * sizeof(float);
+        window_dense_kernel<false><<<nb, 128, dsm, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
     }
     return launched(c, 2);
 }

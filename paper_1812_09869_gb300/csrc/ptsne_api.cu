@@ -71,7 +71,7 @@ void free_all(ptsne_ctx* c) {
                     c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
-                    c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk};
+                    c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -250,6 +250,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         AL(c->maxnorm, 1);
         AL(c->dense_rows, n);
         AL(c->dense_cnt, nc);
+        AL(c->row_dense, n);
         AL(c->d_colblk, (int64_t)colblk.size());
     }
     AL(c->D, m);

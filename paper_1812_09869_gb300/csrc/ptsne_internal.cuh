@@ -153,6 +153,7 @@ struct ptsne_ctx {
     // and the chunks' 128-column blocks (TileDesc{chunk, 0, block})
     int32_t* dense_rows = nullptr;     // n (chunk c's list starts at off[c])
     int* dense_cnt = nullptr;          // n_chunks
+    uint8_t* row_dense = nullptr;      // n: 1 = row listed in dense_rows (set by the coarse search)
     ptsne::TileDesc* d_colblk = nullptr;
     std::vector<int64_t> colblk_start; // n_chunks + 1
     int chunk_of(int64_t r) const {     // chunk holding row r (off is sorted)
@@ -320,6 +321,26 @@ __device__ __forceinline__ void update_point(float* y, float* vel, float* gains,
         vel[k] = v;
         y[k] += v;
     }
+}
+
+// Window of the mixed-precision distances: the largest d~ whose true distance
+// can still carry weight exp(-beta (d - m)) >= exp(-T) of the row's largest.
+// With u = 2^-8 (BF16 unit roundoff), e = u max|x| (1.01 margin) and the FP32
+// accumulation slack s, |d - d~| <= E(d~) = 4 e sqrt(d~) + 4 e^2 + s; entry j
+// is a candidate when d~ - E(d~) <= lim = T / (0.8 beta~) + m~ + E(m~), i.e.
+// (solving in sqrt d~) d~ <= (2e + sqrt(8 e^2 + s + lim))^2, widened by 1e-6
+// relative.  beta~ comes from a coarse search (|H - ln perp| <= 1e-3 nats);
+// the 1/0.8 widening covers its error.  FLT_MAX (everything) when beta~ <= 0.
+constexpr float kWindowT = 25.0f;      // e^-25 ~ 1.4e-11 of the row's largest weight
+constexpr float kBf16U = 0.00390625f;  // 2^-8
+__device__ __forceinline__ float window_dmax(float beta, float m, float xmax, int dp) {
+    if (!(beta > 0.f)) return 3.0e38f;
+    const float e = kBf16U * xmax * 1.01f;
+    const float slack = 4.0f * (float)dp * 6.0e-8f * xmax * xmax;
+    const float Em = 4.0f * e * sqrtf(fmaxf(m, 0.f)) + 4.0f * e * e + slack;
+    const float lim = kWindowT / (0.8f * beta) + m + Em;
+    const float u = 2.0f * e + sqrtf(8.0f * e * e + slack + lim);
+    return u * u * (1.0f + 1e-6f);
 }
 
 // Learning rate: fixed, or Eq. 13 from the extent [ymin, ymax] of the chunk's map.
