@@ -274,23 +274,25 @@ __device__ __forceinline__ void cost_task(const float* map, int zcap, int own, i
 // Copy a warp's share of a staged tile into registers:
 // row-wise (lane = tile row) for tile columns [c0, c0 + N), or
 // column-wise (lane = tile column) for tile rows [r0, r0 + N).
-template <int N>
-__device__ __forceinline__ void tile_row_share(const float* tile, int lane, int c0, float (&pv)[N]) {
+// The share's first column (row) C0 (R0) is a compile-time constant, so the
+// swizzled offsets fold into a few lane constants and immediate offsets.
+template <int N, int C0>
+__device__ __forceinline__ void tile_row_share(const float* tile, int lane, float (&pv)[N]) {
     const float* trow = tile + lane * kPT;
     const int l7 = lane & 7;
 #pragma unroll
     for (int m = 0; m < N / 4; ++m) {
-        const int c4 = (c0 >> 2) + m;
+        const int c4 = (C0 >> 2) + m;
         const float4 v = *reinterpret_cast<const float4*>(trow + ((c4 ^ l7) << 2));
         pv[4 * m] = v.x; pv[4 * m + 1] = v.y; pv[4 * m + 2] = v.z; pv[4 * m + 3] = v.w;
     }
 }
-template <int N>
-__device__ __forceinline__ void tile_col_share(const float* tile, int lane, int r0, float (&pv)[N]) {
+template <int N, int R0>
+__device__ __forceinline__ void tile_col_share(const float* tile, int lane, float (&pv)[N]) {
     const int hi = lane >> 2, lo = lane & 3;
 #pragma unroll
     for (int t = 0; t < N; ++t) {
-        const int r = r0 + t;
+        const int r = R0 + t;
         pv[t] = tile[r * kPT + (((hi ^ (r & 7)) << 2) | lo)];
     }
 }
@@ -351,13 +353,14 @@ struct KSum {
 // One warp's share of a tile.  G = 2: one warp takes rows of a (tile
 // row-wise), the other rows of b (tile column-wise); G = 4 halves each.  A
 // diagonal tile (a == b) is read row-wise only, its columns split G ways.
-template <int OD, int N>
+template <int OD, int N, int START>
 __device__ __forceinline__ void consume_share(const float* tile, const float* map, int zcap, int z, int a, int b,
-                                              int lane, int colwise, int start, bool cost, float* acc,
+                                              int lane, int colwise, bool cost, float* acc,
                                               uint32_t empty_bar, KSum (&part)[4], bool diag_owner) {
+    constexpr int start = START;
     float pv[N];
-    if (colwise) tile_col_share<N>(tile, lane, start, pv);
-    else tile_row_share<N>(tile, lane, start, pv);
+    if (colwise) tile_col_share<N, START>(tile, lane, pv);
+    else tile_row_share<N, START>(tile, lane, pv);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty_bar);   // the buffer is free again
     const int own = (colwise ? b : a) * kPT + lane;
@@ -523,15 +526,23 @@ __global__ void __launch_bounds__(544, 1) iterate_kernel(IterArgs A) {
                         // of column `lane` drops that row's w_ii = 1
                         const int w = kPT / G, c0 = sub * w;
                         const bool own_diag = lane >= c0 && lane < c0 + w;
-                        if (G == 2) consume_share<OD, 16>(tile, map, zcap, z, a, b, lane, 0, c0, cost, acc, ebar, part, own_diag);
-                        else consume_share<OD, 8>(tile, map, zcap, z, a, b, lane, 0, c0, cost, acc, ebar, part, own_diag);
+                        if (G == 2) {
+                            if (sub == 0) consume_share<OD, 16, 0>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else consume_share<OD, 16, 16>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                        } else {
+                            if (sub == 0) consume_share<OD, 8, 0>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else if (sub == 1) consume_share<OD, 8, 8>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else if (sub == 2) consume_share<OD, 8, 16>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else consume_share<OD, 8, 24>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                        }
                     } else {
                         // the slot's warps swap directions on alternate tiles, so the
                         // slower column-wise read is shared evenly between them
                         const int h = G / 2;                        // warps per direction
-                        const int colwise = (sub >= h) ^ (kth & 1), start = (sub % h) * (kPT / h);
-                        if (G == 2) consume_share<OD, 32>(tile, map, zcap, z, a, b, lane, colwise, start, cost, acc, ebar, part, false);
-                        else consume_share<OD, 16>(tile, map, zcap, z, a, b, lane, colwise, start, cost, acc, ebar, part, false);
+                        const int colwise = (sub >= h) ^ (kth & 1);
+                        if (G == 2) consume_share<OD, 32, 0>(tile, map, zcap, z, a, b, lane, colwise, cost, acc, ebar, part, false);
+                        else if (sub % 2 == 0) consume_share<OD, 16, 0>(tile, map, zcap, z, a, b, lane, colwise, cost, acc, ebar, part, false);
+                        else consume_share<OD, 16, 16>(tile, map, zcap, z, a, b, lane, colwise, cost, acc, ebar, part, false);
                     }
                 }
             }
