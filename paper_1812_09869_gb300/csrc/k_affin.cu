@@ -23,10 +23,12 @@ constexpr float kBig = 1e37f;          // stands for "excluded" (diagonal, tail 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTolFine = 1e-6f;      // |H - ln perp| (nats) accepted from the FP32 search
 constexpr float kTolCoarse = 1e-3f;    // switch to compensated sums below this
-// accepted when the FP32 bracket has collapsed: one ulp of beta then moves H
-// by beta^2 Var(t) 6e-8, so sharp rows cannot get closer in FP32, and the FP64
-// result would round to the same FP32 beta
-constexpr float kTolResolved = 2e-5f;
+// The entropy error f maps to a relative beta error f / (beta^2 Var(t))
+// (dH / d ln beta = -beta^2 Var(t)), and a relative beta error e moves an
+// entry p ~ exp(-beta t) by e beta t relative: entries down to 1e-6 of the
+// row's largest (beta t ~ 14) stay within ~4e-5 when e <= 3e-6.  So a row is
+// accepted when |f| <= min(kTolFine, kTolBeta beta^2 Var(t)).
+constexpr float kTolBeta = 3e-6f;
 constexpr double kTol64 = 1e-9;        // FP64 fallback tolerance
 constexpr int kMaxEval32 = 64;
 constexpr int kMaxEval64 = 200;
@@ -216,16 +218,20 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                     best_f = fabsf(f); best_beta = beta; best_S = s.S; best_ulp_h = denom * 6e-8f;
                 }
                 // accept only from a compensated evaluation (coarse: from any, to 1e-3 nats)
-                if (coarse ? fabsf(f) <= kTolCoarse : (fine && fabsf(f) <= kTolFine)) { conv = true; break; }
+                if (coarse ? fabsf(f) <= kTolCoarse : (fine && fabsf(f) <= fminf(kTolFine, kTolBeta * denom))) {
+                    conv = true;
+                    break;
+                }
                 if (f > 0.f) lo = beta; else hi = beta;
                 float step = denom > 0.f ? f / denom : 0.f;
                 step = fminf(fmaxf(step, -3.f), 3.f);
                 float nb = beta * expf(step);
                 if (!(nb > lo && nb < hi)) nb = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
                 if (nb == beta || (hi - lo) <= 4e-7f * beta) {   // FP32 bracket collapsed
-                    if (best_f <= fmaxf(kTolResolved, 4.f * best_ulp_h)) {
-                        beta = best_beta; s.S = best_S; f = best_f; conv = true;
-                    }
+                    // sharp rows: when the error is within 4 ulps of beta's effect on H,
+                    // beta is resolved as finely as FP32 allows and an FP64 root would
+                    // round to it; otherwise the row is redone in FP64
+                    if (best_f <= 4.f * best_ulp_h) { beta = best_beta; s.S = best_S; f = best_f; conv = true; }
                     break;
                 }
                 beta = nb;
