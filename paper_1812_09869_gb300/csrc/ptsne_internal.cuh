@@ -115,9 +115,9 @@ struct Optim {                     // optimiser settings
 
 // Launch shape of the batched iteration kernel (chosen by the autotuner).
 struct IterTune {
-    int cluster = 1;               // blocks sharing one chunk (1, 2 or 4)
+    int cluster = 2;               // blocks sharing one chunk (1, 2 or 4)
     int group = 2;                 // consumer warps per tile (2 or 4)
-    int consumer_warps = 16;       // consumer warps per block (multiple of group, <= 16)
+    int consumer_warps = 20;       // consumer warps per block (multiple of group, <= 20)
 };
 
 }  // namespace ptsne

@@ -225,7 +225,7 @@ def test_batched_iterations_equal_plain_per_chunk_form(dev):
 
 
 # every launch shape of the batched kernel: blocks per chunk (cluster) x warps per tile (group)
-TUNINGS = [(1, 2, 16), (1, 4, 16), (2, 4, 16), (4, 4, 12), (2, 2, 16), (4, 2, 8), (1, 4, 4)]
+TUNINGS = [(1, 2, 16), (1, 4, 16), (2, 4, 16), (4, 4, 12), (2, 2, 16), (4, 2, 8), (1, 4, 4), (2, 2, 20), (1, 4, 20), (4, 2, 20)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
