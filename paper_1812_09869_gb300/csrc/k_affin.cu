@@ -43,24 +43,6 @@ __device__ __forceinline__ void two_sum_add(float& s, float& c, float v, float c
     c = c + cv + e;
 }
 
-// Sum over the 128-thread group of per-thread (s, c) pairs, FP32 accuracy
-// independently of the order; every thread receives the same value.
-__device__ __forceinline__ float group_sum_comp(float s, float c, float (*red)[2]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float so = __shfl_xor_sync(0xffffffffu, s, o);
-        const float co = __shfl_xor_sync(0xffffffffu, c, o);
-        two_sum_add(s, c, so, co);
-    }
-    if (lane == 0) { red[warp][0] = s; red[warp][1] = c; }
-    __syncthreads();
-    float a = red[0][0], ac = red[0][1];
-#pragma unroll
-    for (int w = 1; w < kGroup / 32; ++w) two_sum_add(a, ac, red[w][0], red[w][1]);
-    __syncthreads();
-    return a + ac;
-}
 __device__ __forceinline__ float group_sum(float v, float* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_sum(v);
@@ -99,30 +81,77 @@ struct RowSums {
     float S, T1, T2;
 };
 
-// S, T1, T2 of the row held in registers (excluded entries are kBig: e = 0).
-template <int VPT>
-__device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, bool fine, float (*red2)[2],
-                                            float* red) {
-    const float b2 = beta * kLog2e;
+// S, T1 and T2 summed over the 128-thread group in one pass (one shared-memory
+// round, two barriers); with comp, S and T1 carry their rounding errors
+// (s + c pairs combined by error-free two-sums).  Every thread gets the sums.
+__device__ __forceinline__ RowSums group_sums3(float S, float cS, float T1, float cT, float T2, bool comp,
+                                               float (*red)[5]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (comp) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s1 = __shfl_xor_sync(0xffffffffu, S, o), c1 = __shfl_xor_sync(0xffffffffu, cS, o);
+            const float s2 = __shfl_xor_sync(0xffffffffu, T1, o), c2 = __shfl_xor_sync(0xffffffffu, cT, o);
+            T2 += __shfl_xor_sync(0xffffffffu, T2, o);
+            two_sum_add(S, cS, s1, c1);
+            two_sum_add(T1, cT, s2, c2);
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            S += __shfl_xor_sync(0xffffffffu, S, o);
+            T1 += __shfl_xor_sync(0xffffffffu, T1, o);
+            T2 += __shfl_xor_sync(0xffffffffu, T2, o);
+        }
+    }
+    if (lane == 0) {
+        red[warp][0] = S; red[warp][1] = cS; red[warp][2] = T1; red[warp][3] = cT; red[warp][4] = T2;
+    }
+    __syncthreads();
+    float a = red[0][0], ac = red[0][1], b = red[0][2], bc = red[0][3], c = red[0][4];
+#pragma unroll
+    for (int w = 1; w < kGroup / 32; ++w) {
+        if (comp) {
+            two_sum_add(a, ac, red[w][0], red[w][1]);
+            two_sum_add(b, bc, red[w][2], red[w][3]);
+        } else {
+            a += red[w][0];
+            b += red[w][2];
+        }
+        c += red[w][4];
+    }
+    __syncthreads();
     RowSums out;
+    out.S = a + ac;
+    out.T1 = b + bc;
+    out.T2 = c;
+    return out;
+}
+
+// S, T1, T2 of the row held in registers (excluded entries are kBig: e = 0).
+// Segment q (entries 512 q .. 512 q + 511 of the row) is skipped by the whole
+// group when it lies beyond the chunk (z <= 512 q), so rows of small chunks do
+// not pay for the register width of the largest one.
+template <int VPT>
+__device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, bool fine, float (*red5)[5], int z) {
+    const float b2 = beta * kLog2e;
     if (!fine) {
         float S = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
+            if (4 * kGroup * (k / 4) >= z) break;
             const float e = hw_ex2(-b2 * t[k]);
             const float te = t[k] * e;
             S += e;
             T1 += te;
             T2 = fmaf(te, t[k], T2);
         }
-        out.S = group_sum(S, red);
-        out.T1 = group_sum(T1, red);
-        out.T2 = group_sum(T2, red);
-        return out;
+        return group_sums3(S, 0.f, T1, 0.f, T2, false, red5);
     }
     float S = 0.f, cS = 0.f, T1 = 0.f, cT = 0.f, T2 = 0.f;   // Kahan: true sum = S - cS
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
+        if (4 * kGroup * (k / 4) >= z) break;
         const float e = hw_ex2(-b2 * t[k]);
         const float te = t[k] * e;
         float y = e - cS, s2 = S + y;
@@ -131,10 +160,7 @@ __device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, b
         cT = (s2 - T1) - y; T1 = s2;
         T2 = fmaf(te, t[k], T2);
     }
-    out.S = group_sum_comp(S, -cS, red2);
-    out.T1 = group_sum_comp(T1, -cT, red2);
-    out.T2 = group_sum(T2, red);
-    return out;
+    return group_sums3(S, -cS, T1, -cT, T2, true, red5);
 }
 
 // One row per 128-thread block; thread `tid` holds entries j = 4 tid + 512 q + e.
@@ -145,7 +171,7 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                     DeviceStats* st, const float* beta_init, int coarse, const unsigned int* maxnorm,
                     int32_t* __restrict__ dense_rows, int* __restrict__ dense_cnt, uint8_t* __restrict__ row_dense) {
     __shared__ float red[kGroup / 32];
-    __shared__ float red2[kGroup / 32][2];
+    __shared__ float red5[kGroup / 32][5];
     __shared__ double redd[kGroup / 32];
     const int tid = threadIdx.x;
     const float ln_perp = (float)ln_perp_d;
@@ -207,7 +233,7 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
             float best_f = INFINITY, best_beta = beta, best_S = 0.f, best_ulp_h = 0.f;
             for (int it = 0; it < kMaxEval32; ++it) {
                 const bool fine = !coarse && fabsf(f) < kTolCoarse;
-                s = row_sums<VPT>(t, beta, fine, red2, red);
+                s = row_sums<VPT>(t, beta, fine, red5, z);
                 ++evals;
                 // H in nats; logf and the division are correctly rounded to ~1 ulp
                 f = (logf(s.S) + beta * (s.T1 / s.S)) - ln_perp;
@@ -247,6 +273,7 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                     double sS = 0.0, sT1 = 0.0, sT2 = 0.0;
 #pragma unroll
                     for (int k = 0; k < VPT; ++k) {
+                        if (4 * kGroup * (k / 4) >= z) break;
                         if (t[k] >= kBig) continue;
                         const double e = exp(-b * (double)t[k]);
                         sS += e; sT1 += (double)t[k] * e; sT2 += (double)t[k] * t[k] * e;
