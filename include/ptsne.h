@@ -217,8 +217,12 @@ int ptsne_cost(ptsne_ctx* ctx, const int32_t* perm_dev, const float* Y_dev,
  * each, epochs x n), `iters` gradient iterations of every chunk from the
  * current map, pooling into Y_dev (n x out_dim, in: start map, out: result).
  * cost_out_host (optional): epochs x 2 doubles, {avg KL, avg normalised cost}
- * at the end of each epoch.  Synchronous: returns after the work completes,
- * with PTSNE_WBISECT if some row missed the perplexity tolerance. */
+ * at the end of each epoch.  From the second epoch on, each row's perplexity
+ * search starts from the precision its point had in the previous epoch (the
+ * root is unique, so only the number of evaluations changes); the first
+ * epoch of every call starts cold, so identical calls give identical results.
+ * Synchronous: returns after the work completes, with PTSNE_WBISECT if some
+ * row missed the perplexity tolerance. */
 int ptsne_run(ptsne_ctx* ctx, const float* X_dev, const int32_t* perms_dev,
               int32_t epochs, float* Y_dev, double* cost_out_host, void* stream);
 

@@ -5,9 +5,10 @@
 // chunk is owned by a cluster of K blocks (K = 1, 2 or 4); the chunk's map
 // lives in every block's shared memory and each block takes every K-th round
 // of the chunk's tile tournament.  Within a block:
-//   - one producer lane streams the block's P tiles (4 KB each, stored once
+//   - one producer warp streams the block's P tiles (4 KB each, stored once
 //     per unordered pair of 32-row blocks) from HBM into a ring of shared
-//     buffers with cp.async.bulk, completion tracked by mbarriers;
+//     buffers with cp.async.bulk, one tile per lane in batches of at most the
+//     ring size, completion tracked by mbarriers;
 //   - consumer warps take the tiles in stream order, G = 2 or 4 warps per
 //     tile: a tile (rows a, columns b) serves both directions — rows of a
 //     against columns of b (the tile read row-wise) and rows of b against

@@ -39,7 +39,7 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t*
         int k = (int)(t - r * width);
         const int64_t pr = perm[r];
         if (pr < 0 || pr >= n) {
-            if (k == 0) atomicAdd(bad_index, 1u);
+            if (k == 0 && bad_index) atomicAdd(bad_index, 1u);
             dst[t] = 0.0f;
             continue;
         }
@@ -56,7 +56,7 @@ __global__ void scatter_rows_kernel(const float* __restrict__ src, const int32_t
         int k = (int)(t - r * width);
         const int64_t pr = perm[r];
         if (pr < 0 || pr >= n) {
-            if (k == 0) atomicAdd(bad_index, 1u);
+            if (k == 0 && bad_index) atomicAdd(bad_index, 1u);
             continue;
         }
         dst[pr * width + k] = src[t];
@@ -112,6 +112,20 @@ cudaError_t launch_scatter_rows(const ptsne_ctx* c, const float* src, const int3
                                 float* dst, cudaStream_t s) {
     const int64_t n = c->p.n;
     scatter_rows_kernel<<<grid_for(n * width, 256), 256, 0, s>>>(src, perm, n, width, dst, &c->dstats->bad_index);
+    return launched(c, 1);
+}
+
+// Per-point precisions of the previous epoch (original order) -> warm starts
+// of this epoch's search (partition order), and back.  Bad permutation entries
+// are counted by the X gather already.
+cudaError_t launch_beta_warm(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s) {
+    const int64_t n = c->p.n;
+    gather_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(c->beta_pt, perm, n, 1, c->beta, nullptr);
+    return launched(c, 1);
+}
+cudaError_t launch_beta_keep(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s) {
+    const int64_t n = c->p.n;
+    scatter_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(c->beta, perm, n, 1, c->beta_pt, nullptr);
     return launched(c, 1);
 }
 

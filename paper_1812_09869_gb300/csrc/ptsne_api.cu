@@ -71,7 +71,8 @@ void free_all(ptsne_ctx* c) {
                     c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
-                    c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense};
+                    c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense,
+                    c->beta_pt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -262,6 +263,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         AL(c->P, m);
     }
     AL(c->beta, n);
+    AL(c->beta_pt, n);
     AL(c->mrow, n);
     AL(c->Srow, n);
     AL(c->Yc, n * od);
@@ -338,13 +340,20 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cu
     if (mixed) CK(launch_gather_bf16(c, s));
     if (Y_run) CK(launch_gather_y(c, Y_run, perm, c->Yc, s));
     CK(launch_reset_optim(c, s));
+    // ptsne_run: each row's search starts from its point's beta of the last
+    // epoch (the root is unique; only the number of evaluations changes)
+    const float* warm = nullptr;
+    if (Y_run) {
+        CK(launch_beta_warm(c, perm, s));
+        warm = c->beta;
+    }
     mark(c, PTSNE_STAGE_DISTANCES, s);
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
         if (mixed) CK(launch_dist_bf16(c, 0, c->ntiles128, s));
         else CK(launch_dist_fp32(c, 0, c->ntiles, s));
         mark(c, PTSNE_STAGE_PERPLEXITY, s);
         // mixed precision: a coarse search on d~ only places the windows
-        CK(launch_bisect(c, 0, c->p.n, s, nullptr, mixed ? 1 : 0));
+        CK(launch_bisect(c, 0, c->p.n, s, warm, mixed ? 1 : 0));
         if (mixed) {
             // FP32 distances inside each row's window, then the search again from beta~
             CK(launch_window_recompute(c, 0, c->p.n, s));
@@ -356,7 +365,7 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cu
         for (int k = 0; k < c->p.n_chunks; ++k) {
             if (mixed) CK(launch_dist_bf16(c, c->tile_start128[k], c->tile_start128[k + 1], s));
             else CK(launch_dist_fp32(c, c->tile_start[k], c->tile_start[k + 1], s));
-            CK(launch_bisect(c, c->off[k], c->off[k + 1], s, nullptr, mixed ? 1 : 0));
+            CK(launch_bisect(c, c->off[k], c->off[k + 1], s, warm, mixed ? 1 : 0));
             if (mixed) {
                 CK(launch_window_recompute(c, c->off[k], c->off[k + 1], s));
                 CK(launch_bisect(c, c->off[k], c->off[k + 1], s, c->beta));
@@ -366,6 +375,7 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cu
         mark(c, PTSNE_STAGE_PERPLEXITY, s);
         mark(c, PTSNE_STAGE_JOINT_P, s);
     }
+    if (Y_run) CK(launch_beta_keep(c, perm, s));
     c->have_P = true;
     return PTSNE_OK;
 }
@@ -530,8 +540,9 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
         const int st = capture_epoch(c, X, Y, want_cost);
         if (st != PTSNE_OK) return st;
     }
-    // counters accumulate over the whole run
+    // counters accumulate over the whole run; the first epoch's search starts cold
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
+    CK(cudaMemsetAsync(c->beta_pt, 0, sizeof(float) * n, s));
     for (int e = 0; e < epochs; ++e) {
         const int32_t* perm = perms + (int64_t)e * n;
         const int slot = e % kCostHist;

@@ -167,6 +167,7 @@ struct ptsne_ctx {
     float* D = nullptr;                // mtotal pair distances
     float* P = nullptr;                // mtotal joint probabilities
     float* beta = nullptr;             // n (permuted)
+    float* beta_pt = nullptr;          // n, original order: last search's beta of each point (ptsne_run warm starts)
     float* mrow = nullptr;             // n row minima of the distances
     float* Srow = nullptr;             // n row normalisers at beta
     float* Yc = nullptr;               // n x od (permuted)
@@ -232,6 +233,8 @@ cudaError_t launch_dist_fp32(const ptsne_ctx* c, int64_t tile_begin, int64_t til
 cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
 // beta_init (optional): start each row's search from this beta instead of 1 / mean(d - m)
+cudaError_t launch_beta_warm(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s);
+cudaError_t launch_beta_keep(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s);
 cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
                           const float* beta_init = nullptr, int coarse = 0);
 cudaError_t launch_gather_bf16(const ptsne_ctx* c, cudaStream_t s);

@@ -92,3 +92,27 @@ def test_profiled_graph_records_stage_times(dev):
     Ye, ce, _ = _run(dev, X, off, perms, Y0, 0)
     assert rel_max(Yd.cpu().numpy() - Y0, Ye - Y0) <= 1e-4
     assert np.abs(cost - ce).max() <= 1e-5 * np.abs(ce).max()
+
+
+def test_identical_runs_give_identical_maps(dev):
+    """Each epoch's perplexity search starts from the previous epoch's
+    precisions, but every ptsne_run call starts cold: two identical
+    multi-epoch calls on one context produce the same map, up to the
+    floating-point order of the shared-memory accumulation."""
+    from paper_1812_09869_gb300 import ptsne
+    X, off, perms, Y0 = _setup(epochs=3)
+    cfg = ptsne.Config(n=X.shape[0], d=X.shape[1], offsets=off, perplexity=30.0, iters=5,
+                       precision="bf16_window")
+    Xd, Pd = torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev)
+    with ptsne.Context(cfg) as ctx:
+        outs = []
+        for _ in range(2):
+            Yd = torch.from_numpy(Y0.copy()).to(dev)
+            cost = np.zeros((3, 2))
+            ctx.run(Xd, Pd, 3, Yd, cost_out=cost)
+            torch.cuda.synchronize()
+            outs.append((Yd.cpu().numpy(), cost.copy()))
+            st = ctx.stats()
+            assert st.bisect_failed_rows == 0
+    assert rel_max(outs[0][0] - Y0, outs[1][0] - Y0) <= 1e-5
+    assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-6 * np.abs(outs[0][1]).max()
