@@ -278,6 +278,7 @@ def learned_form(dev, stream, train_epochs=10, mapper_epochs=20, warm_iters=25, 
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with M.Mapper(w.d, synth.mlp_init(w.d, 2, seed=505), batch=4096) as m:
         orders = torch.from_numpy(synth.permutations(half, mapper_epochs, seed=605)).to(dev)
+        split = m.autotune(Xtr, Ytr, orders[0][:4096].contiguous())   # split-K of the weight gradients
         t0 = time.perf_counter()
         m.fit_scaler(Ytr)
         loss = m.train(Xtr, Ytr, orders, mapper_epochs)
@@ -306,7 +307,7 @@ def learned_form(dev, stream, train_epochs=10, mapper_epochs=20, warm_iters=25, 
     return {"workload": "mapper-1m+1m-d50", "mlp": "50-256-256-2 GELU, BF16 tcgen05, AdamW",
             "train_ptsne": {"epochs": train_epochs, "iters": train_epochs * w.iters, "seconds": t_ptsne_tr,
                             "final_kl": kl_tr[-1]},
-            "mapper_train": {"epochs": mapper_epochs, "batch": 4096, "seconds": t_train,
+            "mapper_train": {"epochs": mapper_epochs, "batch": 4096, "seconds": t_train, "split_k": split,
                              "loss_first_last": [float(loss[0]), float(loss[-1])]},
             "mapper_infer": {"points": half, "seconds": t_infer, "points_per_s": half / t_infer},
             "cold": {"iters": train_epochs * w.iters, "seconds": t_cold, "final_kl": target},

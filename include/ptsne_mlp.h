@@ -90,6 +90,15 @@ int ptsne_mlp_train_step(ptsne_mlp* m, const float* X_dev, const float* T_dev, i
 int ptsne_mlp_train(ptsne_mlp* m, const float* X_dev, const float* T_dev, int64_t n, const int32_t* orders_dev,
                     int32_t epochs, double* loss_out_host, void* stream);
 
+/* Autotuner of the weight-gradient GEMMs (K = batch): times the forward and
+ * backward pass of the batch rows_dev (parameters untouched) for 1, 2, 4, ...
+ * CTAs along K (at most batch / 64 and 64) and keeps the fastest for this
+ * handle.  cache_path (optional): text file of earlier choices keyed by
+ * device, d_in, out_dim and batch; a hit skips the timing and a new choice is
+ * appended.  split_out (optional): the choice.  Synchronous. */
+int ptsne_mlp_autotune(ptsne_mlp* m, const float* X_dev, const float* T_dev, int64_t n, const int32_t* rows_dev,
+                       const char* cache_path, int32_t* split_out, void* stream);
+
 /* Map n points: X_dev (n x d_in) -> Y_out_dev (n x out_dim), de-standardised
  * by the scaler.  Runs in slabs of infer_rows rows.  Async. */
 int ptsne_mlp_infer(ptsne_mlp* m, const float* X_dev, int64_t n, float* Y_out_dev, void* stream);

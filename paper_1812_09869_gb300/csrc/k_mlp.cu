@@ -29,6 +29,8 @@
 //   AdamW on the FP32 master parameters, rewriting the BF16 copies.
 #include <float.h>
 #include <math.h>
+#include <stdio.h>
+#include <string.h>
 
 #include <mutex>
 #include <string>
@@ -472,6 +474,7 @@ struct ptsne_mlp {
     int loss_cap = 0;
     bf16 *Xs = nullptr, *H1s = nullptr;
     unsigned int* dflags = nullptr;   // [0] timeouts, [1] bad rows
+    int split = 0;                    // CTAs along K of the weight-gradient GEMMs (0: heuristic)
     CUtensorMap tmXb, tmW1b, tmH1, tmW2b, tmdA2T, tmH1T, tmdA2, tmW2Tb, tmdA1T, tmXbT, tmXs, tmH1s;
     std::string err;
 };
@@ -531,9 +534,11 @@ GemmArgs base_args(ptsne_mlp* m) {
     return a;
 }
 
-// split-K shape of a K = B contraction: (K blocks per CTA, CTAs along K)
-void split_k(int kblocks, int* per, int* splits) {
-    int sp = kblocks < 16 ? kblocks : 16;
+// split-K shape of a K = B contraction: (K blocks per CTA, CTAs along K);
+// `want` CTAs along K (0: at most 16)
+void split_k(int kblocks, int want, int* per, int* splits) {
+    int sp = want > 0 ? want : 16;
+    if (sp > kblocks) sp = kblocks;
     *per = (kblocks + sp - 1) / sp;
     *splits = (kblocks + *per - 1) / *per;
 }
@@ -577,7 +582,7 @@ cudaError_t run_grad_od(ptsne_mlp* m, const float* X, const float* T, int64_t n,
     if ((e = launch_gemm<kH, EPI_HEAD_TRAIN, OD>(m->tmH1, m->tmW2b, a, B / 128, 1, s)) != cudaSuccess) return e;
     // dW2 = dA2^T H1
     int per, sp;
-    split_k(B / 64, &per, &sp);
+    split_k(B / 64, m->split, &per, &sp);
     a = base_args(m);
     a.M = kH;
     a.kblocks = B / 64;
@@ -838,6 +843,74 @@ int ptsne_mlp_train(ptsne_mlp* m, const float* X, const float* T, int64_t n, con
     MCK(cudaStreamSynchronize(s));
     if (flags[0]) return mfail(m, PTSNE_ETIMEOUT, "a bounded wait inside a GEMM ran out");
     if (flags[1]) return mfail(m, PTSNE_EINVAL, "orders holds entries outside [0, n)");
+    return PTSNE_OK;
+}
+
+int ptsne_mlp_autotune(ptsne_mlp* m, const float* X, const float* T, int64_t n, const int32_t* rows,
+                       const char* cache_path, int32_t* split_out, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!X || !T || !rows || n < 1) return mfail(m, PTSNE_EINVAL, "X, T and rows must be device pointers, n >= 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    MCK(cudaGetDevice(&dev));
+    MCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaDeviceProp prop;
+    MCK(cudaGetDeviceProperties(&prop, dev));
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (ch == ' ' || ch == '|') ch = '_';
+    char key[512];
+    snprintf(key, sizeof key, "mlp|%s|sm%d|din%d|od%d|batch%d", name.c_str(), sms, m->din, m->od, m->B);
+    if (cache_path) {   // the last matching record wins
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[1024], k[600];
+            int sp = 0;
+            bool found = false;
+            while (fgets(line, sizeof line, f))
+                if (sscanf(line, "%599s %d", k, &sp) == 2 && strcmp(k, key) == 0 && sp > 0) {
+                    m->split = sp;
+                    found = true;
+                }
+            fclose(f);
+            if (found) {
+                if (split_out) *split_out = m->split;
+                return PTSNE_OK;
+            }
+        }
+    }
+    // time the forward + backward pass (parameters untouched) for each split
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MCK(cudaEventCreate(&e0));
+    MCK(cudaEventCreate(&e1));
+    const int kblocks = m->B / 64;
+    int best = 0;
+    float best_ms = 0.f;
+    cudaError_t e = cudaSuccess;
+    for (int sp = 1; sp <= 64 && e == cudaSuccess; sp *= 2) {
+        if (sp > kblocks) break;
+        m->split = sp;
+        e = run_grad(m, X, T, n, rows, m->loss, s);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = run_grad(m, X, T, n, rows, m->loss, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best == 0 || ms < best_ms)) { best = sp; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        m->split = 0;
+        return mfail(m, PTSNE_ECUDA, cudaGetErrorString(e));
+    }
+    m->split = best;
+    if (cache_path)
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %.6f\n", key, best, best_ms / 5.0);
+            fclose(f);
+        }
+    if (split_out) *split_out = best;
     return PTSNE_OK;
 }
 

@@ -6,6 +6,7 @@ library's CUDA kernels.  Tensors are torch CUDA tensors.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -71,6 +72,7 @@ def lib():
         L.ptsne_mlp_train_step.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp]
         L.ptsne_mlp_train.argtypes = [vp, vp, vp, C.c_int64, vp, C.c_int32, C.POINTER(C.c_double), vp]
         L.ptsne_mlp_infer.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.ptsne_mlp_autotune.argtypes = [vp, vp, vp, C.c_int64, vp, C.c_char_p, C.POINTER(C.c_int32), vp]
         _bound = True
     return L
 
@@ -138,6 +140,14 @@ class Mapper:
         self._check(lib().ptsne_mlp_train(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(orders), int(epochs),
                                           loss.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
         return loss[:int(epochs)]
+
+    def autotune(self, X, T, rows, cache_path=None, stream=None) -> int:
+        """Pick the split-K of the weight-gradient GEMMs by timing; returns it."""
+        sp = C.c_int32(0)
+        cp = None if cache_path is None else os.fsencode(cache_path)
+        self._check(lib().ptsne_mlp_autotune(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(rows), cp,
+                                             C.byref(sp), _stream(stream)))
+        return int(sp.value)
 
     def infer(self, X, Y_out, stream=None):
         return self._check(lib().ptsne_mlp_infer(self.h, _ptr(X), int(X.shape[0]), _ptr(Y_out), _stream(stream)))

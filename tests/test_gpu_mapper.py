@@ -190,3 +190,30 @@ def test_warm_start_gains_over_plain_ptsne(dev):
     chance = 10.0 / half
     assert pres["map"] > 10 * chance
     assert pres["warm"] >= 0.75 * pres["cold"]
+
+
+def test_autotuned_split_gives_the_same_gradient(dev, tmp_path):
+    """The weight-gradient GEMMs' split along K changes only the FP32
+    summation order: the gradient after autotuning matches the oracle, and a
+    second handle reads the choice from the cache."""
+    from paper_1812_09869_gb300 import mapper as M
+    n, d_in, batch = 4096, 50, 2048
+    X, _ = synth.gaussian_mixture(n, d_in, 6, seed=95)
+    X = _bf16(X)
+    T = np.random.default_rng(96).standard_normal((n, 2)).astype(np.float32)
+    rows = synth.permutations(n, 1, seed=97)[0][:batch].copy()
+    W = _weights(d_in, 2, 98)
+    cache = str(tmp_path / "mlp_tune.txt")
+    Xd, Td, rd = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(rows).to(dev)
+    with M.Mapper(d_in, W, batch=batch) as m:
+        sp = m.autotune(Xd, Td, rd, cache_path=cache)
+        assert 1 <= sp <= 32
+        g = torch.zeros(M.n_params(d_in, 2), dtype=torch.float32, device=dev)
+        m.grad(Xd, Td, rd, g)
+        torch.cuda.synchronize()
+        G = M.unpack(g.cpu().numpy(), d_in, 2)
+    _, G_ref = O.mlp_loss_grad(_f64(W), X[rows], T[rows])
+    for k in M.PARAM_ORDER:
+        assert rel_max(G[k], G_ref[k]) <= MLP_GRAD_TOL, k
+    with M.Mapper(d_in, W, batch=batch) as m2:
+        assert m2.autotune(Xd, Td, rd, cache_path=cache) == sp
