@@ -33,7 +33,11 @@
 namespace ptsne {
 
 namespace {
-constexpr float kPad = 1e18f;                  // map coordinate of padding rows: w ~ 1e-36, p = 0
+// Padding rows (z <= i < 32 nb) sit at (i - z + 1) * kPad on every axis: any
+// pair with a padding row is >= 1e18 apart, so w <= 1e-36 (or 0 once the
+// square overflows) and p = 0, and padding rows can be processed like real
+// ones without changing A, R or Z (their own updates are never written).
+constexpr float kPad = 1e18f;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
 constexpr float kLn2f = 0.69314718055994531f;
 constexpr int kTileBytes = kPTileStride * 4;    // P tile + trailer, one bulk copy
@@ -322,7 +326,7 @@ struct Cursor {
     __device__ __forceinline__ void advance_ring(uint32_t delta, uint32_t ring) {
         q += delta;
         buf += delta;
-        while (buf >= ring) { buf -= ring; ph ^= 1u; }
+        if (buf >= ring) { buf -= ring; ph ^= 1u; }   // delta <= ring: at most one wrap
     }
     // set s and normalise (j, p) for a stream of jd pair rounds of tpr tiles
     __device__ __forceinline__ void seek(int s_, int jd, int tpr) {
@@ -366,8 +370,7 @@ __device__ __forceinline__ void consume_share(const float* tile, const float* ma
     if (lane == 0) mbar_arrive(empty_bar);   // the buffer is free again
     const int own = (colwise ? b : a) * kPT + lane;
     const int pbase = (colwise ? a : b) * kPT + start;
-    if (own >= z) return;
-    if (!cost) {
+    if (!cost) {   // rows own >= z are padding: their sums are zero (see kPad)
         float av[OD], rv[OD], w;
         if constexpr (OD == 2) grad_task_2d<N>(map, zcap, own, pbase, pv, av, rv, w);
         else grad_task_3d<N>(map, zcap, own, pbase, pv, av, rv, w);
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
 
         for (int i = tid; i < zr; i += nthreads) {
 #pragma unroll
-            for (int k = 0; k < OD; ++k) map[k * zcap + i] = i < z ? A.Yc[(off + i) * OD + k] : kPad;
+            for (int k = 0; k < OD; ++k) map[k * zcap + i] = i < z ? A.Yc[(off + i) * OD + k] : kPad * (float)(i - z + 1);
         }
         for (int i = tid; i < 2 * OD * zcap; i += nthreads) acc[i] = 0.f;
         __syncthreads();
@@ -521,7 +524,8 @@ __global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
                     if (!mbar_wait(full_a + 8 * cur.buf, cur.ph, A.timeouts) && lane == 0) atomicAdd(A.timeouts, 1u);
                     __syncwarp();
                     const float* tile = ring + (size_t)cur.buf * kPTileStride;
-                    const int a = __float_as_int(tile[kPTileFloats]), b = __float_as_int(tile[kPTileFloats + 1]);
+                    const int2 ab = *reinterpret_cast<const int2*>(tile + kPTileFloats);
+                    const int a = ab.x, b = ab.y;
                     const uint32_t ebar = empty_a + 8 * cur.buf;
                     if (a == b) {
                         // diagonal: rows of a against columns split G ways; the owner
