@@ -224,14 +224,18 @@ def _timed_epochs(ctx, Xd, perm_rows, Y, stream):
 
 def compare_forms(w, Xd, perms, dev, stream, tuning):
     """Plain FP32 (per-chunk launches, FP32 SIMT distances, dense P), batched
-    FP32 and batched mixed precision, each running the same two epochs
+    FP32, batched mixed precision, and batched mixed precision with the
+    paper's Eq. 13 learning rate, each running the same two epochs
     (partitions 0 and 1) from the same start map; the second epoch is timed
     and the final KL compared."""
     import torch
     from paper_1812_09869_gb300 import ptsne
     kinds = {"plain_fp32": dict(precision="fp32", schedule="per_chunk", use_graph=0),
              "batched_fp32": dict(precision="fp32", schedule="batched", use_graph=1),
-             "batched_bf16_window": dict(precision="bf16_window", schedule="batched", use_graph=1)}
+             "batched_bf16_window": dict(precision="bf16_window", schedule="batched", use_graph=1),
+             # the paper's own update: adaptive learning rate of Eq. 13, no gains
+             "batched_bf16_window_lr_eq13": dict(precision="bf16_window", schedule="batched", use_graph=1,
+                                                 lr_mode=ptsne.LR_PAPER, use_gains=0)}
     out = {}
     for name, kw in kinds.items():
         cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,

@@ -47,6 +47,7 @@ def lib():
                                    C.c_int32, _D, _D, _I32]
         L.orc_affinities.argtypes = [_D, C.c_int64, C.c_int32, C.c_double, C.c_double,
                                      C.c_int32, _D, _D, _D]
+        L.orc_affinities_from_distances.argtypes = [_D, C.c_int64, C.c_double, C.c_double, C.c_int32, _D, _D, _D]
         L.orc_cauchy_Z.argtypes = [_D, C.c_int64, C.c_int32]
         L.orc_cauchy_Z.restype = C.c_double
         L.orc_gradient.argtypes = [_D, _D, C.c_int64, C.c_int32, _D, _D]
@@ -115,6 +116,19 @@ def affinities(Xc, perp, tol=BISECT_TOL, maxit=BISECT_MAXIT, want_cond=False):
     if st < 0:
         raise ValueError(f"orc_affinities failed: {st}")
     return (P, beta, cond, st) if want_cond else (P, beta, st)
+
+
+def affinities_from_distances(D, perp, tol=BISECT_TOL, maxit=BISECT_MAXIT):
+    """Joint P (z x z), beta (z) and the number of unconverged rows from a
+    precomputed z x z dissimilarity matrix D."""
+    D = _f64(D)
+    z = D.shape[0]
+    P = np.empty((z, z))
+    beta = np.empty(z)
+    st = lib().orc_affinities_from_distances(_d(D), z, perp, tol, maxit, _d(P), _d(beta), None)
+    if st < 0:
+        raise ValueError(f"orc_affinities_from_distances failed: {st}")
+    return P, beta, st
 
 
 def cauchy_Z(Y):

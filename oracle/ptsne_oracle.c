@@ -162,14 +162,16 @@ static void row_conditional(const double* drow, int64_t z, int64_t i,
  * optional) receives p_{j|i} at [i*z + j].  D_scratch (z x z, optional) is
  * used instead of a fresh allocation.  Returns the number of rows whose search
  * did not converge (>= 0) or a negative error. */
-int orc_affinities(const double* Xc, int64_t z, int32_t d, double perp,
-                   double tol, int32_t maxit, double* P, double* beta,
-                   double* Pcond) {
-    if (!Xc || !P || z < 2 || d < 1) return ORC_EINVAL;
-    double* D = (double*)malloc(sizeof(double) * (size_t)(z * z));
+/* Joint P (Eq. 3, n := z) of one chunk from its z x z matrix of dissimilarities
+ * D (squared Euclidean distances, or any precomputed ones such as graph path
+ * lengths): beta_i by the search of orc_row_beta on row i of D (Eq. 1, Eq. 2),
+ * conditionals p_{j|i}, then P_ij = (p_{j|i} + p_{i|j}) / (2z).  Returns the
+ * number of rows that missed the tolerance. */
+int orc_affinities_from_distances(const double* D, int64_t z, double perp, double tol, int32_t maxit,
+                                  double* P, double* beta, double* Pcond) {
+    if (!D || !P || z < 2) return ORC_EINVAL;
     double* C = Pcond ? Pcond : (double*)malloc(sizeof(double) * (size_t)(z * z));
-    if (!D || !C) { free(D); if (!Pcond) free(C); return ORC_ENOMEM; }
-    orc_sqdist(Xc, z, d, D);
+    if (!C) return ORC_ENOMEM;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+:bad)
     for (int64_t i = 0; i < z; ++i) {
@@ -184,8 +186,21 @@ int orc_affinities(const double* Xc, int64_t z, int32_t d, double perp,
     for (int64_t i = 0; i < z; ++i)
         for (int64_t j = 0; j < z; ++j)
             P[i * z + j] = (i == j) ? 0.0 : (C[i * z + j] + C[j * z + i]) * inv2n;
-    free(D);
     if (!Pcond) free(C);
+    return bad;
+}
+
+/* Joint P of one chunk of points Xc (z x d): squared Euclidean distances
+ * (input-space similarities of the ptSNE section), then the above. */
+int orc_affinities(const double* Xc, int64_t z, int32_t d, double perp,
+                   double tol, int32_t maxit, double* P, double* beta,
+                   double* Pcond) {
+    if (!Xc || !P || z < 2 || d < 1) return ORC_EINVAL;
+    double* D = (double*)malloc(sizeof(double) * (size_t)(z * z));
+    if (!D) return ORC_ENOMEM;
+    orc_sqdist(Xc, z, d, D);
+    const int bad = orc_affinities_from_distances(D, z, perp, tol, maxit, P, beta, Pcond);
+    free(D);
     return bad;
 }
 

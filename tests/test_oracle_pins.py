@@ -382,3 +382,47 @@ def test_knn_preservation_brute_force():
         return {j for _, j in sorted(d)[:k]}
     ref = np.mean([len(nn(X, i, 5) & nn(Y, i, 5)) / 5 for i in range(40)])
     assert O.knn_preservation(X, X, Y, Y, k=5) == pytest.approx(ref, abs=1e-15)
+
+
+def test_affinities_from_distances_equal_point_affinities():
+    """The point form is the distance form applied to squared distances."""
+    X = np.random.default_rng(40).standard_normal((70, 6))
+    P1, b1, _ = O.affinities(X, 12.0)
+    P2, b2, bad = O.affinities_from_distances(O.sqdist(X), 12.0)
+    assert bad == 0
+    assert np.array_equal(P1, P2) and np.array_equal(b1, b2)
+
+
+def test_affinities_from_graph_path_lengths():
+    """Precomputed non-Euclidean dissimilarities (shortest-path lengths of a
+    random connected graph): every row reaches the target perplexity (2^H
+    re-evaluated here from beta and the row, and beta equal to an independent
+    brentq root), P is symmetric with unit mass."""
+    from scipy.optimize import brentq
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import shortest_path
+    rng = np.random.default_rng(41)
+    z, perp = 120, 15.0
+    W = np.zeros((z, z))
+    for i in range(z):                       # a ring keeps the graph connected, plus random chords
+        W[i, (i + 1) % z] = rng.uniform(0.5, 2.0)
+    for _ in range(3 * z):
+        i, j = rng.integers(0, z, 2)
+        if i != j:
+            W[i, j] = rng.uniform(0.5, 4.0)
+    G = shortest_path(csr_matrix(W), directed=False)
+    P, beta, bad = O.affinities_from_distances(G, perp)
+    assert bad == 0
+    assert np.allclose(P, P.T, rtol=0, atol=0) and abs(P.sum() - 1.0) < 1e-12
+    for i in range(z):
+        d = np.delete(G[i], i)
+        t = d - d.min()
+
+        def H(b):
+            e = np.exp(-b * t)
+            p = e / e.sum()
+            return -(p[p > 0] * np.log(p[p > 0])).sum()
+        assert abs(np.exp(H(beta[i])) - perp) <= 1e-5
+        if i % 20 == 0:
+            root = brentq(lambda b: H(b) - np.log(perp), 1e-8, 1e3, xtol=1e-14, rtol=1e-14)
+            assert abs(beta[i] - root) <= 1e-6 * root
