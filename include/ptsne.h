@@ -188,6 +188,19 @@ const char* ptsne_last_error(const ptsne_ctx* ctx);
 int ptsne_affinities(ptsne_ctx* ctx, const float* X_dev, const int32_t* perm_dev,
                      float* P_out_dev, float* beta_out_dev, void* stream);
 
+/* ptsne_affinities from precomputed dissimilarities instead of points (for
+ * instance shortest-path lengths of a graph, the paper's non-vector input):
+ * D_dev is n x n float32, row-major with leading dimension ldd >= n, D[i][j]
+ * the dissimilarity of points i and j in ORIGINAL order (need not be
+ * symmetric; the diagonal is ignored).  Each chunk's block is gathered through
+ * perm_dev; the search and joint P follow as in ptsne_affinities, at FP32
+ * whatever the context's precision (there is nothing to recompute).
+ * Non-finite entries are counted in nonfinite_inputs and read as 0.  P_out,
+ * beta_out, the kept P and the optimiser reset as ptsne_affinities; follow
+ * with ptsne_step / ptsne_cost.  Async. */
+int ptsne_affinities_from_distances(ptsne_ctx* ctx, const float* D_dev, int64_t ldd, const int32_t* perm_dev,
+                                    float* P_out_dev, float* beta_out_dev, void* stream);
+
 /* Pairwise squared distances of every chunk of the partition perm_dev, at
  * the context's precision and before any window recompute: FP32 direct
  * differences (PTSNE_PREC_FP32), or |x~_i|^2 + |x~_j|^2 - 2 x~_i . x~_j from

@@ -115,6 +115,44 @@ cudaError_t launch_scatter_rows(const ptsne_ctx* c, const float* src, const int3
     return launched(c, 1);
 }
 
+// Precomputed dissimilarities: chunk blocks of the caller's n x n matrix
+// (original point order, leading dimension ldd) gathered through the
+// partition into the z x ld chunk layout of D.  One warp per chunk row;
+// non-finite entries are counted; permutation entries were checked by the
+// caller's gather of the same partition.
+__global__ void gather_dist_kernel(const float* __restrict__ Dfull, int64_t ldd, const int32_t* __restrict__ perm,
+                                   Layout L, float* __restrict__ D, unsigned long long* nonfinite,
+                                   unsigned int* bad_index) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < L.n; r += warps) {
+        const int c = L.chunk_of_row[r];
+        const int64_t off = L.off[c];
+        const int z = (int)(L.off[c + 1] - off);
+        const int i = (int)(r - off);
+        float* drow = D + L.moff[c] + (int64_t)i * L.ld[c];
+        const int64_t pi = perm[r];
+        const bool pi_ok = pi >= 0 && pi < L.n;
+        if (!pi_ok && lane == 0) atomicAdd(bad_index, 1u);
+        unsigned long long bad = 0;
+        for (int j = lane; j < z; j += 32) {
+            const int64_t pj = perm[off + j];
+            float v = 0.f;
+            if (pi_ok && pj >= 0 && pj < L.n) v = Dfull[pi * ldd + pj];
+            if (!isfinite(v)) { ++bad; v = 0.f; }
+            drow[j] = v;
+        }
+        if (bad) atomicAdd(nonfinite, bad);
+    }
+}
+
+cudaError_t launch_gather_dist(const ptsne_ctx* c, const float* Dfull, int64_t ldd, const int32_t* perm,
+                               cudaStream_t s) {
+    gather_dist_kernel<<<grid_for(c->p.n * 32, 256), 256, 0, s>>>(Dfull, ldd, perm, make_layout(c), c->D,
+                                                                  &c->dstats->nonfinite, &c->dstats->bad_index);
+    return launched(c, 1);
+}
+
 // Per-point precisions of the previous epoch (original order) -> warm starts
 // of this epoch's search (partition order), and back.  Bad permutation entries
 // are counted by the X gather already.

@@ -462,6 +462,31 @@ int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P
     return PTSNE_OK;
 }
 
+int ptsne_affinities_from_distances(ptsne_ctx* c, const float* D_dev, int64_t ldd, const int32_t* perm,
+                                    float* P_out, float* beta_out, void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!D_dev || !perm) return fail(c, PTSNE_EINVAL, "D and perm must be device pointers%s%lld");
+    if (ldd < c->p.n) return fail(c, PTSNE_EINVAL, "ldd must be >= n%s (%lld)", "", ldd);
+    cudaStream_t s = as_stream(stream);
+    CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
+    CK(launch_gather_dist(c, D_dev, ldd, perm, s));
+    CK(launch_reset_optim(c, s));
+    // the given dissimilarities are final: one fine search, then the joint P
+    if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+        CK(launch_bisect(c, 0, c->p.n, s));
+        CK(launch_psym_packed(c, s));
+    } else {
+        for (int k = 0; k < c->p.n_chunks; ++k) {
+            CK(launch_bisect(c, c->off[k], c->off[k + 1], s));
+            CK(launch_psym(c, c->tile_start[k], c->tile_start[k + 1], s));
+        }
+    }
+    c->have_P = true;
+    if (P_out) CK(c->P2 ? launch_export_packed(c, P_out, s) : launch_export_P(c, P_out, s));
+    if (beta_out) CK(launch_scatter_rows(c, c->beta, perm, 1, beta_out, s));
+    return PTSNE_OK;
+}
+
 int ptsne_distances(ptsne_ctx* c, const float* X, const int32_t* perm, float* D_out, void* stream) {
     if (!c) return PTSNE_EINVAL;
     if (!X || !perm || !D_out) return fail(c, PTSNE_EINVAL, "X, perm and D_out must be device pointers%s%lld");

@@ -233,6 +233,8 @@ cudaError_t launch_dist_fp32(const ptsne_ctx* c, int64_t tile_begin, int64_t til
 cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
 // beta_init (optional): start each row's search from this beta instead of 1 / mean(d - m)
+cudaError_t launch_gather_dist(const ptsne_ctx* c, const float* Dfull, int64_t ldd, const int32_t* perm,
+                               cudaStream_t s);
 cudaError_t launch_beta_warm(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s);
 cudaError_t launch_beta_keep(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s);
 cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,

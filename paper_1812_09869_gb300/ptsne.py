@@ -97,6 +97,7 @@ def lib():
         L.ptsne_affinities.argtypes = [vp, vp, vp, vp, vp, vp]
         L.ptsne_step.argtypes = [vp, vp, vp, vp, vp, vp]
         L.ptsne_distances.argtypes = [vp, vp, vp, vp, vp]
+        L.ptsne_affinities_from_distances.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
         L.ptsne_cost.argtypes = [vp, vp, vp, vp, vp]
         L.ptsne_run.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
         L.ptsne_run_host.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
@@ -191,6 +192,12 @@ class Context:
     def affinities(self, X, perm, P_out=None, beta_out=None, stream=None):
         return self._check(lib().ptsne_affinities(self.h, _ptr(X), _ptr(perm), _ptr(P_out), _ptr(beta_out),
                                                   _stream(stream)))
+
+    def affinities_from_distances(self, D, perm, P_out=None, beta_out=None, ldd=None, stream=None):
+        """D: n x n float32 dissimilarities in original point order."""
+        ldd = int(D.shape[-1]) if ldd is None else int(ldd)
+        return self._check(lib().ptsne_affinities_from_distances(self.h, _ptr(D), ldd, _ptr(perm), _ptr(P_out),
+                                                                 _ptr(beta_out), _stream(stream)))
 
     def distances(self, X, perm, D_out, stream=None):
         return self._check(lib().ptsne_distances(self.h, _ptr(X), _ptr(perm), _ptr(D_out), _stream(stream)))
