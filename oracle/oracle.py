@@ -66,6 +66,8 @@ def lib():
                                        C.POINTER(OrcParams), _D, _D, _D, _D]
         L.orc_ptsne_run.argtypes = [_D, C.c_int64, C.c_int32, C.c_int32, _I32, _I64,
                                     C.c_int32, C.POINTER(OrcParams), _D, _D]
+        L.orc_ptsne_run_layers.argtypes = [_D, C.c_int64, C.c_int32, C.c_int32, _I32, _I64, C.c_int32,
+                                           C.c_int32, C.POINTER(OrcParams), _D, _D]
         L.orc_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -211,6 +213,25 @@ def ptsne_run(X, Y0, perms, offsets, prm: OrcParams):
                              C.byref(prm), _d(Y), _d(cost))
     if st < 0:
         raise ValueError(f"orc_ptsne_run failed: {st}")
+    return Y, cost
+
+
+def ptsne_run_layers(X, Y0, perms, offsets, layers, prm: OrcParams):
+    """ptSNE with layers: thread t runs elementary chunks t .. t+layers-1 (mod
+    T); Y0 and the result hold `layers` maps of n points, layer-major
+    (layers*n x out_dim).  Returns (Y, cost[epochs, 2])."""
+    X = _f64(X)
+    Y = _f64(Y0).copy()
+    n, d = X.shape
+    od = Y.shape[1]
+    assert Y.shape[0] == layers * n
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    cost = np.empty((prm.epochs, 2))
+    st = lib().orc_ptsne_run_layers(_d(X), n, d, od, perms.ctypes.data_as(_I32), offsets.ctypes.data_as(_I64),
+                                    len(offsets) - 1, layers, C.byref(prm), _d(Y), _d(cost))
+    if st < 0:
+        raise ValueError(f"orc_ptsne_run_layers failed: {st}")
     return Y, cost
 
 

@@ -402,6 +402,64 @@ int orc_partial_tsne(const double* Xc, int64_t z, int32_t d, int32_t od,
  * receives the average over chunks of KL (Eq. 5) and of the pseudo-normalised
  * cost (Eq. 9) at the end of each epoch.  One layer (each point in exactly one
  * chunk per epoch). */
+/* The ptSNE cycle with layers (ptSNE section, subsections "layers" and
+ * "thread-size"): each epoch's permutation and the offsets define T
+ * elementary chunks; thread t runs the L chunks t, t+1, ..., t+L-1 (mod T)
+ * together, so consecutive threads share L-1 chunks, and every point takes
+ * part in L threads.  The point of elementary chunk (t + k) mod T sits in slot
+ * k of thread t and reads and writes layer k of the map: Y holds L maps of n
+ * points, layer-major (row k n + p).  The threads of an epoch all start from
+ * the epoch's maps and never write the same row.  cost: per epoch, the
+ * averages over threads.  With layers = 1 this is orc_ptsne_run. */
+int orc_ptsne_run_layers(const double* X, int64_t n, int32_t d, int32_t od,
+                         const int32_t* perms, const int64_t* offsets, int32_t n_chunks, int32_t layers,
+                         const orc_params* prm, double* Y, double* cost) {
+    if (!X || !Y || !perms || !offsets || n_chunks < 1 || !prm) return ORC_EINVAL;
+    if (layers < 1 || layers > n_chunks) return ORC_EINVAL;
+    if (offsets[0] != 0 || offsets[n_chunks] != n) return ORC_EINVAL;
+    int bad = 0;
+    for (int32_t e = 0; e < prm->epochs; ++e) {
+        const int32_t* perm = perms + (int64_t)e * n;
+        double kl_sum = 0.0, nc_sum = 0.0;
+        for (int32_t t = 0; t < n_chunks; ++t) {
+            int64_t z = 0;
+            for (int32_t k = 0; k < layers; ++k) {
+                const int32_t c = (t + k) % n_chunks;
+                z += offsets[c + 1] - offsets[c];
+            }
+            double* Xc = (double*)malloc(sizeof(double) * (size_t)(z * d));
+            double* Yc = (double*)malloc(sizeof(double) * (size_t)(z * od));
+            int64_t* row = (int64_t*)malloc(sizeof(int64_t) * (size_t)z);   // row of Y of each thread row
+            if (!Xc || !Yc || !row) { free(Xc); free(Yc); free(row); return ORC_ENOMEM; }
+            int64_t r = 0;
+            for (int32_t k = 0; k < layers; ++k) {
+                const int32_t c = (t + k) % n_chunks;
+                for (int64_t i = offsets[c]; i < offsets[c + 1]; ++i, ++r) {
+                    const int64_t p = perm[i];
+                    row[r] = (int64_t)k * n + p;
+                    memcpy(Xc + r * d, X + p * d, sizeof(double) * (size_t)d);
+                    memcpy(Yc + r * od, Y + row[r] * od, sizeof(double) * (size_t)od);
+                }
+            }
+            double kl = 0.0, nc = 0.0;
+            int st = orc_partial_tsne(Xc, z, d, od, prm, Yc, NULL, &kl, &nc);
+            if (st < 0) { free(Xc); free(Yc); free(row); return st; }
+            bad += st;
+            /* the rows this thread writes are read by no other thread */
+            for (int64_t q = 0; q < z; ++q)
+                memcpy(Y + row[q] * od, Yc + q * od, sizeof(double) * (size_t)od);
+            free(Xc); free(Yc); free(row);
+            kl_sum += kl;
+            nc_sum += nc;
+        }
+        if (cost) {
+            cost[2 * e] = kl_sum / n_chunks;
+            cost[2 * e + 1] = nc_sum / n_chunks;
+        }
+    }
+    return bad;
+}
+
 int orc_ptsne_run(const double* X, int64_t n, int32_t d, int32_t od,
                   const int32_t* perms, const int64_t* offsets, int32_t n_chunks,
                   const orc_params* prm, double* Y, double* cost) {

@@ -426,3 +426,44 @@ def test_affinities_from_graph_path_lengths():
         if i % 20 == 0:
             root = brentq(lambda b: H(b) - np.log(perp), 1e-8, 1e3, xtol=1e-14, rtol=1e-14)
             assert abs(beta[i] - root) <= 1e-6 * root
+
+
+def test_layers_one_is_the_plain_cycle():
+    X = np.random.default_rng(42).standard_normal((150, 5))
+    off = np.array([0, 50, 100, 150])
+    perms = np.stack([np.random.default_rng(43 + e).permutation(150) for e in range(2)]).astype(np.int32)
+    Y0 = np.random.default_rng(44).standard_normal((150, 2)) * 1e-2
+    prm = O.params(perplexity=8.0, iters=10, epochs=2)
+    Y1, c1 = O.ptsne_run(X, Y0, perms, off, prm)
+    Y2, c2 = O.ptsne_run_layers(X, Y0, perms, off, 1, prm)
+    assert np.array_equal(Y1, Y2) and np.array_equal(c1, c2)
+
+
+def test_layers_chain_matches_an_explicit_assembly():
+    """Thread t of a layered epoch is the partial t-SNE of elementary chunks
+    t .. t+L-1 (mod T), slot k reading and writing layer k: restated here with
+    explicit loops over threads and slots."""
+    rng = np.random.default_rng(45)
+    n, T, L = 120, 4, 3
+    X = rng.standard_normal((n, 4))
+    off = np.array([0, 30, 55, 90, 120])
+    perm = rng.permutation(n).astype(np.int32)
+    Y0 = rng.standard_normal((L * n, 2)) * 1e-2
+    prm = O.params(perplexity=10.0, iters=8, epochs=1)
+    Y, cost = O.ptsne_run_layers(X, Y0, perm[None, :], off, L, prm)
+    Yref = Y0.copy()
+    kls = []
+    for t in range(T):
+        rows = []
+        for k in range(L):
+            c = (t + k) % T
+            rows += [(k, int(p)) for p in perm[off[c]:off[c + 1]]]
+        Xc = np.array([X[p] for _, p in rows])
+        Yc = np.array([Y0[k * n + p] for k, p in rows])
+        Yt, kl, _, st = O.partial_tsne(Xc, Yc, prm)
+        assert st == 0
+        for q, (k, p) in enumerate(rows):
+            Yref[k * n + p] = Yt[q]
+        kls.append(kl)
+    assert np.array_equal(Y, Yref)
+    assert cost[0, 0] == pytest.approx(np.mean(kls), rel=1e-15)
