@@ -101,6 +101,18 @@ typedef struct {
                                      X, Y, the tuning, profiling or the cost request
                                      change); 0: plain launches.  Profiling marks are
                                      captured as event nodes of the graph. */
+    int32_t layers;               /* L >= 1 (at most n_chunks): the chunks of chunk_offsets are
+                                     the elementary chunks of a partition; thread t runs
+                                     elementary chunks t, t+1, ..., t+L-1 (mod n_chunks)
+                                     together (ptSNE section, "layers"), so each point runs
+                                     in L threads and keeps L maps.  With L > 1 every Y,
+                                     grad and beta array holds L layers of n rows,
+                                     layer-major (row k n + i = point i in layer k; the
+                                     point in slot k of a thread reads and writes layer k);
+                                     P_out holds one z x z block per thread and Z_out one
+                                     value per thread; permutations stay n entries.
+                                     Thread sizes z_t = sum of its L chunk sizes must be
+                                     in [2, 8192].  1: the plain scheme. */
 } ptsne_params;
 
 typedef struct {

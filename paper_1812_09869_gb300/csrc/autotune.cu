@@ -114,7 +114,9 @@ extern "C" int ptsne_autotune(ptsne_ctx* c, const float* X, const int32_t* perm,
     if ((e = cudaMalloc(&g0, m * sizeof(float))) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaEventCreate(&e1)) != cudaSuccess) return cuda_fail(e);
-    if ((e = launch_gather_y(c, Y, perm, c->Yc, s)) != cudaSuccess) return cuda_fail(e);
+    const int32_t* vperm = virtual_perm(c, perm, s, &e);   // the thread rows' permutation (layers)
+    if (e != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_gather_y(c, Y, vperm, c->Yc, s)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemcpyAsync(y0, c->Yc, m * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaMemcpyAsync(v0, c->vel, m * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)

@@ -8,8 +8,10 @@ namespace ptsne {
 
 // X (n x d, original order) -> Xg (n x dp, permuted order, zero padded), one
 // warp per row; counts non-finite inputs.
+// Rows of X in partition order (with layers, entry v of the permutation is
+// layer * npts + point, and the row is point = v mod npts).
 __global__ void gather_x_kernel(const float* __restrict__ X, const int32_t* __restrict__ perm,
-                                int64_t n, int d, int dp, float* __restrict__ Xg,
+                                int64_t n, int64_t npts, int d, int dp, float* __restrict__ Xg,
                                 unsigned long long* nonfinite, unsigned int* bad_index) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -18,7 +20,7 @@ __global__ void gather_x_kernel(const float* __restrict__ X, const int32_t* __re
         const int64_t pr = perm[r];
         const bool ok = pr >= 0 && pr < n;
         if (!ok && lane == 0) atomicAdd(bad_index, 1u);
-        const float* src = X + (ok ? pr : 0) * d;
+        const float* src = X + (ok ? pr % npts : 0) * d;
         float* dst = Xg + r * dp;
         for (int k = lane; k < dp; k += 32) {
             float v = (k < d && ok) ? __ldg(src + k) : 0.0f;
@@ -95,7 +97,7 @@ static int grid_for(int64_t work, int block) {
 
 cudaError_t launch_gather(const ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s) {
     const int64_t n = c->p.n;
-    gather_x_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(X, perm, n, c->p.d, c->dp, c->Xg,
+    gather_x_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(X, perm, n, c->npts, c->p.d, c->dp, c->Xg,
                                                           &c->dstats->nonfinite, &c->dstats->bad_index);
     return launched(c, 1);
 }
@@ -121,7 +123,7 @@ cudaError_t launch_scatter_rows(const ptsne_ctx* c, const float* src, const int3
 // non-finite entries are counted; permutation entries were checked by the
 // caller's gather of the same partition.
 __global__ void gather_dist_kernel(const float* __restrict__ Dfull, int64_t ldd, const int32_t* __restrict__ perm,
-                                   Layout L, float* __restrict__ D, unsigned long long* nonfinite,
+                                   int64_t npts, Layout L, float* __restrict__ D, unsigned long long* nonfinite,
                                    unsigned int* bad_index) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -131,14 +133,15 @@ __global__ void gather_dist_kernel(const float* __restrict__ Dfull, int64_t ldd,
         const int z = (int)(L.off[c + 1] - off);
         const int i = (int)(r - off);
         float* drow = D + L.moff[c] + (int64_t)i * L.ld[c];
-        const int64_t pi = perm[r];
-        const bool pi_ok = pi >= 0 && pi < L.n;
+        const int64_t pv = perm[r];
+        const bool pi_ok = pv >= 0 && pv < L.n;
+        const int64_t pi = pi_ok ? pv % npts : 0;
         if (!pi_ok && lane == 0) atomicAdd(bad_index, 1u);
         unsigned long long bad = 0;
         for (int j = lane; j < z; j += 32) {
-            const int64_t pj = perm[off + j];
+            const int64_t pw = perm[off + j];
             float v = 0.f;
-            if (pi_ok && pj >= 0 && pj < L.n) v = Dfull[pi * ldd + pj];
+            if (pi_ok && pw >= 0 && pw < L.n) v = Dfull[pi * ldd + pw % npts];
             if (!isfinite(v)) { ++bad; v = 0.f; }
             drow[j] = v;
         }
@@ -148,9 +151,29 @@ __global__ void gather_dist_kernel(const float* __restrict__ Dfull, int64_t ldd,
 
 cudaError_t launch_gather_dist(const ptsne_ctx* c, const float* Dfull, int64_t ldd, const int32_t* perm,
                                cudaStream_t s) {
-    gather_dist_kernel<<<grid_for(c->p.n * 32, 256), 256, 0, s>>>(Dfull, ldd, perm, make_layout(c), c->D,
+    gather_dist_kernel<<<grid_for(c->p.n * 32, 256), 256, 0, s>>>(Dfull, ldd, perm, c->npts, make_layout(c), c->D,
                                                                   &c->dstats->nonfinite, &c->dstats->bad_index);
     return launched(c, 1);
+}
+
+// Layers: thread row r takes point perm[vsrc[r]] of layer vbase[r] / npts.
+// Entries of perm outside [0, npts) give -1 (counted by the gathers).
+__global__ void virtual_perm_kernel(const int32_t* __restrict__ perm, const int32_t* __restrict__ vsrc,
+                                    const int32_t* __restrict__ vbase, int64_t rows, int64_t npts,
+                                    int32_t* __restrict__ vperm) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = perm[vsrc[r]];
+        vperm[r] = (p >= 0 && p < npts) ? vbase[r] + p : -1;
+    }
+}
+
+const int32_t* virtual_perm(ptsne_ctx* c, const int32_t* perm, cudaStream_t s, cudaError_t* err) {
+    *err = cudaSuccess;
+    if (c->layers == 1) return perm;
+    virtual_perm_kernel<<<grid_for(c->p.n, 256), 256, 0, s>>>(perm, c->d_vsrc, c->d_vbase, c->p.n, c->npts,
+                                                              c->vperm);
+    *err = launched(c, 1);
+    return c->vperm;
 }
 
 // Per-point precisions of the previous epoch (original order) -> warm starts

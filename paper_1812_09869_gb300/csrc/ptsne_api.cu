@@ -51,6 +51,17 @@ int fail(ptsne_ctx* c, int code, const char* fmt, const char* a = "", long long 
                                            (long long)__LINE__);                          \
     } while (0)
 
+// The permutation the kernels use: the caller's, or with layers the virtual
+// one of the thread rows (enqueued on s).
+#define VPERM(var, perm, s)                                                              \
+    const int32_t* var;                                                                  \
+    do {                                                                                 \
+        cudaError_t ve_;                                                                 \
+        var = virtual_perm(c, (perm), (s), &ve_);                                        \
+        if (ve_ != cudaSuccess) return fail(c, PTSNE_ECUDA, "%s: %lld", cudaGetErrorString(ve_), \
+                                            (long long)__LINE__);                        \
+    } while (0)
+
 template <class T>
 int dalloc(ptsne_ctx* c, T** p, size_t count) {
     const size_t bytes = sizeof(T) * (count ? count : 1);
@@ -72,7 +83,7 @@ void free_all(ptsne_ctx* c) {
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
                     c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense,
-                    c->beta_pt};
+                    c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -121,10 +132,21 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (!p.chunk_offsets) return bad("chunk_offsets is NULL", 0);
     if (p.chunk_offsets[0] != 0 || p.chunk_offsets[p.n_chunks] != p.n)
         return bad("chunk offsets must start at 0 and end at n", p.chunk_offsets[p.n_chunks]);
+    if (p.layers < 1 || p.layers > p.n_chunks) return bad("layers must be in [1, n_chunks]", p.layers);
+    if ((double)p.layers * (double)p.n >= 2147483647.0) return bad("layers x n must be < 2^31", p.layers);
+    for (int k = 0; k < p.n_chunks; ++k)
+        if (p.chunk_offsets[k + 1] < p.chunk_offsets[k]) return bad("chunk offsets must not decrease", k);
+    // threads: chunk t chained with the next layers - 1 chunks
+    std::vector<int64_t> toff(p.n_chunks + 1, 0);
     int64_t zmin = INT64_MAX, zmax = 0;
-    for (int k = 0; k < p.n_chunks; ++k) {
-        const int64_t z = p.chunk_offsets[k + 1] - p.chunk_offsets[k];
-        if (z < 2 || z > kMaxChunk) return bad("every chunk size must be in [2, 8192]", z);
+    for (int t = 0; t < p.n_chunks; ++t) {
+        int64_t z = 0;
+        for (int k = 0; k < p.layers; ++k) {
+            const int e = (t + k) % p.n_chunks;
+            z += p.chunk_offsets[e + 1] - p.chunk_offsets[e];
+        }
+        if (z < 2 || z > kMaxChunk) return bad("every chunk (thread) size must be in [2, 8192]", z);
+        toff[t + 1] = toff[t] + z;
         zmin = std::min(zmin, z);
         zmax = std::max(zmax, z);
     }
@@ -144,10 +166,28 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
 
     c->p = p;
     c->p.chunk_offsets = nullptr;
+    c->npts = p.n;
+    c->layers = p.layers;
+    c->n_elem = p.n_chunks;
+    c->p.n = toff[p.n_chunks];   // rows: layers x points
     c->zmin = zmin;
     c->zmax = zmax;
     const int nc = p.n_chunks;
-    c->off.assign(p.chunk_offsets, p.chunk_offsets + nc + 1);
+    c->off = toff;
+    // layers: thread row -> (layer, position in the caller's permutation)
+    std::vector<int32_t> vsrc, vbase;
+    if (p.layers > 1) {
+        vsrc.reserve((size_t)c->p.n);
+        vbase.reserve((size_t)c->p.n);
+        for (int t = 0; t < nc; ++t)
+            for (int k = 0; k < p.layers; ++k) {
+                const int e = (t + k) % nc;
+                for (int64_t i = p.chunk_offsets[e]; i < p.chunk_offsets[e + 1]; ++i) {
+                    vsrc.push_back((int32_t)i);
+                    vbase.push_back((int32_t)(k * p.n));
+                }
+            }
+    }
     c->ld.resize(nc);
     c->moff.resize(nc);
     c->tile_start.resize(nc + 1);
@@ -219,13 +259,13 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     std::stable_sort(c->order.begin(), c->order.end(), [&](int a, int b) {
         return (c->off[a + 1] - c->off[a]) > (c->off[b + 1] - c->off[b]);
     });
-    std::vector<int32_t> cor(p.n);
+    std::vector<int32_t> cor(c->p.n);
     for (int k = 0; k < nc; ++k)
         for (int64_t r = c->off[k]; r < c->off[k + 1]; ++r) cor[r] = k;
     c->dp = (p.d + 3) & ~3;
     c->kp = (p.d + 63) & ~63;
 
-    const int64_t n = p.n, od = p.out_dim;
+    const int64_t n = c->p.n, od = p.out_dim;
     int st = PTSNE_OK;
 #define AL(ptr, count)                                               \
     do {                                                             \
@@ -279,7 +319,12 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     AL(c->cost_hist, 2 * kCostHist);
     AL(c->queue, 4);
     AL(c->dstats, 1);
-    AL(c->perm_cur, n);
+    AL(c->perm_cur, c->npts);
+    if (p.layers > 1) {
+        AL(c->d_vsrc, n);
+        AL(c->d_vbase, n);
+        AL(c->vperm, n);
+    }
     AL(c->cost_cur, 2);
 #undef AL
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -296,6 +341,10 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (e == cudaSuccess && c->ntiles128)
         e = up(c->d_tiles128, tiles128.data(), sizeof(TileDesc) * tiles128.size());
     if (e == cudaSuccess && !colblk.empty()) e = up(c->d_colblk, colblk.data(), sizeof(TileDesc) * colblk.size());
+    if (e == cudaSuccess && p.layers > 1) {
+        e = up(c->d_vsrc, vsrc.data(), sizeof(int32_t) * vsrc.size());
+        if (e == cudaSuccess) e = up(c->d_vbase, vbase.data(), sizeof(int32_t) * vbase.size());
+    }
     if (e == cudaSuccess && c->ntiles2) {
         e = up(c->d_ptile_off, ptoff.data(), sizeof(int64_t) * nc);
         if (e == cudaSuccess) e = up(c->d_tiles2, tiles2.data(), sizeof(TileDesc2) * tiles2.size());
@@ -385,8 +434,9 @@ static int iterate_rows(ptsne_ctx* c, float* grad_perm, cudaStream_t s);
 // One epoch of ptsne_run on the partition perm: affinities, every gradient
 // iteration of every chunk, the pool back into Y and, if want_cost, the
 // epoch's average cost into cost_dst (2 doubles).
-static int run_epoch(ptsne_ctx* c, const float* X, const int32_t* perm, float* Y, bool want_cost, double* cost_dst,
+static int run_epoch(ptsne_ctx* c, const float* X, const int32_t* perm_in, float* Y, bool want_cost, double* cost_dst,
                      cudaStream_t s) {
+    VPERM(perm, perm_in, s);
     int st = affinities_impl(c, X, perm, s, false, Y);
     if (st != PTSNE_OK) return st;
     mark(c, PTSNE_STAGE_ITERATE, s);
@@ -450,25 +500,28 @@ static int capture_epoch(ptsne_ctx* c, const float* X, float* Y, bool want_cost)
     return PTSNE_OK;
 }
 
-int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P_out, float* beta_out,
+int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm_in, float* P_out, float* beta_out,
                      void* stream) {
     if (!c) return PTSNE_EINVAL;
-    if (!X || !perm) return fail(c, PTSNE_EINVAL, "X and perm must be device pointers%s%lld");
+    if (!X || !perm_in) return fail(c, PTSNE_EINVAL, "X and perm must be device pointers%s%lld");
     cudaStream_t s = as_stream(stream);
-    int st = affinities_impl(c, X, perm, s, true, nullptr);
+    CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
+    VPERM(perm, perm_in, s);
+    int st = affinities_impl(c, X, perm, s, false, nullptr);
     if (st != PTSNE_OK) return st;
     if (P_out) CK(c->P2 ? launch_export_packed(c, P_out, s) : launch_export_P(c, P_out, s));
     if (beta_out) CK(launch_scatter_rows(c, c->beta, perm, 1, beta_out, s));
     return PTSNE_OK;
 }
 
-int ptsne_affinities_from_distances(ptsne_ctx* c, const float* D_dev, int64_t ldd, const int32_t* perm,
+int ptsne_affinities_from_distances(ptsne_ctx* c, const float* D_dev, int64_t ldd, const int32_t* perm_in,
                                     float* P_out, float* beta_out, void* stream) {
     if (!c) return PTSNE_EINVAL;
-    if (!D_dev || !perm) return fail(c, PTSNE_EINVAL, "D and perm must be device pointers%s%lld");
-    if (ldd < c->p.n) return fail(c, PTSNE_EINVAL, "ldd must be >= n%s (%lld)", "", ldd);
+    if (!D_dev || !perm_in) return fail(c, PTSNE_EINVAL, "D and perm must be device pointers%s%lld");
+    if (ldd < c->npts) return fail(c, PTSNE_EINVAL, "ldd must be >= n%s (%lld)", "", ldd);
     cudaStream_t s = as_stream(stream);
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
+    VPERM(perm, perm_in, s);
     CK(launch_gather_dist(c, D_dev, ldd, perm, s));
     CK(launch_reset_optim(c, s));
     // the given dissimilarities are final: one fine search, then the joint P
@@ -487,10 +540,11 @@ int ptsne_affinities_from_distances(ptsne_ctx* c, const float* D_dev, int64_t ld
     return PTSNE_OK;
 }
 
-int ptsne_distances(ptsne_ctx* c, const float* X, const int32_t* perm, float* D_out, void* stream) {
+int ptsne_distances(ptsne_ctx* c, const float* X, const int32_t* perm_in, float* D_out, void* stream) {
     if (!c) return PTSNE_EINVAL;
-    if (!X || !perm || !D_out) return fail(c, PTSNE_EINVAL, "X, perm and D_out must be device pointers%s%lld");
+    if (!X || !perm_in || !D_out) return fail(c, PTSNE_EINVAL, "X, perm and D_out must be device pointers%s%lld");
     cudaStream_t s = as_stream(stream);
+    VPERM(perm, perm_in, s);
     CK(launch_gather(c, X, perm, s));
     if (c->p.precision == PTSNE_PREC_BF16_WINDOW) {
         CK(launch_gather_bf16(c, s));
@@ -517,11 +571,12 @@ static int iterate_rows(ptsne_ctx* c, float* grad_perm, cudaStream_t s) {
     return PTSNE_OK;
 }
 
-int ptsne_step(ptsne_ctx* c, const int32_t* perm, float* Y, float* grad_out, double* Z_out, void* stream) {
+int ptsne_step(ptsne_ctx* c, const int32_t* perm_in, float* Y, float* grad_out, double* Z_out, void* stream) {
     if (!c) return PTSNE_EINVAL;
-    if (!perm || !Y) return fail(c, PTSNE_EINVAL, "perm and Y must be device pointers%s%lld");
+    if (!perm_in || !Y) return fail(c, PTSNE_EINVAL, "perm and Y must be device pointers%s%lld");
     if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_step before ptsne_affinities%s%lld");
     cudaStream_t s = as_stream(stream);
+    VPERM(perm, perm_in, s);
     CK(launch_gather_y(c, Y, perm, c->Yc, s));
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
         CK(launch_iterate(c, 1, 0, grad_out ? c->gradp : nullptr, c->Zc, nullptr, s));
@@ -536,11 +591,12 @@ int ptsne_step(ptsne_ctx* c, const int32_t* perm, float* Y, float* grad_out, dou
     return PTSNE_OK;
 }
 
-int ptsne_cost(ptsne_ctx* c, const int32_t* perm, const float* Y, double* out_dev, void* stream) {
+int ptsne_cost(ptsne_ctx* c, const int32_t* perm_in, const float* Y, double* out_dev, void* stream) {
     if (!c) return PTSNE_EINVAL;
-    if (!perm || !Y || !out_dev) return fail(c, PTSNE_EINVAL, "perm, Y and out must be device pointers%s%lld");
+    if (!perm_in || !Y || !out_dev) return fail(c, PTSNE_EINVAL, "perm, Y and out must be device pointers%s%lld");
     if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_cost before ptsne_affinities%s%lld");
     cudaStream_t s = as_stream(stream);
+    VPERM(perm, perm_in, s);
     CK(launch_gather_y(c, Y, perm, c->Yc, s));
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
         CK(launch_iterate(c, 0, 1, nullptr, nullptr, c->cost_chunk, s));
@@ -557,7 +613,7 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
     if (!X || !perms || !Y) return fail(c, PTSNE_EINVAL, "X, perms and Y must be device pointers%s%lld");
     if (epochs < 0) return fail(c, PTSNE_EINVAL, "epochs must be >= 0%s (%lld)", "", epochs);
     cudaStream_t s = as_stream(stream);
-    const int64_t n = c->p.n;
+    const int64_t n = c->p.n, npts = c->npts;   // rows, points
     const bool want_cost = cost_out != nullptr;
     const bool use_graph = c->p.use_graph != 0;
     if (use_graph && (!c->graph || c->graph_X != X || c->graph_Y != Y || c->graph_cost != (int)want_cost ||
@@ -569,10 +625,10 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
     CK(cudaMemsetAsync(c->beta_pt, 0, sizeof(float) * n, s));
     for (int e = 0; e < epochs; ++e) {
-        const int32_t* perm = perms + (int64_t)e * n;
+        const int32_t* perm = perms + (int64_t)e * npts;
         const int slot = e % kCostHist;
         if (use_graph) {
-            CK(cudaMemcpyAsync(c->perm_cur, perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(c->perm_cur, perm, sizeof(int32_t) * npts, cudaMemcpyDeviceToDevice, s));
             CK(cudaGraphLaunch(c->graph, s));
             c->launches += c->graph_launches;
             if (want_cost)
@@ -616,17 +672,17 @@ int ptsne_run_host(ptsne_ctx* c, const float* X_host, const int32_t* perms_host,
     if (!X_host || !perms_host || !Y_host) return fail(c, PTSNE_EINVAL, "host buffers must be non-NULL%s%lld");
     if (epochs < 0) return fail(c, PTSNE_EINVAL, "epochs must be >= 0%s (%lld)", "", epochs);
     cudaStream_t s = as_stream(stream);
-    const int64_t n = c->p.n, d = c->p.d, od = c->p.out_dim;
+    const int64_t n = c->p.n, npts = c->npts, d = c->p.d, od = c->p.out_dim;   // n: map rows
     int st;
-    if (!c->hX && (st = dalloc(c, &c->hX, (size_t)(n * d))) != PTSNE_OK) return st;
+    if (!c->hX && (st = dalloc(c, &c->hX, (size_t)(npts * d))) != PTSNE_OK) return st;
     if (!c->hY && (st = dalloc(c, &c->hY, (size_t)(n * od))) != PTSNE_OK) return st;
-    if (c->hperms_cap < (int64_t)epochs * n) {
+    if (c->hperms_cap < (int64_t)epochs * npts) {
         if (c->hperms) { cudaFree(c->hperms); c->ws_bytes -= sizeof(int32_t) * c->hperms_cap; c->hperms = nullptr; }
-        if ((st = dalloc(c, &c->hperms, (size_t)epochs * n)) != PTSNE_OK) return st;
-        c->hperms_cap = (int64_t)epochs * n;
+        if ((st = dalloc(c, &c->hperms, (size_t)epochs * npts)) != PTSNE_OK) return st;
+        c->hperms_cap = (int64_t)epochs * npts;
     }
-    CK(cudaMemcpyAsync(c->hX, X_host, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->hperms, perms_host, sizeof(int32_t) * epochs * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->hX, X_host, sizeof(float) * npts * d, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->hperms, perms_host, sizeof(int32_t) * epochs * npts, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->hY, Y_host, sizeof(float) * n * od, cudaMemcpyHostToDevice, s));
     st = ptsne_run(c, c->hX, c->hperms, epochs, c->hY, cost_out, stream);
     if (st < 0) return st;

@@ -123,7 +123,14 @@ struct IterTune {
 }  // namespace ptsne
 
 struct ptsne_ctx {
-    ptsne_params p{};
+    ptsne_params p{};                  // p.n is the number of ROWS: layers x points
+    int64_t npts = 0;                  // points (the caller's n)
+    int layers = 1;
+    int n_elem = 0;                    // elementary chunks of the caller's offsets
+    // layers > 1: thread row r holds point perm[vsrc[r]] of layer vlayer[r]
+    int32_t* d_vsrc = nullptr;         // rows
+    int32_t* d_vbase = nullptr;        // rows: layer * npts
+    int32_t* vperm = nullptr;          // rows: the virtual permutation of the current call
     std::vector<int64_t> off, moff;
     std::vector<int32_t> ld, order;
     int64_t zmin = 0, zmax = 0, mtotal = 0, ntiles = 0;
@@ -233,6 +240,9 @@ cudaError_t launch_dist_fp32(const ptsne_ctx* c, int64_t tile_begin, int64_t til
 cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
 // beta_init (optional): start each row's search from this beta instead of 1 / mean(d - m)
+// layers > 1: the caller's permutation (npts entries) -> the virtual one of
+// the thread rows (layer * npts + point); returns the pointer to use.
+const int32_t* virtual_perm(ptsne_ctx* c, const int32_t* perm, cudaStream_t s, cudaError_t* err);
 cudaError_t launch_gather_dist(const ptsne_ctx* c, const float* Dfull, int64_t ldd, const int32_t* perm,
                                cudaStream_t s);
 cudaError_t launch_beta_warm(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s);

@@ -47,6 +47,7 @@ class Params(C.Structure):
         ("precision", C.c_int32),
         ("schedule", C.c_int32),
         ("use_graph", C.c_int32),
+        ("layers", C.c_int32),
     ]
 
 
@@ -140,6 +141,7 @@ class Config:
     precision: str = "fp32"
     schedule: str = "batched"
     use_graph: int = 1
+    layers: int = 1              # > 1: threads chain `layers` elementary chunks; maps hold layers x n rows
 
 
 class Context:
@@ -151,7 +153,8 @@ class Context:
         self._off = np.ascontiguousarray(np.asarray(cfg.offsets, dtype=np.int64))
         p = Params(cfg.n, cfg.d, cfg.out_dim, cfg.perplexity, len(self._off) - 1,
                    self._off.ctypes.data_as(C.POINTER(C.c_int64)), cfg.iters, cfg.lr, cfg.momentum,
-                   cfg.lr_mode, cfg.use_gains, _PRECISION[cfg.precision], _SCHEDULE[cfg.schedule], cfg.use_graph)
+                   cfg.lr_mode, cfg.use_gains, _PRECISION[cfg.precision], _SCHEDULE[cfg.schedule], cfg.use_graph,
+                   cfg.layers)
         h = C.c_void_p()
         rc = lib().ptsne_create(C.byref(h), C.byref(p))
         if rc != OK:

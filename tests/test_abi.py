@@ -41,11 +41,12 @@ def _params(**kw):
     from paper_1812_09869_gb300 import ptsne
     off = np.asarray(kw.pop("offsets", [0, 100, 200]), dtype=np.int64)
     base = dict(n=int(off[-1]), d=8, out_dim=2, perplexity=10.0, n_chunks=len(off) - 1, iters=10, lr=200.0,
-                momentum=0.5, lr_mode=0, use_gains=1, precision=0, schedule=0, use_graph=1)
+                momentum=0.5, lr_mode=0, use_gains=1, precision=0, schedule=0, use_graph=1, layers=1)
     base.update(kw)
     p = ptsne.Params(base["n"], base["d"], base["out_dim"], base["perplexity"], base["n_chunks"],
                      off.ctypes.data_as(C.POINTER(C.c_int64)), base["iters"], base["lr"], base["momentum"],
-                     base["lr_mode"], base["use_gains"], base["precision"], base["schedule"], base["use_graph"])
+                     base["lr_mode"], base["use_gains"], base["precision"], base["schedule"], base["use_graph"],
+                     base["layers"])
     return p, off
 
 
@@ -54,6 +55,7 @@ def _params(**kw):
     dict(perplexity=float("nan")), dict(offsets=[0, 1, 200]), dict(offsets=[0, 100, 9000]),
     dict(n=150), dict(iters=-1), dict(lr=0.0), dict(momentum=1.0), dict(lr_mode=7), dict(use_gains=2),
     dict(precision=9), dict(schedule=3), dict(offsets=[0, 9000, 9100], perplexity=5.0), dict(use_graph=2),
+    dict(layers=0), dict(layers=3), dict(offsets=[0, 5000, 9000], layers=2),
 ])
 def test_create_rejects_bad_parameters_on_the_host(lib, bad):
     p, off = _params(**bad)
