@@ -293,3 +293,35 @@ def test_errors_nonfinite_input_and_call_order(dev):
         ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perm).to(dev), 1, torch.zeros(300, 2, device=dev))
     assert e.value.code == ptsne.ENONFINITE
     ctx.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp32", "bf16_window"])
+def test_maximum_chunk_size(dev, precision):
+    """z = 8192, the largest chunk: the batched kernel's map and accumulators
+    take 196 KB of shared memory, so it runs with fewer consumer slots; P, β,
+    the gradient and Z after one step still match the oracle."""
+    z = 8192
+    X, _ = synth.gaussian_mixture(z + 700, 16, 12, seed=80, anisotropic=True)
+    off = np.array([0, 700, z + 700])                  # a small chunk and a maximal one
+    perm = synth.permutations(z + 700, 1, seed=81)[0]
+    Y0 = synth.init_disk(z + 700, seed=82)
+    ctx, _, pd, blocks, beta = _gpu_affinities(dev, X, perm, off, perplexity=30.0, precision=precision)
+    Yd = torch.from_numpy(Y0.copy()).to(dev)
+    gd = torch.zeros_like(Yd)
+    Zd = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.step(pd, Yd, grad_out=gd, Z_out=Zd)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.close()
+    assert st.bisect_failed_rows == 0 and st.wait_timeouts == 0
+    g, Z = gd.cpu().numpy(), Zd.cpu().numpy()
+    for c in range(2):
+        idx = perm[off[c]:off[c + 1]]
+        Pr, br, bad = O.affinities(X[idx], 30.0)
+        assert bad == 0
+        assert p_error(blocks[c], Pr) <= P_TOL, (c, p_error(blocks[c], Pr))
+        assert np.abs(beta[idx] - br).max() <= 1e-4 * br.max()
+        gr, Zr = O.gradient(Pr, Y0[idx])
+        assert rel_max(g[idx], gr) <= GRAD_TOL
+        assert abs(Z[c] - Zr) <= 1e-6 * Zr
