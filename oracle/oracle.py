@@ -236,6 +236,31 @@ def ptsne_run_layers(X, Y0, perms, offsets, layers, prm: OrcParams):
 
 
 # ---------------------------------------------------------------------------
+# Perplexity-adaptive kernel density estimate of a 2-D map (paKDE, the
+# paper's Clustering section): the sample smoothing estimator with Gaussian
+# kernels K_j = exp(-beta_j |c - y_j|^2) / pi and h_j^2 = 1 / beta_j, i.e.
+#     f(c) = (S / n) sum_j (beta_j / pi) exp(-beta_j |c - y_j|^2)
+# on a regular grid of cells c of area S; beta_j from the perplexity search on
+# the map's own distances.  Plain numpy, every point against every cell.
+# ---------------------------------------------------------------------------
+
+def kde_grid(Y, beta, gx, gy, box):
+    """Density of each cell of a gx x gy grid over box = (xmin, xmax, ymin,
+    ymax), evaluated at the cell centres; returns (gy, gx) float64."""
+    Y, beta = _f64(Y), _f64(beta)
+    x0, x1, y0, y1 = map(float, box)
+    dx, dy = (x1 - x0) / gx, (y1 - y0) / gy
+    cx = x0 + (np.arange(gx) + 0.5) * dx
+    cy = y0 + (np.arange(gy) + 0.5) * dy
+    f = np.zeros((gy, gx))
+    for j in range(Y.shape[0]):
+        ex = np.exp(-beta[j] * (cx - Y[j, 0]) ** 2)
+        ey = np.exp(-beta[j] * (cy - Y[j, 1]) ** 2)
+        f += (beta[j] / math.pi) * np.outer(ey, ex)
+    return f * (dx * dy) / Y.shape[0]
+
+
+# ---------------------------------------------------------------------------
 # Learned out-of-sample mapper (not in the paper): MLP d_in -> 256 -> 256 -> 2
 # with exact (erf) GELU, trained by mean squared error on standardised ptSNE
 # coordinates with AdamW.  FP64 numpy, written as the plain definition.

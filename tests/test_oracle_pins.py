@@ -467,3 +467,36 @@ def test_layers_chain_matches_an_explicit_assembly():
         kls.append(kl)
     assert np.array_equal(Y, Yref)
     assert cost[0, 0] == pytest.approx(np.mean(kls), rel=1e-15)
+
+
+def test_kde_cell_masses_match_gaussian_integrals():
+    """For one kernel, S times the density at a cell centre approximates the
+    exact Gaussian mass of the cell (products of erf differences) to second
+    order in the cell size, and the masses sum to 1 over a grid covering
+    +-8 standard deviations."""
+    from scipy.special import erf
+    beta, y = 3.0, np.array([[0.13, -0.21]])
+    s = 1.0 / math.sqrt(2.0 * beta)                  # per-axis standard deviation
+    box = (-8 * s + 0.13, 8 * s + 0.13, -8 * s - 0.21, 8 * s - 0.21)
+    g = 400
+    f = O.kde_grid(y, np.array([beta]), g, g, box)
+    edges_x = np.linspace(box[0], box[1], g + 1)
+    edges_y = np.linspace(box[2], box[3], g + 1)
+    mx = 0.5 * np.diff(erf((edges_x - y[0, 0]) / (math.sqrt(2) * s)))
+    my = 0.5 * np.diff(erf((edges_y - y[0, 1]) / (math.sqrt(2) * s)))
+    exact = np.outer(my, mx)
+    h = (box[1] - box[0]) / g
+    assert np.abs(f - exact).max() <= 0.5 * (h / s) ** 2 * exact.max()
+    assert abs(f.sum() - 1.0) <= 1e-6
+
+
+def test_kde_is_the_average_of_the_kernels():
+    """n points: the estimate is the mean of the one-point estimates (the
+    S / n normalisation), and scales with beta as a 2-D density."""
+    rng = np.random.default_rng(47)
+    Y = rng.standard_normal((5, 2))
+    beta = rng.uniform(0.5, 4.0, 5)
+    box = (-4.0, 4.0, -3.0, 5.0)
+    f = O.kde_grid(Y, beta, 60, 50, box)
+    parts = [O.kde_grid(Y[j:j + 1], beta[j:j + 1], 60, 50, box) for j in range(5)]
+    assert np.allclose(f, np.mean(parts, axis=0), rtol=1e-13, atol=0)
