@@ -184,8 +184,8 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* params);
 void ptsne_destroy(ptsne_ctx* ctx);
 
 /* Text of the last error recorded on ctx (never NULL).  With ctx == NULL:
- * the reason of the last failed ptsne_create or ptsne_gradient_static on the
- * calling thread. */
+ * the reason of the last failed ptsne_create, ptsne_gradient_static or
+ * ptsne_kde_grid on the calling thread. */
 const char* ptsne_last_error(const ptsne_ctx* ctx);
 
 /* Input affinities for the partition perm_dev (Eq. 1-3 per chunk, n := z).
@@ -263,6 +263,21 @@ int ptsne_get_stats(ptsne_ctx* ctx, ptsne_stats* out, void* stream);
 
 /* Bytes of device workspace held by ctx. */
 size_t ptsne_workspace_bytes(const ptsne_ctx* ctx);
+
+/* Perplexity-adaptive kernel density estimate of a 2-D map (paKDE, the
+ * paper's Clustering section): the sample smoothing estimator with Gaussian
+ * kernels, f(c) = (S / n) sum_j (beta_j / pi) exp(-beta_j |c - y_j|^2), at the
+ * centres of a gx x gy grid of cells of area S over box_host = {xmin, xmax,
+ * ymin, ymax} (host, 4 floats).  Y_dev: n x 2 float32 map; beta_dev: n
+ * precisions, obtained with the same perplexity search as the input
+ * affinities applied to the map (ptsne_affinities on a context with d = 2,
+ * X := Y).  density_dev: gy x gx float32 (row = y cell), overwritten; its sum
+ * is the kernel mass inside the box (1 when the box covers the map).  Kernels
+ * are dropped beyond beta r^2 = 30, and points with a non-positive or
+ * non-finite beta or position are ignored.  n >= 1, 1 <= gx, gy <= 16384;
+ * else PTSNE_EINVAL with the reason in ptsne_last_error(NULL).  Async. */
+int ptsne_kde_grid(const float* Y_dev, const float* beta_dev, int64_t n, int32_t gx, int32_t gy,
+                   const float* box_host, float* density_dev, void* stream);
 
 /* Largest chunk ptsne_gradient_static accepts. */
 #define PTSNE_STATIC_MAX_ROWS 32768

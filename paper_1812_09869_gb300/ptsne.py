@@ -112,6 +112,7 @@ def lib():
         L.ptsne_autotune.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_char_p, C.POINTER(TuneTrial), C.c_int32,
                                      C.POINTER(C.c_int32), vp]
         L.ptsne_gradient_static.argtypes = [vp, C.c_int64, vp, C.c_int32, C.c_int32, vp, vp, vp]
+        L.ptsne_kde_grid.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_float), vp, vp]
         _lib = L
     return _lib
 
@@ -263,6 +264,17 @@ def gradient_static(P, Y, grad_out, Z_out=None, ld=None, stream=None):
     z, od = int(Y.shape[0]), int(Y.shape[1])
     ld = int(P.shape[-1]) if ld is None else int(ld)
     rc = lib().ptsne_gradient_static(_ptr(P), ld, _ptr(Y), z, od, _ptr(grad_out), _ptr(Z_out), _stream(stream))
+    if rc != OK:
+        raise PtsneError(rc, lib().ptsne_last_error(None).decode())
+    return rc
+
+
+def kde_grid(Y, beta, gx, gy, box, density_out, stream=None):
+    """ptsne_kde_grid: paKDE of the map Y (n x 2) with precisions beta (n) on a
+    gx x gy grid over box = (xmin, xmax, ymin, ymax) into density_out (gy x gx)."""
+    b = (C.c_float * 4)(*[float(v) for v in box])
+    rc = lib().ptsne_kde_grid(_ptr(Y), _ptr(beta), int(Y.shape[0]), int(gx), int(gy), b, _ptr(density_out),
+                              _stream(stream))
     if rc != OK:
         raise PtsneError(rc, lib().ptsne_last_error(None).decode())
     return rc

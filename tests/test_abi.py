@@ -109,3 +109,15 @@ def test_mapper_pack_roundtrip():
     back = M.unpack(flat, 50, 3)
     for k in M.PARAM_ORDER:
         assert np.array_equal(back[k], W[k])
+
+
+def test_kde_grid_rejects_bad_arguments_on_the_host(lib):
+    from paper_1812_09869_gb300 import ptsne
+    fake = C.c_void_p(0x1000)
+    box = (C.c_float * 4)(0.0, 1.0, 0.0, 1.0)
+    bad_box = (C.c_float * 4)(1.0, 0.0, 0.0, 1.0)
+    assert lib.ptsne_kde_grid(fake, fake, 10, 0, 8, box, fake, None) == ptsne.EINVAL
+    assert lib.ptsne_kde_grid(fake, fake, 0, 8, 8, box, fake, None) == ptsne.EINVAL
+    assert lib.ptsne_kde_grid(fake, fake, 10, 8, 8, bad_box, fake, None) == ptsne.EINVAL
+    assert lib.ptsne_kde_grid(None, fake, 10, 8, 8, box, fake, None) == ptsne.EINVAL
+    assert "ptsne_kde_grid" in lib.ptsne_last_error(None).decode()
