@@ -359,7 +359,7 @@ struct KSum {
 // row-wise), the other rows of b (tile column-wise); G = 4 halves each.  A
 // diagonal tile (a == b) is read row-wise only, its columns split G ways.
 template <int OD, int N, int START>
-__device__ __forceinline__ void consume_share(const float* tile, const float* map, int zcap, int z, int a, int b,
+__device__ __forceinline__ void consume_share(const float* tile, const float* map, int zcap, int a, int b,
                                               int lane, int colwise, bool cost, float* acc,
                                               uint32_t empty_bar, KSum (&part)[4], bool diag_owner) {
     constexpr int start = START;
@@ -533,22 +533,22 @@ __global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
                         const int w = kPT / G, c0 = sub * w;
                         const bool own_diag = lane >= c0 && lane < c0 + w;
                         if (G == 2) {
-                            if (sub == 0) consume_share<OD, 16, 0>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else consume_share<OD, 16, 16>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            if (sub == 0) consume_share<OD, 16, 0>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else consume_share<OD, 16, 16>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
                         } else {
-                            if (sub == 0) consume_share<OD, 8, 0>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else if (sub == 1) consume_share<OD, 8, 8>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else if (sub == 2) consume_share<OD, 8, 16>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else consume_share<OD, 8, 24>(tile, map, zcap, z, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            if (sub == 0) consume_share<OD, 8, 0>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else if (sub == 1) consume_share<OD, 8, 8>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else if (sub == 2) consume_share<OD, 8, 16>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
+                            else consume_share<OD, 8, 24>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
                         }
                     } else {
                         // the slot's warps swap directions on alternate tiles, so the
                         // slower column-wise read is shared evenly between them
                         const int h = G / 2;                        // warps per direction
                         const int colwise = (sub >= h) ^ (kth & 1);
-                        if (G == 2) consume_share<OD, 32, 0>(tile, map, zcap, z, a, b, lane, colwise, cost, acc, ebar, part, false);
-                        else if (sub % 2 == 0) consume_share<OD, 16, 0>(tile, map, zcap, z, a, b, lane, colwise, cost, acc, ebar, part, false);
-                        else consume_share<OD, 16, 16>(tile, map, zcap, z, a, b, lane, colwise, cost, acc, ebar, part, false);
+                        if (G == 2) consume_share<OD, 32, 0>(tile, map, zcap, a, b, lane, colwise, cost, acc, ebar, part, false);
+                        else if (sub % 2 == 0) consume_share<OD, 16, 0>(tile, map, zcap, a, b, lane, colwise, cost, acc, ebar, part, false);
+                        else consume_share<OD, 16, 16>(tile, map, zcap, a, b, lane, colwise, cost, acc, ebar, part, false);
                     }
                 }
             }
