@@ -141,9 +141,11 @@ int ptsne_reset_counters(ptsne_ctx* ctx);
 
 /* Launch shape of the batched iteration kernel (no effect on results beyond
  * FP32 summation order).  cluster: thread blocks sharing one chunk through
- * distributed shared memory (1, 2 or 4); group: consumer warps that split
- * each P tile (2 or 4); consumer_warps: per block, a multiple of group in
- * [group, 20].  Defaults {2, 2, 20}; ptsne_autotune picks by timing. */
+ * distributed shared memory (1, 2 or 4); group: consumer warps per P tile,
+ * 1 (each consumer warp evaluates whole tiles; other values are rejected);
+ * consumer_warps: per block, 1 .. 20 (16 or fewer run a build of the kernel
+ * with more registers per thread).  Defaults {2, 1, 20}; ptsne_autotune picks
+ * by timing. */
 typedef struct {
     int32_t cluster;
     int32_t group;

@@ -9,17 +9,18 @@
 //     per unordered pair of 32-row blocks) from HBM into a ring of shared
 //     buffers with cp.async.bulk, one tile per lane in batches of at most the
 //     ring size, completion tracked by mbarriers;
-//   - consumer warps take the tiles in stream order, G = 2 or 4 warps per
-//     tile: a tile (rows a, columns b) serves both directions — rows of a
-//     against columns of b (the tile read row-wise) and rows of b against
-//     columns of a (read column-wise) — so every ordered pair (i, j) is
-//     evaluated once per iteration and P is read once per unordered pair
-//     (2 bytes per ordered pair).  Each warp copies its share of the tile into
-//     registers and releases the buffer before computing;
-//   - per ordered pair: w = 1 / (1 + |y_i - y_j|^2), and the row sums
-//     A_i += p_ij w (y_i - y_j), R_i += w^2 (y_i - y_j), Z_i += w (two pairs at
-//     a time per lane with packed f32x2 arithmetic for 2-D maps), merged into
-//     shared-memory accumulators with atomic adds;
+//   - consumer warps take whole tiles in stream order (warp w: tiles q with
+//     q = w mod the warp count); a warp copies its tile into registers and
+//     releases the buffer before computing;
+//   - an off-diagonal tile (rows a, columns b) is evaluated once per unordered
+//     pair: w = 1 / (1 + |y_i - y_j|^2) and the terms p_ij w (y_i - y_j) of
+//     A and w^2 (y_i - y_j) of R go to row i and, negated, to row j (column
+//     sums travel around rings of lanes, see the tile evaluation below), and
+//     2 w to Z; a diagonal tile holds both orders and is evaluated row-wise.
+//     So P is read once per unordered pair (2 bytes per ordered pair) and w is
+//     computed once per unordered pair.  Packed f32x2 arithmetic for 2-D
+//     maps; the sums are merged into shared-memory accumulators with atomic
+//     adds;
 //   - then Z = sum_i Z_i (FP64, over the cluster through distributed shared
 //     memory), dC/dy_i = 4 (A_i - R_i / Z) (Eq. 6), and the update of each
 //     block's slice of rows, broadcast to every block's copy of the map.
@@ -59,8 +60,7 @@ struct IterArgs {
     int* queue;                 // chunk work queue (zeroed before launch)
     unsigned int* timeouts;
     int zcap;                   // rows of the shared map / accumulators (multiple of 32)
-    int ring;                   // ring buffers: a multiple of the consumer slots (see below)
-    int group;                  // consumer warps per tile (2 or 4)
+    int ring;                   // ring buffers: a multiple of the consumer warps (see below)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -176,129 +176,249 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
     return d;
 }
 
-// ---------------------------------------------------------------- per-pair arithmetic
+// ---------------------------------------------------------------- tile evaluation
 // The shared map is structure-of-arrays: coordinate k of row i at map[k * zcap + i].
+//
+// One consumer warp evaluates a whole 32 x 32 tile (rows of block a, columns
+// of block b).  Lane L = 16 h + g owns rows 2g and 2g + 1 of a and the ring h
+// of b's columns 16h..16h+15, met in the order (g + t) & 15, two columns per
+// double step s (t = 2s, 2s + 1).  Per pair: w = 1 / (1 + |y_i - y_j|^2) and
+// the terms p w (y_i - y_j) and w^2 (y_i - y_j) of A and R, plus w for Z.
+//
+// Off-diagonal tile (a != b): every unordered pair is evaluated once.  Its
+// terms go to the lane's row sums and, with the opposite sign, to a column
+// packet (the sums of the two columns of the double step).  After each double
+// step the packets move two lanes down the ring (lane g receives from lane
+// g + 2), so the packet of columns (c, c + 1) meets the 8 lanes g = c - 2s;
+// at the end lane g holds column (g - 2)'s partial and column (g - 1)'s, and
+// the two partials of a column (from lanes of either parity) are added.
+// Diagonal tile (a == b): both (i, j) and (j, i) are stored, so the tile is
+// evaluated row-wise only, every ordered pair once.
+//
+// Rows and columns at or beyond z are padding far from everything (see kPad):
+// their pairs add nothing, and their own sums are never read.
 
-// Gradient sums of one lane's row (own) against n partner rows pbase..pbase+n-1
-// with P values pv, 2-D maps, two pairs per packed instruction.
-template <int N>
-__device__ __forceinline__ void grad_task_2d(const float* map, int zcap, int own, int pbase, const float (&pv)[N],
-                                             float (&a)[2], float (&r)[2], float& z) {
-    const float* xs = map;
-    const float* ys = map + zcap;
-    const float ox = xs[own], oy = ys[own];
-    const f2 OX = pk(ox, ox), OY = pk(oy, oy), NEG = pk(-1.f, -1.f), ONE = pk(1.f, 1.f);
-    // one accumulator set: a second set shortens the dependency chains but costs
-    // the registers that let the compiler overlap the steps (measured slower)
-    f2 AX = 0, AY = 0, RX = 0, RY = 0, Z = 0;
-#pragma unroll
-    for (int m = 0; m < N / 4; ++m) {
-        const float4 x4 = *reinterpret_cast<const float4*>(xs + pbase + 4 * m);
-        const float4 y4 = *reinterpret_cast<const float4*>(ys + pbase + 4 * m);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const f2 X = h ? pk(x4.z, x4.w) : pk(x4.x, x4.y);
-            const f2 Yv = h ? pk(y4.z, y4.w) : pk(y4.x, y4.y);
-            const f2 Pp = pk(pv[4 * m + 2 * h], pv[4 * m + 2 * h + 1]);
-            const f2 DX = fma2(X, NEG, OX);     // own - other
-            const f2 DY = fma2(Yv, NEG, OY);
-            f2 Q = fma2(DX, DX, ONE);
-            Q = fma2(DY, DY, Q);
-            float q0, q1;
-            upk(Q, q0, q1);
-            const f2 W = pk(hw_rcp(q0), hw_rcp(q1));
-            Z = add2(Z, W);
-            const f2 PW = mul2(Pp, W), WW = mul2(W, W);
-            AX = fma2(PW, DX, AX);
-            AY = fma2(PW, DY, AY);
-            RX = fma2(WW, DX, RX);
-            RY = fma2(WW, DY, RY);
-        }
-    }
-    float l, h;
-    upk(AX, l, h); a[0] = l + h;
-    upk(AY, l, h); a[1] = l + h;
-    upk(RX, l, h); r[0] = l + h;
-    upk(RY, l, h); r[1] = l + h;
-    upk(Z, l, h); z = l + h;
+__device__ __forceinline__ f2 shfl_f2(f2 v, int src) {
+    float lo, hi;
+    upk(v, lo, hi);
+    lo = __shfl_sync(0xffffffffu, lo, src);
+    hi = __shfl_sync(0xffffffffu, hi, src);
+    return pk(lo, hi);
+}
+__device__ __forceinline__ float hsum2(f2 v) {
+    float lo, hi;
+    upk(v, lo, hi);
+    return lo + hi;
 }
 
-// Same sums for 3-D maps (scalar arithmetic).
-template <int N>
-__device__ __forceinline__ void grad_task_3d(const float* map, int zcap, int own, int pbase, const float (&pv)[N],
-                                             float (&a)[3], float (&r)[3], float& z) {
-    float o[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { o[k] = map[k * zcap + own]; a[k] = 0.f; r[k] = 0.f; }
-    z = 0.f;
-#pragma unroll
-    for (int t = 0; t < N; ++t) {
-        float d[3], q = 1.0f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            d[k] = o[k] - map[k * zcap + pbase + t];
-            q = fmaf(d[k], d[k], q);
-        }
-        const float w = hw_rcp(q);
-        z += w;
-        const float pw = pv[t] * w, w2 = w * w;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            a[k] = fmaf(pw, d[k], a[k]);
-            r[k] = fmaf(w2, d[k], r[k]);
-        }
-    }
-}
-
-// Cost sums of one lane's row: sum p ln p, sum p ln w, sum p, sum w (Eq. 5, Eq. 9).
-template <int OD, int N>
-__device__ __forceinline__ void cost_task(const float* map, int zcap, int own, int pbase, const float (&pv)[N],
-                                          float (&c)[4]) {
-    float o[OD];
-#pragma unroll
-    for (int k = 0; k < OD; ++k) o[k] = map[k * zcap + own];
-    c[0] = c[1] = c[2] = c[3] = 0.f;
-#pragma unroll
-    for (int t = 0; t < N; ++t) {
-        float q = 1.0f;
-#pragma unroll
-        for (int k = 0; k < OD; ++k) {
-            const float d = o[k] - map[k * zcap + pbase + t];
-            q = fmaf(d, d, q);
-        }
-        c[3] += hw_rcp(q);
-        const float p = pv[t];
-        if (p >= FLT_MIN) {
-            c[0] += p * (hw_lg2(p) * kLn2f);
-            c[1] -= p * (hw_lg2(q) * kLn2f);
-            c[2] += p;
-        }
-    }
-}
-
-// Copy a warp's share of a staged tile into registers:
-// row-wise (lane = tile row) for tile columns [c0, c0 + N), or
-// column-wise (lane = tile column) for tile rows [r0, r0 + N).
-// The share's first column (row) C0 (R0) is a compile-time constant, so the
-// swizzled offsets fold into a few lane constants and immediate offsets.
-template <int N, int C0>
-__device__ __forceinline__ void tile_row_share(const float* tile, int lane, float (&pv)[N]) {
-    const float* trow = tile + lane * kPT;
+// A lane's 32 P values: float4 s holds rows (2g, 2g + 1) x steps (2s, 2s + 1).
+__device__ __forceinline__ void tile_lane_values(const float* tile, int lane, float4 (&pv)[8]) {
+    const float* base = tile + lane * kPT;
     const int l7 = lane & 7;
 #pragma unroll
-    for (int m = 0; m < N / 4; ++m) {
-        const int c4 = (C0 >> 2) + m;
-        const float4 v = *reinterpret_cast<const float4*>(trow + ((c4 ^ l7) << 2));
-        pv[4 * m] = v.x; pv[4 * m + 1] = v.y; pv[4 * m + 2] = v.z; pv[4 * m + 3] = v.w;
-    }
+    for (int s = 0; s < 8; ++s) pv[s] = *reinterpret_cast<const float4*>(base + ((s ^ l7) << 2));
 }
-template <int N, int R0>
-__device__ __forceinline__ void tile_col_share(const float* tile, int lane, float (&pv)[N]) {
-    const int hi = lane >> 2, lo = lane & 3;
+
+// Row sums of 2 rows kept by one lane of the pair (h, h ^ 1): lane h keeps row
+// 2g + h and adds the other lane's partial of it.
+__device__ __forceinline__ float keep_row(float mine0, float mine1, int h) {
+    const float keep = h ? mine1 : mine0, give = h ? mine0 : mine1;
+    return keep + __shfl_xor_sync(0xffffffffu, give, 16);
+}
+
+// Gradient sums of one tile, 2-D maps (packed f32x2 over the two columns of a
+// double step).  Adds A and R into acc, returns the lane's sum of w (both
+// orders of each pair of an off-diagonal tile).
+template <bool SYM>
+__device__ __forceinline__ float tile_grad_2d(const float* map, int zcap, int a, int b, int lane,
+                                              const float4 (&pv)[8], float* acc) {
+    const float* xs = map;
+    const float* ys = map + zcap;
+    const int g = lane & 15, h = lane >> 4;
+    const int ra = a * kPT + 2 * g, cb = b * kPT + 16 * h;
+    const float2 ox = *reinterpret_cast<const float2*>(xs + ra);
+    const float2 oy = *reinterpret_cast<const float2*>(ys + ra);
+    const f2 OX0 = pk(ox.x, ox.x), OX1 = pk(ox.y, ox.y), OY0 = pk(oy.x, oy.x), OY1 = pk(oy.y, oy.y);
+    const f2 NEG = pk(-1.f, -1.f), ONE = pk(1.f, 1.f);
+    f2 AX0 = 0, AY0 = 0, RX0 = 0, RY0 = 0, AX1 = 0, AY1 = 0, RX1 = 0, RY1 = 0, Z = 0;
+    f2 CAX = 0, CAY = 0, CRX = 0, CRY = 0;   // column packet (SYM)
+    const int nxt = (lane & 16) | ((g + 2) & 15);
 #pragma unroll
-    for (int t = 0; t < N; ++t) {
-        const int r = R0 + t;
-        pv[t] = tile[r * kPT + (((hi ^ (r & 7)) << 2) | lo)];
+    for (int s = 0; s < 8; ++s) {
+        const int c0 = cb + ((g + 2 * s) & 15), c1 = cb + ((g + 2 * s + 1) & 15);
+        const f2 XC = pk(xs[c0], xs[c1]), YC = pk(ys[c0], ys[c1]);
+        const f2 P0 = pk(pv[s].x, pv[s].y), P1 = pk(pv[s].z, pv[s].w);
+        const f2 DX0 = fma2(XC, NEG, OX0), DY0 = fma2(YC, NEG, OY0);   // own - other
+        const f2 DX1 = fma2(XC, NEG, OX1), DY1 = fma2(YC, NEG, OY1);
+        f2 Q0 = fma2(DX0, DX0, ONE);
+        Q0 = fma2(DY0, DY0, Q0);
+        f2 Q1 = fma2(DX1, DX1, ONE);
+        Q1 = fma2(DY1, DY1, Q1);
+        float q0, q1, q2, q3;
+        upk(Q0, q0, q1);
+        upk(Q1, q2, q3);
+        const f2 W0 = pk(hw_rcp(q0), hw_rcp(q1)), W1 = pk(hw_rcp(q2), hw_rcp(q3));
+        Z = add2(Z, add2(W0, W1));
+        const f2 PW0 = mul2(P0, W0), WW0 = mul2(W0, W0), PW1 = mul2(P1, W1), WW1 = mul2(W1, W1);
+        AX0 = fma2(PW0, DX0, AX0);
+        AY0 = fma2(PW0, DY0, AY0);
+        RX0 = fma2(WW0, DX0, RX0);
+        RY0 = fma2(WW0, DY0, RY0);
+        AX1 = fma2(PW1, DX1, AX1);
+        AY1 = fma2(PW1, DY1, AY1);
+        RX1 = fma2(WW1, DX1, RX1);
+        RY1 = fma2(WW1, DY1, RY1);
+        if constexpr (SYM) {
+            CAX = fma2(PW1, DX1, fma2(PW0, DX0, CAX));
+            CAY = fma2(PW1, DY1, fma2(PW0, DY0, CAY));
+            CRX = fma2(WW1, DX1, fma2(WW0, DX0, CRX));
+            CRY = fma2(WW1, DY1, fma2(WW0, DY0, CRY));
+            if (s < 7) {
+                CAX = shfl_f2(CAX, nxt);
+                CAY = shfl_f2(CAY, nxt);
+                CRX = shfl_f2(CRX, nxt);
+                CRY = shfl_f2(CRY, nxt);
+            }
+        }
+    }
+    const int row = ra + h;
+    atomicAdd(acc + row, keep_row(hsum2(AX0), hsum2(AX1), h));
+    atomicAdd(acc + zcap + row, keep_row(hsum2(AY0), hsum2(AY1), h));
+    atomicAdd(acc + 2 * zcap + row, keep_row(hsum2(RX0), hsum2(RX1), h));
+    atomicAdd(acc + 3 * zcap + row, keep_row(hsum2(RY0), hsum2(RY1), h));
+    if constexpr (SYM) {
+        const int prv = (lane & 16) | ((g + 15) & 15);
+        const int col = cb + ((g + 14) & 15);
+        float lo, hi;
+        upk(CAX, lo, hi);
+        atomicAdd(acc + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
+        upk(CAY, lo, hi);
+        atomicAdd(acc + zcap + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
+        upk(CRX, lo, hi);
+        atomicAdd(acc + 2 * zcap + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
+        upk(CRY, lo, hi);
+        atomicAdd(acc + 3 * zcap + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
+        return 2.0f * hsum2(Z);
+    }
+    return hsum2(Z);
+}
+
+// Same sums for 3-D maps (scalar arithmetic, same lane order and packets).
+template <bool SYM>
+__device__ __forceinline__ float tile_grad_3d(const float* map, int zcap, int a, int b, int lane,
+                                              const float4 (&pv)[8], float* acc) {
+    const int g = lane & 15, h = lane >> 4;
+    const int ra = a * kPT + 2 * g, cb = b * kPT + 16 * h;
+    const float* pf = reinterpret_cast<const float*>(pv);
+    float o[2][3], ra_[2][3], rr_[2][3], ca[2][3], cr[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[r][k] = map[k * zcap + ra + r];
+            ra_[r][k] = 0.f;
+            rr_[r][k] = 0.f;
+            ca[r][k] = 0.f;
+            cr[r][k] = 0.f;
+        }
+    float z = 0.f;
+    const int nxt = (lane & 16) | ((g + 2) & 15);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int cc = cb + ((g + 2 * s + e) & 15);
+            float xc[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) xc[k] = map[k * zcap + cc];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float d[3], q = 1.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    d[k] = o[r][k] - xc[k];
+                    q = fmaf(d[k], d[k], q);
+                }
+                const float w = hw_rcp(q);
+                z += w;
+                const float pw = pf[4 * s + 2 * r + e] * w, ww = w * w;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    ra_[r][k] = fmaf(pw, d[k], ra_[r][k]);
+                    rr_[r][k] = fmaf(ww, d[k], rr_[r][k]);
+                    if constexpr (SYM) {
+                        ca[e][k] = fmaf(pw, d[k], ca[e][k]);
+                        cr[e][k] = fmaf(ww, d[k], cr[e][k]);
+                    }
+                }
+            }
+        }
+        if constexpr (SYM) {
+            if (s < 7) {
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        ca[e][k] = __shfl_sync(0xffffffffu, ca[e][k], nxt);
+                        cr[e][k] = __shfl_sync(0xffffffffu, cr[e][k], nxt);
+                    }
+            }
+        }
+    }
+    const int row = ra + h;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        atomicAdd(acc + k * zcap + row, keep_row(ra_[0][k], ra_[1][k], h));
+        atomicAdd(acc + (3 + k) * zcap + row, keep_row(rr_[0][k], rr_[1][k], h));
+    }
+    if constexpr (SYM) {
+        const int prv = (lane & 16) | ((g + 15) & 15);
+        const int col = cb + ((g + 14) & 15);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(acc + k * zcap + col, -(ca[0][k] + __shfl_sync(0xffffffffu, ca[1][k], prv)));
+            atomicAdd(acc + (3 + k) * zcap + col, -(cr[0][k] + __shfl_sync(0xffffffffu, cr[1][k], prv)));
+        }
+        return 2.0f * z;
+    }
+    return z;
+}
+
+// Cost sums of a lane's 32 pairs: sum p ln p, sum p ln w, sum p, sum w (Eq. 5,
+// Eq. 9), doubled for an off-diagonal tile (each pair stands for both orders).
+template <int OD, bool SYM>
+__device__ __forceinline__ void tile_cost(const float* map, int zcap, int a, int b, int lane, const float4 (&pv)[8],
+                                          float (&c)[4]) {
+    const int g = lane & 15, h = lane >> 4;
+    const int ra = a * kPT + 2 * g, cb = b * kPT + 16 * h;
+    const float* pf = reinterpret_cast<const float*>(pv);
+    c[0] = c[1] = c[2] = c[3] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        float o[OD];
+#pragma unroll
+        for (int k = 0; k < OD; ++k) o[k] = map[k * zcap + ra + r];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int cc = cb + ((g + t) & 15);
+            float q = 1.0f;
+#pragma unroll
+            for (int k = 0; k < OD; ++k) {
+                const float d = o[k] - map[k * zcap + cc];
+                q = fmaf(d, d, q);
+            }
+            c[3] += hw_rcp(q);
+            const float p = pf[4 * (t >> 1) + 2 * r + (t & 1)];
+            if (p >= FLT_MIN) {
+                c[0] += p * (hw_lg2(p) * kLn2f);
+                c[1] -= p * (hw_lg2(q) * kLn2f);
+                c[2] += p;
+            }
+        }
+    }
+    if constexpr (SYM) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] *= 2.0f;
     }
 }
 
@@ -355,54 +475,16 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// One warp's share of a tile.  G = 2: one warp takes rows of a (tile
-// row-wise), the other rows of b (tile column-wise); G = 4 halves each.  A
-// diagonal tile (a == b) is read row-wise only, its columns split G ways.
-template <int OD, int N, int START>
-__device__ __forceinline__ void consume_share(const float* tile, const float* map, int zcap, int a, int b,
-                                              int lane, int colwise, bool cost, float* acc,
-                                              uint32_t empty_bar, KSum (&part)[4], bool diag_owner) {
-    constexpr int start = START;
-    float pv[N];
-    if (colwise) tile_col_share<N, START>(tile, lane, pv);
-    else tile_row_share<N, START>(tile, lane, pv);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(empty_bar);   // the buffer is free again
-    const int own = (colwise ? b : a) * kPT + lane;
-    const int pbase = (colwise ? a : b) * kPT + start;
-    if (!cost) {   // rows own >= z are padding: their sums are zero (see kPad)
-        float av[OD], rv[OD], w;
-        if constexpr (OD == 2) grad_task_2d<N>(map, zcap, own, pbase, pv, av, rv, w);
-        else grad_task_3d<N>(map, zcap, own, pbase, pv, av, rv, w);
-#pragma unroll
-        for (int k = 0; k < OD; ++k) {
-            atomicAdd(acc + k * zcap + own, av[k]);
-            atomicAdd(acc + (OD + k) * zcap + own, rv[k]);
-        }
-        part[0].add(diag_owner ? w - 1.0f : w);   // drop the w_ii = 1 term of this row
-    } else {
-        float cs[4];
-        cost_task<OD, N>(map, zcap, own, pbase, pv, cs);
-        part[0].add(diag_owner ? cs[3] - 1.0f : cs[3]);
-        part[1].add(cs[0]);
-        part[2].add(cs[1]);
-        part[3].add(cs[2]);
-    }
-}
-
-template <int OD>
-// At most 20 consumer warps + 1 producer warp (672 threads, 80 registers per
-// thread): more warps in flight outweigh the few spilled registers (measured
-// 6% faster than 16 consumer warps at 96 registers).
-__global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
+// Compiled for at most MAXT threads: 672 (20 consumer warps + the producer,
+// 80 registers per thread) or 544 (16 + 1, 96 registers).
+template <int OD, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = blockDim.x;
     const int Wc = (nthreads >> 5) - 1;            // consumer warps; the last warp produces
     const bool is_producer = warp == Wc;
-    const int G = A.group;
-    const int sub = warp % G;                       // this warp's share of each of its tiles
-    const int slot = warp / G, nslots = Wc / G;     // tiles q with q % nslots == slot
+    const int slot = warp, nslots = Wc;             // consumer warp: tiles q with q % nslots == slot
     const uint32_t ring_n = (uint32_t)A.ring;
     const int zcap = A.zcap;
 
@@ -423,7 +505,7 @@ __global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
     if (tid == 0) {
         for (int b = 0; b < A.ring; ++b) {
             mbar_init(full_a + 8 * b, 1);
-            mbar_init(empty_a + 8 * b, (uint32_t)G);
+            mbar_init(empty_a + 8 * b, 1u);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -515,8 +597,11 @@ __global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
                     __syncwarp();
                 }
             } else {
-                int kth = 0;    // tiles this warp has taken in the pass (alternates the roles)
-                for (; cur.q < qend; cur.advance_ring((uint32_t)nslots, ring_n), ++kth) {
+                // w of the pair (i, i), which a diagonal tile's row-wise pass counts
+                // in its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own column)
+                const float w_ii = hw_rcp(1.0f);
+                const bool diag_lane = (lane >> 4) == ((lane & 15) >> 3);
+                for (; cur.q < qend; cur.advance_ring((uint32_t)nslots, ring_n)) {
                     // The ring holds a whole number of consumer slots, so tile q - ring
                     // (this buffer's previous use) belonged to this same slot and was
                     // waited for before: the barrier is at most one phase behind, and
@@ -526,29 +611,27 @@ __global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
                     const float* tile = ring + (size_t)cur.buf * kPTileStride;
                     const int2 ab = *reinterpret_cast<const int2*>(tile + kPTileFloats);
                     const int a = ab.x, b = ab.y;
-                    const uint32_t ebar = empty_a + 8 * cur.buf;
-                    if (a == b) {
-                        // diagonal: rows of a against columns split G ways; the owner
-                        // of column `lane` drops that row's w_ii = 1
-                        const int w = kPT / G, c0 = sub * w;
-                        const bool own_diag = lane >= c0 && lane < c0 + w;
-                        if (G == 2) {
-                            if (sub == 0) consume_share<OD, 16, 0>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else consume_share<OD, 16, 16>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                        } else {
-                            if (sub == 0) consume_share<OD, 8, 0>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else if (sub == 1) consume_share<OD, 8, 8>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else if (sub == 2) consume_share<OD, 8, 16>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                            else consume_share<OD, 8, 24>(tile, map, zcap, a, b, lane, 0, cost, acc, ebar, part, own_diag);
-                        }
+                    float4 pv[8];
+                    tile_lane_values(tile, lane, pv);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty_a + 8 * cur.buf);   // the buffer is free again
+                    const bool diag = a == b;
+                    const float drop = diag && diag_lane ? 2.0f * w_ii : 0.0f;
+                    if (!cost) {
+                        float zl;
+                        if constexpr (OD == 2) zl = diag ? tile_grad_2d<false>(map, zcap, a, b, lane, pv, acc)
+                                                         : tile_grad_2d<true>(map, zcap, a, b, lane, pv, acc);
+                        else zl = diag ? tile_grad_3d<false>(map, zcap, a, b, lane, pv, acc)
+                                       : tile_grad_3d<true>(map, zcap, a, b, lane, pv, acc);
+                        part[0].add(zl - drop);
                     } else {
-                        // the slot's warps swap directions on alternate tiles, so the
-                        // slower column-wise read is shared evenly between them
-                        const int h = G / 2;                        // warps per direction
-                        const int colwise = (sub >= h) ^ (kth & 1);
-                        if (G == 2) consume_share<OD, 32, 0>(tile, map, zcap, a, b, lane, colwise, cost, acc, ebar, part, false);
-                        else if (sub % 2 == 0) consume_share<OD, 16, 0>(tile, map, zcap, a, b, lane, colwise, cost, acc, ebar, part, false);
-                        else consume_share<OD, 16, 16>(tile, map, zcap, a, b, lane, colwise, cost, acc, ebar, part, false);
+                        float cs[4];
+                        if (diag) tile_cost<OD, false>(map, zcap, a, b, lane, pv, cs);
+                        else tile_cost<OD, true>(map, zcap, a, b, lane, pv, cs);
+                        part[0].add(cs[3] - drop);
+                        part[1].add(cs[0]);
+                        part[2].add(cs[1]);
+                        part[3].add(cs[2]);
                     }
                 }
             }
@@ -633,7 +716,7 @@ __global__ void __launch_bounds__(672, 1) iterate_kernel(IterArgs A) {
 
 // ---------------------------------------------------------------- packed P assembly and export
 
-// Joint P (Eq. 3) of one stored 32 x 32 tile, written packed and swizzled:
+// Joint P (Eq. 3) of one stored 32 x 32 tile, written in the packed order:
 //   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ji - m_j)) / S_j) / (2z),
 // zero on the diagonal and outside the chunk.  D need not be symmetric: after
 // the window recompute each row holds its own exact entries.
@@ -678,8 +761,14 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
             }
         }
     }
+    // reorder through shared memory into the stored order, then write the
+    // tile with coalesced 16-byte stores
+    __shared__ __align__(16) float ot[kPTileFloats];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e)] = out[e];
+    __syncthreads();
     float* dst = P2 + (ptile_off[c] + td.pos) * kPTileStride;
-    *reinterpret_cast<float4*>(dst + packed_index(r, c4 * 4)) = make_float4(out[0], out[1], out[2], out[3]);
+    reinterpret_cast<float4*>(dst)[tid] = reinterpret_cast<const float4*>(ot)[tid];
     if (tid == 0)   // trailer: the tile's row and column blocks
         *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, 0, 0);
 }
@@ -745,13 +834,13 @@ cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t 
 cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc, double* cost_chunk,
                            cudaStream_t s) {
     if (iters <= 0 && !cost_pass) return cudaSuccess;
-    const int K = c->tune.cluster, G = c->tune.group;
-    if (G != 2 && G != 4) return cudaErrorInvalidValue;
+    const int K = c->tune.cluster;
+    if (c->tune.group != 1) return cudaErrorInvalidValue;
     int Wc = c->tune.consumer_warps;
-    int ring = iterate_ring(c->p.out_dim, c->zmax, Wc / G);
-    while (ring == 0 && Wc > G) {   // very large chunks: fewer consumer slots
-        Wc -= G;
-        ring = iterate_ring(c->p.out_dim, c->zmax, Wc / G);
+    int ring = iterate_ring(c->p.out_dim, c->zmax, Wc);
+    while (ring == 0 && Wc > 1) {   // very large chunks: fewer consumer warps
+        --Wc;
+        ring = iterate_ring(c->p.out_dim, c->zmax, Wc);
     }
     if (ring == 0) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, ring);
@@ -774,9 +863,9 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     a.timeouts = &c->dstats->timeouts;
     a.zcap = (int)((c->zmax + kPT - 1) / kPT * kPT);
     a.ring = ring;
-    a.group = G;
 
-    void (*kern)(IterArgs) = c->p.out_dim == 2 ? iterate_kernel<2> : iterate_kernel<3>;
+    void (*kern)(IterArgs) = c->p.out_dim == 2 ? (Wc > 16 ? iterate_kernel<2, 672> : iterate_kernel<2, 544>)
+                                               : (Wc > 16 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;

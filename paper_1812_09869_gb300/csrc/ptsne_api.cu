@@ -728,9 +728,7 @@ int ptsne_set_profiling(ptsne_ctx* c, int on) {
 int ptsne_set_tuning(ptsne_ctx* c, const ptsne_tuning* t) {
     if (!c || !t) return PTSNE_EINVAL;
     const bool ok_k = t->cluster == 1 || t->cluster == 2 || t->cluster == 4;
-    const bool ok_g = t->group == 2 || t->group == 4;
-    if (!ok_k || !ok_g || t->consumer_warps < t->group || t->consumer_warps > 20 ||
-        t->consumer_warps % t->group != 0)
+    if (!ok_k || t->group != 1 || t->consumer_warps < 1 || t->consumer_warps > 20)
         return fail(c, PTSNE_EINVAL, "invalid tuning%s (cluster %lld)", "", t->cluster);
     c->tune.cluster = t->cluster;
     c->tune.group = t->group;

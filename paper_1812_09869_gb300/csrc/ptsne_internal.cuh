@@ -33,9 +33,8 @@ struct TileDesc {
 // round-robin tournament over the chunk's nb row blocks: in every round each
 // block meets exactly one partner (or its own diagonal tile), so one pass over
 // the tiles in storage order touches every block once per round.  Inside a
-// tile, element (r, c) sits at r*32 + (((c >> 2) ^ (r & 7)) << 2 | (c & 3))
-// (16-byte chunks XOR-swizzled by row), which makes both a row-wise float4
-// read (lane = r) and a column read (lane = c) free of bank conflicts.
+// tile the 1024 values are ordered for the warp that evaluates it (see
+// packed_index): lane L owns 32 consecutive floats, read as 8 float4.
 constexpr int kPT = 32;                      // packed tile edge
 constexpr int kPTileFloats = kPT * kPT;      // 1024 floats = 4 KB of P
 // Stored tile: the 4 KB of P followed by a 16-byte trailer {a, b, 0, 0} (int
@@ -76,8 +75,16 @@ struct TourSched {
     }
 };
 
+// Position of element (r, c) of a stored tile.  The consuming warp's lane
+// L = 16 h + g owns rows 2g and 2g + 1 and the ring h of columns 16h..16h+15,
+// which it meets in the order (g + t) & 15, t = 0..15.  Its 32 values are
+// 8 float4, one per double step s = t / 2: {(2g, 2s), (2g, 2s+1), (2g+1, 2s),
+// (2g+1, 2s+1)} in (row, step) terms; the float4 index is XOR-swizzled by
+// L & 7 so that a warp-wide float4 read is free of bank conflicts.
 __host__ __device__ inline int packed_index(int r, int c) {
-    return r * kPT + ((((c >> 2) ^ (r & 7)) << 2) | (c & 3));
+    const int g = r >> 1, L = (c & 16) | g;
+    const int t = ((c & 15) - g) & 15;
+    return L * kPT + ((((t >> 1) ^ (L & 7)) << 2) | ((r & 1) << 1) | (t & 1));
 }
 
 // Device view of the chunk layout, passed by value to kernels.
@@ -116,8 +123,8 @@ struct Optim {                     // optimiser settings
 // Launch shape of the batched iteration kernel (chosen by the autotuner).
 struct IterTune {
     int cluster = 2;               // blocks sharing one chunk (1, 2 or 4)
-    int group = 2;                 // consumer warps per tile (2 or 4)
-    int consumer_warps = 20;       // consumer warps per block (multiple of group, <= 20)
+    int group = 1;                 // consumer warps per tile (1: each warp evaluates whole tiles)
+    int consumer_warps = 20;       // consumer warps per block (1 .. 20)
 };
 
 }  // namespace ptsne

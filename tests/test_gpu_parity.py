@@ -224,8 +224,10 @@ def test_batched_iterations_equal_plain_per_chunk_form(dev):
     assert rel_max(out[0] - Y0, out[1] - Y0) <= 1e-4
 
 
-# every launch shape of the batched kernel: blocks per chunk (cluster) x warps per tile (group)
-TUNINGS = [(1, 2, 16), (1, 4, 16), (2, 4, 16), (4, 4, 12), (2, 2, 16), (4, 2, 8), (1, 4, 4), (2, 2, 20), (1, 4, 20), (4, 2, 20)]
+# launch shapes of the batched kernel: blocks per chunk (cluster) x consumer warps,
+# both builds (<= 16 and > 16 consumer warps), one warp and a ring of 17 slots
+TUNINGS = [(1, 1, 16), (2, 1, 16), (4, 1, 12), (4, 1, 8), (1, 1, 4), (1, 1, 1), (2, 1, 17), (2, 1, 20), (1, 1, 20),
+           (4, 1, 20)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
