@@ -170,6 +170,11 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ f2 add2(f2 a, f2 b) {
     f2 d;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -239,7 +244,7 @@ __device__ __forceinline__ float tile_grad_2d(const float* map, int zcap, int a,
     const float2 ox = *reinterpret_cast<const float2*>(xs + ra);
     const float2 oy = *reinterpret_cast<const float2*>(ys + ra);
     const f2 OX0 = pk(ox.x, ox.x), OX1 = pk(ox.y, ox.y), OY0 = pk(oy.x, oy.x), OY1 = pk(oy.y, oy.y);
-    const f2 NEG = pk(-1.f, -1.f), ONE = pk(1.f, 1.f);
+    const f2 ONE = pk(1.f, 1.f);
     f2 AX0 = 0, AY0 = 0, RX0 = 0, RY0 = 0, AX1 = 0, AY1 = 0, RX1 = 0, RY1 = 0, Z = 0;
     f2 CAX = 0, CAY = 0, CRX = 0, CRY = 0;   // column packet (SYM)
     const int nxt = (lane & 16) | ((g + 2) & 15);
@@ -248,8 +253,8 @@ __device__ __forceinline__ float tile_grad_2d(const float* map, int zcap, int a,
         const int c0 = cb + ((g + 2 * s) & 15), c1 = cb + ((g + 2 * s + 1) & 15);
         const f2 XC = pk(xs[c0], xs[c1]), YC = pk(ys[c0], ys[c1]);
         const f2 P0 = pk(pv[s].x, pv[s].y), P1 = pk(pv[s].z, pv[s].w);
-        const f2 DX0 = fma2(XC, NEG, OX0), DY0 = fma2(YC, NEG, OY0);   // own - other
-        const f2 DX1 = fma2(XC, NEG, OX1), DY1 = fma2(YC, NEG, OY1);
+        const f2 DX0 = sub2(OX0, XC), DY0 = sub2(OY0, YC);   // own - other
+        const f2 DX1 = sub2(OX1, XC), DY1 = sub2(OY1, YC);
         f2 Q0 = fma2(DX0, DX0, ONE);
         Q0 = fma2(DY0, DY0, Q0);
         f2 Q1 = fma2(DX1, DX1, ONE);
@@ -475,8 +480,56 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// A consumer warp's tiles of one pass: tiles q = slot, slot + nslots, ...
+// below qend, each waited for, copied into registers, released and evaluated
+// (COST: the cost sums instead of the gradient sums).
+template <int OD, bool COST>
+__device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qend, uint32_t nslots, uint32_t ring_n,
+                                             const float* ring, uint32_t full_a, uint32_t empty_a,
+                                             unsigned int* timeouts, const float* map, int zcap, float* acc, int lane,
+                                             KSum (&part)[4]) {
+    // w of the pair (i, i), which a diagonal tile's row-wise pass counts in
+    // its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own columns)
+    const float w_ii = hw_rcp(1.0f);
+    const bool diag_lane = (lane >> 4) == ((lane & 15) >> 3);
+    for (; cur.q < qend; cur.advance_ring(nslots, ring_n)) {
+        // The ring holds a whole number of consumer slots, so tile q - ring
+        // (this buffer's previous use) belonged to this same slot and was
+        // waited for before: the barrier is at most one phase behind, and
+        // the parity test cannot mistake an older phase for this one.
+        if (!mbar_wait(full_a + 8 * cur.buf, cur.ph, timeouts) && lane == 0) atomicAdd(timeouts, 1u);
+        __syncwarp();
+        const float* tile = ring + (size_t)cur.buf * kPTileStride;
+        const int2 ab = *reinterpret_cast<const int2*>(tile + kPTileFloats);
+        const int a = ab.x, b = ab.y;
+        float4 pv[8];
+        tile_lane_values(tile, lane, pv);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty_a + 8 * cur.buf);   // the buffer is free again
+        const bool diag = a == b;
+        const float drop = diag && diag_lane ? 2.0f * w_ii : 0.0f;
+        if constexpr (!COST) {
+            float zl;
+            if constexpr (OD == 2) zl = diag ? tile_grad_2d<false>(map, zcap, a, b, lane, pv, acc)
+                                             : tile_grad_2d<true>(map, zcap, a, b, lane, pv, acc);
+            else zl = diag ? tile_grad_3d<false>(map, zcap, a, b, lane, pv, acc)
+                           : tile_grad_3d<true>(map, zcap, a, b, lane, pv, acc);
+            part[0].add(zl - drop);
+        } else {
+            float cs[4];
+            if (diag) tile_cost<OD, false>(map, zcap, a, b, lane, pv, cs);
+            else tile_cost<OD, true>(map, zcap, a, b, lane, pv, cs);
+            part[0].add(cs[3] - drop);
+            part[1].add(cs[0]);
+            part[2].add(cs[1]);
+            part[3].add(cs[2]);
+        }
+    }
+}
+
 // Compiled for at most MAXT threads: 672 (20 consumer warps + the producer,
-// 80 registers per thread) or 544 (16 + 1, 96 registers).
+// 80 registers per thread), 544 (16 + 1, 96 registers) or 416 (12 + 1, 128
+// registers, 2-D maps).
 template <int OD, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -597,43 +650,10 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                     __syncwarp();
                 }
             } else {
-                // w of the pair (i, i), which a diagonal tile's row-wise pass counts
-                // in its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own column)
-                const float w_ii = hw_rcp(1.0f);
-                const bool diag_lane = (lane >> 4) == ((lane & 15) >> 3);
-                for (; cur.q < qend; cur.advance_ring((uint32_t)nslots, ring_n)) {
-                    // The ring holds a whole number of consumer slots, so tile q - ring
-                    // (this buffer's previous use) belonged to this same slot and was
-                    // waited for before: the barrier is at most one phase behind, and
-                    // the parity test cannot mistake an older phase for this one.
-                    if (!mbar_wait(full_a + 8 * cur.buf, cur.ph, A.timeouts) && lane == 0) atomicAdd(A.timeouts, 1u);
-                    __syncwarp();
-                    const float* tile = ring + (size_t)cur.buf * kPTileStride;
-                    const int2 ab = *reinterpret_cast<const int2*>(tile + kPTileFloats);
-                    const int a = ab.x, b = ab.y;
-                    float4 pv[8];
-                    tile_lane_values(tile, lane, pv);
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(empty_a + 8 * cur.buf);   // the buffer is free again
-                    const bool diag = a == b;
-                    const float drop = diag && diag_lane ? 2.0f * w_ii : 0.0f;
-                    if (!cost) {
-                        float zl;
-                        if constexpr (OD == 2) zl = diag ? tile_grad_2d<false>(map, zcap, a, b, lane, pv, acc)
-                                                         : tile_grad_2d<true>(map, zcap, a, b, lane, pv, acc);
-                        else zl = diag ? tile_grad_3d<false>(map, zcap, a, b, lane, pv, acc)
-                                       : tile_grad_3d<true>(map, zcap, a, b, lane, pv, acc);
-                        part[0].add(zl - drop);
-                    } else {
-                        float cs[4];
-                        if (diag) tile_cost<OD, false>(map, zcap, a, b, lane, pv, cs);
-                        else tile_cost<OD, true>(map, zcap, a, b, lane, pv, cs);
-                        part[0].add(cs[3] - drop);
-                        part[1].add(cs[0]);
-                        part[2].add(cs[1]);
-                        part[3].add(cs[2]);
-                    }
-                }
+                if (!cost) consume_pass<OD, false>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts,
+                                                   map, zcap, acc, lane, part);
+                else consume_pass<OD, true>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts, map,
+                                            zcap, acc, lane, part);
             }
             // block partials (fixed order), then the cluster total
 #pragma unroll
@@ -864,8 +884,10 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     a.zcap = (int)((c->zmax + kPT - 1) / kPT * kPT);
     a.ring = ring;
 
-    void (*kern)(IterArgs) = c->p.out_dim == 2 ? (Wc > 16 ? iterate_kernel<2, 672> : iterate_kernel<2, 544>)
-                                               : (Wc > 16 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>);
+    // the build for the fewest threads that hold the block: more registers per thread
+    void (*kern)(IterArgs);
+    if (c->p.out_dim == 2) kern = Wc > 16 ? iterate_kernel<2, 672> : Wc > 12 ? iterate_kernel<2, 544> : iterate_kernel<2, 416>;
+    else kern = Wc > 16 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
