@@ -135,7 +135,7 @@ extern "C" int ptsne_autotune(ptsne_ctx* c, const float* X, const int32_t* perm,
     IterTune best = keep;
     double best_ms = 1e300;
     int nt = 0;
-    const int clusters[] = {1, 2, 4}, groups[] = {1}, warps[] = {12, 16, 20};
+    const int clusters[] = {1, 2, 4}, groups[] = {1}, warps[] = {12, 16, 19, 20};
     for (int cl : clusters)
         for (int g : groups)
             for (int w : warps) {

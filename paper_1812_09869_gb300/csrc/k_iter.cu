@@ -528,8 +528,9 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
 }
 
 // Compiled for at most MAXT threads: 672 (20 consumer warps + the producer,
-// 80 registers per thread), 544 (16 + 1, 96 registers) or 416 (12 + 1, 128
-// registers, 2-D maps).
+// 80 registers per thread), 640 (19 + 1, 96 registers, 2-D maps), 544 (16 + 1,
+// 96 registers) or 416 (12 + 1, 128 registers, 2-D maps).  Registers are
+// granted per 4 warps, so 21 warps get 80 and 20 warps 96.
 template <int OD, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -886,7 +887,11 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
 
     // the build for the fewest threads that hold the block: more registers per thread
     void (*kern)(IterArgs);
-    if (c->p.out_dim == 2) kern = Wc > 16 ? iterate_kernel<2, 672> : Wc > 12 ? iterate_kernel<2, 544> : iterate_kernel<2, 416>;
+    if (c->p.out_dim == 2)
+        kern = Wc > 19   ? iterate_kernel<2, 672>
+               : Wc > 16 ? iterate_kernel<2, 640>
+               : Wc > 12 ? iterate_kernel<2, 544>
+                         : iterate_kernel<2, 416>;
     else kern = Wc > 16 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -225,9 +225,9 @@ def test_batched_iterations_equal_plain_per_chunk_form(dev):
 
 
 # launch shapes of the batched kernel: blocks per chunk (cluster) x consumer warps,
-# both builds (<= 16 and > 16 consumer warps), one warp and a ring of 17 slots
-TUNINGS = [(1, 1, 16), (2, 1, 16), (4, 1, 12), (4, 1, 8), (1, 1, 4), (1, 1, 1), (2, 1, 17), (2, 1, 20), (1, 1, 20),
-           (4, 1, 20)]
+# every build (12, 16, 19 and 20 consumer warps at most), one warp and a ring of 17 slots
+TUNINGS = [(1, 1, 16), (2, 1, 16), (4, 1, 12), (4, 1, 8), (1, 1, 4), (1, 1, 1), (2, 1, 17), (1, 1, 19), (2, 1, 20),
+           (1, 1, 20), (4, 1, 20)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
