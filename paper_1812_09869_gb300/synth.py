@@ -249,6 +249,18 @@ def _uneven_1m(epochs: int = 10):
                     precision="bf16_window")
 
 
+def _uneven_100k(epochs: int = 2):
+    """The 1M workload's recipe at 100k points (about 33 chunks of U{1000..5000}):
+    the same kernels at a size small enough for detailed profiler captures."""
+    n, d, k = 100_000, 64, 50
+    X, lab = gaussian_mixture(n, d, k, seed=3, sizes=zipf_sizes(n, k, 1.2), anisotropic=True)
+    off = uniform_chunk_offsets(n, 1000, 5000, seed=303)
+    perms = permutations(n, epochs, seed=103)
+    Y0 = init_gaussian(n, 2, 1e-4, seed=203)
+    return Workload("uneven-100k-d64", X, lab, off, perms, Y0, 30.0, epochs, 100,
+                    precision="bf16_window")
+
+
 def _sparse_200k(epochs: int = 1):
     n = 200_000
     X, lab = sparse_images(n, seed=4)
@@ -274,6 +286,7 @@ WORKLOADS = {
     "plain-2000x10": _plain_2000,
     "ptsne-100k-d50-64chunks": _chunks64_100k,
     "uneven-1m-d64": _uneven_1m,
+    "uneven-100k-d64": _uneven_100k,
     "sparse-200k-d784": _sparse_200k,
     "mapper-1m+1m-d50": _mapper_2m,
 }
