@@ -164,35 +164,61 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
     if (warp == 0) tc::tmem_dealloc(tmem, tc::kTileRows);
 }
 
-// Exact FP32 squared distance by direct differences (row xi staged in shared memory).
+// Exact FP32 squared distance by direct differences (row xi staged in shared
+// memory), dimensions in order k = 0, 1, ...: KR > 0 is the padded dimension
+// count known at compile time (every load of xj issued at once), KR = 0 a
+// runtime dp.
+template <int KR>
 __device__ __forceinline__ float exact_d2(const float* __restrict__ xi, const float* __restrict__ xj, int dp) {
     float s = 0.f;
-    for (int k = 0; k < dp; k += 4) {
-        const float4 a = *reinterpret_cast<const float4*>(xi + k);
-        const float4 q = *reinterpret_cast<const float4*>(xj + k);
-        float t = a.x - q.x; s = fmaf(t, t, s);
-        t = a.y - q.y; s = fmaf(t, t, s);
-        t = a.z - q.z; s = fmaf(t, t, s);
-        t = a.w - q.w; s = fmaf(t, t, s);
+    if constexpr (KR > 0) {
+        float4 q[KR / 4];
+#pragma unroll
+        for (int k = 0; k < KR / 4; ++k) q[k] = k * 4 < dp ? *reinterpret_cast<const float4*>(xj + 4 * k) : float4{};
+#pragma unroll
+        for (int k = 0; k < KR / 4; ++k) {
+            if (k * 4 >= dp) break;
+            const float4 a = *reinterpret_cast<const float4*>(xi + 4 * k);
+            float t = a.x - q[k].x; s = fmaf(t, t, s);
+            t = a.y - q[k].y; s = fmaf(t, t, s);
+            t = a.z - q[k].z; s = fmaf(t, t, s);
+            t = a.w - q[k].w; s = fmaf(t, t, s);
+        }
+    } else {
+        for (int k = 0; k < dp; k += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(xi + k);
+            const float4 q = *reinterpret_cast<const float4*>(xj + k);
+            float t = a.x - q.x; s = fmaf(t, t, s);
+            t = a.y - q.y; s = fmaf(t, t, s);
+            t = a.z - q.z; s = fmaf(t, t, s);
+            t = a.w - q.w; s = fmaf(t, t, s);
+        }
     }
     return s;
 }
 
 // Window recompute of the sparse rows (the coarse search has listed the rows
 // whose window covers >= 1/16 of the chunk for the tiled kernel below): one
-// warp per row; candidates d~_ij <= window_dmax(...) are compacted with a
-// ballot into a per-warp list and recomputed 32 at a time, one per lane, by
-// direct differences.  Only the row's own entries (i, j) are rewritten.
+// warp per row.  The row of D is scanned 256 entries per step (two float4 per
+// lane, the next step's loads issued before this step's are used);
+// candidates d~_ij <= window_dmax(...) are compacted with ballots into a
+// per-warp list and recomputed 32 at a time, one per lane, by direct
+// differences.  Only the row's own entries (i, j) are rewritten; the order in
+// which candidates are recomputed does not matter.
+constexpr int kWinStep = 256;                 // D entries scanned per step
+constexpr int kWinSlots = 32 + kWinStep;      // candidate list: < 32 left over + one step
+template <int KR>
 __global__ void __launch_bounds__(256)
 window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int64_t r0, int64_t r1,
               const float* __restrict__ beta, const float* __restrict__ mrow, const unsigned int* maxnorm,
               unsigned long long* pairs, const uint8_t* __restrict__ row_dense) {
-    extern __shared__ float wsm[];   // per warp: one staged row of Xg (dp floats) + 64 candidate slots
+    extern __shared__ float wsm[];   // per warp: one staged row of Xg (dp floats) + kWinSlots candidate slots
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int dp = L.dp;
-    float* xi = wsm + (size_t)warp * (dp + 64);
+    float* xi = wsm + (size_t)warp * (dp + kWinSlots);
     int* cand = reinterpret_cast<int*>(xi + dp);
     const float xmax = __uint_as_float(*maxnorm);
+    const unsigned lt = (1u << lane) - 1u;
     unsigned long long count = 0;
     for (int64_t r = r0 + (int64_t)blockIdx.x * nw + warp; r < r1; r += (int64_t)gridDim.x * nw) {
         const int c = L.chunk_of_row[r];
@@ -208,31 +234,38 @@ window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int
         for (int k = lane; k < dp; k += 32) xi[k] = Xg[r * dp + k];
         __syncwarp();
         const float dmax = window_dmax(beta[r], mrow[r], xmax, dp);
+        // a float4 at entry j (a multiple of 4 below z) ends within the row: ld is a multiple of 64 >= z
+        auto load = [&](int j) {
+            return j < z ? *reinterpret_cast<const float4*>(Drow + j) : make_float4(FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX);
+        };
+        float4 v0 = load(4 * lane), v1 = load(128 + 4 * lane);
         int nbuf = 0;
-        for (int j0 = 0; j0 < z; j0 += 32) {
-            const int j = j0 + lane;
-            const bool is_c = j < z && j != i && Drow[j] <= dmax;
-            const unsigned mask = __ballot_sync(0xffffffffu, is_c);
-            if (is_c) cand[nbuf + __popc(mask & ((1u << lane) - 1u))] = j;
-            nbuf += __popc(mask);
-            __syncwarp();
-            // recompute full batches of 32, and the remainder after the last column block
-            while (nbuf >= 32 || (j0 + 32 >= z && nbuf > 0)) {
-                const int take = nbuf < 32 ? nbuf : 32;
-                if (lane < take) {
-                    const int jj = cand[lane];
-                    Drow[jj] = exact_d2(xi, Xg + (off + jj) * dp, dp);
-                }
-                count += (lane < take) ? 1 : 0;
-                __syncwarp();
-                const int rest = nbuf - take;   // at most 31 left: move them to the front
-                int moved = 0;
-                if (lane < rest) moved = cand[take + lane];
-                __syncwarp();
-                if (lane < rest) cand[lane] = moved;
-                nbuf = rest;
-                __syncwarp();
+        for (int j0 = 0; j0 < z; j0 += kWinStep) {
+            const float4 c0 = v0, c1 = v1;
+            v0 = load(j0 + kWinStep + 4 * lane);
+            v1 = load(j0 + kWinStep + 128 + 4 * lane);
+            const float vals[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int j = j0 + (e >> 2) * 128 + 4 * lane + (e & 3);
+                const bool is_c = j < z && j != i && vals[e] <= dmax;
+                const unsigned mask = __ballot_sync(0xffffffffu, is_c);
+                if (is_c) cand[nbuf + __popc(mask & lt)] = j;
+                nbuf += __popc(mask);
             }
+            __syncwarp();
+            // recompute full batches of 32, and the remainder after the last step
+            while (nbuf >= 32 || (j0 + kWinStep >= z && nbuf > 0)) {
+                const int take = nbuf < 32 ? nbuf : 32;
+                const int rest = nbuf - take;
+                int jj = 0;
+                if (lane < take) jj = cand[rest + lane];   // take from the top of the list
+                __syncwarp();
+                if (lane < take) Drow[jj] = exact_d2<KR>(xi, Xg + (off + jj) * dp, dp);
+                count += (lane < take) ? 1 : 0;
+                nbuf = rest;
+            }
+            __syncwarp();
         }
         __syncwarp();
     }
@@ -433,13 +466,18 @@ cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64
     const int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
     // sparse rows (the coarse search has listed the dense ones)
-    const size_t smem = (size_t)8 * (c->dp + 64) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)8 * (c->dp + kWinSlots) * sizeof(float);
+    void (*wk)(float*, const float*, Layout, int64_t, int64_t, const float*, const float*, const unsigned int*,
+               unsigned long long*, const uint8_t*) = c->dp <= 16   ? window_kernel<16>
+                                                      : c->dp <= 32 ? window_kernel<32>
+                                                      : c->dp <= 64 ? window_kernel<64>
+                                                                    : window_kernel<0>;
+    cudaError_t e = cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    window_kernel<<<(unsigned)blocks, 256, smem, s>>>(c->D, c->Xg, make_layout(c), row_begin, row_end, c->beta,
-                                                      c->mrow, c->maxnorm, &c->dstats->window_pairs, c->row_dense);
+    wk<<<(unsigned)blocks, 256, smem, s>>>(c->D, c->Xg, make_layout(c), row_begin, row_end, c->beta, c->mrow,
+                                           c->maxnorm, &c->dstats->window_pairs, c->row_dense);
     // dense rows: the column blocks of the chunks these rows belong to
     const int c0 = c->chunk_of(row_begin), c1 = c->chunk_of(row_end - 1);
     const int64_t b0 = c->colblk_start[c0], b1 = c->colblk_start[c1 + 1];
