@@ -34,6 +34,35 @@ constexpr int kMaxEval32 = 64;
 constexpr int kMaxEval64 = 200;
 }  // namespace
 
+// packed FP32 pairs (f32x2 arithmetic, round to nearest like the scalar ops)
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // s + v with the rounding error carried in c (error-free two-sum)
 __device__ __forceinline__ void two_sum_add(float& s, float& c, float v, float cv) {
     const float t = s + v;
@@ -128,39 +157,68 @@ __device__ __forceinline__ RowSums group_sums3(float S, float cS, float T1, floa
     return out;
 }
 
-// S, T1, T2 of the row held in registers (excluded entries are kBig: e = 0).
+// S, T1, T2 of the row held in registers (excluded entries are kBig: e = 0),
+// two entries per packed f32x2 instruction (two partial sums per thread).
 // Segment q (entries 512 q .. 512 q + 511 of the row) is skipped by the whole
 // group when it lies beyond the chunk (z <= 512 q), so rows of small chunks do
 // not pay for the register width of the largest one.
 template <int VPT>
 __device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, bool fine, float (*red5)[5], int z) {
     const float b2 = beta * kLog2e;
+    const f2 NB = pk(-b2, -b2);
+    float lo, hi;
     if (!fine) {
-        float S = 0.f, T1 = 0.f, T2 = 0.f;
+        f2 S = 0, T1 = 0, T2 = 0;
 #pragma unroll
-        for (int k = 0; k < VPT; ++k) {
+        for (int k = 0; k < VPT; k += 2) {
             if (4 * kGroup * (k / 4) >= z) break;
-            const float e = hw_ex2(-b2 * t[k]);
-            const float te = t[k] * e;
-            S += e;
-            T1 += te;
-            T2 = fmaf(te, t[k], T2);
+            const f2 T = pk(t[k], t[k + 1]);
+            float x0, x1;
+            upk(mul2(NB, T), x0, x1);
+            const f2 E = pk(hw_ex2(x0), hw_ex2(x1));
+            const f2 TE = mul2(T, E);
+            S = add2(S, E);
+            T1 = add2(T1, TE);
+            T2 = fma2(TE, T, T2);
         }
-        return group_sums3(S, 0.f, T1, 0.f, T2, false, red5);
+        float s, t1, t2;
+        upk(S, lo, hi); s = lo + hi;
+        upk(T1, lo, hi); t1 = lo + hi;
+        upk(T2, lo, hi); t2 = lo + hi;
+        return group_sums3(s, 0.f, t1, 0.f, t2, false, red5);
     }
-    float S = 0.f, cS = 0.f, T1 = 0.f, cT = 0.f, T2 = 0.f;   // Kahan: true sum = S - cS
+    // Kahan per half: true sum = S - cS
+    f2 S = 0, cS = 0, T1 = 0, cT = 0, T2 = 0;
 #pragma unroll
-    for (int k = 0; k < VPT; ++k) {
+    for (int k = 0; k < VPT; k += 2) {
         if (4 * kGroup * (k / 4) >= z) break;
-        const float e = hw_ex2(-b2 * t[k]);
-        const float te = t[k] * e;
-        float y = e - cS, s2 = S + y;
-        cS = (s2 - S) - y; S = s2;
-        y = te - cT; s2 = T1 + y;
-        cT = (s2 - T1) - y; T1 = s2;
-        T2 = fmaf(te, t[k], T2);
+        const f2 T = pk(t[k], t[k + 1]);
+        float x0, x1;
+        upk(mul2(NB, T), x0, x1);
+        const f2 E = pk(hw_ex2(x0), hw_ex2(x1));
+        const f2 TE = mul2(T, E);
+        f2 y = sub2(E, cS), s2 = add2(S, y);
+        cS = sub2(sub2(s2, S), y);
+        S = s2;
+        y = sub2(TE, cT);
+        s2 = add2(T1, y);
+        cT = sub2(sub2(s2, T1), y);
+        T1 = s2;
+        T2 = fma2(TE, T, T2);
     }
-    return group_sums3(S, -cS, T1, -cT, T2, true, red5);
+    // the two halves' (sum, error) pairs combined error-free
+    float s, cs, t1, ct, chi, t2;
+    upk(S, s, hi);
+    upk(cS, cs, chi);
+    cs = -cs;
+    two_sum_add(s, cs, hi, -chi);
+    upk(T1, t1, hi);
+    upk(cT, ct, chi);
+    ct = -ct;
+    two_sum_add(t1, ct, hi, -chi);
+    upk(T2, lo, hi);
+    t2 = lo + hi;
+    return group_sums3(s, cs, t1, ct, t2, true, red5);
 }
 
 // One row per 128-thread block; thread `tid` holds entries j = 4 tid + 512 q + e.
