@@ -3,8 +3,8 @@
 //
 // One persistent launch runs every iteration of every chunk of an epoch.  A
 // chunk is owned by a cluster of K blocks (K = 1, 2 or 4); the chunk's map
-// lives in every block's shared memory and each block takes every K-th round
-// of the chunk's tile tournament.  Within a block:
+// lives in every block's shared memory and each block takes every K-th tile
+// of the chunk's stored tiles.  Within a block:
 //   - one producer warp streams the block's P tiles (4 KB each, stored once
 //     per unordered pair of 32-row blocks) from HBM into a ring of shared
 //     buffers with cp.async.bulk, one tile per lane in batches of at most the
@@ -427,44 +427,27 @@ __device__ __forceinline__ void tile_cost(const float* map, int zcap, int a, int
     }
 }
 
-// Tile stream of one block of the cluster: the rounds r = rank, rank + K, ...
-// of the chunk's tournament, every tile of each round in storage order (the
-// pair rounds first, then, for an even block count, the diagonal round).
+// Tile stream of one block of the cluster: the chunk's stored tiles
+// g = rank, rank + K, rank + 2K, ... (storage follows the tournament rounds,
+// so consecutive tiles of a stream mostly lie in one round and touch disjoint
+// row blocks); the K streams differ in length by at most one tile.
 struct Stream {
-    TourSched T;
-    int jd;      // pair rounds owned by this block
     int nq;      // tiles per pass
-    __device__ Stream(int nb, uint32_t rank, uint32_t K) : T(nb) {
-        jd = (int)rank < T.M ? (T.M - 1 - (int)rank) / (int)K + 1 : 0;
-        nq = jd * T.tpr;
-        if (!(nb & 1) && (nb - 1) % (int)K == (int)rank) nq += nb;  // the diagonal round
+    __device__ Stream(int nb, uint32_t rank, uint32_t K) {
+        const int total = nb * (nb + 1) / 2;
+        nq = total > (int)rank ? (total - 1 - (int)rank) / (int)K + 1 : 0;
     }
 };
 
-// Position in a stream, advanced by additions only: ring buffer and phase of
-// the stream index q, and (j, p) = (j-th round of this block, tile in round)
-// of the index s within the current pass.
+// Position of a consumer warp in the ring: stream index q, its buffer and the
+// buffer's phase parity.
 struct Cursor {
     unsigned long long q;
     uint32_t buf, ph;
-    int s, j, p;
     __device__ __forceinline__ void advance_ring(uint32_t delta, uint32_t ring) {
         q += delta;
         buf += delta;
         if (buf >= ring) { buf -= ring; ph ^= 1u; }   // delta <= ring: at most one wrap
-    }
-    // set s and normalise (j, p) for a stream of jd pair rounds of tpr tiles
-    __device__ __forceinline__ void seek(int s_, int jd, int tpr) {
-        s = s_; j = 0; p = s_;
-        while (j < jd && p >= tpr) { p -= tpr; ++j; }
-    }
-    __device__ __forceinline__ void step(int delta, int jd, int tpr) {
-        s += delta; p += delta;
-        while (j < jd && p >= tpr) { p -= tpr; ++j; }
-    }
-    // round of the current tile (the diagonal round after the pair rounds)
-    __device__ __forceinline__ int round(uint32_t rank, uint32_t K, int jd, int nb) const {
-        return j < jd ? (int)rank + j * (int)K : nb - 1;
     }
 };
 
@@ -635,16 +618,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                         const uint32_t t = q0r + (uint32_t)s;
                         const uint32_t buf = t % ring_n, ph = q0ph ^ ((t / ring_n) & 1u);
                         if (!mbar_wait(empty_a + 8 * buf, ph ^ 1u, A.timeouts)) atomicAdd(A.timeouts, 1u);
-                        int r, p;
-                        if (s < S.jd * S.T.tpr) {
-                            const int j = s / S.T.tpr;
-                            p = s - j * S.T.tpr;
-                            r = (int)rank + j * (int)K;
-                        } else {
-                            r = nb - 1;
-                            p = s - S.jd * S.T.tpr;
-                        }
-                        const float* src = P2c + (S.T.round_base(r) + p) * kPTileStride;
+                        const float* src = P2c + ((int64_t)rank + (int64_t)K * s) * kPTileStride;
                         mbar_expect_tx(full_a + 8 * buf, kTileBytes);
                         bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
                     }
