@@ -630,14 +630,15 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 else consume_pass<OD, true>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts, map,
                                             zcap, acc, lane, part);
             }
-            // block partials (fixed order), then the cluster total
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            // block partials (fixed order), then the cluster total; a gradient pass
+            // has only Z (the cost sums are zero there)
+            const int nsum = cost ? 4 : 1;
+            for (int k = 0; k < nsum; ++k) {
                 const double v = warp_sum(part[k].value());
                 if (lane == 0) s_red[warp][k] = v;
             }
             __syncthreads();
-            if (tid < 4) {
+            if (tid < nsum) {
                 double v = 0.0;
                 for (int w = 0; w < Wc; ++w) v += s_red[w][tid];
                 s_part[tid] = v;
@@ -645,8 +646,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             sync_owner(K);
             double tot[4] = {0.0, 0.0, 0.0, 0.0};
             for (uint32_t rr = 0; rr < K; ++rr)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < nsum; ++k)
                     tot[k] += K > 1 ? ld_cl_f64(map_rank(smem_u32(&s_part[k]), rr)) : s_part[k];
             if (cost) {
                 if (rank == 0 && tid == 0) {
@@ -686,7 +686,8 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 }
             }
             sync_owner(K);   // new map everywhere; remote reads of acc are done
-            for (int i = tid; i < 2 * OD * zcap; i += nthreads) acc[i] = 0.f;
+            for (int i = tid; i < OD * zcap / 2; i += nthreads)   // 2 OD zcap floats, zcap a multiple of 32
+                reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             __syncthreads();
             q0 = qend;
         }
