@@ -222,8 +222,11 @@ __device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, b
 }
 
 // One row per 128-thread block; thread `tid` holds entries j = 4 tid + 512 q + e.
+// The search is bound by each row's chain of evaluations, so the more rows in
+// flight the better: up to 40 entries per thread the kernel fits 8 blocks per
+// SM (64 registers; measured 8% faster than 4 blocks at 121 registers).
 template <int VPT>
-__global__ void __launch_bounds__(kGroup, VPT >= 48 ? 3 : (VPT >= 16 ? 4 : 6))
+__global__ void __launch_bounds__(kGroup, VPT >= 48 ? 3 : (VPT >= 16 ? 8 : 6))
 bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, double ln_perp_d,
                     float* __restrict__ beta_out, float* __restrict__ m_out, float* __restrict__ S_out,
                     DeviceStats* st, const float* beta_init, int coarse, const unsigned int* maxnorm,
