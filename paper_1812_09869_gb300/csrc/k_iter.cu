@@ -732,6 +732,21 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
     // the (b, a) block of D, transposed: dT[jj][ii] = d_{j i}, so that each
     // conditional of Eq. 3 is taken from its own row of D
     __shared__ float dT[kPT][kPT + 1];
+    // beta log2(e), m and 1 / S of the tile's rows (side 0) and columns (side 1)
+    __shared__ float pb[2][kPT], pm[2][kPT], ps[2][kPT];
+    if (tid < 2 * kPT) {
+        const int side = tid >> 5, k = tid & (kPT - 1);
+        const int g = (side ? td.b : td.a) * kPT + k;
+        float b = 0.f, m = 0.f, si = 0.f;
+        if (g < z) {
+            b = beta[off + g] * kLog2e;
+            m = mrow[off + g];
+            si = 1.0f / Srow[off + g];
+        }
+        pb[side][k] = b;
+        pm[side][k] = m;
+        ps[side][k] = si;
+    }
     {
         const int jr = td.b * kPT + r;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -743,13 +758,14 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
     if (i < z) {
         const float4 dv = *reinterpret_cast<const float4*>(D + L.moff[c] + (int64_t)i * ld + j0);
         const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
-        const float bi = beta[off + i] * kLog2e, mi = mrow[off + i], si = 1.0f / Srow[off + i];
+        const float bi = pb[0][r], mi = pm[0][r], si = ps[0][r];
         const float inv2z = 1.0f / (2.0f * (float)z);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int j = j0 + e;
             if (j < z && j != i) {
-                const float bj = beta[off + j] * kLog2e, mj = mrow[off + j], sj = 1.0f / Srow[off + j];
+                const int jj = c4 * 4 + e;
+                const float bj = pb[1][jj], mj = pm[1][jj], sj = ps[1][jj];
                 // explicitly rounded: the two halves of a diagonal tile round identically
                 const float cij = __fmul_rn(hw_ex2(-bi * (d4[e] - mi)), si);
                 const float cji = __fmul_rn(hw_ex2(-bj * (dT[c4 * 4 + e][r] - mj)), sj);
