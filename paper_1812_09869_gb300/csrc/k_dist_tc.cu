@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(128)
 window_dense_reg_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L,
                         const TileDesc* __restrict__ colblk, const int32_t* __restrict__ dense_rows,
                         const int* __restrict__ dense_cnt) {
-    __shared__ __align__(16) float xiT[KR][8];
+    __shared__ __align__(16) float xiT[2][KR][8];   // double-buffered groups of 8 dense rows
     const TileDesc td = colblk[blockIdx.x];
     const int c = td.chunk;
     const int cnt = dense_cnt[c];
@@ -323,19 +323,34 @@ window_dense_reg_kernel(float* __restrict__ D, const float* __restrict__ Xg, Lay
         xj[k] = v.x; xj[k + 1] = v.y; xj[k + 2] = v.z; xj[k + 3] = v.w;
     }
     float* Dc = D + L.moff[c];
-    for (int rg = 0; rg < cnt; rg += 8) {
+    // the next group's rows are loaded into registers while this group computes
+    constexpr int kPer = 8 * KR / 128;   // staged values per thread and group
+    float pre[kPer];
+    auto gather = [&](int rg) {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = tid + 128 * q, r = idx & 7, k = idx >> 3;
+            pre[q] = (rg + r < cnt && k < dp) ? Xg[(off + dense_rows[off + rg + r]) * dp + k] : 0.f;
+        }
+    };
+    gather(0);
+    int buf = 0;
+    for (int rg = 0; rg < cnt; rg += 8, buf ^= 1) {
         const int R = min(8, cnt - rg);
-        __syncthreads();   // previous group's reads of xiT are done
-        for (int idx = tid; idx < 8 * KR; idx += 128) {
-            const int r = idx & 7, k = idx >> 3;
-            xiT[k][r] = (r < R && k < dp) ? Xg[(off + dense_rows[off + rg + r]) * dp + k] : 0.f;
+        // buffer `buf` was last read two groups ago, before every thread passed
+        // the previous group's barrier
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = tid + 128 * q;
+            xiT[buf][idx >> 3][idx & 7] = pre[q];
         }
         __syncthreads();
+        if (rg + 8 < cnt) gather(rg + 8);
         f2x acc[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
-            const float4 a = *reinterpret_cast<const float4*>(&xiT[k][0]);
-            const float4 b = *reinterpret_cast<const float4*>(&xiT[k][4]);
+            const float4 a = *reinterpret_cast<const float4*>(&xiT[buf][k][0]);
+            const float4 b = *reinterpret_cast<const float4*>(&xiT[buf][k][4]);
             const f2x XJ = pk2(xj[k], xj[k]);
             f2x t = sub2x(pk2(a.x, a.y), XJ);
             acc[0] = fma2x(t, t, acc[0]);
