@@ -137,6 +137,40 @@ def test_step_three_dims_paper_lr_no_gains(dev, schedule):
         assert rel_max(Y1[idx] - Y0[idx], Yr - Y0[idx]) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("tuning", [(2, 1, 20), (1, 1, 12)])
+def test_three_dims_every_build_gradient_and_cost(dev, tuning):
+    """3-D maps through both builds of the batched kernel for 3-D (more and
+    fewer than 16 consumer warps): one step's gradient and Z, and the cost
+    (Eq. 5, Eq. 9), against the oracle; two chunks with ragged last blocks."""
+    X, _ = synth.gaussian_mixture(1300, 10, 4, seed=60)
+    off = np.array([0, 610, 1300])     # 20 and 22 row blocks, both ragged
+    perm = synth.permutations(1300, 1, seed=61)[0]
+    Y0 = synth.init_gaussian(1300, 3, 2.0, seed=62)
+    ctx, Xd, pd, _, _ = _gpu_affinities(dev, X, perm, off, perplexity=12.0, out_dim=3)
+    ctx.set_tuning(*tuning)
+    Yd = torch.from_numpy(Y0.copy()).to(dev)
+    cost = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.cost(pd, Yd, cost)
+    gd = torch.zeros_like(Yd)
+    Zd = torch.zeros(2, dtype=torch.float64, device=dev)
+    ctx.step(pd, Yd, grad_out=gd, Z_out=Zd)
+    torch.cuda.synchronize()
+    assert ctx.stats().wait_timeouts == 0
+    ctx.close()
+    g, Z = gd.cpu().numpy(), Zd.cpu().numpy()
+    kl, nc = cost.cpu().numpy()
+    kl_r = nc_r = 0.0
+    for c in range(2):
+        idx = perm[off[c]:off[c + 1]]
+        Pr, _, _ = O.affinities(X[idx], 12.0)
+        gr, Zr = O.gradient(Pr, Y0[idx])
+        assert rel_max(g[idx], gr) <= GRAD_TOL, (c, rel_max(g[idx], gr))
+        assert abs(Z[c] - Zr) <= 1e-6 * Zr
+        kl_r += O.kl(Pr, Y0[idx]) / 2
+        nc_r += O.normalized_cost(Pr, Y0[idx]) / 2
+    assert abs(kl - kl_r) <= 1e-4 * abs(kl_r) and abs(nc - nc_r) <= 1e-4 * nc_r, (kl, kl_r, nc, nc_r)
+
+
 def test_cost_matches_oracle(dev):
     X, _ = synth.gaussian_mixture(1500, 16, 5, seed=39)
     off = np.array([0, 640, 1500])
