@@ -1,5 +1,5 @@
 // Autotuner of the batched iteration kernel's launch shape: times every
-// candidate (blocks per chunk x warps per tile x consumer warps) on the
+// candidate (blocks per chunk x consumer warps; one warp per tile) on the
 // caller's chunk layout and keeps the fastest; results persist in a small text
 // cache keyed by device and layout.
 #include <stdio.h>
