@@ -100,6 +100,9 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     nj[tid] = (j0 + tid < z) ? xnorm[off + j0 + tid] : 0.f;
+    // this thread's accumulator row: its norm is loaded before the main loop
+    const int row = warp * 32 + lane, i = i0 + row;
+    const float ni = i < z ? xnorm[off + i] : 0.f;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -132,8 +135,6 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
     tc::tc_fence_after();
 
     // epilogue: warp w owns accumulator lanes (tile rows) 32w .. 32w + 31
-    const int row = warp * 32 + lane, i = i0 + row;
-    const float ni = i < z ? xnorm[off + i] : 0.f;
     float* base = D + L.moff[c];
     for (int cc = 0; cc < tc::kTileRows / 32; ++cc) {
         float v[32];

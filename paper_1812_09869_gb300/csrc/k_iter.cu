@@ -747,16 +747,19 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
         pm[side][k] = m;
         ps[side][k] = si;
     }
+    // both 16-byte loads of D are issued before the barrier
+    const float* Dc = D + L.moff[c];
+    float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < z) dv = *reinterpret_cast<const float4*>(Dc + (int64_t)i * ld + j0);
     {
         const int jr = td.b * kPT + r;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jr < z) v = *reinterpret_cast<const float4*>(D + L.moff[c] + (int64_t)jr * ld + td.a * kPT + c4 * 4);
+        if (jr < z) v = *reinterpret_cast<const float4*>(Dc + (int64_t)jr * ld + td.a * kPT + c4 * 4);
         dT[r][c4 * 4 + 0] = v.x; dT[r][c4 * 4 + 1] = v.y; dT[r][c4 * 4 + 2] = v.z; dT[r][c4 * 4 + 3] = v.w;
     }
     __syncthreads();
     float out[4] = {0.f, 0.f, 0.f, 0.f};
     if (i < z) {
-        const float4 dv = *reinterpret_cast<const float4*>(D + L.moff[c] + (int64_t)i * ld + j0);
         const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
         const float bi = pb[0][r], mi = pm[0][r], si = ps[0][r];
         const float inv2z = 1.0f / (2.0f * (float)z);
