@@ -1,0 +1,124 @@
+// Packed symmetric P: the joint P of Eq. 3 written into the stored 32 x 32
+// tiles the iteration kernel streams (one tile per unordered pair of 32-row
+// blocks, values in the order of the warp that evaluates them, see
+// packed_index), and the export of those tiles to dense per-chunk matrices.
+#include "ptsne_internal.cuh"
+
+namespace ptsne {
+
+// Joint P (Eq. 3) of one stored 32 x 32 tile, written in the packed order:
+//   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ji - m_j)) / S_j) / (2z),
+// zero on the diagonal and outside the chunk.  D need not be symmetric: after
+// the window recompute each row holds its own exact entries.
+__global__ void __launch_bounds__(256)
+psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
+                   const TileDesc2* __restrict__ tiles, int64_t t0, const float* __restrict__ beta,
+                   const float* __restrict__ mrow, const float* __restrict__ Srow) {
+    constexpr float kLog2e = 1.4426950408889634f;
+    const TileDesc2 td = tiles[t0 + blockIdx.x];
+    const int c = td.chunk;
+    const int64_t off = L.off[c];
+    const int z = (int)(L.off[c + 1] - off);
+    const int ld = L.ld[c];
+    const int tid = threadIdx.x, r = tid >> 3, c4 = tid & 7;
+    const int i = td.a * kPT + r;
+    const int j0 = td.b * kPT + c4 * 4;
+    // the (b, a) block of D, transposed: dT[jj][ii] = d_{j i}, so that each
+    // conditional of Eq. 3 is taken from its own row of D
+    __shared__ float dT[kPT][kPT + 1];
+    // beta log2(e), m and 1 / S of the tile's rows (side 0) and columns (side 1)
+    __shared__ float pb[2][kPT], pm[2][kPT], ps[2][kPT];
+    if (tid < 2 * kPT) {
+        const int side = tid >> 5, k = tid & (kPT - 1);
+        const int g = (side ? td.b : td.a) * kPT + k;
+        float b = 0.f, m = 0.f, si = 0.f;
+        if (g < z) {
+            b = beta[off + g] * kLog2e;
+            m = mrow[off + g];
+            si = 1.0f / Srow[off + g];
+        }
+        pb[side][k] = b;
+        pm[side][k] = m;
+        ps[side][k] = si;
+    }
+    // both 16-byte loads of D are issued before the barrier
+    const float* Dc = D + L.moff[c];
+    float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < z) dv = *reinterpret_cast<const float4*>(Dc + (int64_t)i * ld + j0);
+    {
+        const int jr = td.b * kPT + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jr < z) v = *reinterpret_cast<const float4*>(Dc + (int64_t)jr * ld + td.a * kPT + c4 * 4);
+        dT[r][c4 * 4 + 0] = v.x; dT[r][c4 * 4 + 1] = v.y; dT[r][c4 * 4 + 2] = v.z; dT[r][c4 * 4 + 3] = v.w;
+    }
+    __syncthreads();
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < z) {
+        const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
+        const float bi = pb[0][r], mi = pm[0][r], si = ps[0][r];
+        const float inv2z = 1.0f / (2.0f * (float)z);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = j0 + e;
+            if (j < z && j != i) {
+                const int jj = c4 * 4 + e;
+                const float bj = pb[1][jj], mj = pm[1][jj], sj = ps[1][jj];
+                // explicitly rounded: the two halves of a diagonal tile round identically
+                const float cij = __fmul_rn(hw_ex2(-bi * (d4[e] - mi)), si);
+                const float cji = __fmul_rn(hw_ex2(-bj * (dT[c4 * 4 + e][r] - mj)), sj);
+                out[e] = __fmul_rn(__fadd_rn(cij, cji), inv2z);
+            }
+        }
+    }
+    // reorder through shared memory into the stored order, then write the
+    // tile with coalesced 16-byte stores
+    __shared__ __align__(16) float ot[kPTileFloats];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e)] = out[e];
+    __syncthreads();
+    float* dst = P2 + (ptile_off[c] + td.pos) * kPTileStride;
+    reinterpret_cast<float4*>(dst)[tid] = reinterpret_cast<const float4*>(ot)[tid];
+    if (tid == 0)   // trailer: the tile's row and column blocks
+        *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, 0, 0);
+}
+
+// Packed tiles -> dense z x z per chunk (chunks concatenated), both halves.
+__global__ void __launch_bounds__(256)
+export_packed_kernel(const float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
+                     const TileDesc2* __restrict__ tiles, const int64_t* __restrict__ dense_off, float* __restrict__ out) {
+    const TileDesc2 td = tiles[blockIdx.x];
+    const int c = td.chunk;
+    const int z = (int)(L.off[c + 1] - L.off[c]);
+    const float* src = P2 + (ptile_off[c] + td.pos) * kPTileStride;
+    float* dst = out + dense_off[c];
+    for (int e = threadIdx.x; e < kPTileFloats; e += blockDim.x) {
+        const int r = e >> 5, cc = e & 31;
+        const int i = td.a * kPT + r, j = td.b * kPT + cc;
+        if (i < z && j < z) {
+            const float v = src[packed_index(r, cc)];
+            dst[(int64_t)i * z + j] = v;
+            dst[(int64_t)j * z + i] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s) {
+    if (c->ntiles2 <= 0) return cudaSuccess;
+    int k = 0;
+    for (int64_t b = 0; b < c->ntiles2; b += 2147483647LL, ++k) {
+        const int64_t cnt = (c->ntiles2 - b) < 2147483647LL ? (c->ntiles2 - b) : 2147483647LL;
+        psym_packed_kernel<<<(unsigned)cnt, 256, 0, s>>>(c->D, c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2, b,
+                                                         c->beta, c->mrow, c->Srow);
+    }
+    return launched(c, k);
+}
+
+cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t s) {
+    export_packed_kernel<<<(unsigned)c->ntiles2, 256, 0, s>>>(c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2,
+                                                              c->d_dense_off, P_out);
+    return launched(c, 1);
+}
+
+}  // namespace ptsne
