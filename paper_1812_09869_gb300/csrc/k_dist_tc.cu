@@ -470,11 +470,15 @@ cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t til
     if (nt <= 0) return cudaSuccess;
     CUtensorMap tm;
     if (!tc::make_bf16_tmap(&tm, c->Xb, (uint64_t)c->p.n, (uint64_t)c->kp)) return cudaErrorInvalidValue;
-    const size_t smem = 2 * 2 * tc::kTileBytes + 1024;
+    // two operand stages; with a single K block (D <= 64) only stage 0 is used,
+    // and 48 KB per block lets 4 blocks share an SM — as many as the TMEM holds
+    // (4 x 128 accumulator columns) — where two stages allow 3
+    const int kblocks = (int)(c->kp / tc::kTileK);
+    const size_t smem = kblocks == 1 ? (size_t)48 * 1024 : 2 * 2 * tc::kTileBytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(dist_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dist_bf16_kernel<<<(unsigned)nt, 128, smem, s>>>(tm, c->D, make_layout(c), c->d_tiles128, tile_begin, c->xnorm,
-                                                     c->kp / tc::kTileK, &c->dstats->timeouts);
+                                                     kblocks, &c->dstats->timeouts);
     return launched(c, 1);
 }
 
