@@ -9,8 +9,10 @@
 // accelerated by Newton steps in ln(beta) (dH/dln(beta) = -beta^2 Var_p(t))
 // whenever the Newton point falls inside the bracket.  Sums are FP32 per
 // thread (compensated once the root is near) and combined across the group
-// with error-free two-sums.  A row whose FP32 search stalls (bracket
-// collapsed, or 64 evaluations) is redone in FP64 by the same group.
+// with error-free two-sums; warp 0 combines them, takes the step and
+// publishes the next beta through shared memory.  A row whose FP32 search
+// stalls (bracket collapsed, or 64 evaluations) is redone in FP64 by the same
+// group.
 #include <float.h>
 
 #include "ptsne_internal.cuh"
@@ -110,11 +112,12 @@ struct RowSums {
     float S, T1, T2;
 };
 
-// S, T1 and T2 summed over the 128-thread group in one pass (one shared-memory
-// round, two barriers); with comp, S and T1 carry their rounding errors
-// (s + c pairs combined by error-free two-sums).  Every thread gets the sums.
-__device__ __forceinline__ RowSums group_sums3(float S, float cS, float T1, float cT, float T2, bool comp,
-                                               float (*red)[5]) {
+// S, T1 and T2 summed over the 128-thread group: each warp reduces its sums
+// with shuffles and lane 0 publishes them (with comp, S and T1 carry their
+// rounding errors, combined by error-free two-sums); after a barrier,
+// combine_sums3 adds the 4 warps' partials in a fixed order.
+__device__ __forceinline__ void publish_sums3(float S, float cS, float T1, float cT, float T2, bool comp,
+                                              float (*red)[5]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (comp) {
 #pragma unroll
@@ -136,7 +139,8 @@ __device__ __forceinline__ RowSums group_sums3(float S, float cS, float T1, floa
     if (lane == 0) {
         red[warp][0] = S; red[warp][1] = cS; red[warp][2] = T1; red[warp][3] = cT; red[warp][4] = T2;
     }
-    __syncthreads();
+}
+__device__ __forceinline__ RowSums combine_sums3(bool comp, const float (*red)[5]) {
     float a = red[0][0], ac = red[0][1], b = red[0][2], bc = red[0][3], c = red[0][4];
 #pragma unroll
     for (int w = 1; w < kGroup / 32; ++w) {
@@ -149,7 +153,6 @@ __device__ __forceinline__ RowSums group_sums3(float S, float cS, float T1, floa
         }
         c += red[w][4];
     }
-    __syncthreads();
     RowSums out;
     out.S = a + ac;
     out.T1 = b + bc;
@@ -158,12 +161,13 @@ __device__ __forceinline__ RowSums group_sums3(float S, float cS, float T1, floa
 }
 
 // S, T1, T2 of the row held in registers (excluded entries are kBig: e = 0),
-// two entries per packed f32x2 instruction (two partial sums per thread).
+// two entries per packed f32x2 instruction (two partial sums per thread),
+// published per warp (see publish_sums3).
 // Segment q (entries 512 q .. 512 q + 511 of the row) is skipped by the whole
 // group when it lies beyond the chunk (z <= 512 q), so rows of small chunks do
 // not pay for the register width of the largest one.
 template <int VPT>
-__device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, bool fine, float (*red5)[5], int z) {
+__device__ __forceinline__ void row_sums(const float (&t)[VPT], float beta, bool fine, float (*red5)[5], int z) {
     const float b2 = beta * kLog2e;
     const f2 NB = pk(-b2, -b2);
     float lo, hi;
@@ -185,7 +189,8 @@ __device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, b
         upk(S, lo, hi); s = lo + hi;
         upk(T1, lo, hi); t1 = lo + hi;
         upk(T2, lo, hi); t2 = lo + hi;
-        return group_sums3(s, 0.f, t1, 0.f, t2, false, red5);
+        publish_sums3(s, 0.f, t1, 0.f, t2, false, red5);
+        return;
     }
     // Kahan per half: true sum = S - cS
     f2 S = 0, cS = 0, T1 = 0, cT = 0, T2 = 0;
@@ -218,7 +223,7 @@ __device__ __forceinline__ RowSums row_sums(const float (&t)[VPT], float beta, b
     two_sum_add(t1, ct, hi, -chi);
     upk(T2, lo, hi);
     t2 = lo + hi;
-    return group_sums3(s, cs, t1, ct, t2, true, red5);
+    publish_sums3(s, cs, t1, ct, t2, true, red5);
 }
 
 // One row per 128-thread block; thread `tid` holds entries j = 4 tid + 512 q + e.
@@ -234,7 +239,8 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
     __shared__ float red[kGroup / 32];
     __shared__ float red5[kGroup / 32][5];
     __shared__ double redd[kGroup / 32];
-    const int tid = threadIdx.x;
+    __shared__ float s_bc[4];    // warp 0's decision: next beta, S, f, state
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float ln_perp = (float)ln_perp_d;
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const int c = L.chunk_of_row[r];
@@ -288,42 +294,67 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                 const float b0 = beta_init[r];
                 if (b0 > 0.f && isfinite(b0)) { beta = b0; f = 0.f; }
             }
+            // Every warp evaluates its share of the row; warp 0 combines the sums,
+            // keeps the bracket and the best compensated evaluation (H step one
+            // ulp of beta makes there), decides, and publishes the next beta:
+            // the other warps skip that scalar work.
             bool conv = false;
-            RowSums s{};
-            // best compensated evaluation, and the H step one ulp of beta makes there
             float best_f = INFINITY, best_beta = beta, best_S = 0.f, best_ulp_h = 0.f;
+            float Scur = 0.f;
             for (int it = 0; it < kMaxEval32; ++it) {
                 const bool fine = !coarse && fabsf(f) < kTolCoarse;
-                s = row_sums<VPT>(t, beta, fine, red5, z);
+                row_sums<VPT>(t, beta, fine, red5, z);
                 ++evals;
-                // H in nats; logf and the division are correctly rounded to ~1 ulp
-                f = (logf(s.S) + beta * (s.T1 / s.S)) - ln_perp;
-                const float mean = s.T1 / s.S;
-                const float var = fmaxf(s.T2 / s.S - mean * mean, 0.f);
-                const float denom = beta * beta * var;   // -dH / d ln(beta)
-                if (fine && fabsf(f) < best_f) {
-                    best_f = fabsf(f); best_beta = beta; best_S = s.S; best_ulp_h = denom * 6e-8f;
+                __syncthreads();
+                if (warp == 0) {
+                    const RowSums s = combine_sums3(fine, red5);
+                    float nbeta = beta, fo, So = s.S;
+                    int state = 0;
+                    bool cv = false;
+                    // H in nats; logf and the division are correctly rounded to ~1 ulp
+                    fo = (logf(s.S) + beta * (s.T1 / s.S)) - ln_perp;
+                    const float mean = s.T1 / s.S;
+                    const float var = fmaxf(s.T2 / s.S - mean * mean, 0.f);
+                    const float denom = beta * beta * var;   // -dH / d ln(beta)
+                    if (fine && fabsf(fo) < best_f) {
+                        best_f = fabsf(fo); best_beta = beta; best_S = s.S; best_ulp_h = denom * 6e-8f;
+                    }
+                    // accept only from a compensated evaluation (coarse: from any, to 1e-3 nats)
+                    if (coarse ? fabsf(fo) <= kTolCoarse : (fine && fabsf(fo) <= fminf(kTolFine, kTolBeta * denom))) {
+                        cv = true;
+                        state = 1;
+                    } else {
+                        if (fo > 0.f) lo = beta; else hi = beta;
+                        float step = denom > 0.f ? fo / denom : 0.f;
+                        step = fminf(fmaxf(step, -3.f), 3.f);
+                        float nb = beta * expf(step);
+                        if (!(nb > lo && nb < hi)) nb = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
+                        if (nb == beta || (hi - lo) <= 4e-7f * beta) {   // FP32 bracket collapsed
+                            // sharp rows: when the error is within 4 ulps of beta's effect on H,
+                            // beta is resolved as finely as FP32 allows and an FP64 root would
+                            // round to it; otherwise the row is redone in FP64
+                            if (best_f <= 4.f * best_ulp_h) { nbeta = best_beta; So = best_S; fo = best_f; cv = true; }
+                            state = 1;
+                        } else {
+                            nbeta = nb;
+                        }
+                    }
+                    if (lane == 0) {
+                        s_bc[0] = nbeta;
+                        s_bc[1] = So;
+                        s_bc[2] = fo;
+                        s_bc[3] = (float)(state | (cv ? 2 : 0));
+                    }
                 }
-                // accept only from a compensated evaluation (coarse: from any, to 1e-3 nats)
-                if (coarse ? fabsf(f) <= kTolCoarse : (fine && fabsf(f) <= fminf(kTolFine, kTolBeta * denom))) {
-                    conv = true;
-                    break;
-                }
-                if (f > 0.f) lo = beta; else hi = beta;
-                float step = denom > 0.f ? f / denom : 0.f;
-                step = fminf(fmaxf(step, -3.f), 3.f);
-                float nb = beta * expf(step);
-                if (!(nb > lo && nb < hi)) nb = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
-                if (nb == beta || (hi - lo) <= 4e-7f * beta) {   // FP32 bracket collapsed
-                    // sharp rows: when the error is within 4 ulps of beta's effect on H,
-                    // beta is resolved as finely as FP32 allows and an FP64 root would
-                    // round to it; otherwise the row is redone in FP64
-                    if (best_f <= 4.f * best_ulp_h) { beta = best_beta; s.S = best_S; f = best_f; conv = true; }
-                    break;
-                }
-                beta = nb;
+                __syncthreads();
+                beta = s_bc[0];
+                Scur = s_bc[1];
+                f = s_bc[2];
+                const int st = (int)s_bc[3];
+                conv = (st & 2) != 0;
+                if (st & 1) break;
             }
-            S = s.S;
+            S = Scur;
             herr = fabsf(f);
             if (coarse) conv = true;   // only brackets the window; never redone in FP64
             if (!conv) {
