@@ -85,17 +85,6 @@ __device__ __forceinline__ float group_sum(float v, float* red) {
     __syncthreads();
     return a;
 }
-__device__ __forceinline__ double group_sum(double v, double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double a = red[0];
-#pragma unroll
-    for (int w = 1; w < kGroup / 32; ++w) a += red[w];
-    __syncthreads();
-    return a;
-}
 __device__ __forceinline__ float group_min(float v, float* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_min(v);
@@ -238,8 +227,9 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                     int32_t* __restrict__ dense_rows, int* __restrict__ dense_cnt, uint8_t* __restrict__ row_dense) {
     __shared__ float red[kGroup / 32];
     __shared__ float red5[kGroup / 32][5];
-    __shared__ double redd[kGroup / 32];
     __shared__ float s_bc[4];    // warp 0's decision: next beta, S, f, state
+    __shared__ double redd3[kGroup / 32][3];
+    __shared__ double s_bd[4];   // the same for the FP64 search
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float ln_perp = (float)ln_perp_d;
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
@@ -358,7 +348,9 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
             herr = fabsf(f);
             if (coarse) conv = true;   // only brackets the window; never redone in FP64
             if (!conv) {
-                // FP64 redo of the same search on the held (FP32) row
+                // FP64 redo of the same search on the held (FP32) row; as above,
+                // warp 0 combines the sums (one reduction of three values) and
+                // takes the step
                 fp64 = true;
                 double b = beta, blo = 0.0, bhi = INFINITY, fd = INFINITY, Sd = 0.0;
                 for (int it = 0; it < kMaxEval64; ++it) {
@@ -370,22 +362,50 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                         const double e = exp(-b * (double)t[k]);
                         sS += e; sT1 += (double)t[k] * e; sT2 += (double)t[k] * t[k] * e;
                     }
-                    sS = group_sum(sS, redd);
-                    sT1 = group_sum(sT1, redd);
-                    sT2 = group_sum(sT2, redd);
+                    sS = warp_sum(sS);
+                    sT1 = warp_sum(sT1);
+                    sT2 = warp_sum(sT2);
+                    if (lane == 0) { redd3[warp][0] = sS; redd3[warp][1] = sT1; redd3[warp][2] = sT2; }
                     ++evals;
-                    Sd = sS;
-                    fd = log(sS) + b * sT1 / sS - ln_perp_d;
-                    if (fabs(fd) <= kTol64) break;
-                    if (fd > 0.0) blo = b; else bhi = b;
-                    const double mean = sT1 / sS;
-                    const double var = fmax(sT2 / sS - mean * mean, 0.0);
-                    double step = var > 0.0 ? fd / (b * b * var) : 0.0;
-                    step = fmin(fmax(step, -3.0), 3.0);
-                    double nb = b * exp(step);
-                    if (!(nb > blo && nb < bhi)) nb = isinf(bhi) ? 2.0 * b : 0.5 * (blo + bhi);
-                    if (nb == b) break;
-                    b = nb;
+                    __syncthreads();
+                    if (warp == 0) {
+                        sS = redd3[0][0];
+                        sT1 = redd3[0][1];
+                        sT2 = redd3[0][2];
+#pragma unroll
+                        for (int w = 1; w < kGroup / 32; ++w) {
+                            sS += redd3[w][0];
+                            sT1 += redd3[w][1];
+                            sT2 += redd3[w][2];
+                        }
+                        double nbd = b;
+                        int state = 0;
+                        const double fo = log(sS) + b * sT1 / sS - ln_perp_d;
+                        if (fabs(fo) <= kTol64) {
+                            state = 1;
+                        } else {
+                            if (fo > 0.0) blo = b; else bhi = b;
+                            const double mean = sT1 / sS;
+                            const double var = fmax(sT2 / sS - mean * mean, 0.0);
+                            double step = var > 0.0 ? fo / (b * b * var) : 0.0;
+                            step = fmin(fmax(step, -3.0), 3.0);
+                            double nb = b * exp(step);
+                            if (!(nb > blo && nb < bhi)) nb = isinf(bhi) ? 2.0 * b : 0.5 * (blo + bhi);
+                            if (nb == b) state = 1;
+                            else nbd = nb;
+                        }
+                        if (lane == 0) {
+                            s_bd[0] = nbd;
+                            s_bd[1] = sS;
+                            s_bd[2] = fo;
+                            s_bd[3] = (double)state;
+                        }
+                    }
+                    __syncthreads();
+                    b = s_bd[0];
+                    Sd = s_bd[1];
+                    fd = s_bd[2];
+                    if (s_bd[3] != 0.0) break;
                 }
                 beta = (float)b;
                 S = (float)Sd;
