@@ -609,8 +609,11 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 // Lane l issues tile s = base + l of each batch.  A batch spans at most
                 // `ring` tiles, so it uses every buffer at most once, and the warp ends
                 // batch k before starting batch k + 1: each buffer's uses stay in
-                // stream order, one phase at a time.
-                const int batch = A.ring < 32 ? A.ring : 32;
+                // stream order, one phase at a time.  Batches of 8: a batch waits for
+                // the slowest of its buffers to be released, so long batches hold
+                // back copies whose buffers are already free (batches of 19 measured
+                // 3.5% slower), while batches of 3 or fewer cannot keep the ring fed.
+                const int batch = A.ring < 8 ? A.ring : 8;
                 const uint32_t q0r = (uint32_t)(q0 % ring_n), q0ph = (uint32_t)(q0 / ring_n) & 1u;
                 for (int base = 0; base < S.nq; base += batch) {
                     const int s = base + lane;
