@@ -7,8 +7,8 @@
 // of the chunk's stored tiles.  Within a block:
 //   - one producer warp streams the block's P tiles (4 KB each, stored once
 //     per unordered pair of 32-row blocks) from HBM into a ring of shared
-//     buffers with cp.async.bulk, one tile per lane in batches of at most the
-//     ring size, completion tracked by mbarriers;
+//     buffers with cp.async.bulk, one tile per lane in batches of 8 (at most
+//     the ring size), completion tracked by mbarriers;
 //   - consumer warps take whole tiles in stream order (warp w: tiles q with
 //     q = w mod the warp count); a warp copies its tile into registers and
 //     releases the buffer before computing;
