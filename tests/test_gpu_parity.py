@@ -264,6 +264,21 @@ TUNINGS = [(1, 1, 16), (2, 1, 16), (4, 1, 12), (4, 1, 8), (1, 1, 4), (1, 1, 1), 
            (1, 1, 20), (4, 1, 20)]
 
 
+def test_invalid_launch_shapes_are_rejected(dev):
+    """ptsne_set_tuning refuses shapes the kernel has no build for (a cluster
+    of 3, more than one warp per tile, 0 or 21 consumer warps) and keeps the
+    previous shape."""
+    from paper_1812_09869_gb300 import ptsne
+    X, _ = synth.gaussian_mixture(300, 6, 3, seed=57)
+    ctx = _ctx(X, np.array([0, 150, 300]), perplexity=5.0)
+    ctx.set_tuning(1, 1, 12)
+    for bad in [(3, 1, 16), (2, 2, 16), (2, 4, 16), (2, 1, 0), (2, 1, 21), (0, 1, 8)]:
+        with pytest.raises(ptsne.PtsneError):
+            ctx.set_tuning(*bad)
+        assert ctx.tuning() == (1, 1, 12), bad
+    ctx.close()
+
+
 @pytest.mark.parametrize("tuning", TUNINGS)
 def test_gradient_for_every_launch_shape(dev, tuning):
     """Gradient, Z, updated map and cost of one step for each launch shape,
