@@ -2,8 +2,9 @@
 
 The kernel streams P tiles through a ring of shared-memory buffers: one
 producer issues tile q into buffer q % ring after the buffer's `empty` barrier
-completes, and the G warps of consumer slot q % slots wait on the buffer's
-`full` barrier with phase parity (q / ring) & 1.  An mbarrier parity wait only
+completes, and the consumer warp of slot q % slots (the kernel evaluates a
+tile with one warp; the model also covers groups of G warps per slot) waits on
+the buffer's `full` barrier with phase parity (q / ring) & 1.  An mbarrier parity wait only
 distinguishes the current phase from the previous one, so a consumer must never
 wait two phases ahead.  The kernel guarantees this by sizing the ring as a whole
 number of slots.  This test replays the protocol under random interleavings and
@@ -106,11 +107,14 @@ def test_ring_smaller_than_the_slots_is_caught():
     assert results != {"ok"}
 
 
-@pytest.mark.parametrize("slots,group,per_slot", [(8, 2, 3), (4, 4, 4), (6, 2, 4), (12, 2, 2), (16, 1, 3)])
-def test_warp_parallel_producer_batches_of_at_most_ring(slots, group, per_slot):
+@pytest.mark.parametrize("slots,group,per_slot", [(8, 2, 3), (4, 4, 4), (6, 2, 4), (12, 2, 2), (16, 1, 3),
+                                                   (19, 1, 1), (12, 1, 2), (20, 1, 1), (5, 1, 1)])
+@pytest.mark.parametrize("max_batch", [8, 32])
+def test_warp_parallel_producer_batches_of_at_most_ring(slots, group, per_slot, max_batch):
+    """Batches of min(8, ring) (the kernel's) or min(32, ring) tiles."""
     ring = slots * per_slot
     for seed in range(15):
-        assert replay(slots, group, ring, 200, seed, batch=min(32, ring)) == "ok"
+        assert replay(slots, group, ring, 200, seed, batch=min(max_batch, ring)) == "ok"
 
 
 def test_producer_batch_larger_than_ring_is_caught():
