@@ -50,7 +50,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--tuning", default=None,
-                    help="fixed launch shape 'cluster,group,warps' of the iteration kernel (skips the autotuner)")
+                    help="fixed launch shape 'cluster,group,warps' of the iteration kernel, group 1 (skips the autotuner)")
     return ap.parse_args(argv)
 
 
