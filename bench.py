@@ -212,7 +212,7 @@ def _timed_epochs(ctx, Xd, perm_rows, Y, stream):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     secs = 0.0
     for pr in perm_rows:
-        cost = np.zeros((1, 2))
+        cost = np.zeros((1, 3))
         a.record(stream)
         ctx.run(Xd, pr, 1, Y, cost_out=cost)
         b.record(stream)
@@ -341,7 +341,7 @@ def bench_ours(args, rank, world, local_rank):
     Xd = torch.from_numpy(w.X).to(dev)
     perms = torch.from_numpy(w.perms).to(dev)
     Y = torch.from_numpy(w.Y0.copy()).to(dev)
-    cost = np.zeros((1, 2))
+    cost = np.zeros((1, 3))
     stream = torch.cuda.current_stream()
 
     def epochs_from(k0, count):
@@ -359,8 +359,8 @@ def bench_ours(args, rank, world, local_rank):
     # the warm-up steps so that the timed steps replay the same graph
     ctx.set_profiling(True)
     warm_perms, timed_perms = epochs_from(0, args.warmup), epochs_from(args.warmup, args.steps)
-    ctx.run(Xd, warm_perms, args.warmup, Y, cost_out=np.zeros((args.warmup, 2)))
-    cost = np.zeros((args.steps, 2))
+    ctx.run(Xd, warm_perms, args.warmup, Y, cost_out=np.zeros((args.warmup, 3)))
+    cost = np.zeros((args.steps, 3))
     ctx.reset_counters()
     sampler = ClockSampler(local_rank)
     torch.cuda.synchronize()
@@ -405,7 +405,7 @@ def bench_ours(args, rank, world, local_rank):
     Xh = torch.from_numpy(w.X).pin_memory()
     Ph = torch.from_numpy(w.perms).pin_memory()
     Yh = torch.from_numpy(w.Y0.copy()).pin_memory()
-    cost = np.zeros((1, 2))
+    cost = np.zeros((1, 3))
     ctx.run_host(Xh, Ph[0], 1, Yh)   # first call allocates the staging buffers
     e2e_steps = max(1, min(args.steps, 3))
     barrier(world)

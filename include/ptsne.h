@@ -15,7 +15,8 @@
  *                 update in the descent direction (Eq. 12) with optional gains
  *                 or the auto-adaptive learning rate (Eq. 13);
  *   evaluation  — KL (Eq. 5) and pseudo-normalised cost (Eq. 9) averaged over
- *                 chunks.
+ *                 chunks, and the embedding size (the diagonal of the map's
+ *                 bounding box) that the paper monitors beside the cost.
  *
  * Conventions for every entry point:
  *   - Pointers named *_dev are device pointers on the current CUDA device;
@@ -240,11 +241,21 @@ int ptsne_step(ptsne_ctx* ctx, const int32_t* perm_dev, float* Y_dev,
 int ptsne_cost(ptsne_ctx* ctx, const int32_t* perm_dev, const float* Y_dev,
                double* out_dev, void* stream);
 
+/* Embedding size of a map (ptSNE section, the monitoring of cost and size at
+ * the end of each epoch): the length of the diagonal of the map's bounding
+ * box, sqrt(sum_k (max_i Y[i][k] - min_i Y[i][k])^2), over every row of Y_dev
+ * (the context's rows x out_dim floats: n rows, or layers x n with layers > 1).
+ * The extremes are exact; the sum and square root run in FP64.  NaN
+ * coordinates are ignored.  out_dev: 1 double on the device.  Uses the
+ * context's workspace, so calls on one context must be ordered (one stream).
+ * Async. */
+int ptsne_embedding_size(ptsne_ctx* ctx, const float* Y_dev, double* out_dev, void* stream);
+
 /* The ptSNE cycle: for e in [0, epochs): affinities for perms_dev[e] (n int32
  * each, epochs x n), `iters` gradient iterations of every chunk from the
  * current map, pooling into Y_dev (n x out_dim, in: start map, out: result).
- * cost_out_host (optional): epochs x 2 doubles, {avg KL, avg normalised cost}
- * at the end of each epoch.  From the second epoch on, each row's perplexity
+ * cost_out_host (optional): epochs x 3 doubles, {avg KL, avg normalised cost,
+ * embedding size of the pooled map} at the end of each epoch.  From the second epoch on, each row's perplexity
  * search starts from the precision its point had in the previous epoch (the
  * root is unique, so only the number of evaluations changes); the first
  * epoch of every call starts cold, so identical calls give identical results.
@@ -276,19 +287,24 @@ size_t ptsne_workspace_bytes(const ptsne_ctx* ctx);
  * X := Y).  density_dev: gy x gx float32 (row = y cell), overwritten; its sum
  * is the kernel mass inside the box (1 when the box covers the map).  Kernels
  * are dropped beyond beta r^2 = 30, and points with a non-positive or
- * non-finite beta or position are ignored.  n >= 1, 1 <= gx, gy <= 16384;
- * else PTSNE_EINVAL with the reason in ptsne_last_error(NULL).  Async. */
+ * non-finite beta or position are ignored.  A point whose kernel would cover
+ * more than PTSNE_KDE_MAX_CELLS cells of the grid is left out (its precision is
+ * far too small for the grid; this bounds the work per point) and counted in
+ * *dropped_dev (optional, 1 int64 on the device, overwritten).  n >= 1,
+ * 1 <= gx, gy <= 16384; else PTSNE_EINVAL with the reason in
+ * ptsne_last_error(NULL).  Async. */
+#define PTSNE_KDE_MAX_CELLS (1 << 20)
 int ptsne_kde_grid(const float* Y_dev, const float* beta_dev, int64_t n, int32_t gx, int32_t gy,
-                   const float* box_host, float* density_dev, void* stream);
+                   const float* box_host, float* density_dev, int64_t* dropped_dev, void* stream);
 
 /* Largest chunk ptsne_gradient_static accepts. */
 #define PTSNE_STATIC_MAX_ROWS 32768
 
 /* The exact gradient of one chunk WITHOUT any device allocation and without a
  * context.  The paper has no counterpart: it exists for callers that cannot
- * call cudaMalloc (a host framework that owns the whole device memory pool,
- * code running under an active stream capture in global or thread-local
- * mode, callers that must not block on an allocation).
+ * call cudaMalloc (a host framework that owns the whole device memory pool
+ * and forbids allocations outside its own accounting, callers that must not
+ * block on an allocation, which may synchronise the device).
  *   P_dev:    z rows of ld floats (ld >= z), the symmetric joint P of the
  *             chunk (e.g. one block of ptsne_affinities' P_out, ld = z);
  *             the diagonal is ignored.
@@ -302,7 +318,10 @@ int ptsne_kde_grid(const float* Y_dev, const float* beta_dev, int64_t n, int32_t
  * memory, shared by every call on a device: calls that can overlap on the GPU
  * race on it; calls ordered on one stream are safe, and nothing needs
  * clearing between them.  The first call on each device looks up the array's
- * address and may load the module: make it before any stream capture.  Async. */
+ * address (and the SM count) and may load the module: make it before any
+ * stream capture.  The address is kept per device together with the CUDA
+ * context it was taken in, and looked up again after that context has been
+ * destroyed and re-created (cudaDeviceReset).  Async. */
 int ptsne_gradient_static(const float* P_dev, int64_t ld, const float* Y_dev, int32_t z, int32_t out_dim,
                           float* grad_out_dev, double* Z_out_dev, void* stream);
 

@@ -51,6 +51,7 @@ def lib():
         L.orc_cauchy_Z.argtypes = [_D, C.c_int64, C.c_int32]
         L.orc_cauchy_Z.restype = C.c_double
         L.orc_gradient.argtypes = [_D, _D, C.c_int64, C.c_int32, _D, _D]
+        L.orc_gradient_rows.argtypes = [_D, _I64, C.c_int64, _D, C.c_int64, C.c_int32, C.c_double, _D]
         L.orc_kl.argtypes = [_D, _D, C.c_int64, C.c_int32]
         L.orc_kl.restype = C.c_double
         L.orc_normalized_cost.argtypes = [_D, _D, C.c_int64, C.c_int32]
@@ -145,6 +146,20 @@ def gradient(P, Y):
     Z = C.c_double()
     assert lib().orc_gradient(_d(P), _d(Y), z, od, _d(g), C.byref(Z)) == 0
     return g, Z.value
+
+
+def gradient_rows(Prows, rows, Y, Z):
+    """Eq. 6 at the chunk rows `rows` from their P rows (len(rows) x z) and the
+    chunk's Z (cauchy_Z(Y)), for chunks too large for a dense FP64 P."""
+    Prows, Y = _f64(Prows), _f64(Y)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    z, od = Y.shape
+    assert Prows.shape == (len(rows), z)
+    g = np.empty((len(rows), od))
+    rc = lib().orc_gradient_rows(_d(Prows), rows.ctypes.data_as(_I64), len(rows), _d(Y), z, od, float(Z), _d(g))
+    if rc != 0:
+        raise ValueError(f"orc_gradient_rows failed: {rc}")
+    return g
 
 
 def kl(P, Y):

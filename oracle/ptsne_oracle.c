@@ -154,19 +154,13 @@ static void row_conditional(const double* drow, int64_t z, int64_t i,
     for (int64_t j = 0; j < z; ++j) out[j] /= S;
 }
 
-/* Input affinities of one chunk of z points (a partial t-SNE: ptSNE section,
- * "threads"), with n := z in Eq. 3:
- *   D_ij = ||x_i - x_j||^2, beta_i by the perplexity search,
- *   p_{j|i} (Eq. 1),  P_ij = (p_{j|i} + p_{i|j}) / (2z)  (Eq. 3).
- * P is z x z row-major with zero diagonal; beta has z entries.  Pcond (z x z,
- * optional) receives p_{j|i} at [i*z + j].  D_scratch (z x z, optional) is
- * used instead of a fresh allocation.  Returns the number of rows whose search
- * did not converge (>= 0) or a negative error. */
 /* Joint P (Eq. 3, n := z) of one chunk from its z x z matrix of dissimilarities
  * D (squared Euclidean distances, or any precomputed ones such as graph path
  * lengths): beta_i by the search of orc_row_beta on row i of D (Eq. 1, Eq. 2),
- * conditionals p_{j|i}, then P_ij = (p_{j|i} + p_{i|j}) / (2z).  Returns the
- * number of rows that missed the tolerance. */
+ * conditionals p_{j|i}, then P_ij = (p_{j|i} + p_{i|j}) / (2z).  P is z x z
+ * row-major with zero diagonal; beta (optional) has z entries; Pcond (z x z,
+ * optional) receives p_{j|i} at [i*z + j].  Returns the number of rows whose
+ * search missed the tolerance (>= 0) or a negative error. */
 int orc_affinities_from_distances(const double* D, int64_t z, double perp, double tol, int32_t maxit,
                                   double* P, double* beta, double* Pcond) {
     if (!D || !P || z < 2) return ORC_EINVAL;
@@ -190,8 +184,10 @@ int orc_affinities_from_distances(const double* D, int64_t z, double perp, doubl
     return bad;
 }
 
-/* Joint P of one chunk of points Xc (z x d): squared Euclidean distances
- * (input-space similarities of the ptSNE section), then the above. */
+/* Input affinities of one chunk of z points Xc (z x d; a partial t-SNE:
+ * ptSNE section, "threads"), with n := z in Eq. 3: D_ij = ||x_i - x_j||^2 (the
+ * input-space similarities of the ptSNE section), then
+ * orc_affinities_from_distances on D.  Same outputs and return value. */
 int orc_affinities(const double* Xc, int64_t z, int32_t d, double perp,
                    double tol, int32_t maxit, double* P, double* beta,
                    double* Pcond) {
@@ -251,6 +247,30 @@ int orc_gradient(const double* P, const double* Y, int64_t z, int32_t od,
         }
     }
     if (Z_out) *Z_out = Z;
+    return ORC_OK;
+}
+
+/* Eq. 6 for selected rows only, for chunks whose z x z P is too large to
+ * hold in FP64: grad_r = 4 sum_{j != i} (p_ij - w_ij / Z) w_ij (y_i - y_j)
+ * for i = rows[r], with Prows[r * z + j] = p_ij (the rows' P entries) and Z
+ * the chunk's normaliser of Eq. 4 (orc_cauchy_Z).  grad is nr x od. */
+int orc_gradient_rows(const double* Prows, const int64_t* rows, int64_t nr, const double* Y, int64_t z,
+                      int32_t od, double Z, double* grad) {
+    if (!Prows || !rows || !Y || !grad || z < 2 || od < 1 || nr < 0 || !(Z > 0.0)) return ORC_EINVAL;
+    for (int64_t r = 0; r < nr; ++r)
+        if (rows[r] < 0 || rows[r] >= z) return ORC_EINVAL;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nr; ++r) {
+        const int64_t i = rows[r];
+        for (int32_t k = 0; k < od; ++k) grad[r * od + k] = 0.0;
+        for (int64_t j = 0; j < z; ++j) {
+            if (j == i) continue;
+            double w = cauchy(Y, od, i, j);
+            double c = 4.0 * (Prows[r * z + j] - w / Z) * w;
+            for (int32_t k = 0; k < od; ++k)
+                grad[r * od + k] += c * (Y[i * od + k] - Y[j * od + k]);
+        }
+    }
     return ORC_OK;
 }
 
@@ -395,13 +415,6 @@ int orc_partial_tsne(const double* Xc, int64_t z, int32_t d, int32_t od,
     return st;
 }
 
-/* The ptSNE epoch cycle (ptSNE section, "epochs"): for every epoch e the
- * partition perms[e] (n entries) is cut at `offsets` into n_chunks chunks;
- * each chunk runs a partial t-SNE from its current positions and the results
- * are pooled back into Y (n x od, in/out).  cost (optional, epochs x 2)
- * receives the average over chunks of KL (Eq. 5) and of the pseudo-normalised
- * cost (Eq. 9) at the end of each epoch.  One layer (each point in exactly one
- * chunk per epoch). */
 /* The ptSNE cycle with layers (ptSNE section, subsections "layers" and
  * "thread-size"): each epoch's permutation and the offsets define T
  * elementary chunks; thread t runs the L chunks t, t+1, ..., t+L-1 (mod T)
@@ -460,6 +473,13 @@ int orc_ptsne_run_layers(const double* X, int64_t n, int32_t d, int32_t od,
     return bad;
 }
 
+/* The ptSNE epoch cycle (ptSNE section, "epochs"): for every epoch e the
+ * partition perms[e] (n entries) is cut at `offsets` into n_chunks chunks;
+ * each chunk runs a partial t-SNE from its current positions and the results
+ * are pooled back into Y (n x od, in/out).  cost (optional, epochs x 2)
+ * receives the average over chunks of KL (Eq. 5) and of the pseudo-normalised
+ * cost (Eq. 9) at the end of each epoch.  One layer (each point in exactly one
+ * chunk per epoch). */
 int orc_ptsne_run(const double* X, int64_t n, int32_t d, int32_t od,
                   const int32_t* perms, const int64_t* offsets, int32_t n_chunks,
                   const orc_params* prm, double* Y, double* cost) {

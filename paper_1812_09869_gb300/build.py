@@ -33,7 +33,7 @@ def _nvcc() -> str:
 
 def _headers_digest() -> str:
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "ptsne.h")]):
+    for f in sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))):
         h.update(open(f, "rb").read())
     h.update(" ".join(ARCH + NVFLAGS).encode())
     return h.hexdigest()

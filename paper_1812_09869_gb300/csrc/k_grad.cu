@@ -234,6 +234,95 @@ __global__ void cost_final_kernel(const double* __restrict__ chunk, int n_chunks
     }
 }
 
+// ---------------------------------------------------------------- embedding size
+// The paper monitors, next to the cost, the size of the embedding: the length
+// of the diagonal of the map's bounding box, sqrt(sum_k (max_i y_ik - min_i
+// y_ik)^2), taken over every row of the pooled map.  Each block reduces a
+// grid-stride share of the rows to per-coordinate extremes; the last block to
+// finish (counted in `done`) combines the blocks' extremes and writes the
+// size in FP64, then re-arms the counter for the next launch.  Minimum and
+// maximum are exact in any order, so the result does not depend on the
+// schedule.  NaN coordinates are ignored (fminf / fmaxf).
+constexpr int kSizeThreads = 256;
+
+template <int OD>
+__global__ void __launch_bounds__(kSizeThreads)
+embedding_size_kernel(const float* __restrict__ Y, int64_t rows, float* __restrict__ part, unsigned int* done,
+                      double* __restrict__ out) {
+    __shared__ float s_ext[kSizeThreads / 32][2 * OD];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float lo[OD], hi[OD];
+#pragma unroll
+    for (int k = 0; k < OD; ++k) { lo[k] = FLT_MAX; hi[k] = -FLT_MAX; }
+    for (int64_t i = (int64_t)blockIdx.x * kSizeThreads + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * kSizeThreads) {
+        float v[OD];
+        if constexpr (OD == 2) {
+            const float2 t = reinterpret_cast<const float2*>(Y)[i];
+            v[0] = t.x;
+            v[1] = t.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < OD; ++k) v[k] = Y[i * OD + k];
+        }
+#pragma unroll
+        for (int k = 0; k < OD; ++k) { lo[k] = fminf(lo[k], v[k]); hi[k] = fmaxf(hi[k], v[k]); }
+    }
+#pragma unroll
+    for (int k = 0; k < OD; ++k) {
+        lo[k] = warp_min(lo[k]);
+        hi[k] = warp_max(hi[k]);
+        if (lane == 0) { s_ext[warp][k] = lo[k]; s_ext[warp][OD + k] = hi[k]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < OD; ++k) {
+            float a = FLT_MAX, b = -FLT_MAX;
+            for (int w = 0; w < kSizeThreads / 32; ++w) { a = fminf(a, s_ext[w][k]); b = fmaxf(b, s_ext[w][OD + k]); }
+            part[blockIdx.x * 2 * OD + k] = a;
+            part[blockIdx.x * 2 * OD + OD + k] = b;
+        }
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < OD; ++k) { lo[k] = FLT_MAX; hi[k] = -FLT_MAX; }
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kSizeThreads) {
+#pragma unroll
+        for (int k = 0; k < OD; ++k) {
+            lo[k] = fminf(lo[k], __ldcg(part + b * 2 * OD + k));
+            hi[k] = fmaxf(hi[k], __ldcg(part + b * 2 * OD + OD + k));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < OD; ++k) {
+        lo[k] = warp_min(lo[k]);
+        hi[k] = warp_max(hi[k]);
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < OD; ++k) { s_ext[warp][k] = lo[k]; s_ext[warp][OD + k] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < OD; ++k) {
+            float a = FLT_MAX, b = -FLT_MAX;
+            for (int w = 0; w < kSizeThreads / 32; ++w) { a = fminf(a, s_ext[w][k]); b = fmaxf(b, s_ext[w][OD + k]); }
+            const double e = (double)b - (double)a;
+            s += e * e;
+        }
+        *out = sqrt(s);
+        *done = 0u;
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 
 static Optim optim_of(const ptsne_ctx* c) {
@@ -300,6 +389,18 @@ cudaError_t launch_cost(const ptsne_ctx* c, double* out2, cudaStream_t s) {
 
 cudaError_t launch_cost_final(const ptsne_ctx* c, double* out2, cudaStream_t s) {
     cost_final_kernel<<<1, 32, 0, s>>>(c->cost_chunk, c->p.n_chunks, out2);
+    return launched(c, 1);
+}
+
+cudaError_t launch_embedding_size(const ptsne_ctx* c, const float* Y, double* out, cudaStream_t s) {
+    const int64_t rows = c->p.n;
+    int64_t b = (rows + kSizeThreads - 1) / kSizeThreads;
+    if (b > kSizeBlocks) b = kSizeBlocks;
+    if (b < 1) b = 1;
+    if (c->p.out_dim == 2)
+        embedding_size_kernel<2><<<(unsigned)b, kSizeThreads, 0, s>>>(Y, rows, c->size_part, c->size_done, out);
+    else
+        embedding_size_kernel<3><<<(unsigned)b, kSizeThreads, 0, s>>>(Y, rows, c->size_part, c->size_done, out);
     return launched(c, 1);
 }
 

@@ -4,12 +4,11 @@
 // Who needs it.  Every other entry point works on a context whose workspace
 // ptsne_create obtains with cudaMalloc.  Some callers cannot do that: a host
 // framework that owns the whole device memory pool and forbids allocations
-// outside its own accounting, code that runs while a stream capture in global
-// or thread-local mode is active (cudaMalloc is an error there), and callers
-// that must not block, since cudaMalloc may synchronise the device.  Such a
-// caller allocates its inputs and outputs itself and calls this function,
-// which allocates nothing: its scratch (per-row partial sums) lives in a
-// fixed array in the library's own device memory, loaded with the module.
+// outside its own accounting, and callers that must not block, since
+// cudaMalloc may synchronise the device.  Such a caller allocates its inputs
+// and outputs itself and calls this function, which allocates nothing: its
+// scratch (per-row partial sums) lives in a fixed array in the library's own
+// device memory, loaded with the module.
 //
 // Scratch contract.
 //  - g_static_scratch holds kStaticScratchBytes (1 MiB): per-row Z partials
@@ -18,12 +17,18 @@
 //  - Its device address is looked up with cudaGetSymbolAddress once per
 //    device, on the first call made while that device is current.  That first
 //    lookup may load the module, so make it before any stream capture begins.
+//    The address is cached together with the identity of the CUDA context it
+//    was taken in; when the device's context has been destroyed and created
+//    again (cudaDeviceReset), the module may load at another address, so the
+//    next call sees the new context and looks the address up again.
 //  - Every call on a device shares the one array.  Calls whose kernels can
 //    overlap on the GPU (different streams, or several host threads without
 //    ordering) race on it and give wrong results; calls in one stream are
 //    ordered and safe.
 //  - Every scratch word a call reads is written earlier by the same call, so
 //    nothing has to be cleared between calls.
+#include <cuda.h>   // CUcontext / CUresult types of the two driver calls fetched below
+
 #include <mutex>
 
 #include "ptsne_internal.cuh"
@@ -38,8 +43,40 @@ constexpr int kMaxDevices = 64;
 constexpr int kRowWarps = 8;
 constexpr int kFinalThreads = 1024;
 
+// Per device: the scratch address, the context it belongs to and the SM count.
+struct ScratchSlot {
+    unsigned long long ctx_id;   // 0: not looked up yet
+    void* ptr;
+    int sms;
+};
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices];
+ScratchSlot g_slot[kMaxDevices];
+
+// Unique id of the calling thread's current CUDA context (the driver's
+// cuCtxGetCurrent and cuCtxGetId, fetched through the runtime so that the
+// library does not link the driver library itself).  0 if unavailable.
+unsigned long long current_ctx_id() {
+    typedef CUresult (*GetCurrent)(CUcontext*);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+        tried = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -127,8 +164,10 @@ grad_final_static_kernel(const float* __restrict__ acc, const double* __restrict
     }
 }
 
-// Device address of g_static_scratch on the current device (looked up once per device).
-int static_scratch(unsigned char** out) {
+// Device address of g_static_scratch on the current device, and its SM count
+// (looked up once per device and context; the runtime has made the device's
+// primary context current by the time cudaGetSymbolAddress returns).
+int static_scratch(unsigned char** out, int* sms_out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -140,7 +179,9 @@ int static_scratch(unsigned char** out) {
         return PTSNE_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot& sl = g_slot[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!sl.ptr || id == 0 || sl.ctx_id != id) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) {
@@ -148,9 +189,19 @@ int static_scratch(unsigned char** out) {
                                                    : "ptsne_gradient_static: scratch address lookup returned NULL");
             return PTSNE_ECUDA;
         }
-        g_scratch_ptr[dev] = p;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || sms < 1) {
+            ptsne::set_last_error(e != cudaSuccess ? cudaGetErrorString(e)
+                                                   : "ptsne_gradient_static: device reports no multiprocessors");
+            return PTSNE_ECUDA;
+        }
+        sl.ptr = p;
+        sl.sms = sms;
+        sl.ctx_id = current_ctx_id();   // the lookup made the primary context current
     }
-    *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    *out = static_cast<unsigned char*>(sl.ptr);
+    *sms_out = sl.sms;
     return PTSNE_OK;
 }
 
@@ -181,13 +232,14 @@ extern "C" int ptsne_gradient_static(const float* P_dev, int64_t ld, const float
         return PTSNE_EINVAL;
     }
     unsigned char* base = nullptr;
-    const int rc = static_scratch(&base);
+    int sms = 0;
+    const int rc = static_scratch(&base, &sms);
     if (rc != PTSNE_OK) return rc;
     double* rowz = reinterpret_cast<double*>(base);
     float* acc = reinterpret_cast<float*>(base + kZBytes);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int blocks = (z + kRowWarps - 1) / kRowWarps;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sms * 8) blocks = sms * 8;   // 8 blocks of 256 threads fill an SM
     if (out_dim == 2) {
         grad_rows_static_kernel<2><<<blocks, kRowWarps * 32, 0, s>>>(P_dev, ld, Y_dev, z, acc, rowz);
         grad_final_static_kernel<2><<<1, kFinalThreads, 0, s>>>(acc, rowz, z, grad_out_dev, Z_out_dev);

@@ -26,7 +26,13 @@
 //     block's slice of rows, broadcast to every block's copy of the map.
 // Every mbarrier wait is bounded in time; a wait that runs out is counted in
 // DeviceStats::timeouts (the host then reports PTSNE_ETIMEOUT) and the kernel
-// runs to completion without blocking.
+// runs to completion without blocking.  The first wait that runs out freezes
+// the block's pipeline (a shared flag): from then on every wait fails at
+// once, the producer issues no further copy and no consumer reads or releases
+// a buffer, so a copy never lands in a buffer that is being read or that still
+// has a copy in flight, and a stale barrier phase is never taken for a
+// completed one.  Before the block exits, the producer waits (bounded) for the
+// last copy it issued into each buffer.
 #include <float.h>
 
 #include "ptsne_internal.cuh"
@@ -93,14 +99,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 // Wait for the phase of the given parity; false if it did not complete within
-// kWaitNs, or at once when an earlier wait of the launch already ran out (so a
-// failed launch drains quickly instead of timing out on every tile).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const unsigned int* timeouts) {
+// kWaitNs.  `fail` is the block's shared freeze flag: once set (by this wait
+// running out, or by any earlier failed wait of the block or of the launch),
+// every wait returns false at once without looking at the barrier, so a phase
+// left incomplete by a skipped copy or release is never mistaken for a later
+// one of the same parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const unsigned int* timeouts,
+                                          volatile int* fail) {
+    if (*fail) return false;
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try(bar, parity)) {
-        if (*(volatile const unsigned int*)timeouts != 0u) return false;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (*fail || *(volatile const unsigned int*)timeouts != 0u || global_ns() - t0 > kWaitNs) {
+            *fail = 1;
+            return false;
+        }
     }
     return true;
 }
@@ -469,8 +482,8 @@ struct KSum {
 template <int OD, bool COST>
 __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qend, uint32_t nslots, uint32_t ring_n,
                                              const float* ring, uint32_t full_a, uint32_t empty_a,
-                                             unsigned int* timeouts, const float* map, int zcap, float* acc, int lane,
-                                             KSum (&part)[4]) {
+                                             unsigned int* timeouts, volatile int* fail, int nb, const float* map,
+                                             int zcap, float* acc, int lane, KSum (&part)[4]) {
     // w of the pair (i, i), which a diagonal tile's row-wise pass counts in
     // its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own columns)
     const float w_ii = hw_rcp(1.0f);
@@ -480,11 +493,18 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
         // (this buffer's previous use) belonged to this same slot and was
         // waited for before: the barrier is at most one phase behind, and
         // the parity test cannot mistake an older phase for this one.
-        if (!mbar_wait(full_a + 8 * cur.buf, cur.ph, timeouts) && lane == 0) atomicAdd(timeouts, 1u);
-        __syncwarp();
+        // A tile whose wait failed is skipped whole: no read, no release (the
+        // buffer may still receive its copy), no arithmetic.
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(full_a + 8 * cur.buf, cur.ph, timeouts, fail));
+        if (!ok) {
+            if (lane == 0) atomicAdd(timeouts, 1u);
+            continue;
+        }
         const float* tile = ring + (size_t)cur.buf * kPTileStride;
         const int2 ab = *reinterpret_cast<const int2*>(tile + kPTileFloats);
-        const int a = ab.x, b = ab.y;
+        // the trailer is written by the joint-P kernel; clamp it anyway so
+        // that no shared-memory index can leave the chunk's rows
+        const int a = min(max(ab.x, 0), nb - 1), b = min(max(ab.y, 0), nb - 1);
         float4 pv[8];
         tile_lane_values(tile, lane, pv);
         __syncwarp();
@@ -536,13 +556,18 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     __shared__ int s_item;
     __shared__ float s_mn[32], s_mx[32];
     __shared__ float s_eta;
+    __shared__ int s_fail;                          // the block's freeze flag (see mbar_wait)
+    __shared__ unsigned char s_issued[64];          // buffer received a copy from the producer
+    __shared__ unsigned char s_lastph[64];          // full-barrier parity of that buffer's last copy
 
     const uint32_t K = cl_size(), rank = cl_rank();
     const uint32_t ring_a = smem_u32(ring), full_a = smem_u32(fullb), empty_a = smem_u32(emptyb);
     if (tid == 0) {
+        s_fail = 0;
         for (int b = 0; b < A.ring; ++b) {
             mbar_init(full_a + 8 * b, 1);
             mbar_init(empty_a + 8 * b, 1u);
+            s_issued[b] = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -620,18 +645,24 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                     if (lane < batch && s < S.nq) {
                         const uint32_t t = q0r + (uint32_t)s;
                         const uint32_t buf = t % ring_n, ph = q0ph ^ ((t / ring_n) & 1u);
-                        if (!mbar_wait(empty_a + 8 * buf, ph ^ 1u, A.timeouts)) atomicAdd(A.timeouts, 1u);
-                        const float* src = P2c + ((int64_t)rank + (int64_t)K * s) * kPTileStride;
-                        mbar_expect_tx(full_a + 8 * buf, kTileBytes);
-                        bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
+                        // a copy is issued only into a buffer known to be released
+                        if (mbar_wait(empty_a + 8 * buf, ph ^ 1u, A.timeouts, &s_fail)) {
+                            const float* src = P2c + ((int64_t)rank + (int64_t)K * s) * kPTileStride;
+                            mbar_expect_tx(full_a + 8 * buf, kTileBytes);
+                            bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
+                            s_issued[buf] = 1;
+                            s_lastph[buf] = (unsigned char)ph;
+                        } else {
+                            atomicAdd(A.timeouts, 1u);
+                        }
                     }
                     __syncwarp();
                 }
             } else {
                 if (!cost) consume_pass<OD, false>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts,
-                                                   map, zcap, acc, lane, part);
-                else consume_pass<OD, true>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts, map,
-                                            zcap, acc, lane, part);
+                                                   &s_fail, nb, map, zcap, acc, lane, part);
+                else consume_pass<OD, true>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts,
+                                            &s_fail, nb, map, zcap, acc, lane, part);
             }
             // block partials (fixed order), then the cluster total; a gradient pass
             // has only Z (the cost sums are zero there)
@@ -699,16 +730,26 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             for (int k = 0; k < OD; ++k) A.Yc[(off + i) * OD + k] = map[k * zcap + i];
         __syncthreads();
     }
-    // every issued copy has been waited for by a consumer; if a wait ran out,
-    // wait (bounded) for the copies still in flight before the block exits
-    if (is_producer && lane == 0) {
-        const unsigned long long n = q0 < (unsigned long long)A.ring ? q0 : (unsigned long long)A.ring;
-        uint32_t buf = (uint32_t)((q0 - n) % ring_n), ph = (uint32_t)((q0 - n) / ring_n) & 1u;
-        for (unsigned long long q = q0 - n; q < q0; ++q) {
-            const unsigned long long t0 = global_ns();
-            while (!mbar_try(full_a + 8 * buf, ph))
-                if (global_ns() - t0 > kWaitNs) break;
-            if (++buf == ring_n) { buf = 0; ph ^= 1u; }
+    // Normally every issued copy has been waited for by a consumer.  After a
+    // failed wait some may still be in flight: before the block exits, wait
+    // (bounded, whatever the freeze flag says) for the phase of the last copy
+    // issued into each buffer.  Copies into one buffer are issued one at a
+    // time (each after the release of the previous one), so that phase is the
+    // only one a buffer can still owe.
+    if (is_producer) {
+        __syncwarp();
+        if (lane == 0) {
+            for (int b = 0; b < A.ring; ++b) {
+                if (!s_issued[b]) continue;
+                const uint32_t bar = full_a + 8 * b, ph = s_lastph[b];
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try(bar, ph)) {
+                    if (global_ns() - t0 > kWaitNs) {
+                        atomicAdd(A.timeouts, 1u);
+                        break;
+                    }
+                }
+            }
         }
     }
 }

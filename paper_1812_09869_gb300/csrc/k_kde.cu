@@ -8,7 +8,10 @@
 //
 // One warp per point splats its kernel onto the cells within exp(-30) of
 // its peak (FP32 atomic adds; the remaining tail is below FP32 resolution
-// relative to the peak).
+// relative to the peak).  A point whose kernel would cover more than
+// PTSNE_KDE_MAX_CELLS cells (a precision far too small for the grid, e.g. an
+// isolated point of a widely spread map) is dropped and counted, so that the
+// work per point stays bounded.
 #include <float.h>
 #include <stdio.h>
 
@@ -20,7 +23,8 @@ constexpr float kKdeCut = 30.0f;   // beta r^2 beyond which a kernel is dropped
 
 __global__ void __launch_bounds__(256)
 kde_splat_kernel(const float* __restrict__ Y, const float* __restrict__ beta, int64_t n, int gx, int gy, float x0,
-                 float y0, float dx, float dy, float scale, float* __restrict__ f) {
+                 float y0, float dx, float dy, float scale, float* __restrict__ f,
+                 unsigned long long* __restrict__ dropped) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
@@ -37,6 +41,10 @@ kde_splat_kernel(const float* __restrict__ Y, const float* __restrict__ beta, in
         if (ix1 < ix0 || iy1 < iy0) continue;
         const int w = ix1 - ix0 + 1;
         const int64_t cells = (int64_t)w * (iy1 - iy0 + 1);
+        if (cells > PTSNE_KDE_MAX_CELLS) {
+            if (lane == 0 && dropped) atomicAdd(dropped, 1ull);
+            continue;
+        }
         const float amp = scale * b;
         for (int64_t t = lane; t < cells; t += 32) {
             const int ix = ix0 + (int)(t % w), iy = iy0 + (int)(t / w);
@@ -51,7 +59,7 @@ kde_splat_kernel(const float* __restrict__ Y, const float* __restrict__ beta, in
 }  // namespace
 
 extern "C" int ptsne_kde_grid(const float* Y_dev, const float* beta_dev, int64_t n, int32_t gx, int32_t gy,
-                              const float* box_host, float* density_dev, void* stream) {
+                              const float* box_host, float* density_dev, int64_t* dropped_dev, void* stream) {
     char msg[256];
     if (!Y_dev || !beta_dev || !density_dev || !box_host) {
         ptsne::set_last_error("ptsne_kde_grid: Y, beta, box and density must be non-NULL");
@@ -72,11 +80,13 @@ extern "C" int ptsne_kde_grid(const float* Y_dev, const float* beta_dev, int64_t
     const float dx = (x1 - x0) / (float)gx, dy = (y1 - y0) / (float)gy;
     const float scale = (float)((double)dx * (double)dy / ((double)n * 3.14159265358979323846));
     cudaError_t e = cudaMemsetAsync(density_dev, 0, sizeof(float) * (size_t)gx * (size_t)gy, s);
+    if (e == cudaSuccess && dropped_dev) e = cudaMemsetAsync(dropped_dev, 0, sizeof(int64_t), s);
     if (e == cudaSuccess) {
         int64_t blocks = (n + 7) / 8;
         if (blocks > 152 * 16) blocks = 152 * 16;
         kde_splat_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y_dev, beta_dev, n, gx, gy, x0, y0, dx, dy, scale,
-                                                          density_dev);
+                                                          density_dev,
+                                                          reinterpret_cast<unsigned long long*>(dropped_dev));
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -83,7 +83,7 @@ void free_all(ptsne_ctx* c) {
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
                     c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense,
-                    c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm};
+                    c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm, c->size_part, c->size_done};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -316,7 +316,9 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     AL(c->ystat, 2 * nc);
     AL(c->cost_rows, 4 * n);
     AL(c->cost_chunk, 2 * nc);
-    AL(c->cost_hist, 2 * kCostHist);
+    AL(c->cost_hist, 3 * kCostHist);
+    AL(c->size_part, (int64_t)kSizeBlocks * 2 * od);
+    AL(c->size_done, 1);
     AL(c->queue, 4);
     AL(c->dstats, 1);
     AL(c->perm_cur, c->npts);
@@ -325,7 +327,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         AL(c->d_vbase, n);
         AL(c->vperm, n);
     }
-    AL(c->cost_cur, 2);
+    AL(c->cost_cur, 3);
 #undef AL
     auto up = [&](void* dst, const void* src, size_t bytes) {
         return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -350,6 +352,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         if (e == cudaSuccess) e = up(c->d_tiles2, tiles2.data(), sizeof(TileDesc2) * tiles2.size());
     }
     if (e == cudaSuccess) e = cudaMemset(c->dstats, 0, sizeof(DeviceStats));
+    if (e == cudaSuccess) e = cudaMemset(c->size_done, 0, sizeof(unsigned int));
     // zero P once so that padded columns read as exact zeros before the first assembly
     if (e == cudaSuccess && c->P) e = cudaMemset(c->P, 0, sizeof(float) * (size_t)m);
     if (e != cudaSuccess) {
@@ -433,7 +436,8 @@ static int iterate_rows(ptsne_ctx* c, float* grad_perm, cudaStream_t s);
 
 // One epoch of ptsne_run on the partition perm: affinities, every gradient
 // iteration of every chunk, the pool back into Y and, if want_cost, the
-// epoch's average cost into cost_dst (2 doubles).
+// epoch's average costs and the pooled map's embedding size into cost_dst
+// (3 doubles).
 static int run_epoch(ptsne_ctx* c, const float* X, const int32_t* perm_in, float* Y, bool want_cost, double* cost_dst,
                      cudaStream_t s) {
     VPERM(perm, perm_in, s);
@@ -455,6 +459,7 @@ static int run_epoch(ptsne_ctx* c, const float* X, const int32_t* perm_in, float
     if (want_cost) {
         if (c->p.schedule == PTSNE_SCHED_BATCHED) CK(launch_cost_final(c, cost_dst, s));
         else CK(launch_cost(c, cost_dst, s));
+        CK(launch_embedding_size(c, Y, cost_dst + 2, s));
     }
     return PTSNE_OK;
 }
@@ -607,6 +612,13 @@ int ptsne_cost(ptsne_ctx* c, const int32_t* perm_in, const float* Y, double* out
     return PTSNE_OK;
 }
 
+int ptsne_embedding_size(ptsne_ctx* c, const float* Y, double* out_dev, void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!Y || !out_dev) return fail(c, PTSNE_EINVAL, "Y and out must be device pointers%s%lld");
+    CK(launch_embedding_size(c, Y, out_dev, as_stream(stream)));
+    return PTSNE_OK;
+}
+
 int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs, float* Y, double* cost_out,
               void* stream) {
     if (!c) return PTSNE_EINVAL;
@@ -632,14 +644,14 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
             CK(cudaGraphLaunch(c->graph, s));
             c->launches += c->graph_launches;
             if (want_cost)
-                CK(cudaMemcpyAsync(c->cost_hist + 2 * slot, c->cost_cur, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                CK(cudaMemcpyAsync(c->cost_hist + 3 * slot, c->cost_cur, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
                                    s));
         } else {
-            const int st = run_epoch(c, X, perm, Y, want_cost, c->cost_hist + 2 * slot, s);
+            const int st = run_epoch(c, X, perm, Y, want_cost, c->cost_hist + 3 * slot, s);
             if (st != PTSNE_OK) return st;
         }
         if (want_cost && (slot == kCostHist - 1 || e == epochs - 1))
-            CK(cudaMemcpyAsync(cost_out + 2 * (int64_t)(e - slot), c->cost_hist, sizeof(double) * 2 * (slot + 1),
+            CK(cudaMemcpyAsync(cost_out + 3 * (int64_t)(e - slot), c->cost_hist, sizeof(double) * 3 * (slot + 1),
                                cudaMemcpyDeviceToHost, s));
         if (c->profiling) {
             CK(cudaEventRecord(c->ev[PTSNE_N_STAGES], s));

@@ -20,6 +20,9 @@ namespace ptsne {
 // every row starts 256-byte aligned and float4 loads never straddle rows.
 constexpr int kTile = 64;
 constexpr int kMaxChunk = 8192;
+// Blocks of the embedding-size reduction (4 per SM of a GB300); the context
+// keeps one set of per-coordinate extremes per block.
+constexpr int kSizeBlocks = 608;
 
 // One upper-triangular tile (I <= J) of one chunk's z x z pair matrix.
 struct TileDesc {
@@ -194,7 +197,9 @@ struct ptsne_ctx {
     float* ystat = nullptr;            // n_chunks x 2 (min, max coordinate)
     double* cost_rows = nullptr;       // n x 3 per-row cost partials
     double* cost_chunk = nullptr;      // n_chunks x 2
-    double* cost_hist = nullptr;       // 2 x kCostHist per-epoch costs of ptsne_run
+    double* cost_hist = nullptr;       // 3 x kCostHist per-epoch {KL, cost, size} of ptsne_run
+    float* size_part = nullptr;        // kSizeBlocks x 2 od: per-block extremes of the map
+    unsigned int* size_done = nullptr; // blocks of the embedding-size reduction done (0 between launches)
     int* queue = nullptr;              // work-queue counters
     ptsne::DeviceStats* dstats = nullptr;
 
@@ -211,7 +216,7 @@ struct ptsne_ctx {
     // graph-captured epoch of ptsne_run: it reads the partition from perm_cur
     // and leaves the epoch's cost in cost_cur, so one graph serves every epoch
     int32_t* perm_cur = nullptr;       // n
-    double* cost_cur = nullptr;        // 2
+    double* cost_cur = nullptr;        // 3: {avg KL, avg normalised cost, embedding size}
     cudaStream_t cap_stream = nullptr; // private stream the epoch is captured on
     cudaGraphExec_t graph = nullptr;
     const float* graph_X = nullptr;
@@ -265,6 +270,8 @@ cudaError_t launch_update(const ptsne_ctx* c, int64_t row_begin, int64_t row_end
                           cudaStream_t s);
 cudaError_t launch_cost(const ptsne_ctx* c, double* out2, cudaStream_t s);
 cudaError_t launch_cost_final(const ptsne_ctx* c, double* out2, cudaStream_t s);
+// embedding size of the map Y (all c->p.n rows, original order) into *out
+cudaError_t launch_embedding_size(const ptsne_ctx* c, const float* Y, double* out, cudaStream_t s);
 
 // batched schedule (packed symmetric P)
 cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s);

@@ -12,6 +12,8 @@ import ctypes as C
 import os
 from dataclasses import dataclass
 
+import numpy as np
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libptsne.so")
 
@@ -100,6 +102,7 @@ def lib():
         L.ptsne_distances.argtypes = [vp, vp, vp, vp, vp]
         L.ptsne_affinities_from_distances.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
         L.ptsne_cost.argtypes = [vp, vp, vp, vp, vp]
+        L.ptsne_embedding_size.argtypes = [vp, vp, vp, vp]
         L.ptsne_run.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
         L.ptsne_run_host.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_double), vp]
         L.ptsne_get_stats.argtypes = [vp, C.POINTER(Stats), vp]
@@ -112,7 +115,7 @@ def lib():
         L.ptsne_autotune.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_char_p, C.POINTER(TuneTrial), C.c_int32,
                                      C.POINTER(C.c_int32), vp]
         L.ptsne_gradient_static.argtypes = [vp, C.c_int64, vp, C.c_int32, C.c_int32, vp, vp, vp]
-        L.ptsne_kde_grid.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_float), vp, vp]
+        L.ptsne_kde_grid.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_float), vp, vp, vp]
         _lib = L
     return _lib
 
@@ -213,15 +216,28 @@ class Context:
     def cost(self, perm, Y, out, stream=None):
         return self._check(lib().ptsne_cost(self.h, _ptr(perm), _ptr(Y), _ptr(out), _stream(stream)))
 
+    def embedding_size(self, Y, out, stream=None):
+        """ptsne_embedding_size: the diagonal of Y's bounding box into out (1 float64, device)."""
+        return self._check(lib().ptsne_embedding_size(self.h, _ptr(Y), _ptr(out), _stream(stream)))
+
+    @staticmethod
+    def _cost_ptr(cost_out, epochs):
+        if cost_out is None:
+            return None
+        if cost_out.dtype != np.float64 or cost_out.size < 3 * epochs or not cost_out.flags.c_contiguous:
+            raise ValueError("cost_out must be a C-contiguous float64 array of epochs x 3")
+        return cost_out.ctypes.data_as(C.POINTER(C.c_double))
+
     def run(self, X, perms, epochs, Y, cost_out=None, stream=None):
-        """cost_out: optional float64 numpy array (epochs x 2)."""
-        cp = None if cost_out is None else cost_out.ctypes.data_as(C.POINTER(C.c_double))
+        """cost_out: optional float64 numpy array (epochs x 3): avg KL, avg
+        normalised cost and embedding size after each epoch."""
+        cp = self._cost_ptr(cost_out, epochs)
         return self._check(lib().ptsne_run(self.h, _ptr(X), _ptr(perms), epochs, _ptr(Y), cp, _stream(stream)),
                            warn_ok=True)
 
     def run_host(self, X_host, perms_host, epochs, Y_host, cost_out=None, stream=None):
         """Host tensors (ideally pinned); Y_host is updated in place."""
-        cp = None if cost_out is None else cost_out.ctypes.data_as(C.POINTER(C.c_double))
+        cp = self._cost_ptr(cost_out, epochs)
         return self._check(lib().ptsne_run_host(self.h, _ptr(X_host), _ptr(perms_host), epochs, _ptr(Y_host),
                                                 cp, _stream(stream)), warn_ok=True)
 
@@ -269,12 +285,14 @@ def gradient_static(P, Y, grad_out, Z_out=None, ld=None, stream=None):
     return rc
 
 
-def kde_grid(Y, beta, gx, gy, box, density_out, stream=None):
+def kde_grid(Y, beta, gx, gy, box, density_out, dropped_out=None, stream=None):
     """ptsne_kde_grid: paKDE of the map Y (n x 2) with precisions beta (n) on a
-    gx x gy grid over box = (xmin, xmax, ymin, ymax) into density_out (gy x gx)."""
+    gx x gy grid over box = (xmin, xmax, ymin, ymax) into density_out (gy x gx);
+    dropped_out (optional, 1 int64 device tensor) counts the points left out
+    because their kernel covers more than PTSNE_KDE_MAX_CELLS cells."""
     b = (C.c_float * 4)(*[float(v) for v in box])
     rc = lib().ptsne_kde_grid(_ptr(Y), _ptr(beta), int(Y.shape[0]), int(gx), int(gy), b, _ptr(density_out),
-                              _stream(stream))
+                              _ptr(dropped_out), _stream(stream))
     if rc != OK:
         raise PtsneError(rc, lib().ptsne_last_error(None).decode())
     return rc

@@ -179,6 +179,23 @@ def init_disk(n: int, seed: int) -> np.ndarray:
     return np.stack([r * np.cos(t), r * np.sin(t)], axis=1).astype(np.float32)
 
 
+def lowrank_affinity_rows(z: int, seed: int, rows) -> np.ndarray:
+    """Rows `rows` of a seeded symmetric non-negative z x z float32 matrix
+    shaped like a joint P (entries ~1/z^2, varied over rows and columns):
+    (u_i u_j + v_i v_j) / s with u ~ U[0.5, 1.5], v ~ U[0, 1]^3 and s the sum
+    over all pairs.  Any subset of rows can be drawn on its own, bit for bit
+    equal to the same rows of a full draw, so chunks too large for a dense
+    host matrix can be generated block by block.  The diagonal is left as is
+    (consumers ignore it)."""
+    rng = _rng(seed)
+    u = rng.uniform(0.5, 1.5, z)
+    v = rng.uniform(0.0, 1.0, z) ** 3
+    s = u.sum() ** 2 + v.sum() ** 2
+    uf, vf = (u / np.sqrt(s)).astype(np.float32), (v / np.sqrt(s)).astype(np.float32)
+    rows = np.asarray(rows, dtype=np.int64)
+    return np.outer(uf[rows], uf) + np.outer(vf[rows], vf)
+
+
 def mlp_init(d_in: int, out_dim: int, seed: int, hidden: int = 256) -> dict:
     """Initial mapper parameters: weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)),
     biases zero, float32 (W1 hidden x d_in, W2 hidden x hidden, W3 out x hidden)."""

@@ -116,8 +116,8 @@ def test_kde_grid_rejects_bad_arguments_on_the_host(lib):
     fake = C.c_void_p(0x1000)
     box = (C.c_float * 4)(0.0, 1.0, 0.0, 1.0)
     bad_box = (C.c_float * 4)(1.0, 0.0, 0.0, 1.0)
-    assert lib.ptsne_kde_grid(fake, fake, 10, 0, 8, box, fake, None) == ptsne.EINVAL
-    assert lib.ptsne_kde_grid(fake, fake, 0, 8, 8, box, fake, None) == ptsne.EINVAL
-    assert lib.ptsne_kde_grid(fake, fake, 10, 8, 8, bad_box, fake, None) == ptsne.EINVAL
-    assert lib.ptsne_kde_grid(None, fake, 10, 8, 8, box, fake, None) == ptsne.EINVAL
+    assert lib.ptsne_kde_grid(fake, fake, 10, 0, 8, box, fake, None, None) == ptsne.EINVAL
+    assert lib.ptsne_kde_grid(fake, fake, 0, 8, 8, box, fake, None, None) == ptsne.EINVAL
+    assert lib.ptsne_kde_grid(fake, fake, 10, 8, 8, bad_box, fake, None, None) == ptsne.EINVAL
+    assert lib.ptsne_kde_grid(None, fake, 10, 8, 8, box, fake, None, None) == ptsne.EINVAL
     assert "ptsne_kde_grid" in lib.ptsne_last_error(None).decode()

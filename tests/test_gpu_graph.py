@@ -38,7 +38,7 @@ def _run(dev, X, off, perms, Y0, use_graph, schedule="batched", precision="fp32"
         if tuning:
             ctx.set_tuning(*tuning)
         Yd = torch.from_numpy(Y0.copy()).to(dev) if Yd is None else Yd
-        cost = np.zeros((perms.shape[0], 2))
+        cost = np.zeros((perms.shape[0], 3))
         ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev), perms.shape[0], Yd, cost_out=cost)
         torch.cuda.synchronize()
         return Yd.cpu().numpy(), cost, ctx.stats().kernel_launches
@@ -66,7 +66,7 @@ def test_graph_is_recaptured_when_its_inputs_change(dev):
             if tun:
                 ctx.set_tuning(*tun)
             Yd = torch.from_numpy(Y0.copy()).to(dev)      # a new Y buffer each time
-            cost = np.zeros((1, 2)) if k != 1 else None    # cost request toggles too
+            cost = np.zeros((1, 3)) if k != 1 else None    # cost request toggles too
             ctx.run(Xd, Pd, 1, Yd, cost_out=cost)
             torch.cuda.synchronize()
             outs.append(Yd.cpu().numpy())
@@ -82,7 +82,7 @@ def test_profiled_graph_records_stage_times(dev):
     with ptsne.Context(cfg) as ctx:
         ctx.set_profiling(True)
         Yd = torch.from_numpy(Y0.copy()).to(dev)
-        cost = np.zeros((2, 2))
+        cost = np.zeros((2, 3))
         ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev), 2, Yd, cost_out=cost)
         torch.cuda.synchronize()
         st = ctx.stats()
@@ -108,7 +108,7 @@ def test_identical_runs_give_identical_maps(dev):
         outs = []
         for _ in range(2):
             Yd = torch.from_numpy(Y0.copy()).to(dev)
-            cost = np.zeros((3, 2))
+            cost = np.zeros((3, 3))
             ctx.run(Xd, Pd, 3, Yd, cost_out=cost)
             torch.cuda.synchronize()
             outs.append((Yd.cpu().numpy(), cost.copy()))

@@ -51,3 +51,25 @@ def test_pakde_matches_oracle(dev, grid):
     assert np.abs(f - f_ref).max() <= 1e-3 * f_ref.max()
     assert abs(f.sum() - f_ref.sum()) <= 1e-4
     assert abs(f_ref.sum() - 1.0) <= 2e-2            # the box holds almost all of the mass
+
+
+def test_kernels_too_wide_for_the_grid_are_counted_and_left_out(dev):
+    """A point whose precision is far too small for the grid (its kernel would
+    cover more than PTSNE_KDE_MAX_CELLS cells) is left out and counted; the
+    others are splatted as the oracle evaluates them."""
+    from paper_1812_09869_gb300 import ptsne
+    gx = gy = 2048
+    Y = np.array([[0.1, 0.2], [0.5, 0.5], [-0.3, 0.4]], dtype=np.float32)
+    beta = np.array([4.0e4, 1.0e-3, 2.5e4], dtype=np.float32)   # the middle kernel spans the whole box
+    box = (-1.0, 1.0, -1.0, 1.0)
+    fd = torch.full((gy, gx), float("nan"), dtype=torch.float32, device=dev)
+    dropped = torch.full((1,), -1, dtype=torch.int64, device=dev)
+    ptsne.kde_grid(torch.from_numpy(Y).to(dev), torch.from_numpy(beta).to(dev), gx, gy, box, fd,
+                   dropped_out=dropped)
+    torch.cuda.synchronize()
+    assert dropped.item() == 1
+    keep = np.array([0, 2])
+    # the estimator's 1/n uses all three points; the dropped one adds nothing
+    f_ref = O.kde_grid(Y[keep], beta[keep].astype(np.float64), gx, gy, box) * (2.0 / 3.0)
+    f = fd.cpu().numpy().astype(np.float64)
+    assert np.abs(f - f_ref).max() <= 1e-3 * f_ref.max()

@@ -85,7 +85,7 @@ def test_layered_epochs_match_oracle(dev):
     cfg = ptsne.Config(n=n, d=X.shape[1], offsets=off, perplexity=30.0, iters=40, layers=L)
     with ptsne.Context(cfg) as ctx:
         Yd = torch.from_numpy(Y0.copy()).to(dev)
-        cost = np.zeros((2, 2))
+        cost = np.zeros((2, 3))
         ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev), 2, Yd, cost_out=cost)
         torch.cuda.synchronize()
     _, cref = O.ptsne_run_layers(X, Y0, perms, off, L, O.params(perplexity=30.0, iters=40, epochs=2))

@@ -155,7 +155,7 @@ def test_warm_start_gains_over_plain_ptsne(dev):
         cfg = ptsne.Config(n=half, d=d_in, offsets=off, perplexity=30.0, iters=iters)
         with ptsne.Context(cfg) as ctx:
             Yd = torch.from_numpy(np.ascontiguousarray(Y0, dtype=np.float32)).to(dev)
-            cost = np.zeros((epochs, 2))
+            cost = np.zeros((epochs, 3))
             ctx.run(Xd, torch.from_numpy(synth.permutations(half, epochs, seed)).to(dev), epochs, Yd, cost_out=cost)
             torch.cuda.synchronize()
             return Yd.cpu().numpy(), cost[-1, 0]

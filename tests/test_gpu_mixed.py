@@ -117,7 +117,7 @@ def test_bf16_window_final_kl_2000x10(dev):
     w = synth.workload("plain-2000x10")
     ctx = _ctx(w.X, w.offsets, perplexity=30.0, iters=100, precision="bf16_window")
     Yd = torch.from_numpy(w.Y0.copy()).to(dev)
-    cost = np.zeros((1, 2))
+    cost = np.zeros((1, 3))
     ctx.run(torch.from_numpy(w.X).to(dev), torch.from_numpy(w.perms).to(dev), 1, Yd, cost_out=cost)
     ctx.close()
     _, cref = O.ptsne_run(w.X, w.Y0, w.perms, w.offsets, O.params(perplexity=30.0, iters=100, epochs=1))

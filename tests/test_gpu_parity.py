@@ -201,7 +201,7 @@ def test_final_kl_within_one_percent_2000x10(dev, schedule):
     Xd = torch.from_numpy(w.X).to(dev)
     pd = torch.from_numpy(w.perms).to(dev)
     Yd = torch.from_numpy(w.Y0.copy()).to(dev)
-    cost = np.zeros((1, 2))
+    cost = np.zeros((1, 3))
     rc = ctx.run(Xd, pd, 1, Yd, cost_out=cost)
     assert rc == 0
     ctx.close()
@@ -217,7 +217,7 @@ def test_multi_epoch_run_matches_oracle_cost(dev):
     Y0 = synth.init_gaussian(4000, 2, 1e-4, seed=44)
     ctx = _ctx(X, off, perplexity=30.0, iters=60)
     Yd = torch.from_numpy(Y0.copy()).to(dev)
-    cost = np.zeros((3, 2))
+    cost = np.zeros((3, 3))
     ctx.run(torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev), 3, Yd, cost_out=cost)
     ctx.close()
     prm = O.params(perplexity=30.0, iters=60, epochs=3)

@@ -19,6 +19,8 @@ MUTANTS = {
         ("double c = 4.0 * (P[i * z + j] - q) * w;", "double c = 2.0 * (P[i * z + j] - q) * w;"),
     "p + q instead of p - q (Eq. 6)":
         ("double c = 4.0 * (P[i * z + j] - q) * w;", "double c = 4.0 * (P[i * z + j] + q) * w;"),
+    "row-restricted gradient with p + q (Eq. 6)":
+        ("double c = 4.0 * (Prows[r * z + j] - w / Z) * w;", "double c = 4.0 * (Prows[r * z + j] + w / Z) * w;"),
     "joint P divided by n instead of 2n (Eq. 3)":
         ("const double inv2n = 1.0 / (2.0 * (double)z);", "const double inv2n = 1.0 / ((double)z);"),
     "Z includes the diagonal (Eq. 4)":

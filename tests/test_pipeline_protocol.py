@@ -11,6 +11,21 @@ number of slots.  This test replays the protocol under random interleavings and
 out-of-order copy completion: every consumer must read exactly the tile it
 expects and the pipeline must never stall, and the ring/slot mismatch that the
 sizing rule excludes must be caught by the model.
+
+The second half models the bounded waits running out.  Any wait that is not
+yet satisfied may run out at any moment, and another block's failure may
+freeze the block at any moment.  The kernel's rules: the first failed wait
+sets the block's freeze flag, after which every wait fails at once; a
+consumer whose wait failed skips its tile whole (no read, no release); the
+producer issues a copy only after a successful wait on the buffer's `empty`
+barrier; before exiting, the producer waits for the phase of the last copy it
+issued into each buffer.  The model checks that no copy is ever issued into a
+buffer that still has one in flight or whose content was not released, that
+every read sees the tile it expects with no copy in flight into it, that the
+block exits with no copy in flight, and that the run always ends.  The rules
+the kernel had before (a failed consumer wait still released the buffer, a
+failed producer wait still issued the copy, the exit drain waited on stream
+positions) must be caught.
 """
 import random
 
@@ -120,3 +135,136 @@ def test_warp_parallel_producer_batches_of_at_most_ring(slots, group, per_slot, 
 def test_producer_batch_larger_than_ring_is_caught():
     results = {replay(4, 2, 8, 200, seed, batch=32) for seed in range(10)}
     assert results != {"ok"}
+
+
+# ---------------------------------------------------------------- waits that run out
+
+def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=0.002, old_rules=False):
+    """One block, one warp per slot.  Returns "ok", or the first violation."""
+    rng = random.Random(seed)
+    full = [MBarrier(1) for _ in range(ring)]
+    empty = [MBarrier(1) for _ in range(ring)]
+    content = [None] * ring
+    released = [True] * ring      # the buffer's last copy was read and released (or none yet)
+    inflight = {}                 # buffer -> tile of the copy in flight
+    issued_ph = {}                # buffer -> full-barrier parity of the last copy issued
+    fail = False
+    pending, next_batch = [], 0
+    next_tile = list(range(slots))   # consumer warp w: its next tile
+    for _ in range(10 ** 6):
+        if not pending and next_batch < ntiles:
+            pending = list(range(next_batch, min(ntiles, next_batch + batch)))
+            next_batch += batch
+        moves = []
+        for q in pending:
+            b, ph = q % ring, (q // ring) & 1
+            ready = empty[b].try_wait(ph ^ 1)
+            if fail and not old_rules:
+                moves.append(("skip_issue", q))
+            elif ready:
+                moves.append(("issue", q))
+            elif fail or rng.random() < p_out:
+                moves.append(("issue_out", q))
+        if inflight:
+            moves.append(("land", None))
+        for w in range(slots):
+            q = next_tile[w]
+            if q >= ntiles:
+                continue
+            b, ph = q % ring, (q // ring) & 1
+            if fail and not old_rules:
+                moves.append(("skip_read", w))
+            elif full[b].try_wait(ph):
+                moves.append(("read", w))
+            elif fail or rng.random() < p_out:
+                moves.append(("read_out", w))
+        if not fail and rng.random() < p_freeze:
+            moves.append(("freeze", None))
+        if not moves:
+            if pending or next_batch < ntiles or any(q < ntiles for q in next_tile):
+                return "stall"
+            break
+        kind, arg = rng.choice(moves)
+        if kind == "freeze":
+            fail = True
+        elif kind in ("issue", "issue_out"):
+            q = arg
+            b, ph = q % ring, (q // ring) & 1
+            if kind == "issue_out":
+                fail = True
+            if kind == "issue_out" and not old_rules:
+                pending.remove(q)           # skipped: no copy
+                continue
+            if b in inflight:
+                return "copy issued into a buffer with a copy in flight"
+            if not released[b]:
+                return "copy issued into a buffer that was not released"
+            pending.remove(q)
+            full[b].arrive_expect_tx(1)
+            inflight[b] = q
+            released[b] = False
+            issued_ph[b] = ph
+        elif kind == "skip_issue":
+            pending.remove(arg)
+        elif kind == "land":
+            b = rng.choice(sorted(inflight))
+            content[b] = inflight.pop(b)
+            full[b].complete_tx(1)
+        else:
+            w = arg
+            q = next_tile[w]
+            b = q % ring
+            next_tile[w] = q + slots
+            if kind == "skip_read":
+                continue
+            if kind == "read_out":
+                fail = True
+                if old_rules:             # the earlier kernel still read the header and released
+                    if b in inflight:
+                        return "read of a buffer with a copy in flight"
+                    released[b] = True
+                    empty[b].arrive()
+                continue
+            if b in inflight or content[b] != q:
+                return "read of the wrong tile"
+            released[b] = True
+            empty[b].arrive()
+    # exit drain
+    if old_rules:
+        # the earlier drain: the phases of the last `ring` stream positions
+        for q in range(max(0, ntiles - ring), ntiles):
+            b, ph = q % ring, (q // ring) & 1
+            while not full[b].try_wait(ph) and b in inflight:
+                content[b] = inflight.pop(b)
+                full[b].complete_tx(1)
+        return "ok" if not inflight else "exit with a copy in flight"
+    for b, ph in issued_ph.items():
+        while not full[b].try_wait(ph):
+            if not inflight:
+                return "drain waits on a phase no copy will complete"
+            c = rng.choice(sorted(inflight))          # copies land in any order
+            content[c] = inflight.pop(c)
+            full[c].complete_tx(1)
+    return "ok" if not inflight else "exit with a copy in flight"
+
+
+@pytest.mark.parametrize("slots,per_slot", [(20, 1), (19, 2), (12, 4), (16, 3), (5, 1), (1, 4)])
+def test_waits_that_run_out_never_corrupt_the_ring(slots, per_slot):
+    ring = slots * per_slot
+    batch = min(8, ring)
+    outcomes = set()
+    for seed in range(60):
+        p_out = (0.0, 0.005, 0.05)[seed % 3]
+        r = replay_with_timeouts(slots, ring, 150, seed, batch, p_out=p_out, p_freeze=0.001 * (seed % 4))
+        assert r == "ok", (seed, r)
+        outcomes.add(r)
+
+
+def test_no_timeouts_consumes_every_tile():
+    for seed in range(10):
+        assert replay_with_timeouts(12, 24, 200, seed, 8, p_out=0.0, p_freeze=0.0) == "ok"
+
+
+def test_the_earlier_timeout_rules_are_caught():
+    bad = {replay_with_timeouts(12, 24, 150, seed, 8, p_out=0.05, old_rules=True) for seed in range(40)}
+    assert bad - {"ok"}, bad
