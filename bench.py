@@ -47,6 +47,7 @@ def parse_args(argv=None):
                     help="distance precision (default: the workload's own)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the comparison of forms (plain FP32, batched, mixed precision, learned)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned (mapper) form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--tuning", default=None,
@@ -204,9 +205,10 @@ def oracle_sample(w, seconds: float, max_chunks: int = 64):
 
 # ----------------------------------------------------------------- forms of the method
 
-def _timed_epochs(ctx, Xd, perm_rows, Y, stream):
+def _timed_epochs(ctx, Xd, perm_rows, Y, stream, record=None):
     """Run one epoch per partition row, timing all of them with CUDA events;
-    returns (seconds, avg KL after each epoch)."""
+    returns (seconds, avg KL after each epoch).  record (optional list)
+    receives per epoch {ms, kl, size} and the search counters."""
     import torch
     kls = []
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -217,8 +219,14 @@ def _timed_epochs(ctx, Xd, perm_rows, Y, stream):
         ctx.run(Xd, pr, 1, Y, cost_out=cost)
         b.record(stream)
         torch.cuda.synchronize()
-        secs += a.elapsed_time(b) / 1000.0
+        ms = a.elapsed_time(b)
+        secs += ms / 1000.0
         kls.append(float(cost[0, 0]))
+        if record is not None:
+            st = ctx.stats()
+            record.append({"ms": ms, "kl": float(cost[0, 0]), "size": float(cost[0, 2]),
+                           "window_pairs": int(st.window_pairs), "fp64_rows": int(st.bisect_fp64_rows),
+                           "max_abs_entropy_err": float(st.max_abs_entropy_err)})
     return secs, kls
 
 
@@ -245,9 +253,12 @@ def compare_forms(w, Xd, perms, dev, stream, tuning):
                 c.set_tuning(*tuning)
             Y = torch.from_numpy(w.Y0.copy()).to(dev)
             _timed_epochs(c, Xd, [perms[0]], Y, stream)
-            secs, kls = _timed_epochs(c, Xd, [perms[1]], Y, stream)
+            rec = []
+            secs, kls = _timed_epochs(c, Xd, [perms[1]], Y, stream, record=rec)
         out[name] = {"value": w.n * w.iters / secs, "unit": UNIT, "ms_per_epoch": secs * 1e3,
-                     "final_kl_after_2_epochs": kls[-1], **kw}
+                     "final_kl_after_2_epochs": kls[-1], "window_pairs_per_epoch": rec[-1]["window_pairs"],
+                     "fp64_rows_per_epoch": rec[-1]["fp64_rows"],
+                     "max_abs_entropy_err": rec[-1]["max_abs_entropy_err"], **kw}
     base = out["plain_fp32"]
     for name, r in out.items():
         r["speedup_vs_plain"] = r["value"] / base["value"]
@@ -423,7 +434,8 @@ def bench_ours(args, rank, world, local_rank):
     forms = learned = None
     if not args.no_plain and world == 1:
         forms = compare_forms(w, Xd, perms, dev, stream, tuning)
-        learned = learned_form(dev, stream)
+        if not args.no_learned:
+            learned = learned_form(dev, stream)
     plain = forms["plain_fp32"] if forms else None
 
     cpu = None

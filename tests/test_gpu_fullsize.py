@@ -72,3 +72,50 @@ def test_full_size_bench_configuration(dev):
             gr, Zr = O.gradient(Pr, w.Y0[idx])
             assert rel_max(g[idx], gr) <= GRAD_TOL, (c, rel_max(g[idx], gr))
             assert abs(Z[c] - Zr) <= 1e-6 * Zr
+
+
+@pytest.mark.parametrize("precision", ["bf16_window", "fp32"])
+def test_full_size_precision_stress(dev, precision):
+    """The precision-stress workload at full size: 200,000 sparse image-like
+    vectors (D = 784, ~80% zeros, values in [0, 1]) in 64 chunks of 3125, with
+    the BF16 tensor-core Gram matrix, FP32 window recompute and FP64 redo of
+    stalled rows (and, for comparison, FP32 distances throughout).  Three
+    chunks (first, middle, last) against the FP64 oracle element by element;
+    the errors are printed for the record."""
+    from paper_1812_09869_gb300 import ptsne
+    w = synth.workload("sparse-200k-d784", epochs=1)
+    sizes = np.diff(w.offsets)
+    cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
+                       momentum=w.momentum, precision=precision, schedule="batched")
+    perm = w.perms[0]
+    with ptsne.Context(cfg) as ctx:
+        Xd = torch.from_numpy(w.X).to(dev)
+        pd = torch.from_numpy(perm).to(dev)
+        Yd = torch.from_numpy(w.Y0.copy()).to(dev)
+        Pd = torch.zeros(int((sizes.astype(np.int64) ** 2).sum()), dtype=torch.float32, device=dev)
+        bd = torch.zeros(w.n, dtype=torch.float32, device=dev)
+        ctx.affinities(Xd, pd, P_out=Pd, beta_out=bd)
+        st = ctx.stats()
+        assert st.bisect_failed_rows == 0 and st.wait_timeouts == 0 and st.nonfinite_inputs == 0
+        gd = torch.zeros_like(Yd)
+        Zd = torch.zeros(len(sizes), dtype=torch.float64, device=dev)
+        ctx.step(pd, Yd, grad_out=gd, Z_out=Zd)
+        torch.cuda.synchronize()
+        blocks = torch.split(Pd, [int(z) * int(z) for z in sizes])
+        beta = bd.cpu().numpy().astype(np.float64)
+        g, Z = gd.cpu().numpy(), Zd.cpu().numpy()
+        errs = {"P": 0.0, "beta": 0.0, "grad": 0.0, "Z": 0.0}
+        for c in (0, len(sizes) // 2, len(sizes) - 1):
+            idx = perm[w.offsets[c]:w.offsets[c + 1]]
+            Pr, br, bad = O.affinities(w.X[idx], w.perplexity)
+            assert bad == 0
+            Pg = blocks[c].view(int(sizes[c]), int(sizes[c])).cpu().numpy().astype(np.float64)
+            gr, Zr = O.gradient(Pr, w.Y0[idx])
+            e = {"P": p_error(Pg, Pr), "beta": np.abs(beta[idx] - br).max() / br.max(),
+                 "grad": rel_max(g[idx], gr), "Z": abs(Z[c] - Zr) / Zr}
+            errs = {k: max(errs[k], e[k]) for k in errs}
+        print(f"\n[precision stress {precision}] max over chunks 0, 32, 63: P {errs['P']:.2e} (of row max / "
+              f"relative), beta {errs['beta']:.2e}, gradient {errs['grad']:.2e}, Z {errs['Z']:.2e}; "
+              f"max |H - ln perp| {st.max_abs_entropy_err:.2e} nats; FP64 rows {st.bisect_fp64_rows}, "
+              f"window pairs {st.window_pairs}")
+        assert errs["P"] <= P_TOL and errs["beta"] <= 1e-4 and errs["grad"] <= GRAD_TOL and errs["Z"] <= 1e-6, errs

@@ -235,7 +235,8 @@ def test_multi_epoch_run_matches_oracle_cost(dev):
         ens.append(ck)
     ens = np.stack(ens)
     lo, hi = ens.min(0), ens.max(0)
-    assert np.all(cost >= lo * (1 - KL_TOL)) and np.all(cost <= hi * (1 + KL_TOL)), (cost, ens)
+    kl2 = cost[:, :2]   # the third column is the embedding size (tests/test_gpu_eval.py)
+    assert np.all(kl2 >= lo * (1 - KL_TOL)) and np.all(kl2 <= hi * (1 + KL_TOL)), (cost, ens)
 
 
 def test_batched_iterations_equal_plain_per_chunk_form(dev):
