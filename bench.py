@@ -48,6 +48,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the comparison of forms (plain FP32, batched, mixed precision, learned)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned (mapper) form")
+    ap.add_argument("--mapper-kernels", type=int, default=0, metavar="ROWS",
+                    help="only time the mapper's kernels: inference of ROWS points (one slab) and training "
+                         "epochs over them (batch 4096); prints one JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--tuning", default=None,
@@ -331,6 +334,42 @@ def learned_form(dev, stream, train_epochs=10, mapper_epochs=20, warm_iters=25, 
             "speedup_at_equal_kl": (t_cold / (t_warm + t_infer)) if reached else None}
 
 
+def mapper_kernels(rows: int, dev, stream, reps: int = 5, train_epochs: int = 2) -> dict:
+    """The learned mapper's kernels alone (MLP 50-256-256-2): inference of
+    `rows` points of the D = 50 mixture in one slab, timed over `reps` calls
+    after one warm-up call, and `train_epochs` training epochs over them."""
+    import torch
+    from paper_1812_09869_gb300 import mapper as M
+    from paper_1812_09869_gb300 import synth
+    X, _ = synth.gaussian_mixture(rows, 50, 20, seed=5, anisotropic=True)
+    Xd = torch.from_numpy(X).to(dev)
+    T = torch.from_numpy(synth.init_gaussian(rows, 2, 5.0, seed=6)).to(dev)
+    Y = torch.zeros((rows, 2), dtype=torch.float32, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with M.Mapper(50, synth.mlp_init(50, 2, seed=7), batch=4096, infer_rows=rows) as m:
+        m.fit_scaler(T)
+        m.infer(Xd, Y)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            m.infer(Xd, Y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_inf = a.elapsed_time(b) / reps / 1e3
+        orders = torch.from_numpy(synth.permutations(rows, train_epochs, seed=10)).to(dev)
+        a.record(stream)
+        m.train(Xd, T, orders, train_epochs)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_tr = a.elapsed_time(b) / 1e3
+    flop = 2.0 * rows * (64 * 256 + 256 * 256 + 256 * 2)   # K padded to 64 in layer 1
+    steps = train_epochs * (rows // 4096)
+    return {"metric": "mapper inference points/s", "value": rows / t_inf, "unit": "points/s",
+            "infer_ms": t_inf * 1e3, "infer_tflops": flop / t_inf / 1e12,
+            "train_us_per_step": t_tr / steps * 1e6, "train_steps": steps, "batch": 4096,
+            "config": {"mlp": "50-256-256-2 GELU, BF16 tcgen05", "rows": rows}}
+
+
 # ----------------------------------------------------------------- our arm
 
 def bench_ours(args, rank, world, local_rank):
@@ -512,6 +551,14 @@ def main(argv=None):
             print(json.dumps(out), flush=True)
         return 0
     import torch
+    if args.mapper_kernels:
+        from paper_1812_09869_gb300 import build as pbuild
+        pbuild.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        if rank == 0:
+            print(json.dumps(mapper_kernels(args.mapper_kernels, dev, torch.cuda.current_stream())), flush=True)
+        return 0
     dist_init(world, "nccl" if torch.cuda.is_available() else "gloo")
     out = bench_ours(args, rank, world, local_rank)
     if rank == 0:

@@ -5,10 +5,15 @@
 // and to warm-start ptsne_run.
 //
 // One GEMM kernel serves every contraction: C = A B^T with A (M x K) and
-// B (N x K) BF16, both K-major, staged by TMA (128-byte swizzle, 3-stage ring),
-// one elected thread issuing tcgen05.mma (M = 128, N = NT, K = 16) into an
-// FP32 accumulator of NT columns in tensor memory, and four warps reading it
-// back (tcgen05.ld, one accumulator row per thread) for a fused epilogue:
+// B (N x K) BF16, both K-major, staged by TMA (128-byte swizzle, a ring of
+// up to 3 stages, as many as the CTA's K blocks need), one elected thread
+// issuing tcgen05.mma (M = 128, N = NT, K = 16) into an FP32 accumulator of
+// NT columns in tensor memory, and CG groups of four warps reading it back
+// (tcgen05.ld; warp w reads accumulator rows 32 (w mod 4) .. + 31, one row per
+// thread, and group w / 4 takes NT / CG of the columns) for a fused epilogue.
+// The epilogue (exact GELU per element) is the heavy part, so a CTA carries 8
+// warps and two CTAs share an SM (2 x 256 TMEM columns, <= 2 x 96 KB of
+// stages): one CTA's loads and MMAs run under the other's epilogue.
 //
 //   FWD        u = acc + b; U = u (FP32), H = g(u) (BF16), H^T (BF16)
 //   HEAD_INFER h = g(acc + b2); y = W3 h + b3 per row (the whole hidden row is
@@ -46,7 +51,8 @@ namespace mlp {
 
 constexpr int kH = PTSNE_MLP_HIDDEN;   // 256
 constexpr int kKin = 64;               // input features padded to one K block
-constexpr int kStages = 3;
+constexpr int kStages = 3;              // at most; a CTA uses min(kStages, its K blocks)
+constexpr int kMaxStagesPair = 2;       // stages when K needs more: two CTAs per SM fit
 
 enum Epi { EPI_FWD = 0, EPI_HEAD_INFER = 1, EPI_HEAD_TRAIN = 2, EPI_DGELU = 3, EPI_ATOMIC = 4 };
 
@@ -67,6 +73,7 @@ struct GemmArgs {
     const float* b3;     // HEAD_*: [OD]
     const float* T;      // HEAD_TRAIN: standardised targets [M][OD]
     float invB;          // HEAD_TRAIN
+    int stages;          // ring stages (1 .. kStages)
     double* loss;        // HEAD_TRAIN: accumulates sum |y - t|^2 / (2B)
     float* gW3;          // HEAD_TRAIN: [OD][NT]
     float* gb3;          // HEAD_TRAIN: [OD]
@@ -75,9 +82,80 @@ struct GemmArgs {
     unsigned int* timeouts;
 };
 
-__device__ __forceinline__ float gelu(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678118654752f)); }
+// Exact GELU g(u) = u Phi(u) and g'(u) = Phi(u) + u phi(u), with the normal
+// CDF from the rational approximation of Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26:
+//   erfc(a) = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-a^2), t = 1 / (1 + p a),
+// a >= 0, absolute error <= 1.5e-7 (so |Phi - Phi~| <= 7.5e-8), taken at
+// a = |u| / sqrt 2; Phi(u) = 1 - erfc(a) / 2 for u >= 0 and erfc(a) / 2 below.
+// No cancellation for negative u (erfc is formed directly), one reciprocal
+// and one exponential (both MUFU) shared by g and g'.
+struct NormalParts {
+    float Phi, e;   // Phi(u) and exp(-u^2 / 2)
+};
+__device__ __forceinline__ NormalParts normal_parts(float u) {
+    constexpr float kP = 0.3275911f, kA1 = 0.254829592f, kA2 = -0.284496736f, kA3 = 1.421413741f,
+                    kA4 = -1.453152027f, kA5 = 1.061405429f;
+    constexpr float kRsqrt2 = 0.70710678118654752f, kHalfLog2e = 0.72134752044448170f;
+    const float a = fabsf(u) * kRsqrt2;
+    const float t = hw_rcp(fmaf(kP, a, 1.0f));
+    const float e = hw_ex2(-(u * u) * kHalfLog2e);
+    const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kA5, kA4), kA3), kA2), kA1);
+    const float q = poly * e;   // erfc(|u| / sqrt 2)
+    NormalParts r;
+    r.Phi = u >= 0.f ? fmaf(-0.5f, q, 1.0f) : 0.5f * q;
+    r.e = e;
+    return r;
+}
+// Forward-only GELU of two values at once (packed f32x2), Phi from the
+// approximation of Abramowitz & Stegun formula 7.1.28, which needs a single
+// reciprocal and no exponential:
+//   erfc(a) = (1 + b1 a + b2 a^2 + b3 a^3 + b4 a^4 + b5 a^5 + b6 a^6)^-16,
+// a >= 0, absolute error <= 3e-7 (the 16th power, four squarings in FP32,
+// adds ~1.6e-6 relative to erfc).  erfc overflows to an exact 0 for large a.
+typedef unsigned long long f2m;
+__device__ __forceinline__ f2m pkm(float a, float b) {
+    f2m r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upkm(f2m v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2m fma2m(f2m a, f2m b, f2m c) {
+    f2m d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2m mul2m(f2m a, f2m b) {
+    f2m d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void gelu2(float& x, float& y) {
+    constexpr float kB1 = 0.0705230784f, kB2 = 0.0422820123f, kB3 = 0.0092705272f, kB4 = 0.0001520143f,
+                    kB5 = 0.0002765672f, kB6 = 0.0000430638f, kRsqrt2 = 0.70710678118654752f;
+    const f2m A = pkm(fabsf(x) * kRsqrt2, fabsf(y) * kRsqrt2);
+    f2m P = fma2m(A, pkm(kB6, kB6), pkm(kB5, kB5));
+    P = fma2m(A, P, pkm(kB4, kB4));
+    P = fma2m(A, P, pkm(kB3, kB3));
+    P = fma2m(A, P, pkm(kB2, kB2));
+    P = fma2m(A, P, pkm(kB1, kB1));
+    P = fma2m(A, P, pkm(1.0f, 1.0f));
+    P = mul2m(P, P);
+    P = mul2m(P, P);
+    P = mul2m(P, P);
+    P = mul2m(P, P);
+    float px, py;
+    upkm(P, px, py);
+    const float qx = hw_rcp(px), qy = hw_rcp(py);   // erfc(|u| / sqrt 2)
+    const float fx = x >= 0.f ? fmaf(-0.5f, qx, 1.0f) : 0.5f * qx;
+    const float fy = y >= 0.f ? fmaf(-0.5f, qy, 1.0f) : 0.5f * qy;
+    const f2m G = mul2m(pkm(x, y), pkm(fx, fy));
+    upkm(G, x, y);
+}
+__device__ __forceinline__ float gelu(float u) { return u * normal_parts(u).Phi; }
 __device__ __forceinline__ float gelu_grad(float u) {
-    return 0.5f * (1.0f + erff(u * 0.70710678118654752f)) + u * expf(-0.5f * u * u) * 0.39894228040143268f;
+    const NormalParts n = normal_parts(u);
+    return fmaf(u * 0.39894228040143268f, n.e, n.Phi);
 }
 
 // v[32] on each lane -> on lane l, the sum over the warp's lanes of v[l]
@@ -110,9 +188,24 @@ __device__ __forceinline__ void store_bf16x32(bf16* dst, const float (&v)[32]) {
     }
 }
 
-template <int NT, int EPI, int OD>
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void store_bf16x16(bf16* dst, const float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        uint4 pk;
+        uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+            w[e] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        reinterpret_cast<uint4*>(dst)[q] = pk;
+    }
+}
+
+template <int NT, int EPI, int OD, int CG>
+__global__ void __launch_bounds__(128 * CG, 2)
 mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a) {
+    static_assert((NT / 32) % CG == 0, "column groups must split the accumulator's 32-column chunks");
     constexpr int kBRows = NT < 128 ? 128 : NT;
     constexpr uint32_t kABytes = tc::kTileBytes;
     constexpr uint32_t kBBytes = (uint32_t)kBRows * 128u;
@@ -123,7 +216,12 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     __shared__ uint32_t tmem_base;
     __shared__ float sb[NT];
     __shared__ float sw3[kHead ? OD : 1][NT];
+    __shared__ float s_y[kHead ? CG : 1][128][OD];   // HEAD: per column group, partial outputs of each row
+    constexpr int kThreads = 128 * CG;
+    constexpr int kChunks = NT / 32 / CG;            // 32-column chunks per column group
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = warp >> 2, c0 = grp * kChunks;    // this warp's column group and first chunk
+    const int nst = a.stages;
     const uint32_t sbase = (tc::smem_addr(dsmem) + 1023u) & ~1023u;
     const int m0 = blockIdx.x * 128;
     const int kb0 = blockIdx.y * a.kb_per_split;
@@ -132,7 +230,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem_base), NT < 32 ? 32 : NT);
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < nst; ++s) {
             tc::mbar_init(tc::smem_addr(&full_bar[s]), 1);
             tc::mbar_init(tc::smem_addr(&done_bar[s]), 1);
         }
@@ -140,9 +238,9 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (EPI == EPI_FWD || kHead)
-        for (int n = tid; n < NT; n += 128) sb[n] = a.bias[n];
+        for (int n = tid; n < NT; n += kThreads) sb[n] = a.bias[n];
     if (kHead)
-        for (int idx = tid; idx < OD * NT; idx += 128) sw3[idx / NT][idx % NT] = __bfloat162float(a.W3[idx]);
+        for (int idx = tid; idx < OD * NT; idx += kThreads) sw3[idx / NT][idx % NT] = __bfloat162float(a.W3[idx]);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -152,7 +250,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const uint32_t idesc = tc::idesc_bf16_f32(128, NT);
         bool ok = true;
         auto issue = [&](int i) {
-            const int s = i % kStages;
+            const int s = i % nst;
             const uint32_t fb = tc::smem_addr(&full_bar[s]);
             const uint32_t sa = sbase + (uint32_t)s * kStageBytes, sbb = sa + kABytes;
             tc::mbar_expect_tx(fb, kStageBytes);
@@ -161,10 +259,10 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
             for (int r = 0; r < kBRows / 128; ++r) tc::tma_load_2d(sbb + (uint32_t)r * tc::kTileBytes, &tmB, col, r * 128, fb);
         };
-        for (int i = 0; i < kStages && i < nkb; ++i) issue(i);
+        for (int i = 0; i < nst && i < nkb; ++i) issue(i);
         for (int i = 0; i < nkb; ++i) {
-            const int s = i % kStages;
-            const uint32_t par = (uint32_t)(i / kStages) & 1u;
+            const int s = i % nst;
+            const uint32_t par = (uint32_t)(i / nst) & 1u;
             ok = tc::mbar_wait(tc::smem_addr(&full_bar[s]), par) && ok;
             tc::tc_fence_after();
             const uint32_t sa = sbase + (uint32_t)s * kStageBytes, sbb = sa + kABytes;
@@ -173,60 +271,72 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             for (int k16 = 0; k16 < tc::kTileK / 16; ++k16)
                 tc::mma_bf16(tmem, da + 2 * k16, db + 2 * k16, idesc, (i > 0 || k16 > 0) ? 1u : 0u);
             tc::mma_commit(tc::smem_addr(&done_bar[s]));
-            if (i + kStages < nkb) {   // stage s is free once these MMAs are done
+            if (i + nst < nkb) {   // stage s is free once these MMAs are done
                 ok = tc::mbar_wait(tc::smem_addr(&done_bar[s]), par) && ok;
-                issue(i + kStages);
+                issue(i + nst);
             }
         }
         const int last = nkb - 1;
-        ok = tc::mbar_wait(tc::smem_addr(&done_bar[last % kStages]), (uint32_t)(last / kStages) & 1u) && ok;
+        ok = tc::mbar_wait(tc::smem_addr(&done_bar[last % nst]), (uint32_t)(last / nst) & 1u) && ok;
         if (!ok) atomicAdd(a.timeouts, 1u);
     }
     __syncthreads();
     tc::tc_fence_after();
 
-    const int row = warp * 32 + lane;
+    const int row = (warp & 3) * 32 + lane;
     const int m = m0 + row;
     const bool valid = m < a.M;
-    const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tb = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
     if constexpr (EPI == EPI_FWD) {
-        for (int c = 0; c < NT / 32; ++c) {
-            float v[32];
-            tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
+        // 16 columns at a time (keeps the epilogue within the register budget
+        // of two CTAs per SM)
+        for (int c = 2 * c0; c < 2 * (c0 + kChunks); ++c) {
+            float v[16];
+            tc::tmem_ld16(tb + (uint32_t)(c * 16), v);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] += sb[c * 32 + e];
+            for (int e = 0; e < 16; ++e) v[e] += sb[c * 16 + e];
             if (valid && a.U) {
-                float4* up = reinterpret_cast<float4*>(a.U + (int64_t)m * NT + c * 32);
+                float4* up = reinterpret_cast<float4*>(a.U + (int64_t)m * NT + c * 16);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) up[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                for (int q = 0; q < 4; ++q) up[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = gelu(v[e]);
-            if (valid && a.H) store_bf16x32(a.H + (int64_t)m * NT + c * 32, v);
+            for (int e = 0; e < 16; e += 2) gelu2(v[e], v[e + 1]);
+            if (valid && a.H) store_bf16x16(a.H + (int64_t)m * NT + c * 16, v);
             if (valid && a.HT) {
 #pragma unroll
-                for (int e = 0; e < 32; ++e) a.HT[(int64_t)(c * 32 + e) * a.ldT + m] = __float2bfloat16_rn(v[e]);
+                for (int e = 0; e < 16; ++e) a.HT[(int64_t)(c * 16 + e) * a.ldT + m] = __float2bfloat16_rn(v[e]);
             }
         }
     } else if constexpr (kHead) {
         float y[OD];
 #pragma unroll
         for (int k = 0; k < OD; ++k) y[k] = 0.f;
-        for (int c = 0; c < NT / 32; ++c) {
+        for (int c = c0; c < c0 + kChunks; ++c) {
             float v[32];
             tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                const float h = gelu(v[e] + sb[c * 32 + e]);
+            for (int e = 0; e < 32; e += 2) {
+                float h0 = v[e] + sb[c * 32 + e], h1 = v[e + 1] + sb[c * 32 + e + 1];
+                gelu2(h0, h1);
 #pragma unroll
-                for (int k = 0; k < OD; ++k) y[k] = fmaf(h, sw3[k][c * 32 + e], y[k]);
+                for (int k = 0; k < OD; ++k) y[k] = fmaf(h1, sw3[k][c * 32 + e + 1], fmaf(h0, sw3[k][c * 32 + e], y[k]));
             }
         }
+        // the groups' partial outputs of each row, summed in group order
 #pragma unroll
-        for (int k = 0; k < OD; ++k) y[k] += a.b3[k];
+        for (int k = 0; k < OD; ++k) s_y[grp][row][k] = y[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < OD; ++k) {
+            float t = 0.f;
+#pragma unroll
+            for (int g = 0; g < CG; ++g) t += s_y[g][row][k];
+            y[k] = t + a.b3[k];
+        }
         if constexpr (EPI == EPI_HEAD_INFER) {
-            if (valid) {
+            if (valid && grp == 0) {
 #pragma unroll
                 for (int k = 0; k < OD; ++k)
                     a.Y[(int64_t)m * OD + k] = (float)((double)y[k] * a.scaler[OD + k] + a.scaler[k]);
@@ -240,15 +350,17 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 l2 = fmaf(diff, diff, l2);
                 r[k] = diff * a.invB;
             }
-            const double lw = warp_sum((double)l2);
-            if (lane == 0) atomicAdd(a.loss, lw * 0.5 * (double)a.invB);
+            if (grp == 0) {   // every group holds the same r; group 0 reports it
+                const double lw = warp_sum((double)l2);
+                if (lane == 0) atomicAdd(a.loss, lw * 0.5 * (double)a.invB);
 #pragma unroll
-            for (int k = 0; k < OD; ++k) {
-                const float rs = warp_sum(r[k]);
-                if (lane == 0) atomicAdd(&a.gb3[k], rs);
+                for (int k = 0; k < OD; ++k) {
+                    const float rs = warp_sum(r[k]);
+                    if (lane == 0) atomicAdd(&a.gb3[k], rs);
+                }
             }
-            // second pass over the accumulator: dW3, dA2 and db2
-            for (int c = 0; c < NT / 32; ++c) {
+            // second pass over the group's accumulator columns: dW3, dA2 and db2
+            for (int c = c0; c < c0 + kChunks; ++c) {
                 float v[32], g[32], t[32];
                 tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
 #pragma unroll
@@ -281,7 +393,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             }
         }
     } else if constexpr (EPI == EPI_DGELU) {
-        for (int c = 0; c < NT / 32; ++c) {
+        for (int c = c0; c < c0 + kChunks; ++c) {
             float v[32];
             tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
             if (valid) {
@@ -304,7 +416,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             atomicAdd(&a.colsum[c * 32 + lane], s);
         }
     } else {   // EPI_ATOMIC
-        for (int c = 0; c < NT / 32; ++c) {
+        for (int c = c0; c < c0 + kChunks; ++c) {
             float v[32];
             tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
             if (valid) {
@@ -512,19 +624,30 @@ void free_mlp(ptsne_mlp* m) {
         if (q) cudaFree(q);
 }
 
-size_t gemm_smem(int nt) {
+// Ring stages of a CTA with nkb K blocks: all of them up to two (a single
+// block needs one stage), else two, so that two CTAs share an SM.
+int gemm_stages(int nkb) { return nkb <= kMaxStagesPair ? (nkb < 1 ? 1 : nkb) : kMaxStagesPair; }
+
+size_t gemm_smem(int nt, int stages) {
     const size_t brows = nt < 128 ? 128 : nt;
-    return (size_t)kStages * (tc::kTileBytes + brows * 128) + 1024;
+    return (size_t)stages * (tc::kTileBytes + brows * 128) + 1024;
 }
 
+// Column groups of the epilogue: 2 (8 warps) where the accumulator has 64 or
+// more columns per group.
+template <int NT>
+constexpr int gemm_groups() { return NT >= 64 ? 2 : 1; }
+
 template <int NT, int EPI, int OD>
-cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const GemmArgs& a, int mtiles, int splits,
+cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, GemmArgs a, int mtiles, int splits,
                         cudaStream_t s) {
-    auto kern = mlp_gemm_kernel<NT, EPI, OD>;
-    const size_t smem = gemm_smem(NT);
+    constexpr int CG = gemm_groups<NT>();
+    auto kern = mlp_gemm_kernel<NT, EPI, OD, CG>;
+    a.stages = gemm_stages(a.kb_per_split);
+    const size_t smem = gemm_smem(NT, a.stages);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3((unsigned)mtiles, (unsigned)splits), 128, smem, s>>>(A, B, a);
+    kern<<<dim3((unsigned)mtiles, (unsigned)splits), 128 * CG, smem, s>>>(A, B, a);
     return cudaGetLastError();
 }
 
