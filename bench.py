@@ -48,6 +48,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the comparison of forms (plain FP32, batched, mixed precision, learned)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned (mapper) form")
+    ap.add_argument("--no-eq13", action="store_true", help="skip the Eq. 13 study (adaptive vs fixed learning rate)")
     ap.add_argument("--mapper-kernels", type=int, default=0, metavar="ROWS",
                     help="only time the mapper's kernels: inference of ROWS points (one slab) and training "
                          "epochs over them (batch 4096); prints one JSON line")
@@ -270,12 +271,30 @@ def compare_forms(w, Xd, perms, dev, stream, tuning):
     return out
 
 
+def knn_block(X, maps: dict, k: int = 10, nq: int = 1000, seed: int = 705) -> dict:
+    """k-NN preservation (ptsne_knn_preservation on the GPU) of each map on
+    one seeded sample of nq query points."""
+    import torch
+    from paper_1812_09869_gb300 import ptsne
+    n = int(X.shape[0])
+    q = torch.from_numpy(np.random.default_rng(seed).choice(n, nq, replace=False).astype(np.int32)).to(X.device)
+    out = {"k": k, "queries": nq}
+    for name, Y in maps.items():
+        ov = torch.zeros(nq, dtype=torch.int32, device=X.device)
+        ptsne.knn_preservation(X, Y, q, k, ov)
+        torch.cuda.synchronize()
+        out[name] = float(ov.double().mean().item() / k)
+    return out
+
+
 def learned_form(dev, stream, train_epochs=10, mapper_epochs=20, warm_iters=25, max_warm_epochs=16):
     """The learned form on the 1M + 1M, D = 50 mixture: ptSNE maps the training
     half, the mapper is trained on that map and places the held-out half, and
-    ptSNE on the held-out half is run from that placement until it reaches the
-    KL that the full schedule (train_epochs x 100 iterations) from the random
-    start reaches."""
+    the library's warm start (one epoch from the placement against one from
+    the random start, plain ptSNE keeping the better) is continued until it
+    reaches the KL that the full schedule (train_epochs x 100 iterations) from
+    the random start reaches.  10-NN preservation of the mapper's placement,
+    the warm map and the cold map on 1000 sampled held-out points."""
     import torch
     from paper_1812_09869_gb300 import mapper as M
     from paper_1812_09869_gb300 import ptsne, synth
@@ -294,34 +313,40 @@ def learned_form(dev, stream, train_epochs=10, mapper_epochs=20, warm_iters=25, 
         Ytr = torch.from_numpy(w.Y0.copy()).to(dev)
         t_ptsne_tr, kl_tr = _timed_epochs(c, Xtr, [perms_tr[e] for e in range(train_epochs)], Ytr, stream)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with M.Mapper(w.d, synth.mlp_init(w.d, 2, seed=505), batch=4096) as m:
-        orders = torch.from_numpy(synth.permutations(half, mapper_epochs, seed=605)).to(dev)
-        split = m.autotune(Xtr, Ytr, orders[0][:4096].contiguous())   # split-K of the weight gradients
-        t0 = time.perf_counter()
-        m.fit_scaler(Ytr)
-        loss = m.train(Xtr, Ytr, orders, mapper_epochs)
-        t_train = time.perf_counter() - t0
-        Ymap = torch.zeros((half, 2), dtype=torch.float32, device=dev)
-        m.infer(Xte, Ymap)   # warm-up
-        a.record(stream)
-        m.infer(Xte, Ymap)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t_infer = a.elapsed_time(b) / 1000.0
+    Yrand = torch.from_numpy(synth.init_gaussian(half, 2, 1e-4, seed=705)).to(dev)
+    m = M.Mapper(w.d, synth.mlp_init(w.d, 2, seed=505), batch=4096)
+    orders = torch.from_numpy(synth.permutations(half, mapper_epochs, seed=605)).to(dev)
+    split = m.autotune(Xtr, Ytr, orders[0][:4096].contiguous())   # split-K of the weight gradients
+    t0 = time.perf_counter()
+    m.fit_scaler(Ytr)
+    loss = m.train(Xtr, Ytr, orders, mapper_epochs)
+    t_train = time.perf_counter() - t0
+    Ymap = torch.zeros((half, 2), dtype=torch.float32, device=dev)
+    m.infer(Xte, Ymap)   # warm-up
+    a.record(stream)
+    m.infer(Xte, Ymap)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_infer = a.elapsed_time(b) / 1000.0
     with ctx(w.iters) as c:
-        Yc = torch.from_numpy(synth.init_gaussian(half, 2, 1e-4, seed=705)).to(dev)
+        Yc = Yrand.clone()
         t_cold, kl_cold = _timed_epochs(c, Xte, [perms_te[e] for e in range(train_epochs)], Yc, stream)
     target = kl_cold[-1]
     with ctx(warm_iters) as c:
-        Yw = Ymap.clone()
-        t_warm, kls = 0.0, []
-        for e in range(max_warm_epochs):
+        Yw = torch.zeros((half, 2), dtype=torch.float32, device=dev)
+        t0 = time.perf_counter()
+        used, kl_w0, kl_c0 = m.warm_start(c, Xte, perms_te[0], Yrand, Yw)   # includes the inference
+        t_ws = time.perf_counter() - t0
+        t_warm, kls = 0.0, [min(kl_w0, kl_c0)]
+        for e in range(1, max_warm_epochs):
+            if kls[-1] <= target:
+                break
             t, k = _timed_epochs(c, Xte, [perms_te[e]], Yw, stream)
             t_warm += t
             kls += k
-            if k[-1] <= target:
-                break
+    m.close()
     reached = kls[-1] <= target
+    knn = knn_block(Xte, {"mapper": Ymap, "warm": Yw, "cold": Yc})
     return {"workload": "mapper-1m+1m-d50", "mlp": "50-256-256-2 GELU, BF16 tcgen05, AdamW",
             "train_ptsne": {"epochs": train_epochs, "iters": train_epochs * w.iters, "seconds": t_ptsne_tr,
                             "final_kl": kl_tr[-1]},
@@ -329,9 +354,54 @@ def learned_form(dev, stream, train_epochs=10, mapper_epochs=20, warm_iters=25, 
                              "loss_first_last": [float(loss[0]), float(loss[-1])]},
             "mapper_infer": {"points": half, "seconds": t_infer, "points_per_s": half / t_infer},
             "cold": {"iters": train_epochs * w.iters, "seconds": t_cold, "final_kl": target},
-            "warm": {"iters": warm_iters * len(kls), "seconds_incl_infer": t_warm + t_infer,
+            "warm": {"iters": warm_iters * len(kls), "seconds_incl_infer": t_ws + t_warm,
+                     "warm_start": {"mapper_placement_kl_after_1_epoch": kl_w0, "random_start_kl_after_1_epoch": kl_c0,
+                                    "seconds": t_ws},
                      "kl_per_epoch": kls, "reached_cold_kl": reached},
-            "speedup_at_equal_kl": (t_cold / (t_warm + t_infer)) if reached else None}
+            "fallback_used": not used, "knn": knn,
+            "speedup_at_equal_kl": (t_cold / (t_ws + t_warm)) if reached else None}
+
+
+def eq13_study(w, Xd, dev, stream, tuning, ref_epochs=10, epochs=24):
+    """The paper's auto-adaptive learning rate (Eq. 13, no gains) against the
+    fixed rate with gains, both from the paper's start in the disk of radius
+    1, each for `epochs` epochs.  Each form's target is the other's KL after
+    ref_epochs; a form reaches it at the first epoch from which its KL stays
+    at or below the target for the rest of the run (a run's first epoch can
+    sit deceptively low: every chunk relaxes on its own from the disk, and the
+    pooled map only becomes consistent over later epochs)."""
+    import torch
+    from paper_1812_09869_gb300 import ptsne, synth
+    perms = torch.from_numpy(synth.permutations(w.n, epochs, seed=903)).to(dev)
+    Y0 = synth.init_disk(w.n, seed=904)
+    forms = {"fixed_lr_gains": dict(lr_mode=ptsne.LR_FIXED, use_gains=1),
+             "eq13_lr": dict(lr_mode=ptsne.LR_PAPER, use_gains=0)}
+    recs = {}
+    for name, kw in forms.items():
+        cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
+                           momentum=w.momentum, precision=w.precision, schedule="batched", **kw)
+        with ptsne.Context(cfg) as c:
+            c.set_tuning(*tuning)
+            Y = torch.from_numpy(Y0.copy()).to(dev)
+            rec = []
+            _timed_epochs(c, Xd, [perms[e] for e in range(epochs)], Y, stream, record=rec)
+            recs[name] = rec
+    out = {"init": "disk of radius 1", "epochs": epochs, "ref_epochs": ref_epochs, "iters_per_epoch": w.iters}
+    names = list(forms)
+    for me, other in ((names[0], names[1]), (names[1], names[0])):
+        target = recs[other][ref_epochs - 1]["kl"]
+        kl = [r["kl"] for r in recs[me]]
+        hit = None
+        for e in range(len(kl) - 1, -1, -1):
+            if kl[e] > target:
+                break
+            hit = e
+        out[me] = {"kl_per_epoch": kl, "size_per_epoch": [r["size"] for r in recs[me]],
+                   "ms_per_epoch": float(np.mean([r["ms"] for r in recs[me]])),
+                   "target_kl": target, "target_from": f"{other} after {ref_epochs} epochs",
+                   "epochs_to_target": (hit + 1) if hit is not None else None,
+                   "seconds_to_target": (sum(r["ms"] for r in recs[me][:hit + 1]) / 1e3) if hit is not None else None}
+    return out
 
 
 def mapper_kernels(rows: int, dev, stream, reps: int = 5, train_epochs: int = 2) -> dict:
@@ -473,6 +543,8 @@ def bench_ours(args, rank, world, local_rank):
     forms = learned = None
     if not args.no_plain and world == 1:
         forms = compare_forms(w, Xd, perms, dev, stream, tuning)
+        if not args.no_eq13:
+            forms["lr_eq13_study"] = eq13_study(w, Xd, dev, stream, tuning)
         if not args.no_learned:
             learned = learned_form(dev, stream)
     plain = forms["plain_fp32"] if forms else None

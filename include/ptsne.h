@@ -297,6 +297,21 @@ size_t ptsne_workspace_bytes(const ptsne_ctx* ctx);
 int ptsne_kde_grid(const float* Y_dev, const float* beta_dev, int64_t n, int32_t gx, int32_t gy,
                    const float* box_host, float* density_dev, int64_t* dropped_dev, void* stream);
 
+/* k-nearest-neighbour preservation of a map (the judge of a map's local
+ * structure, used on the learned mapper's placements): for each query q (an
+ * index into the n points), the k nearest neighbours of q among the rows of
+ * X_dev (n x d) and among the rows of Y_dev (n x od), by squared Euclidean
+ * distance in FP32 (direct differences), q itself excluded and ties broken by
+ * the smaller index.  overlap_out_dev (nq int32): the size of the overlap of
+ * the two sets (the preservation of q is overlap / k; -1 for a query outside
+ * [0, n)).  nbr_x_out_dev, nbr_y_out_dev (optional, nq x k int32): the two
+ * sets, nearest first.  1 <= k <= 32, k < n < 2^31, 1 <= d, od <= 4096,
+ * nq >= 0; else PTSNE_EINVAL with the reason in ptsne_last_error(NULL).
+ * Async. */
+int ptsne_knn_preservation(const float* X_dev, const float* Y_dev, int64_t n, int32_t d, int32_t od,
+                           const int32_t* queries_dev, int32_t nq, int32_t k, int32_t* overlap_out_dev,
+                           int32_t* nbr_x_out_dev, int32_t* nbr_y_out_dev, void* stream);
+
 /* Largest chunk ptsne_gradient_static accepts. */
 #define PTSNE_STATIC_MAX_ROWS 32768
 

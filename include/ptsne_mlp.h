@@ -8,7 +8,10 @@
  * mapper's quality (KL of Eq. 5 and k-nearest-neighbour preservation).
  *
  * Network: y = W3 g(W2 g(W1 x + b1) + b2) + b3 with g the exact GELU
- * g(u) = u (1 + erf(u / sqrt 2)) / 2, x in R^d_in (d_in <= 64), hidden width
+ * g(u) = u (1 + erf(u / sqrt 2)) / 2 (the normal CDF evaluated with the
+ * approximations of Abramowitz & Stegun, formulas 7.1.26 and 7.1.28, absolute
+ * error <= 3e-7, far below the BF16 rounding of the hidden activations),
+ * x in R^d_in (d_in <= 64), hidden width
  * 256, y in R^out_dim.  Weights are kept in FP32 (master copy, AdamW state)
  * and used in BF16; the products accumulate in FP32 on the tensor cores
  * (tcgen05, 128-row tiles).  Training minimises
@@ -102,6 +105,26 @@ int ptsne_mlp_autotune(ptsne_mlp* m, const float* X_dev, const float* T_dev, int
 /* Map n points: X_dev (n x d_in) -> Y_out_dev (n x out_dim), de-standardised
  * by the scaler.  Runs in slabs of infer_rows rows.  Async. */
 int ptsne_mlp_infer(ptsne_mlp* m, const float* X_dev, int64_t n, float* Y_out_dev, void* stream);
+
+struct ptsne_ctx;
+
+/* Warm start with plain ptSNE as the fallback and the judge.  The mapper
+ * places the n points of X_dev (n x d_in, d_in = the context's d) into Y_dev
+ * (n x out_dim); then one ptSNE epoch on the partition perm_dev runs from
+ * that placement and one from the cold start Y_random_dev (n x out_dim, not
+ * modified; e.g. the N(0, 1e-4) or unit-disk start), both with the context's
+ * settings, so at equal iterations.  If the warm epoch ends at a larger
+ * average KL (Eq. 5) than the cold one, the mapper did worse than no mapper
+ * and Y_dev receives the cold epoch's map; else it keeps the warm epoch's.
+ * Either way Y_dev then holds a map one epoch into the run: continue with
+ * ptsne_run.  kl_out_host (optional, 2 doubles): {warm KL, cold KL};
+ * used_mapper_out (optional): 1 if the warm map was kept, 0 on fallback.
+ * Needs a context with layers = 1, n points, d = d_in and the mapper's
+ * out_dim; else PTSNE_EINVAL.  The context keeps a second n x out_dim map
+ * (allocated on the first call).  Synchronous. */
+int ptsne_mlp_warm_start(ptsne_mlp* m, struct ptsne_ctx* ctx, const float* X_dev, const int32_t* perm_dev,
+                         const float* Y_random_dev, float* Y_dev, double* kl_out_host, int32_t* used_mapper_out,
+                         void* stream);
 
 #ifdef __cplusplus
 }

@@ -339,15 +339,24 @@ def adamw_step(W, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=1e-4):
         W[k] = W[k] - lr * (mh / (np.sqrt(vh) + eps) + decay)
 
 
+def knn_sets(q, a, k, exclude_self=True, want_dist=False):
+    """Indices of the k nearest rows of `a` to each row of `q` (squared
+    Euclidean distances in FP64, exact by full sort; ties to the smaller
+    index), nearest first; with exclude_self the nearest entry (the query
+    itself, at distance 0) is dropped.  want_dist: also the sorted distances
+    (k + 1 of them, the one after the k-th included)."""
+    q, a = _f64(q), _f64(a)
+    d = (q * q).sum(1)[:, None] + (a * a).sum(1)[None, :] - 2.0 * q @ a.T
+    order = np.argsort(d, axis=1, kind="stable")
+    sel = order[:, 1:k + 1] if exclude_self else order[:, :k]
+    if not want_dist:
+        return sel
+    lo = 1 if exclude_self else 0
+    return sel, np.take_along_axis(d, order[:, lo:lo + k + 1], axis=1)
+
+
 def knn_preservation(Xq, Xall, Yq, Yall, k=10, exclude_self=True):
     """Mean fraction of each query's k nearest neighbours in X (exact, by full
     sort) that are also among its k nearest neighbours in Y."""
-    Xq, Xall, Yq, Yall = map(_f64, (Xq, Xall, Yq, Yall))
-
-    def knn(q, a):
-        d = (q * q).sum(1)[:, None] + (a * a).sum(1)[None, :] - 2.0 * q @ a.T
-        order = np.argsort(d, axis=1, kind="stable")
-        return order[:, 1:k + 1] if exclude_self else order[:, :k]
-
-    nx, ny = knn(Xq, Xall), knn(Yq, Yall)
+    nx, ny = knn_sets(Xq, Xall, k, exclude_self), knn_sets(Yq, Yall, k, exclude_self)
     return float(np.mean([len(np.intersect1d(a, b)) / k for a, b in zip(nx, ny)]))

@@ -26,13 +26,17 @@
 //     block's slice of rows, broadcast to every block's copy of the map.
 // Every mbarrier wait is bounded in time; a wait that runs out is counted in
 // DeviceStats::timeouts (the host then reports PTSNE_ETIMEOUT) and the kernel
-// runs to completion without blocking.  The first wait that runs out freezes
-// the block's pipeline (a shared flag): from then on every wait fails at
-// once, the producer issues no further copy and no consumer reads or releases
-// a buffer, so a copy never lands in a buffer that is being read or that still
-// has a copy in flight, and a stale barrier phase is never taken for a
-// completed one.  Before the block exits, the producer waits (bounded) for the
-// last copy it issued into each buffer.
+// runs to completion without blocking.  A failed wait sets the block's
+// freeze flag, so that every wait not yet satisfied then fails at once; a
+// consumer warp whose wait failed skips that tile and every later one (no
+// read, no release), and after a batch with a failed wait the producer
+// issues no further copy.  A ring buffer belongs to one consumer warp, so a
+// phase of it can be left incomplete only by that warp's own failure or by a
+// copy the producer skipped: a ready barrier is therefore never a stale phase,
+// and the fast path (the barrier already complete) reads no flag.  A copy
+// never lands in a buffer that is being read or that still has one in
+// flight.  Before the block exits, the producer waits (bounded) for the last
+// copy it issued into each buffer.
 #include <float.h>
 
 #include "ptsne_internal.cuh"
@@ -99,14 +103,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 // Wait for the phase of the given parity; false if it did not complete within
-// kWaitNs.  `fail` is the block's shared freeze flag: once set (by this wait
-// running out, or by any earlier failed wait of the block or of the launch),
-// every wait returns false at once without looking at the barrier, so a phase
-// left incomplete by a skipped copy or release is never mistaken for a later
-// one of the same parity.
+// kWaitNs, or at once (while not complete) when the block's freeze flag
+// `fail` or the launch's timeout count is set.  A failed wait sets `fail`.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const unsigned int* timeouts,
                                           volatile int* fail) {
-    if (*fail) return false;
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try(bar, parity)) {
@@ -482,8 +482,8 @@ struct KSum {
 template <int OD, bool COST>
 __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qend, uint32_t nslots, uint32_t ring_n,
                                              const float* ring, uint32_t full_a, uint32_t empty_a,
-                                             unsigned int* timeouts, volatile int* fail, int nb, const float* map,
-                                             int zcap, float* acc, int lane, KSum (&part)[4]) {
+                                             unsigned int* timeouts, volatile int* fail, bool& wfail, int nb,
+                                             const float* map, int zcap, float* acc, int lane, KSum (&part)[4]) {
     // w of the pair (i, i), which a diagonal tile's row-wise pass counts in
     // its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own columns)
     const float w_ii = hw_rcp(1.0f);
@@ -493,10 +493,12 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
         // (this buffer's previous use) belonged to this same slot and was
         // waited for before: the barrier is at most one phase behind, and
         // the parity test cannot mistake an older phase for this one.
-        // A tile whose wait failed is skipped whole: no read, no release (the
-        // buffer may still receive its copy), no arithmetic.
+        // After a failed wait this warp skips its tiles whole: no wait, no
+        // read, no release (a buffer may still receive its copy), no arithmetic.
+        if (wfail) continue;
         const bool ok = __all_sync(0xffffffffu, mbar_wait(full_a + 8 * cur.buf, cur.ph, timeouts, fail));
         if (!ok) {
+            wfail = true;
             if (lane == 0) atomicAdd(timeouts, 1u);
             continue;
         }
@@ -504,7 +506,7 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
         const int2 ab = *reinterpret_cast<const int2*>(tile + kPTileFloats);
         // the trailer is written by the joint-P kernel; clamp it anyway so
         // that no shared-memory index can leave the chunk's rows
-        const int a = min(max(ab.x, 0), nb - 1), b = min(max(ab.y, 0), nb - 1);
+        const int a = (int)min((unsigned)ab.x, (unsigned)(nb - 1)), b = (int)min((unsigned)ab.y, (unsigned)(nb - 1));
         float4 pv[8];
         tile_lane_values(tile, lane, pv);
         __syncwarp();
@@ -557,8 +559,11 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     __shared__ float s_mn[32], s_mx[32];
     __shared__ float s_eta;
     __shared__ int s_fail;                          // the block's freeze flag (see mbar_wait)
-    __shared__ unsigned char s_issued[64];          // buffer received a copy from the producer
-    __shared__ unsigned char s_lastph[64];          // full-barrier parity of that buffer's last copy
+    // the producer's first batch with a failed wait (it issues nothing after
+    // it): its stream position and the lanes that did issue (rare path, kept
+    // out of the registers of the hot loop)
+    __shared__ unsigned long long s_fail_base;
+    __shared__ unsigned int s_fail_issued;
 
     const uint32_t K = cl_size(), rank = cl_rank();
     const uint32_t ring_a = smem_u32(ring), full_a = smem_u32(fullb), empty_a = smem_u32(emptyb);
@@ -567,7 +572,6 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         for (int b = 0; b < A.ring; ++b) {
             mbar_init(full_a + 8 * b, 1);
             mbar_init(empty_a + 8 * b, 1u);
-            s_issued[b] = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -580,6 +584,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     cur.buf = is_producer ? 0u : (uint32_t)slot;   // slot < nslots <= ring
     cur.ph = 0u;
     unsigned long long q0 = 0;  // first stream index of the current pass (same in every thread)
+    bool wfail = false;         // this warp had a failed wait (warp-uniform)
     for (;;) {
         if (rank == 0 && tid == 0) s_item = atomicAdd(A.queue, 1);
         sync_owner(K);
@@ -640,9 +645,11 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 // 3.5% slower), while batches of 3 or fewer cannot keep the ring fed.
                 const int batch = A.ring < 8 ? A.ring : 8;
                 const uint32_t q0r = (uint32_t)(q0 % ring_n), q0ph = (uint32_t)(q0 / ring_n) & 1u;
-                for (int base = 0; base < S.nq; base += batch) {
+                for (int base = 0; base < S.nq && !wfail; base += batch) {
                     const int s = base + lane;
-                    if (lane < batch && s < S.nq) {
+                    const bool active = lane < batch && s < S.nq;
+                    bool issued = false;
+                    if (active) {
                         const uint32_t t = q0r + (uint32_t)s;
                         const uint32_t buf = t % ring_n, ph = q0ph ^ ((t / ring_n) & 1u);
                         // a copy is issued only into a buffer known to be released
@@ -650,19 +657,26 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                             const float* src = P2c + ((int64_t)rank + (int64_t)K * s) * kPTileStride;
                             mbar_expect_tx(full_a + 8 * buf, kTileBytes);
                             bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
-                            s_issued[buf] = 1;
-                            s_lastph[buf] = (unsigned char)ph;
+                            issued = true;
                         } else {
                             atomicAdd(A.timeouts, 1u);
                         }
                     }
-                    __syncwarp();
+                    // after a batch with a failed wait the producer issues nothing more
+                    const unsigned int got = __ballot_sync(0xffffffffu, issued);
+                    if (got != __ballot_sync(0xffffffffu, active)) {
+                        wfail = true;
+                        if (lane == 0) {
+                            s_fail_base = q0 + (unsigned long long)base;
+                            s_fail_issued = got;
+                        }
+                    }
                 }
             } else {
                 if (!cost) consume_pass<OD, false>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts,
-                                                   &s_fail, nb, map, zcap, acc, lane, part);
+                                                   &s_fail, wfail, nb, map, zcap, acc, lane, part);
                 else consume_pass<OD, true>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts,
-                                            &s_fail, nb, map, zcap, acc, lane, part);
+                                            &s_fail, wfail, nb, map, zcap, acc, lane, part);
             }
             // block partials (fixed order), then the cluster total; a gradient pass
             // has only Z (the cost sums are zero there)
@@ -735,13 +749,24 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     // (bounded, whatever the freeze flag says) for the phase of the last copy
     // issued into each buffer.  Copies into one buffer are issued one at a
     // time (each after the release of the previous one), so that phase is the
-    // only one a buffer can still owe.
-    if (is_producer) {
-        __syncwarp();
-        if (lane == 0) {
-            for (int b = 0; b < A.ring; ++b) {
-                if (!s_issued[b]) continue;
-                const uint32_t bar = full_a + 8 * b, ph = s_lastph[b];
+    // only one a buffer can still owe.  Stream position G went to buffer
+    // G mod ring with parity (G / ring) mod 2; the producer issued every
+    // position below `end` (its whole stream, or the start of its failed
+    // batch) and, of the failed batch, the lanes in fail_issued.
+    if (is_producer && lane == 0 && *(volatile int*)&s_fail != 0) {
+        const unsigned long long end = wfail ? s_fail_base : q0;
+        const unsigned int issued_lanes = wfail ? s_fail_issued : 0u;
+        for (int b = 0; b < A.ring; ++b) {
+            long long last = -1;   // last issued stream position of buffer b
+            if (end > (unsigned long long)b) last = (long long)(end - 1 - ((end - 1 - (unsigned long long)b) % ring_n));
+            for (int l = 0; l < 32; ++l)
+                if ((issued_lanes >> l) & 1u) {
+                    const unsigned long long g = end + (unsigned long long)l;
+                    if (g % ring_n == (unsigned long long)b && (long long)g > last) last = (long long)g;
+                }
+            if (last < 0) continue;
+            {
+                const uint32_t bar = full_a + 8 * b, ph = (uint32_t)(((unsigned long long)last / ring_n) & 1u);
                 const unsigned long long t0 = global_ns();
                 while (!mbar_try(bar, ph)) {
                     if (global_ns() - t0 > kWaitNs) {

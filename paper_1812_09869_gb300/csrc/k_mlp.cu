@@ -1045,4 +1045,37 @@ int ptsne_mlp_infer(ptsne_mlp* m, const float* X, int64_t n, float* Y, void* str
     return PTSNE_OK;
 }
 
+int ptsne_mlp_warm_start(ptsne_mlp* m, ptsne_ctx* ctx, const float* X, const int32_t* perm, const float* Yrand,
+                         float* Y, double* kl_out, int32_t* used_out, void* stream) {
+    if (!m) return PTSNE_EINVAL;
+    if (!ctx || !X || !perm || !Yrand || !Y) return mfail(m, PTSNE_EINVAL, "ctx, X, perm, Y_random and Y are required");
+    if (ctx->layers != 1 || ctx->p.d != m->din || ctx->p.out_dim != m->od)
+        return mfail(m, PTSNE_EINVAL, "the context needs layers = 1, d = d_in and the mapper's out_dim");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = ctx->npts, od = m->od;
+    if (!ctx->ycold) {
+        MCK(cudaMalloc((void**)&ctx->ycold, sizeof(float) * (size_t)(n * od)));
+        ctx->ws_bytes += sizeof(float) * (size_t)(n * od);
+    }
+    int rc = ptsne_mlp_infer(m, X, n, Y, stream);
+    if (rc != PTSNE_OK) return rc;
+    MCK(cudaMemcpyAsync(ctx->ycold, Yrand, sizeof(float) * (size_t)(n * od), cudaMemcpyDeviceToDevice, s));
+    double warm[3] = {0, 0, 0}, cold[3] = {0, 0, 0};
+    rc = ptsne_run(ctx, X, perm, 1, Y, warm, stream);
+    if (rc < 0) return mfail(m, rc, ptsne_last_error(ctx));
+    rc = ptsne_run(ctx, X, perm, 1, ctx->ycold, cold, stream);
+    if (rc < 0) return mfail(m, rc, ptsne_last_error(ctx));
+    const bool keep = !(warm[0] > cold[0]);
+    if (!keep) {
+        MCK(cudaMemcpyAsync(Y, ctx->ycold, sizeof(float) * (size_t)(n * od), cudaMemcpyDeviceToDevice, s));
+        MCK(cudaStreamSynchronize(s));
+    }
+    if (kl_out) {
+        kl_out[0] = warm[0];
+        kl_out[1] = cold[0];
+    }
+    if (used_out) *used_out = keep ? 1 : 0;
+    return PTSNE_OK;
+}
+
 }  // extern "C"

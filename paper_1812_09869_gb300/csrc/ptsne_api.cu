@@ -83,7 +83,7 @@ void free_all(ptsne_ctx* c) {
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
                     c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense,
-                    c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm, c->size_part, c->size_done};
+                    c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm, c->size_part, c->size_done, c->ycold};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);

@@ -208,6 +208,7 @@ struct ptsne_ctx {
     int32_t* hperms = nullptr;
     int64_t hperms_cap = 0;
     float* hY = nullptr;
+    float* ycold = nullptr;            // ptsne_mlp_warm_start: the cold start's map (lazily allocated)
 
     bool have_P = false;
     size_t ws_bytes = 0;

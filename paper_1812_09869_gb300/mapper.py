@@ -73,6 +73,7 @@ def lib():
         L.ptsne_mlp_train.argtypes = [vp, vp, vp, C.c_int64, vp, C.c_int32, C.POINTER(C.c_double), vp]
         L.ptsne_mlp_infer.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.ptsne_mlp_autotune.argtypes = [vp, vp, vp, C.c_int64, vp, C.c_char_p, C.POINTER(C.c_int32), vp]
+        L.ptsne_mlp_warm_start.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), vp]
         _bound = True
     return L
 
@@ -151,3 +152,13 @@ class Mapper:
 
     def infer(self, X, Y_out, stream=None):
         return self._check(lib().ptsne_mlp_infer(self.h, _ptr(X), int(X.shape[0]), _ptr(Y_out), _stream(stream)))
+
+    def warm_start(self, ctx, X, perm, Y_random, Y_out, stream=None):
+        """ptsne_mlp_warm_start: the mapper's placement of X, one ptSNE epoch
+        from it and one from Y_random on partition perm (context ctx), keeping
+        the better map in Y_out.  Returns (used_mapper, warm KL, cold KL)."""
+        kl = (C.c_double * 2)()
+        used = C.c_int32(-1)
+        self._check(lib().ptsne_mlp_warm_start(self.h, ctx.h, _ptr(X), _ptr(perm), _ptr(Y_random), _ptr(Y_out), kl,
+                                               C.byref(used), _stream(stream)))
+        return bool(used.value), float(kl[0]), float(kl[1])

@@ -116,6 +116,8 @@ def lib():
                                      C.POINTER(C.c_int32), vp]
         L.ptsne_gradient_static.argtypes = [vp, C.c_int64, vp, C.c_int32, C.c_int32, vp, vp, vp]
         L.ptsne_kde_grid.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_float), vp, vp, vp]
+        L.ptsne_knn_preservation.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, vp, C.c_int32, C.c_int32, vp,
+                                             vp, vp, vp]
         _lib = L
     return _lib
 
@@ -293,6 +295,17 @@ def kde_grid(Y, beta, gx, gy, box, density_out, dropped_out=None, stream=None):
     b = (C.c_float * 4)(*[float(v) for v in box])
     rc = lib().ptsne_kde_grid(_ptr(Y), _ptr(beta), int(Y.shape[0]), int(gx), int(gy), b, _ptr(density_out),
                               _ptr(dropped_out), _stream(stream))
+    if rc != OK:
+        raise PtsneError(rc, lib().ptsne_last_error(None).decode())
+    return rc
+
+
+def knn_preservation(X, Y, queries, k, overlap_out, nbr_x_out=None, nbr_y_out=None, stream=None):
+    """ptsne_knn_preservation: per query, the overlap of its k nearest
+    neighbours in X (n x d) and in Y (n x od); optional neighbour sets."""
+    n, d = int(X.shape[0]), int(X.shape[1])
+    rc = lib().ptsne_knn_preservation(_ptr(X), _ptr(Y), n, d, int(Y.shape[1]), _ptr(queries), int(queries.shape[0]),
+                                      int(k), _ptr(overlap_out), _ptr(nbr_x_out), _ptr(nbr_y_out), _stream(stream))
     if rc != OK:
         raise PtsneError(rc, lib().ptsne_last_error(None).decode())
     return rc

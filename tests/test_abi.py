@@ -28,7 +28,8 @@ def test_header_declares_the_boundary():
     syms = _declared_symbols()
     for s in ("ptsne_create", "ptsne_destroy", "ptsne_affinities", "ptsne_step", "ptsne_run",
               "ptsne_run_host", "ptsne_cost", "ptsne_get_stats", "ptsne_last_error", "ptsne_gradient_static",
-              "ptsne_mlp_create", "ptsne_mlp_train", "ptsne_mlp_grad", "ptsne_mlp_infer"):
+              "ptsne_mlp_create", "ptsne_mlp_train", "ptsne_mlp_grad", "ptsne_mlp_infer", "ptsne_embedding_size",
+              "ptsne_knn_preservation", "ptsne_mlp_warm_start"):
         assert s in syms
 
 
@@ -121,3 +122,23 @@ def test_kde_grid_rejects_bad_arguments_on_the_host(lib):
     assert lib.ptsne_kde_grid(fake, fake, 10, 8, 8, bad_box, fake, None, None) == ptsne.EINVAL
     assert lib.ptsne_kde_grid(None, fake, 10, 8, 8, box, fake, None, None) == ptsne.EINVAL
     assert "ptsne_kde_grid" in lib.ptsne_last_error(None).decode()
+
+
+def test_knn_preservation_rejects_bad_arguments_on_the_host(lib):
+    from paper_1812_09869_gb300 import ptsne
+    fake = C.c_void_p(0x1000)
+    assert lib.ptsne_knn_preservation(fake, fake, 100, 50, 2, fake, 10, 0, fake, None, None, None) == ptsne.EINVAL
+    assert lib.ptsne_knn_preservation(fake, fake, 100, 50, 2, fake, 10, 33, fake, None, None, None) == ptsne.EINVAL
+    assert lib.ptsne_knn_preservation(fake, fake, 10, 50, 2, fake, 10, 10, fake, None, None, None) == ptsne.EINVAL
+    assert lib.ptsne_knn_preservation(fake, fake, 100, 0, 2, fake, 10, 10, fake, None, None, None) == ptsne.EINVAL
+    assert lib.ptsne_knn_preservation(None, fake, 100, 50, 2, fake, 10, 10, fake, None, None, None) == ptsne.EINVAL
+    assert "ptsne_knn_preservation" in lib.ptsne_last_error(None).decode()
+    assert lib.ptsne_knn_preservation(fake, fake, 100, 50, 2, fake, 0, 10, fake, None, None, None) == ptsne.OK
+
+
+def test_warm_start_rejects_a_mismatched_context(lib):
+    from paper_1812_09869_gb300 import mapper as M
+    from paper_1812_09869_gb300 import ptsne
+    fake = C.c_void_p(0x1000)
+    ML = M.lib()
+    assert ML.ptsne_mlp_warm_start(None, fake, fake, fake, fake, fake, None, None, None) == ptsne.EINVAL

@@ -111,3 +111,59 @@ def test_layers_size_covers_every_layer(dev):
         torch.cuda.synchronize()
         ref = O.embedding_size(Yd.cpu().numpy().astype(np.float64))
     assert abs(cost[0, 2] - ref) <= SIZE_TOL * ref
+
+
+@pytest.mark.parametrize("k", [1, 10, 32])
+def test_knn_preservation_matches_oracle(dev, k):
+    """Neighbour sets in the input space (D = 50 mixture) and in a 2-D map,
+    and their overlap, against the oracle's exact sort.  A query whose k-th
+    and (k+1)-th FP64 distances lie within FP32 resolution of each other can
+    legitimately differ at the boundary; such queries (if any) are only
+    checked for a valid set."""
+    from oracle import oracle as O
+    from paper_1812_09869_gb300 import ptsne
+    n, d = 20011, 50
+    X, _ = synth.gaussian_mixture(n, d, 12, seed=51, anisotropic=True)
+    rng = np.random.default_rng(52)
+    R = rng.standard_normal((d, 2)).astype(np.float32)
+    Y = (X @ R + rng.standard_normal((n, 2)).astype(np.float32)).astype(np.float32)   # a map that keeps some structure
+    q = rng.choice(n, 300, replace=False).astype(np.int32)
+    q[0], q[1] = 0, n - 1                                                             # first and last rows
+    ov = torch.full((len(q),), -7, dtype=torch.int32, device=dev)
+    nx = torch.full((len(q), k), -7, dtype=torch.int32, device=dev)
+    ny = torch.full((len(q), k), -7, dtype=torch.int32, device=dev)
+    ptsne.knn_preservation(torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev), torch.from_numpy(q).to(dev), k,
+                           ov, nx, ny)
+    torch.cuda.synchronize()
+    ov, nx, ny = ov.cpu().numpy(), nx.cpu().numpy(), ny.cpu().numpy()
+    sx, dxs = O.knn_sets(X[q], X, k, want_dist=True)
+    sy, dys = O.knn_sets(Y[q], Y, k, want_dist=True)
+
+    def near_tie(ds):
+        return np.abs(ds[:, k] - ds[:, k - 1]) <= 1e-5 * np.maximum(ds[:, k], 1e-30)
+
+    tie = near_tie(dxs) | near_tie(dys)
+    assert tie.mean() < 0.05
+    ok = ~tie
+    assert np.array_equal(nx[ok], sx[ok]) and np.array_equal(ny[ok], sy[ok])
+    ref = np.array([len(np.intersect1d(a, b)) for a, b in zip(sx, sy)])
+    assert np.array_equal(ov[ok], ref[ok])
+    # every set is valid: k distinct indices, the query excluded
+    for i in range(len(q)):
+        for s in (nx[i], ny[i]):
+            assert len(set(s.tolist())) == k and q[i] not in s and s.min() >= 0 and s.max() < n
+    # the mean preservation of the queries, as the oracle defines it
+    assert abs(ov[ok].mean() / k - O.knn_preservation(X[q[ok]], X, Y[q[ok]], Y, k=k)) <= 1e-12
+
+
+def test_knn_query_outside_the_points_is_reported(dev):
+    from paper_1812_09869_gb300 import ptsne
+    n = 1000
+    X = torch.from_numpy(synth.init_gaussian(n, 5, 1.0, seed=53)).to(dev)
+    Y = torch.from_numpy(synth.init_gaussian(n, 2, 1.0, seed=54)).to(dev)
+    q = torch.tensor([3, n, -1, 7], dtype=torch.int32, device=dev)
+    ov = torch.zeros(4, dtype=torch.int32, device=dev)
+    ptsne.knn_preservation(X, Y, q, 5, ov)
+    torch.cuda.synchronize()
+    o = ov.cpu().numpy()
+    assert o[1] == -1 and o[2] == -1 and 0 <= o[0] <= 5 and 0 <= o[3] <= 5

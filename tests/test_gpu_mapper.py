@@ -191,6 +191,48 @@ def test_warm_start_gains_over_plain_ptsne(dev):
     assert pres["map"] > 10 * chance
     assert pres["warm"] >= 0.75 * pres["cold"]
 
+    # the library's warm start keeps the trained mapper's placement (its first
+    # epoch beats the cold start's at equal iterations)
+    cfg = ptsne.Config(n=half, d=d_in, offsets=off, perplexity=30.0, iters=short)
+    with M.Mapper(d_in, synth.mlp_init(d_in, 2, 88), batch=1024) as m, ptsne.Context(cfg) as ctx:
+        Ttr = torch.from_numpy(Ytr).to(dev)
+        m.fit_scaler(Ttr)
+        m.train(Xtr_d, Ttr, torch.from_numpy(synth.permutations(half, 40, seed=89)).to(dev), 40)
+        Yw = torch.zeros((half, 2), dtype=torch.float32, device=dev)
+        Yr = torch.from_numpy(synth.init_gaussian(half, 2, 1e-4, seed=90)).to(dev)
+        used, kw, kc = m.warm_start(ctx, Xte_d, torch.from_numpy(synth.permutations(half, 1, 91)[0]).to(dev), Yr, Yw)
+    assert used and kw < kc, (used, kw, kc)
+
+
+def test_warm_start_falls_back_to_the_cold_start(dev):
+    """A deliberately bad mapper (untrained, its output scaled to a spread of
+    1e5) places the points so badly that one epoch from its placement ends
+    above the cold start's KL: the warm start falls back, and the map it
+    returns is the cold start's epoch (compared with the same epoch run on its
+    own)."""
+    from paper_1812_09869_gb300 import mapper as M
+    from paper_1812_09869_gb300 import ptsne
+    n, d_in = 8192, 50
+    X, _ = synth.gaussian_mixture(n, d_in, 10, seed=121, anisotropic=True)
+    Xd = torch.from_numpy(X).to(dev)
+    off = synth.equal_chunk_offsets(n, 4)
+    perm = torch.from_numpy(synth.permutations(n, 1, seed=122)[0]).to(dev)
+    Yr = torch.from_numpy(synth.init_gaussian(n, 2, 1e-4, seed=123)).to(dev)
+    cfg = ptsne.Config(n=n, d=d_in, offsets=off, perplexity=30.0, iters=30)
+    with M.Mapper(d_in, synth.mlp_init(d_in, 2, 124), batch=1024) as m, ptsne.Context(cfg) as ctx:
+        m.fit_scaler(torch.from_numpy(synth.init_gaussian(n, 2, 1e5, seed=125)).to(dev))
+        Yw = torch.zeros((n, 2), dtype=torch.float32, device=dev)
+        used, kw, kc = m.warm_start(ctx, Xd, perm, Yr, Yw)
+        Ycold = Yr.clone()
+        cost = np.zeros((1, 3))
+        ctx.run(Xd, perm.view(1, -1), 1, Ycold, cost_out=cost)
+        torch.cuda.synchronize()
+    assert not used and kw > kc, (used, kw, kc)
+    assert abs(cost[0, 0] - kc) <= 1e-4 * kc
+    # the iteration kernel's shared-memory atomics sum in a run-dependent
+    # order (~1e-7 relative per step), which 30 iterations amplify to ~1e-3
+    assert rel_max(Yw.cpu().numpy(), Ycold.cpu().numpy()) <= 2e-2
+
 
 def test_autotuned_split_gives_the_same_gradient(dev, tmp_path):
     """The weight-gradient GEMMs' split along K changes only the FP32

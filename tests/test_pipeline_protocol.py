@@ -15,17 +15,23 @@ sizing rule excludes must be caught by the model.
 The second half models the bounded waits running out.  Any wait that is not
 yet satisfied may run out at any moment, and another block's failure may
 freeze the block at any moment.  The kernel's rules: the first failed wait
-sets the block's freeze flag, after which every wait fails at once; a
-consumer whose wait failed skips its tile whole (no read, no release); the
-producer issues a copy only after a successful wait on the buffer's `empty`
-barrier; before exiting, the producer waits for the phase of the last copy it
-issued into each buffer.  The model checks that no copy is ever issued into a
+sets the block's freeze flag, after which every wait that is not yet
+satisfied fails at once; a consumer whose wait failed skips that tile and
+every later one (no read, no release); the producer issues a copy only after
+a successful wait on the buffer's `empty` barrier; before exiting, the
+producer waits for the phase of the last copy it issued into each buffer.  The model checks that no copy is ever issued into a
 buffer that still has one in flight or whose content was not released, that
 every read sees the tile it expects with no copy in flight into it, that the
-block exits with no copy in flight, and that the run always ends.  The rules
-the kernel had before (a failed consumer wait still released the buffer, a
-failed producer wait still issued the copy, the exit drain waited on stream
-positions) must be caught.
+block exits with no copy in flight, and that the run always ends.  A wait
+whose barrier is ready still succeeds after a freeze (the kernel reads the
+freeze flag only while a wait is not yet satisfied), which is safe because a
+ring buffer belongs to one consumer warp: a phase of it can be left
+incomplete only by that warp's own failure (after which it skips its tiles)
+or by a copy the producer skipped (after which the producer issues nothing
+more, so the warp's next wait simply fails).  Weaker rules must be caught:
+the earlier kernel's (a failed consumer wait still released the buffer, a
+failed producer wait still issued the copy, the exit drain followed stream
+positions), and a consumer or a producer that forgets its own failure.
 """
 import random
 
@@ -139,8 +145,17 @@ def test_producer_batch_larger_than_ring_is_caught():
 
 # ---------------------------------------------------------------- waits that run out
 
-def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=0.002, old_rules=False):
-    """One block, one warp per slot.  Returns "ok", or the first violation."""
+def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=0.002, rules="kernel"):
+    """One block, one consumer warp per slot.  rules: "kernel" (the kernel's:
+    a wait whose barrier is ready succeeds; a wait that is not ready fails at
+    once when the block is frozen, else may run out; a consumer that failed a
+    wait skips every later tile; the producer issues only after a successful
+    wait, and after a batch with a failed wait it issues nothing more),
+    "no_consumer_memory" (a consumer goes on waiting normally after its own
+    failure), "no_producer_memory" (the producer goes on issuing after its own
+    failure), "old" (a failed consumer wait still released its buffer, a
+    failed producer wait still issued, the exit drain followed stream
+    positions).  Returns "ok", or the first violation."""
     rng = random.Random(seed)
     full = [MBarrier(1) for _ in range(ring)]
     empty = [MBarrier(1) for _ in range(ring)]
@@ -148,20 +163,28 @@ def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=
     released = [True] * ring      # the buffer's last copy was read and released (or none yet)
     inflight = {}                 # buffer -> tile of the copy in flight
     issued_ph = {}                # buffer -> full-barrier parity of the last copy issued
-    fail = False
+    fail = False                  # the block's freeze flag
+    failed = [False] * slots      # consumer warp's own failure (kept in a register)
+    prod_failed = False           # the producer warp's own failure (noted after each batch)
+    prod_failed_now = False
+    batch_base, fail_base, fail_issued, batch_issued = 0, None, set(), set()
+    old = rules == "old"
     pending, next_batch = [], 0
     next_tile = list(range(slots))   # consumer warp w: its next tile
     for _ in range(10 ** 6):
         if not pending and next_batch < ntiles:
+            prod_failed = prod_failed or prod_failed_now
             pending = list(range(next_batch, min(ntiles, next_batch + batch)))
+            batch_base = next_batch
+            batch_issued = set()
             next_batch += batch
+            if prod_failed and rules != "old" and rules != "no_producer_memory":
+                pending = []              # after its own failure the producer issues nothing more
+                continue
         moves = []
         for q in pending:
             b, ph = q % ring, (q // ring) & 1
-            ready = empty[b].try_wait(ph ^ 1)
-            if fail and not old_rules:
-                moves.append(("skip_issue", q))
-            elif ready:
+            if empty[b].try_wait(ph ^ 1):
                 moves.append(("issue", q))
             elif fail or rng.random() < p_out:
                 moves.append(("issue_out", q))
@@ -172,7 +195,7 @@ def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=
             if q >= ntiles:
                 continue
             b, ph = q % ring, (q // ring) & 1
-            if fail and not old_rules:
+            if failed[w] and rules == "kernel":
                 moves.append(("skip_read", w))
             elif full[b].try_wait(ph):
                 moves.append(("read", w))
@@ -192,20 +215,25 @@ def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=
             b, ph = q % ring, (q // ring) & 1
             if kind == "issue_out":
                 fail = True
-            if kind == "issue_out" and not old_rules:
-                pending.remove(q)           # skipped: no copy
-                continue
+                if not prod_failed_now:
+                    fail_base = batch_base
+                    fail_issued = set(batch_issued)   # lanes of this batch that issued before the failure
+                prod_failed_now = True
+                if not old:
+                    pending.remove(q)       # skipped: no copy
+                    continue
             if b in inflight:
                 return "copy issued into a buffer with a copy in flight"
             if not released[b]:
                 return "copy issued into a buffer that was not released"
             pending.remove(q)
+            batch_issued.add(q)
+            if fail_base is not None and q >= fail_base:
+                fail_issued.add(q)
             full[b].arrive_expect_tx(1)
             inflight[b] = q
             released[b] = False
             issued_ph[b] = ph
-        elif kind == "skip_issue":
-            pending.remove(arg)
         elif kind == "land":
             b = rng.choice(sorted(inflight))
             content[b] = inflight.pop(b)
@@ -219,7 +247,8 @@ def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=
                 continue
             if kind == "read_out":
                 fail = True
-                if old_rules:             # the earlier kernel still read the header and released
+                failed[w] = True
+                if old:                   # the earlier kernel still read the header and released
                     if b in inflight:
                         return "read of a buffer with a copy in flight"
                     released[b] = True
@@ -230,7 +259,7 @@ def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=
             released[b] = True
             empty[b].arrive()
     # exit drain
-    if old_rules:
+    if old:
         # the earlier drain: the phases of the last `ring` stream positions
         for q in range(max(0, ntiles - ring), ntiles):
             b, ph = q % ring, (q // ring) & 1
@@ -238,6 +267,19 @@ def replay_with_timeouts(slots, ring, ntiles, seed, batch, p_out=0.02, p_freeze=
                 content[b] = inflight.pop(b)
                 full[b].complete_tx(1)
         return "ok" if not inflight else "exit with a copy in flight"
+    # the kernel keeps no per-buffer record: it rebuilds the last copy issued
+    # into each buffer from where its stream stopped and the lanes of its
+    # failed batch that did issue
+    end = ntiles if fail_base is None else fail_base
+    rebuilt = {}
+    for b in range(ring):
+        cands = [g for g in fail_issued if g % ring == b]
+        if end > b:
+            cands.append(end - 1 - ((end - 1 - b) % ring))
+        if cands:
+            rebuilt[b] = (max(cands) // ring) & 1
+    if rebuilt != issued_ph:
+        return "rebuilt drain differs from the copies issued"
     for b, ph in issued_ph.items():
         while not full[b].try_wait(ph):
             if not inflight:
@@ -265,6 +307,7 @@ def test_no_timeouts_consumes_every_tile():
         assert replay_with_timeouts(12, 24, 200, seed, 8, p_out=0.0, p_freeze=0.0) == "ok"
 
 
-def test_the_earlier_timeout_rules_are_caught():
-    bad = {replay_with_timeouts(12, 24, 150, seed, 8, p_out=0.05, old_rules=True) for seed in range(40)}
+@pytest.mark.parametrize("rules", ["old", "no_consumer_memory", "no_producer_memory"])
+def test_weaker_timeout_rules_are_caught(rules):
+    bad = {replay_with_timeouts(12, 24, 150, seed, 8, p_out=0.05, rules=rules) for seed in range(60)}
     assert bad - {"ok"}, bad
