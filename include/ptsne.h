@@ -129,6 +129,9 @@ typedef struct {
     double stage_ms[PTSNE_N_STAGES];     /* profiling on: device time per stage of ptsne_run */
     int64_t stage_calls[PTSNE_N_STAGES]; /* profiling on: epochs accumulated into stage_ms */
     int64_t bisect_evals;         /* entropy evaluations (FP32 and FP64) of the last search, all rows */
+    int64_t ptiles_total;         /* batched schedule: stored 32 x 32 tiles of the joint P */
+    int64_t ptiles_nonzero;       /* of those, tiles with a nonzero entry in the last affinities
+                                     (the iteration kernel streams P only for these) */
 } ptsne_stats;
 
 /* Turn on (1) or off (0) per-stage timing of ptsne_run: CUDA events are
@@ -145,8 +148,9 @@ int ptsne_reset_counters(ptsne_ctx* ctx);
  * distributed shared memory (1, 2 or 4); group: consumer warps per P tile,
  * 1 (each consumer warp evaluates whole tiles; other values are rejected);
  * consumer_warps: per block, 1 .. 20 (16 or fewer run a build of the kernel
- * with more registers per thread).  Defaults {2, 1, 20}; ptsne_autotune picks
- * by timing. */
+ * with more registers per thread; 2-D maps use at most 15, the four rows per
+ * lane of their evaluation need 128 registers).  Defaults {2, 1, 20};
+ * ptsne_autotune picks by timing. */
 typedef struct {
     int32_t cluster;
     int32_t group;
@@ -154,6 +158,20 @@ typedef struct {
 } ptsne_tuning;
 
 int ptsne_set_tuning(ptsne_ctx* ctx, const ptsne_tuning* tuning);
+
+/* Locality order of the rows within each chunk (batched schedule; off by
+ * default).  The order of a chunk's rows changes none of the method's
+ * results (Eq. 1-6 are equivariant under it; only the FP32 summation order
+ * moves).  With it on, every affinities computation first places each row
+ * of a chunk next to the rows nearest it (the rows are sorted by their
+ * nearest of the chunk's first 64 rows, a random sample), so that the joint
+ * P concentrates on few 32 x 32 tiles and many tiles are exactly zero (the
+ * FP32 exponentials of far pairs underflow; ptsne_get_stats counts the
+ * nonzero ones).  Exported P and every per-point output stay in the caller's
+ * order; ptsne_step and ptsne_cost use the order of the kept affinities.
+ * ptsne_affinities_from_distances never reorders.  PTSNE_EINVAL on the
+ * per-chunk schedule. */
+int ptsne_set_locality_order(ptsne_ctx* ctx, int on);
 int ptsne_get_tuning(const ptsne_ctx* ctx, ptsne_tuning* tuning);
 
 typedef struct {

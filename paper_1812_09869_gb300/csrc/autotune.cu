@@ -135,10 +135,15 @@ extern "C" int ptsne_autotune(ptsne_ctx* c, const float* X, const int32_t* perm,
     IterTune best = keep;
     double best_ms = 1e300;
     int nt = 0;
-    const int clusters[] = {1, 2, 4}, groups[] = {1}, warps[] = {12, 16, 19, 20};
+    // consumer warps per block: the 2-D evaluation runs with at most 15
+    const int clusters[] = {1, 2, 4}, groups[] = {1};
+    const int warps2[] = {8, 12, 15}, warps3[] = {12, 16, 19, 20};
+    const bool two_d = c->p.out_dim == 2;
+    const int nwarps = two_d ? 3 : 4;
     for (int cl : clusters)
         for (int g : groups)
-            for (int w : warps) {
+            for (int wi = 0; wi < nwarps; ++wi) {
+                const int w = two_d ? warps2[wi] : warps3[wi];
                 c->tune = IterTune{cl, g, w};
                 double ms = 1e300;
                 for (int rep = 0; rep < 2; ++rep) {

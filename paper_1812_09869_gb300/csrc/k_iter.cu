@@ -123,6 +123,11 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// Bring `bytes` at src into L2 ahead of their copy to shared memory (no
+// completion to wait for; a hint the hardware may drop).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ uint32_t cl_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -195,7 +200,15 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
 }
 
 // ---------------------------------------------------------------- tile evaluation
-// The shared map is structure-of-arrays: coordinate k of row i at map[k * zcap + i].
+// The shared map of a 2-D chunk is stored as column pairs, float4 k = (x_2k,
+// x_2k+1, y_2k, y_2k+1), so that a lane reads the two columns of a step with
+// one 16-byte load; a 3-D map is structure-of-arrays (coordinate k of row i
+// at map[k * zcap + i]).
+template <int OD>
+__device__ __forceinline__ int map_idx(int zcap, int i, int k) {
+    if constexpr (OD == 2) return ((i >> 1) << 2) | (k << 1) | (i & 1);
+    else return k * zcap + i;
+}
 //
 // One consumer warp evaluates a whole 32 x 32 tile (rows of block a, columns
 // of block b).  Lane L = 16 h + g owns rows 2g and 2g + 1 of a and the ring h
@@ -245,53 +258,64 @@ __device__ __forceinline__ float keep_row(float mine0, float mine1, int h) {
 }
 
 // Gradient sums of one tile, 2-D maps (packed f32x2 over the two columns of a
-// double step).  Adds A and R into acc, returns the lane's sum of w (both
-// orders of each pair of an off-diagonal tile).
+// step).  Lane L = 8 q + g holds rows 4g .. 4g+3 of block a (the map's column
+// pairs 2g and 2g + 1) and meets the 8 columns of ring q of block b as the
+// natural column pairs (g / 2 + s) & 3, s = 0..3, each read as one float4
+// (x, x', y, y').  Off-diagonal tile: the column packet of a step (the sums of
+// its two columns over the lane's four rows) moves two lanes down the ring
+// after each step (lane g receives from lane g + 2), so it meets the four
+// lanes of one parity; lanes g and g ^ 1 end with the two partial packets of
+// pair (g / 2 - 1) & 3 and each keeps one column.  The row sums of the four
+// rings are reduced over lanes g, g + 8, g + 16, g + 24, each keeping one row.
+// Adds A and R into acc, returns the lane's sum of w (both orders of each pair
+// of an off-diagonal tile).
 template <bool SYM>
 __device__ __forceinline__ float tile_grad_2d(const float* map, int zcap, int a, int b, int lane,
                                               const float4 (&pv)[8], float* acc) {
-    const float* xs = map;
-    const float* ys = map + zcap;
-    const int g = lane & 15, h = lane >> 4;
-    const int ra = a * kPT + 2 * g, cb = b * kPT + 16 * h;
-    const float2 ox = *reinterpret_cast<const float2*>(xs + ra);
-    const float2 oy = *reinterpret_cast<const float2*>(ys + ra);
-    const f2 OX0 = pk(ox.x, ox.x), OX1 = pk(ox.y, ox.y), OY0 = pk(oy.x, oy.x), OY1 = pk(oy.y, oy.y);
+    const float4* mp = reinterpret_cast<const float4*>(map);
+    const int g = lane & 7, q = lane >> 3, u = g >> 1;
+    const float4 o0 = mp[a * 16 + 2 * g], o1 = mp[a * 16 + 2 * g + 1];
+    const f2 OX[4] = {pk(o0.x, o0.x), pk(o0.y, o0.y), pk(o1.x, o1.x), pk(o1.y, o1.y)};
+    const f2 OY[4] = {pk(o0.z, o0.z), pk(o0.w, o0.w), pk(o1.z, o1.z), pk(o1.w, o1.w)};
     const f2 ONE = pk(1.f, 1.f);
-    f2 AX0 = 0, AY0 = 0, RX0 = 0, RY0 = 0, AX1 = 0, AY1 = 0, RX1 = 0, RY1 = 0, Z = 0;
+    f2 AX[4] = {0, 0, 0, 0}, AY[4] = {0, 0, 0, 0}, RX[4] = {0, 0, 0, 0}, RY[4] = {0, 0, 0, 0}, Z = 0;
     f2 CAX = 0, CAY = 0, CRX = 0, CRY = 0;   // column packet (SYM)
-    const int nxt = (lane & 16) | ((g + 2) & 15);
+    const int nxt = (lane & 24) | ((g + 2) & 7);
+    const float4* cbase = mp + b * 16 + 4 * q;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const int c0 = cb + ((g + 2 * s) & 15), c1 = cb + ((g + 2 * s + 1) & 15);
-        const f2 XC = pk(xs[c0], xs[c1]), YC = pk(ys[c0], ys[c1]);
-        const f2 P0 = pk(pv[s].x, pv[s].y), P1 = pk(pv[s].z, pv[s].w);
-        const f2 DX0 = sub2(OX0, XC), DY0 = sub2(OY0, YC);   // own - other
-        const f2 DX1 = sub2(OX1, XC), DY1 = sub2(OY1, YC);
-        f2 Q0 = fma2(DX0, DX0, ONE);
-        Q0 = fma2(DY0, DY0, Q0);
-        f2 Q1 = fma2(DX1, DX1, ONE);
-        Q1 = fma2(DY1, DY1, Q1);
-        float q0, q1, q2, q3;
-        upk(Q0, q0, q1);
-        upk(Q1, q2, q3);
-        const f2 W0 = pk(hw_rcp(q0), hw_rcp(q1)), W1 = pk(hw_rcp(q2), hw_rcp(q3));
-        Z = add2(Z, add2(W0, W1));
-        const f2 PW0 = mul2(P0, W0), WW0 = mul2(W0, W0), PW1 = mul2(P1, W1), WW1 = mul2(W1, W1);
-        AX0 = fma2(PW0, DX0, AX0);
-        AY0 = fma2(PW0, DY0, AY0);
-        RX0 = fma2(WW0, DX0, RX0);
-        RY0 = fma2(WW0, DY0, RY0);
-        AX1 = fma2(PW1, DX1, AX1);
-        AY1 = fma2(PW1, DY1, AY1);
-        RX1 = fma2(WW1, DX1, RX1);
-        RY1 = fma2(WW1, DY1, RY1);
+    for (int s = 0; s < 4; ++s) {
+        const float4 cv = cbase[(u + s) & 3];
+        const f2 XC = pk(cv.x, cv.y), YC = pk(cv.z, cv.w);
+        const f2 P[4] = {pk(pv[2 * s].x, pv[2 * s].y), pk(pv[2 * s].z, pv[2 * s].w),
+                         pk(pv[2 * s + 1].x, pv[2 * s + 1].y), pk(pv[2 * s + 1].z, pv[2 * s + 1].w)};
+        f2 DX[4], DY[4], W[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            DX[r] = sub2(OX[r], XC);   // own - other
+            DY[r] = sub2(OY[r], YC);
+            f2 Q = fma2(DX[r], DX[r], ONE);
+            Q = fma2(DY[r], DY[r], Q);
+            float q0, q1;
+            upk(Q, q0, q1);
+            W[r] = pk(hw_rcp(q0), hw_rcp(q1));
+        }
+        Z = add2(Z, add2(add2(W[0], W[1]), add2(W[2], W[3])));
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const f2 PW = mul2(P[r], W[r]), WW = mul2(W[r], W[r]);
+            AX[r] = fma2(PW, DX[r], AX[r]);
+            AY[r] = fma2(PW, DY[r], AY[r]);
+            RX[r] = fma2(WW, DX[r], RX[r]);
+            RY[r] = fma2(WW, DY[r], RY[r]);
+            if constexpr (SYM) {
+                CAX = fma2(PW, DX[r], CAX);
+                CAY = fma2(PW, DY[r], CAY);
+                CRX = fma2(WW, DX[r], CRX);
+                CRY = fma2(WW, DY[r], CRY);
+            }
+        }
         if constexpr (SYM) {
-            CAX = fma2(PW1, DX1, fma2(PW0, DX0, CAX));
-            CAY = fma2(PW1, DY1, fma2(PW0, DY0, CAY));
-            CRX = fma2(WW1, DX1, fma2(WW0, DX0, CRX));
-            CRY = fma2(WW1, DY1, fma2(WW0, DY0, CRY));
-            if (s < 7) {
+            if (s < 3) {
                 CAX = shfl_f2(CAX, nxt);
                 CAY = shfl_f2(CAY, nxt);
                 CRX = shfl_f2(CRX, nxt);
@@ -299,23 +323,44 @@ __device__ __forceinline__ float tile_grad_2d(const float* map, int zcap, int a,
             }
         }
     }
-    const int row = ra + h;
-    atomicAdd(acc + row, keep_row(hsum2(AX0), hsum2(AX1), h));
-    atomicAdd(acc + zcap + row, keep_row(hsum2(AY0), hsum2(AY1), h));
-    atomicAdd(acc + 2 * zcap + row, keep_row(hsum2(RX0), hsum2(RX1), h));
-    atomicAdd(acc + 3 * zcap + row, keep_row(hsum2(RY0), hsum2(RY1), h));
+    // rows: ring q keeps row 4g + 2 (q >> 1) + (q & 1) of the four rings' sums
+    float v[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        v[r][0] = hsum2(AX[r]);
+        v[r][1] = hsum2(AY[r]);
+        v[r][2] = hsum2(RX[r]);
+        v[r][3] = hsum2(RY[r]);
+    }
+    const bool hi = q >= 2, odd = q & 1;
+    float w2[2][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float keep = hi ? v[2 + h][k] : v[h][k];
+            const float give = hi ? v[h][k] : v[2 + h][k];
+            w2[h][k] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+        }
+    const int row = a * kPT + 4 * g + (hi ? 2 : 0) + (odd ? 1 : 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float keep = odd ? w2[1][k] : w2[0][k];
+        const float give = odd ? w2[0][k] : w2[1][k];
+        atomicAdd(acc + k * zcap + row, keep + __shfl_xor_sync(0xffffffffu, give, 8));
+    }
     if constexpr (SYM) {
-        const int prv = (lane & 16) | ((g + 15) & 15);
-        const int col = cb + ((g + 14) & 15);
-        float lo, hi;
-        upk(CAX, lo, hi);
-        atomicAdd(acc + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
-        upk(CAY, lo, hi);
-        atomicAdd(acc + zcap + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
-        upk(CRX, lo, hi);
-        atomicAdd(acc + 2 * zcap + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
-        upk(CRY, lo, hi);
-        atomicAdd(acc + 3 * zcap + col, -(lo + __shfl_sync(0xffffffffu, hi, prv)));
+        const int oddg = g & 1;
+        const int col = b * kPT + 8 * q + 2 * ((u + 3) & 3) + oddg;
+        float lo, hv;
+        upk(CAX, lo, hv);
+        atomicAdd(acc + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
+        upk(CAY, lo, hv);
+        atomicAdd(acc + zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
+        upk(CRX, lo, hv);
+        atomicAdd(acc + 2 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
+        upk(CRY, lo, hv);
+        atomicAdd(acc + 3 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
         return 2.0f * hsum2(Z);
     }
     return hsum2(Z);
@@ -404,6 +449,42 @@ __device__ __forceinline__ float tile_grad_3d(const float* map, int zcap, int a,
 
 // Cost sums of a lane's 32 pairs: sum p ln p, sum p ln w, sum p, sum w (Eq. 5,
 // Eq. 9), doubled for an off-diagonal tile (each pair stands for both orders).
+// 2-D maps: the ring-8 lane layout of tile_grad_2d.
+template <bool SYM>
+__device__ __forceinline__ void tile_cost_2d(const float* map, int a, int b, int lane, const float4 (&pv)[8],
+                                             float (&c)[4]) {
+    const float4* mp = reinterpret_cast<const float4*>(map);
+    const int g = lane & 7, q = lane >> 3, u = g >> 1;
+    const float4 o0 = mp[a * 16 + 2 * g], o1 = mp[a * 16 + 2 * g + 1];
+    const float ox[4] = {o0.x, o0.y, o1.x, o1.y}, oy[4] = {o0.z, o0.w, o1.z, o1.w};
+    const float* pf = reinterpret_cast<const float*>(pv);
+    c[0] = c[1] = c[2] = c[3] = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float4 cv = mp[b * 16 + 4 * q + ((u + s) & 3)];
+        const float cx[2] = {cv.x, cv.y}, cy[2] = {cv.z, cv.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float dx = ox[r] - cx[e], dy = oy[r] - cy[e];
+                const float qv = fmaf(dy, dy, fmaf(dx, dx, 1.0f));
+                c[3] += hw_rcp(qv);
+                const float p = pf[4 * (2 * s + (r >> 1)) + ((r & 1) << 1) + e];
+                if (p >= FLT_MIN) {
+                    c[0] += p * (hw_lg2(p) * kLn2f);
+                    c[1] -= p * (hw_lg2(qv) * kLn2f);
+                    c[2] += p;
+                }
+            }
+    }
+    if constexpr (SYM) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] *= 2.0f;
+    }
+}
+
+// 3-D maps: the ring-16 lane layout of tile_grad_3d.
 template <int OD, bool SYM>
 __device__ __forceinline__ void tile_cost(const float* map, int zcap, int a, int b, int lane, const float4 (&pv)[8],
                                           float (&c)[4]) {
@@ -486,8 +567,11 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
                                              const float* map, int zcap, float* acc, int lane, KSum (&part)[4]) {
     // w of the pair (i, i), which a diagonal tile's row-wise pass counts in
     // its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own columns)
+    // (ring-8 layout: lanes with q == g / 2 meet their own four rows;
+    // ring-16: lanes with h == g / 8 meet their own two rows)
     const float w_ii = hw_rcp(1.0f);
-    const bool diag_lane = (lane >> 4) == ((lane & 15) >> 3);
+    const bool diag_lane = OD == 2 ? (lane >> 3) == ((lane & 7) >> 1) : (lane >> 4) == ((lane & 15) >> 3);
+    constexpr float kDiagPairs = OD == 2 ? 4.0f : 2.0f;
     for (; cur.q < qend; cur.advance_ring(nslots, ring_n)) {
         // The ring holds a whole number of consumer slots, so tile q - ring
         // (this buffer's previous use) belonged to this same slot and was
@@ -512,7 +596,7 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
         __syncwarp();
         if (lane == 0) mbar_arrive(empty_a + 8 * cur.buf);   // the buffer is free again
         const bool diag = a == b;
-        const float drop = diag && diag_lane ? 2.0f * w_ii : 0.0f;
+        const float drop = diag && diag_lane ? kDiagPairs * w_ii : 0.0f;
         if constexpr (!COST) {
             float zl;
             if constexpr (OD == 2) zl = diag ? tile_grad_2d<false>(map, zcap, a, b, lane, pv, acc)
@@ -522,8 +606,13 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
             part[0].add(zl - drop);
         } else {
             float cs[4];
-            if (diag) tile_cost<OD, false>(map, zcap, a, b, lane, pv, cs);
-            else tile_cost<OD, true>(map, zcap, a, b, lane, pv, cs);
+            if constexpr (OD == 2) {
+                if (diag) tile_cost_2d<false>(map, a, b, lane, pv, cs);
+                else tile_cost_2d<true>(map, a, b, lane, pv, cs);
+            } else {
+                if (diag) tile_cost<OD, false>(map, zcap, a, b, lane, pv, cs);
+                else tile_cost<OD, true>(map, zcap, a, b, lane, pv, cs);
+            }
             part[0].add(cs[3] - drop);
             part[1].add(cs[0]);
             part[2].add(cs[1]);
@@ -532,10 +621,10 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
     }
 }
 
-// Compiled for at most MAXT threads: 672 (20 consumer warps + the producer,
-// 80 registers per thread), 640 (19 + 1, 96 registers, 2-D maps), 544 (16 + 1,
-// 96 registers) or 416 (12 + 1, 128 registers, 2-D maps).  Registers are
-// granted per 4 warps, so 21 warps get 80 and 20 warps 96.
+// Compiled for at most MAXT threads.  2-D maps: 512 (15 consumer warps + the
+// producer) or 416 (12 + 1), both 128 registers per thread.  3-D maps: 672
+// (20 + 1, 80 registers) or 544 (16 + 1, 96 registers).  Registers are granted
+// per 4 warps, so 21 warps get 80, 17 to 20 warps 96 and 16 or fewer 128.
 template <int OD, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -604,7 +693,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
 
         for (int i = tid; i < zr; i += nthreads) {
 #pragma unroll
-            for (int k = 0; k < OD; ++k) map[k * zcap + i] = i < z ? A.Yc[(off + i) * OD + k] : kPad * (float)(i - z + 1);
+            for (int k = 0; k < OD; ++k) map[map_idx<OD>(zcap, i, k)] = i < z ? A.Yc[(off + i) * OD + k] : kPad * (float)(i - z + 1);
         }
         for (int i = tid; i < 2 * OD * zcap; i += nthreads) acc[i] = 0.f;
         __syncthreads();
@@ -617,8 +706,8 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 for (int i = tid; i < z; i += nthreads)
 #pragma unroll
                     for (int k = 0; k < OD; ++k) {
-                        mn = fminf(mn, map[k * zcap + i]);
-                        mx = fmaxf(mx, map[k * zcap + i]);
+                        mn = fminf(mn, map[map_idx<OD>(zcap, i, k)]);
+                        mx = fmaxf(mx, map[map_idx<OD>(zcap, i, k)]);
                     }
                 mn = warp_min(mn);
                 mx = warp_max(mx);
@@ -658,6 +747,12 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                             mbar_expect_tx(full_a + 8 * buf, kTileBytes);
                             bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
                             issued = true;
+                            // the tile this buffer takes next (a ring later; past the
+                            // end of the pass, the next pass's tile) is read into L2
+                            // now, so that its copy, issued once this one is consumed,
+                            // is served from L2 rather than from HBM
+                            const int sn = (s + A.ring) % S.nq;
+                            bulk_prefetch_l2(P2c + ((int64_t)rank + (int64_t)K * sn) * kPTileStride, kTileBytes);
                         } else {
                             atomicAdd(A.timeouts, 1u);
                         }
@@ -709,7 +804,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 for (int i = ulo + tid; i < uhi; i += nthreads) {
                     float Av[OD], Rv[OD], y[OD];
 #pragma unroll
-                    for (int k = 0; k < OD; ++k) { Av[k] = 0.f; Rv[k] = 0.f; y[k] = map[k * zcap + i]; }
+                    for (int k = 0; k < OD; ++k) { Av[k] = 0.f; Rv[k] = 0.f; y[k] = map[map_idx<OD>(zcap, i, k)]; }
                     for (uint32_t rr = 0; rr < K; ++rr) {
 #pragma unroll
                         for (int k = 0; k < OD; ++k) {
@@ -728,8 +823,8 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                     for (uint32_t rr = 0; rr < K; ++rr)
 #pragma unroll
                         for (int k = 0; k < OD; ++k) {
-                            if (K > 1) st_cl_f32(map_rank(smem_u32(map + k * zcap + i), rr), y[k]);
-                            else map[k * zcap + i] = y[k];
+                            if (K > 1) st_cl_f32(map_rank(smem_u32(map + map_idx<OD>(zcap, i, k)), rr), y[k]);
+                            else map[map_idx<OD>(zcap, i, k)] = y[k];
                         }
                 }
             }
@@ -741,7 +836,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         }
         for (int i = ulo + tid; i < uhi; i += nthreads)
 #pragma unroll
-            for (int k = 0; k < OD; ++k) A.Yc[(off + i) * OD + k] = map[k * zcap + i];
+            for (int k = 0; k < OD; ++k) A.Yc[(off + i) * OD + k] = map[map_idx<OD>(zcap, i, k)];
         __syncthreads();
     }
     // Normally every issued copy has been waited for by a consumer.  After a
@@ -806,6 +901,9 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     const int K = c->tune.cluster;
     if (c->tune.group != 1) return cudaErrorInvalidValue;
     int Wc = c->tune.consumer_warps;
+    // the 2-D evaluation (four rows per lane) needs 128 registers per thread,
+    // which a block of at most 16 warps gets: at most 15 consumer warps
+    if (c->p.out_dim == 2 && Wc > 15) Wc = 15;
     int ring = iterate_ring(c->p.out_dim, c->zmax, Wc);
     while (ring == 0 && Wc > 1) {   // very large chunks: fewer consumer warps
         --Wc;
@@ -835,11 +933,7 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
 
     // the build for the fewest threads that hold the block: more registers per thread
     void (*kern)(IterArgs);
-    if (c->p.out_dim == 2)
-        kern = Wc > 19   ? iterate_kernel<2, 672>
-               : Wc > 16 ? iterate_kernel<2, 640>
-               : Wc > 12 ? iterate_kernel<2, 544>
-                         : iterate_kernel<2, 416>;
+    if (c->p.out_dim == 2) kern = Wc > 12 ? iterate_kernel<2, 512> : iterate_kernel<2, 416>;
     else kern = Wc > 16 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

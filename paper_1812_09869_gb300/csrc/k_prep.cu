@@ -2,6 +2,8 @@
 // defines the chunks and pools the partial solutions back).  The partition is
 // a permutation; chunk c is the contiguous run perm[off[c] .. off[c+1]) of it,
 // so gathering rows by perm lays every chunk out contiguously.
+#include <float.h>
+
 #include "ptsne_internal.cuh"
 
 namespace ptsne {
@@ -93,6 +95,204 @@ static int grid_for(int64_t work, int block) {
     if (g < 1) g = 1;
     if (g > 152 * 32) g = 152 * 32;
     return (int)g;
+}
+
+// ---- locality order within chunks -------------------------------------------
+// The order of a chunk's rows changes none of the method's results (P, the
+// gradient and the cost are equivariant under it; only FP32 summation order
+// moves).  Rows of nearby points placed next to each other concentrate the
+// joint P on few 32 x 32 tiles and leave the others exactly zero (the FP32
+// exponentials of far pairs underflow), which the iteration kernel then
+// streams no P for.  The chunk's first kLandmarks rows (a random sample, the
+// partition being random) serve as landmarks: each row's key is its nearest
+// landmark (squared distance, ties to the smaller index); landmarks closer
+// to each other than twice the median nearest-landmark distance are joined
+// into groups (single linkage), so that the rows of one cluster, spread over
+// several landmarks, stay together; the rows are then stably sorted by
+// (group, landmark).
+constexpr int kLandmarks = 64;
+constexpr int kLandK = 32;          // dimensions staged per pass
+
+// Block (row tile of 256, chunk): the chunk's landmarks are staged kLandK
+// dimensions at a time in shared memory; each thread keeps its row's
+// distances to all landmarks in registers.
+__global__ void __launch_bounds__(256)
+landmark_key_kernel(const float* __restrict__ Xg, Layout L, uint8_t* __restrict__ key) {
+    __shared__ float sl[kLandmarks][kLandK];
+    const int c = blockIdx.y;
+    const int64_t off = L.off[c];
+    const int z = (int)(L.off[c + 1] - off);
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (blockIdx.x * 256 >= z) return;   // block-uniform
+    const int nl = z < kLandmarks ? z : kLandmarks;
+    const bool valid = i < z;
+    const float* xr = Xg + (off + (valid ? i : 0)) * L.dp;
+    float acc[kLandmarks];
+#pragma unroll
+    for (int l = 0; l < kLandmarks; ++l) acc[l] = 0.f;
+    for (int k0 = 0; k0 < L.dp; k0 += kLandK) {
+        const int kc = min(kLandK, L.dp - k0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kLandmarks * kLandK; e += 256) {
+            const int l = e / kLandK, k = e % kLandK;
+            sl[l][k] = (l < nl && k < kc) ? Xg[(off + l) * L.dp + k0 + k] : 0.f;
+        }
+        float xv[kLandK];
+#pragma unroll
+        for (int k = 0; k < kLandK; ++k) xv[k] = k < kc ? xr[k0 + k] : 0.f;
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < kLandmarks; ++l) {
+            float d = 0.f;
+#pragma unroll
+            for (int k = 0; k < kLandK; ++k) {
+                const float t = xv[k] - sl[l][k];
+                d = fmaf(t, t, d);
+            }
+            acc[l] += d;
+        }
+    }
+    if (!valid) return;
+    float bd = FLT_MAX;
+    int bl = 0;
+#pragma unroll
+    for (int l = 0; l < kLandmarks; ++l)
+        if (l < nl && acc[l] < bd) { bd = acc[l]; bl = l; }
+    key[off + i] = (uint8_t)bl;
+}
+
+// One block of kLandmarks threads per chunk.  Thread l holds landmark l's
+// squared distances to the others (staged like the rows above), links it to
+// the landmarks within four times the median nearest-landmark distance
+// (squared), and the groups are the connected components; landmarks are
+// ranked by (smallest landmark of their group, index).  Then a stable
+// counting sort of the rows by the rank of their key: thread k writes the
+// rows of rank k in their original order.  perm_out[off + p] is the entry of
+// perm_in that lands at position p; src_row[off + p] = off + (its position
+// in perm_in), for mapping exported matrices back to the caller's order.
+__global__ void __launch_bounds__(kLandmarks)
+chunk_order_kernel(const float* __restrict__ Xg, const uint8_t* __restrict__ key, const int32_t* __restrict__ perm_in,
+                   Layout L, int32_t* __restrict__ perm_out, int32_t* __restrict__ src_row) {
+    __shared__ uint8_t sk[kMaxChunk];
+    __shared__ float sl[kLandmarks][kLandK + 1];
+    __shared__ float snn[kLandmarks];
+    __shared__ unsigned long long sadj[kLandmarks];
+    __shared__ int sgroup[kLandmarks], srank[kLandmarks];
+    __shared__ int start[kLandmarks + 1];
+    const int c = blockIdx.x, t = threadIdx.x;
+    const int64_t off = L.off[c];
+    const int z = (int)(L.off[c + 1] - off);
+    const int nl = z < kLandmarks ? z : kLandmarks;
+    // landmark distances
+    float dl[kLandmarks];
+#pragma unroll
+    for (int m = 0; m < kLandmarks; ++m) dl[m] = 0.f;
+    for (int k0 = 0; k0 < L.dp; k0 += kLandK) {
+        const int kc = min(kLandK, L.dp - k0);
+        __syncthreads();
+        for (int e = t; e < kLandmarks * kLandK; e += kLandmarks) {
+            const int l = e / kLandK, k = e % kLandK;
+            sl[l][k] = (l < nl && k < kc) ? Xg[(off + l) * L.dp + k0 + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int m = 0; m < kLandmarks; ++m) {
+            float d = 0.f;
+            for (int k = 0; k < kLandK; ++k) {
+                const float v = sl[t][k] - sl[m][k];
+                d = fmaf(v, v, d);
+            }
+            dl[m] += d;
+        }
+    }
+    float nn = FLT_MAX;
+#pragma unroll
+    for (int m = 0; m < kLandmarks; ++m)
+        if (m != t && m < nl && dl[m] < nn) nn = dl[m];
+    snn[t] = t < nl ? nn : FLT_MAX;
+    __syncthreads();
+    // median of the nearest-landmark distances (rank counting; ties by index)
+    int below = 0;
+    for (int m = 0; m < nl; ++m) below += (snn[m] < snn[t] || (snn[m] == snn[t] && m < t)) ? 1 : 0;
+    __shared__ float smed;
+    if (t < nl && below == (nl - 1) / 2) smed = snn[t];
+    __syncthreads();
+    const float thr = 4.0f * smed;
+    unsigned long long adj = 0ull;
+#pragma unroll
+    for (int m = 0; m < kLandmarks; ++m)
+        if (t < nl && m < nl && dl[m] <= thr) adj |= 1ull << m;
+    sadj[t] = adj;
+    __syncthreads();
+    if (t == 0) {   // connected components of the linkage graph, labelled by their smallest landmark
+        unsigned long long left = nl == 64 ? ~0ull : ((1ull << nl) - 1ull);
+        while (left) {
+            const int root = __ffsll((long long)left) - 1;
+            unsigned long long comp = 1ull << root, frontier = comp;
+            while (frontier) {
+                unsigned long long next = 0ull;
+                unsigned long long f = frontier;
+                while (f) {
+                    const int v = __ffsll((long long)f) - 1;
+                    f &= f - 1;
+                    next |= sadj[v];
+                }
+                next &= ~comp;
+                comp |= next;
+                frontier = next;
+            }
+            unsigned long long cm = comp;
+            while (cm) {
+                const int v = __ffsll((long long)cm) - 1;
+                cm &= cm - 1;
+                sgroup[v] = root;
+            }
+            left &= ~comp;
+        }
+    }
+    __syncthreads();
+    if (t < nl) {
+        int r = 0;
+        for (int m = 0; m < nl; ++m) r += (sgroup[m] < sgroup[t] || (sgroup[m] == sgroup[t] && m < t)) ? 1 : 0;
+        srank[t] = r;
+    }
+    for (int i = t; i < z; i += kLandmarks) sk[i] = key[off + i];
+    __syncthreads();
+    for (int i = t; i < z; i += kLandmarks) sk[i] = (uint8_t)srank[sk[i]];
+    __syncthreads();
+    int cnt = 0;
+    for (int i = 0; i < z; ++i) cnt += sk[i] == t;
+    start[t + 1] = cnt;
+    __syncthreads();
+    if (t == 0) {
+        start[0] = 0;
+        for (int j = 1; j <= kLandmarks; ++j) start[j] += start[j - 1];
+    }
+    __syncthreads();
+    int p = start[t];
+    for (int i = 0; i < z; ++i) {
+        if (sk[i] == t) {
+            perm_out[off + p] = perm_in[off + i];
+            src_row[off + p] = (int32_t)(off + i);
+            ++p;
+        }
+    }
+}
+
+// The rows of every chunk of the partition perm in locality order: keys from
+// the X rows gathered in perm's order, then the sorted partition in
+// c->perm_loc (and c->src_row); X is gathered again in that order.
+cudaError_t launch_locality_order(ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s) {
+    cudaError_t e = launch_gather(c, X, perm, s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((c->zmax + 255) / 256), (unsigned)c->p.n_chunks);
+    landmark_key_kernel<<<grid, 256, 0, s>>>(c->Xg, make_layout(c), c->lkey);
+    chunk_order_kernel<<<(unsigned)c->p.n_chunks, kLandmarks, 0, s>>>(c->Xg, c->lkey, perm, make_layout(c),
+                                                                        c->perm_loc, c->src_row);
+    c->launches += 2;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_gather(c, X, c->perm_loc, s);
 }
 
 cudaError_t launch_gather(const ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s) {

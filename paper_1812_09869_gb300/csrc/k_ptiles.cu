@@ -13,7 +13,8 @@ namespace ptsne {
 __global__ void __launch_bounds__(256)
 psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
                    const TileDesc2* __restrict__ tiles, int64_t t0, const float* __restrict__ beta,
-                   const float* __restrict__ mrow, const float* __restrict__ Srow) {
+                   const float* __restrict__ mrow, const float* __restrict__ Srow, uint8_t* __restrict__ nz_out,
+                   unsigned long long* __restrict__ nz_count) {
     constexpr float kLog2e = 1.4426950408889634f;
     const TileDesc2 td = tiles[t0 + blockIdx.x];
     const int c = td.chunk;
@@ -74,28 +75,43 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
     // tile with coalesced 16-byte stores
     __shared__ __align__(16) float ot[kPTileFloats];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e)] = out[e];
-    __syncthreads();
-    float* dst = P2 + (ptile_off[c] + td.pos) * kPTileStride;
+    for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e, L.od)] = out[e];
+    // a tile whose every entry is exactly zero (far pairs: the FP32
+    // exponentials underflow) is flagged, and the iteration kernel skips its
+    // P (the attractive terms p w (y_i - y_j) vanish exactly)
+    const int nz = __syncthreads_or(out[0] != 0.f || out[1] != 0.f || out[2] != 0.f || out[3] != 0.f);
+    const int64_t gt = ptile_off[c] + td.pos;
+    float* dst = P2 + gt * kPTileStride;
     reinterpret_cast<float4*>(dst)[tid] = reinterpret_cast<const float4*>(ot)[tid];
-    if (tid == 0)   // trailer: the tile's row and column blocks
-        *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, 0, 0);
+    if (tid == 0) {   // trailer: the tile's row and column blocks and its flag
+        *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, nz, 0);
+        nz_out[gt] = (uint8_t)nz;
+        if (nz) atomicAdd(nz_count, 1ull);
+    }
 }
 
 // Packed tiles -> dense z x z per chunk (chunks concatenated), both halves.
+// src_row (optional): the rows are in locality order; row i of the chunk is
+// row src_row[off + i] - off of the caller's partition, where it goes.
 __global__ void __launch_bounds__(256)
 export_packed_kernel(const float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
-                     const TileDesc2* __restrict__ tiles, const int64_t* __restrict__ dense_off, float* __restrict__ out) {
+                     const TileDesc2* __restrict__ tiles, const int64_t* __restrict__ dense_off,
+                     const int32_t* __restrict__ src_row, float* __restrict__ out) {
     const TileDesc2 td = tiles[blockIdx.x];
     const int c = td.chunk;
-    const int z = (int)(L.off[c + 1] - L.off[c]);
+    const int64_t off = L.off[c];
+    const int z = (int)(L.off[c + 1] - off);
     const float* src = P2 + (ptile_off[c] + td.pos) * kPTileStride;
     float* dst = out + dense_off[c];
     for (int e = threadIdx.x; e < kPTileFloats; e += blockDim.x) {
         const int r = e >> 5, cc = e & 31;
-        const int i = td.a * kPT + r, j = td.b * kPT + cc;
+        int i = td.a * kPT + r, j = td.b * kPT + cc;
         if (i < z && j < z) {
-            const float v = src[packed_index(r, cc)];
+            const float v = src[packed_index(r, cc, L.od)];
+            if (src_row) {   // locality order: back to the caller's rows
+                i = (int)(src_row[off + i] - off);
+                j = (int)(src_row[off + j] - off);
+            }
             dst[(int64_t)i * z + j] = v;
             dst[(int64_t)j * z + i] = v;
         }
@@ -110,14 +126,16 @@ cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s) {
     for (int64_t b = 0; b < c->ntiles2; b += 2147483647LL, ++k) {
         const int64_t cnt = (c->ntiles2 - b) < 2147483647LL ? (c->ntiles2 - b) : 2147483647LL;
         psym_packed_kernel<<<(unsigned)cnt, 256, 0, s>>>(c->D, c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2, b,
-                                                         c->beta, c->mrow, c->Srow);
+                                                         c->beta, c->mrow, c->Srow, c->ptile_nz,
+                                                         &c->dstats->ptiles_nonzero);
     }
     return launched(c, k);
 }
 
 cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t s) {
     export_packed_kernel<<<(unsigned)c->ntiles2, 256, 0, s>>>(c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2,
-                                                              c->d_dense_off, P_out);
+                                                              c->d_dense_off, c->loc_active ? c->src_row : nullptr,
+                                                              P_out);
     return launched(c, 1);
 }
 

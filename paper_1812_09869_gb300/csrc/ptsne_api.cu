@@ -83,7 +83,8 @@ void free_all(ptsne_ctx* c) {
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
                     c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense,
-                    c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm, c->size_part, c->size_done, c->ycold};
+                    c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm, c->size_part, c->size_done, c->ycold,
+                    c->perm_loc, c->src_row, c->lkey, c->ptile_nz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -296,7 +297,11 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     }
     AL(c->D, m);
     if (p.schedule == PTSNE_SCHED_BATCHED) {
+        AL(c->perm_loc, n);
+        AL(c->src_row, n);
+        AL(c->lkey, n);
         AL(c->P2, c->ntiles2 * kPTileStride);
+        AL(c->ptile_nz, c->ntiles2);
         AL(c->d_ptile_off, nc);
         AL(c->d_tiles2, c->ntiles2);
     } else {
@@ -381,14 +386,23 @@ static void mark(ptsne_ctx* c, int k, cudaStream_t s) {
 }
 
 // Gather (and, for ptsne_run, the chunk maps), then the affinities of every
-// chunk of the partition perm.  Opens stages GATHER..JOINT_P; the caller opens
-// ITERATE.
-static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s, bool reset_stats,
+// chunk of the partition *perm_io.  With the locality order on, the rows of
+// each chunk are first put in locality order and *perm_io becomes that
+// partition (c->perm_loc), which the caller then uses for everything of this
+// partition.  Opens stages GATHER..JOINT_P; the caller opens ITERATE.
+static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t** perm_io, cudaStream_t s, bool reset_stats,
                            const float* Y_run) {
     if (reset_stats) CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
     const bool mixed = c->p.precision == PTSNE_PREC_BF16_WINDOW;
     mark(c, PTSNE_STAGE_GATHER, s);
-    CK(launch_gather(c, X, perm, s));
+    c->loc_active = c->locality && c->p.schedule == PTSNE_SCHED_BATCHED;
+    if (c->loc_active) {
+        CK(launch_locality_order(c, X, *perm_io, s));
+        *perm_io = c->perm_loc;
+    } else {
+        CK(launch_gather(c, X, *perm_io, s));
+    }
+    const int32_t* perm = *perm_io;
     if (mixed) CK(launch_gather_bf16(c, s));
     if (Y_run) CK(launch_gather_y(c, Y_run, perm, c->Yc, s));
     CK(launch_reset_optim(c, s));
@@ -440,8 +454,9 @@ static int iterate_rows(ptsne_ctx* c, float* grad_perm, cudaStream_t s);
 // (3 doubles).
 static int run_epoch(ptsne_ctx* c, const float* X, const int32_t* perm_in, float* Y, bool want_cost, double* cost_dst,
                      cudaStream_t s) {
-    VPERM(perm, perm_in, s);
-    int st = affinities_impl(c, X, perm, s, false, Y);
+    VPERM(perm0, perm_in, s);
+    const int32_t* perm = perm0;
+    int st = affinities_impl(c, X, &perm, s, false, Y);
     if (st != PTSNE_OK) return st;
     mark(c, PTSNE_STAGE_ITERATE, s);
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
@@ -502,6 +517,7 @@ static int capture_epoch(ptsne_ctx* c, const float* X, float* Y, bool want_cost)
     c->graph_cost = want_cost ? 1 : 0;
     c->graph_tune = c->tune;
     c->graph_prof = c->profiling ? 1 : 0;
+    c->graph_loc = c->locality ? 1 : 0;
     return PTSNE_OK;
 }
 
@@ -511,8 +527,9 @@ int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm_in, float
     if (!X || !perm_in) return fail(c, PTSNE_EINVAL, "X and perm must be device pointers%s%lld");
     cudaStream_t s = as_stream(stream);
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
-    VPERM(perm, perm_in, s);
-    int st = affinities_impl(c, X, perm, s, false, nullptr);
+    VPERM(perm0, perm_in, s);
+    const int32_t* perm = perm0;
+    int st = affinities_impl(c, X, &perm, s, false, nullptr);
     if (st != PTSNE_OK) return st;
     if (P_out) CK(c->P2 ? launch_export_packed(c, P_out, s) : launch_export_P(c, P_out, s));
     if (beta_out) CK(launch_scatter_rows(c, c->beta, perm, 1, beta_out, s));
@@ -527,6 +544,7 @@ int ptsne_affinities_from_distances(ptsne_ctx* c, const float* D_dev, int64_t ld
     cudaStream_t s = as_stream(stream);
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
     VPERM(perm, perm_in, s);
+    c->loc_active = false;   // the dissimilarities are used in the caller's order
     CK(launch_gather_dist(c, D_dev, ldd, perm, s));
     CK(launch_reset_optim(c, s));
     // the given dissimilarities are final: one fine search, then the joint P
@@ -581,7 +599,9 @@ int ptsne_step(ptsne_ctx* c, const int32_t* perm_in, float* Y, float* grad_out, 
     if (!perm_in || !Y) return fail(c, PTSNE_EINVAL, "perm and Y must be device pointers%s%lld");
     if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_step before ptsne_affinities%s%lld");
     cudaStream_t s = as_stream(stream);
-    VPERM(perm, perm_in, s);
+    VPERM(perm0, perm_in, s);
+    // the partition of the kept affinities, in the row order they were computed in
+    const int32_t* perm = c->loc_active ? c->perm_loc : perm0;
     CK(launch_gather_y(c, Y, perm, c->Yc, s));
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
         CK(launch_iterate(c, 1, 0, grad_out ? c->gradp : nullptr, c->Zc, nullptr, s));
@@ -601,7 +621,8 @@ int ptsne_cost(ptsne_ctx* c, const int32_t* perm_in, const float* Y, double* out
     if (!perm_in || !Y || !out_dev) return fail(c, PTSNE_EINVAL, "perm, Y and out must be device pointers%s%lld");
     if (!c->have_P) return fail(c, PTSNE_ESTATE, "ptsne_cost before ptsne_affinities%s%lld");
     cudaStream_t s = as_stream(stream);
-    VPERM(perm, perm_in, s);
+    VPERM(perm0, perm_in, s);
+    const int32_t* perm = c->loc_active ? c->perm_loc : perm0;
     CK(launch_gather_y(c, Y, perm, c->Yc, s));
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
         CK(launch_iterate(c, 0, 1, nullptr, nullptr, c->cost_chunk, s));
@@ -629,7 +650,8 @@ int ptsne_run(ptsne_ctx* c, const float* X, const int32_t* perms, int32_t epochs
     const bool want_cost = cost_out != nullptr;
     const bool use_graph = c->p.use_graph != 0;
     if (use_graph && (!c->graph || c->graph_X != X || c->graph_Y != Y || c->graph_cost != (int)want_cost ||
-                      c->graph_prof != (c->profiling ? 1 : 0) || !same_tune(c->graph_tune, c->tune))) {
+                      c->graph_prof != (c->profiling ? 1 : 0) || c->graph_loc != (c->locality ? 1 : 0) ||
+                      !same_tune(c->graph_tune, c->tune))) {
         const int st = capture_epoch(c, X, Y, want_cost);
         if (st != PTSNE_OK) return st;
     }
@@ -717,6 +739,8 @@ int ptsne_get_stats(ptsne_ctx* c, ptsne_stats* out, void* stream) {
     out->bad_perm_entries = (int64_t)h.bad_index;
     out->wait_timeouts = (int64_t)h.timeouts;
     out->bisect_evals = (int64_t)h.bisect_evals;
+    out->ptiles_total = c->ntiles2;
+    out->ptiles_nonzero = (int64_t)h.ptiles_nonzero;
     float herr;
     memcpy(&herr, &h.max_herr_bits, sizeof herr);
     out->max_abs_entropy_err = herr;
@@ -745,6 +769,14 @@ int ptsne_set_tuning(ptsne_ctx* c, const ptsne_tuning* t) {
     c->tune.cluster = t->cluster;
     c->tune.group = t->group;
     c->tune.consumer_warps = t->consumer_warps;
+    return PTSNE_OK;
+}
+
+int ptsne_set_locality_order(ptsne_ctx* c, int on) {
+    if (!c) return PTSNE_EINVAL;
+    if (c->p.schedule != PTSNE_SCHED_BATCHED)
+        return fail(c, PTSNE_EINVAL, "the locality order needs the batched schedule%s%lld");
+    c->locality = on != 0;
     return PTSNE_OK;
 }
 

@@ -37,7 +37,8 @@ struct TileDesc {
 // block meets exactly one partner (or its own diagonal tile), so one pass over
 // the tiles in storage order touches every block once per round.  Inside a
 // tile the 1024 values are ordered for the warp that evaluates it (see
-// packed_index): lane L owns 32 consecutive floats, read as 8 float4.
+// packed_index, which depends on the map's dimension): lane L owns 32
+// consecutive floats, read as 8 float4.
 constexpr int kPT = 32;                      // packed tile edge
 constexpr int kPTileFloats = kPT * kPT;      // 1024 floats = 4 KB of P
 // Stored tile: the 4 KB of P followed by a 16-byte trailer {a, b, 0, 0} (int
@@ -78,16 +79,33 @@ struct TourSched {
     }
 };
 
-// Position of element (r, c) of a stored tile.  The consuming warp's lane
-// L = 16 h + g owns rows 2g and 2g + 1 and the ring h of columns 16h..16h+15,
-// which it meets in the order (g + t) & 15, t = 0..15.  Its 32 values are
-// 8 float4, one per double step s = t / 2: {(2g, 2s), (2g, 2s+1), (2g+1, 2s),
-// (2g+1, 2s+1)} in (row, step) terms; the float4 index is XOR-swizzled by
-// L & 7 so that a warp-wide float4 read is free of bank conflicts.
-__host__ __device__ inline int packed_index(int r, int c) {
+// Position of element (r, c) of a stored tile, in the order of the warp that
+// evaluates it: lane L owns 32 consecutive floats, read as 8 float4 whose
+// index is XOR-swizzled by L & 7 so that a warp-wide float4 read is free of
+// bank conflicts.  Two lane layouts:
+//
+// 3-D maps (packed_index_ring16): lane L = 16 h + g owns rows 2g and 2g + 1
+// and the ring h of columns 16h..16h+15, which it meets in the order
+// (g + t) & 15, t = 0..15; float4 s = t / 2 holds {(2g, 2s), (2g, 2s+1),
+// (2g+1, 2s), (2g+1, 2s+1)} in (row, step) terms.
+//
+// 2-D maps (packed_index_ring8): lane L = 8 q + g owns rows 4g .. 4g+3 and
+// the ring q of columns 8q..8q+7, which it meets as natural column pairs:
+// pair (g / 2 + s) & 3 at step s = 0..3; float4 2s + h holds rows 4g + 2h,
+// 4g + 2h + 1 against the two columns of that step's pair.
+__host__ __device__ inline int packed_index_ring16(int r, int c) {
     const int g = r >> 1, L = (c & 16) | g;
     const int t = ((c & 15) - g) & 15;
     return L * kPT + ((((t >> 1) ^ (L & 7)) << 2) | ((r & 1) << 1) | (t & 1));
+}
+__host__ __device__ inline int packed_index_ring8(int r, int c) {
+    const int g = r >> 2, q = c >> 3, L = 8 * q + g;
+    const int s = (((c & 7) >> 1) - (g >> 1)) & 3;
+    const int f = 2 * s + ((r >> 1) & 1);
+    return L * kPT + (((f ^ (L & 7)) << 2) | ((r & 1) << 1) | (c & 1));
+}
+__host__ __device__ inline int packed_index(int r, int c, int od) {
+    return od == 2 ? packed_index_ring8(r, c) : packed_index_ring16(r, c);
 }
 
 // Device view of the chunk layout, passed by value to kernels.
@@ -116,6 +134,7 @@ struct DeviceStats {               // device-side counters, reset per affinities
     unsigned int bad_index;        // permutation entries outside [0, n) (skipped)
     unsigned int timeouts;         // bounded device waits that ran out
     unsigned int pad;
+    unsigned long long ptiles_nonzero;  // stored P tiles with a nonzero entry (batched schedule)
 };
 
 struct Optim {                     // optimiser settings
@@ -160,6 +179,7 @@ struct ptsne_ctx {
     int64_t* d_ptile_off = nullptr;    // n_chunks: first packed tile of each chunk
     ptsne::TileDesc2* d_tiles2 = nullptr;
     float* P2 = nullptr;               // ntiles2 x kPTileStride floats
+    uint8_t* ptile_nz = nullptr;       // ntiles2: 1 if the stored tile has a nonzero entry
     ptsne::IterTune tune;
     // BF16 Gram matrix (PTSNE_PREC_BF16_WINDOW): 128 x 128 upper tiles per chunk
     int64_t ntiles128 = 0;
@@ -209,6 +229,12 @@ struct ptsne_ctx {
     int64_t hperms_cap = 0;
     float* hY = nullptr;
     float* ycold = nullptr;            // ptsne_mlp_warm_start: the cold start's map (lazily allocated)
+    // locality order of the rows within each chunk (batched schedule)
+    bool locality = false;             // on: each affinities call orders the chunks' rows (ptsne_set_locality_order)
+    bool loc_active = false;           // the kept affinities were computed in locality order
+    int32_t* perm_loc = nullptr;       // n: the partition in locality order
+    int32_t* src_row = nullptr;        // n: position in the caller's partition of each row of perm_loc
+    uint8_t* lkey = nullptr;           // n: landmark key of each row
 
     bool have_P = false;
     size_t ws_bytes = 0;
@@ -225,6 +251,7 @@ struct ptsne_ctx {
     int graph_cost = -1;
     int graph_prof = -1;               // profiling marks captured as event nodes
     bool capturing = false;
+    int graph_loc = -1;                // locality order captured in the graph
     ptsne::IterTune graph_tune{};
     long long graph_launches = 0;      // kernels per replay
 
@@ -240,6 +267,8 @@ namespace ptsne {
 
 // --- launchers (host side, defined next to their kernels) -------------------
 cudaError_t launch_gather(const ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s);
+// rows of each chunk in locality order: partition -> c->perm_loc / c->src_row, X gathered in that order
+cudaError_t launch_locality_order(ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s);
 cudaError_t launch_gather_y(const ptsne_ctx* c, const float* Y, const int32_t* perm, float* Yc, cudaStream_t s);
 // all gathers and scatters skip (and count in DeviceStats::bad_index) perm entries outside [0, n)
 cudaError_t launch_scatter_rows(const ptsne_ctx* c, const float* src, const int32_t* perm, int width,
@@ -276,6 +305,7 @@ cudaError_t launch_embedding_size(const ptsne_ctx* c, const float* Y, double* ou
 
 // batched schedule (packed symmetric P)
 cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s);
+// (with the locality order active, rows and columns go back to the caller's order)
 cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t s);
 cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc,
                            double* cost_chunk, cudaStream_t s);

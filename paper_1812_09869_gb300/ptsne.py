@@ -67,6 +67,8 @@ class Stats(C.Structure):
         ("stage_ms", C.c_double * 7),
         ("stage_calls", C.c_int64 * 7),
         ("bisect_evals", C.c_int64),
+        ("ptiles_total", C.c_int64),
+        ("ptiles_nonzero", C.c_int64),
     ]
 
 
@@ -111,6 +113,7 @@ def lib():
         L.ptsne_set_profiling.argtypes = [vp, C.c_int]
         L.ptsne_reset_counters.argtypes = [vp]
         L.ptsne_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.ptsne_set_locality_order.argtypes = [vp, C.c_int]
         L.ptsne_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.ptsne_autotune.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_char_p, C.POINTER(TuneTrial), C.c_int32,
                                      C.POINTER(C.c_int32), vp]
@@ -257,6 +260,9 @@ class Context:
     def set_tuning(self, cluster: int, group: int, consumer_warps: int):
         t = Tuning(cluster, group, consumer_warps)
         return self._check(lib().ptsne_set_tuning(self.h, C.byref(t)))
+
+    def set_locality_order(self, on: bool):
+        return self._check(lib().ptsne_set_locality_order(self.h, int(bool(on))))
 
     def tuning(self) -> tuple:
         t = Tuning()

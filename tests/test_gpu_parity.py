@@ -377,3 +377,44 @@ def test_maximum_chunk_size(dev, precision):
         gr, Zr = O.gradient(Pr, Y0[idx])
         assert rel_max(g[idx], gr) <= GRAD_TOL
         assert abs(Z[c] - Zr) <= 1e-6 * Zr
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_window"])
+def test_locality_order_changes_no_result(dev, precision):
+    """The locality order of the rows within each chunk moves only the FP32
+    summation order: P (exported in the caller's order), beta, the gradient
+    and Z after one step agree with the plain order, and on clustered data it
+    leaves many stored P tiles exactly zero."""
+    from paper_1812_09869_gb300 import ptsne
+    n, d = 6000, 20
+    X, _ = synth.gaussian_mixture(n, d, 12, seed=61, anisotropic=True)
+    off = synth.uniform_chunk_offsets(n, 1000, 2500, seed=62)
+    perm = torch.from_numpy(synth.permutations(n, 1, seed=63)[0]).to(dev)
+    Y0 = synth.init_gaussian(n, 2, 1.0, seed=64)
+    Xd = torch.from_numpy(X).to(dev)
+    sizes = np.diff(off)
+    out = {}
+    for loc in (0, 1):
+        cfg = ptsne.Config(n=n, d=d, offsets=off, perplexity=30.0, iters=1, precision=precision)
+        with ptsne.Context(cfg) as c:
+            c.set_locality_order(bool(loc))
+            Pd = torch.zeros(int((sizes ** 2).sum()), dtype=torch.float32, device=dev)
+            bd = torch.zeros(n, dtype=torch.float32, device=dev)
+            c.affinities(Xd, perm, P_out=Pd, beta_out=bd)
+            st = c.stats()
+            Yd = torch.from_numpy(Y0.copy()).to(dev)
+            gd = torch.zeros_like(Yd)
+            Zd = torch.zeros(len(sizes), dtype=torch.float64, device=dev)
+            c.step(perm, Yd, grad_out=gd, Z_out=Zd)
+            torch.cuda.synchronize()
+            out[loc] = (Pd.cpu().numpy(), bd.cpu().numpy(), gd.cpu().numpy(), Zd.cpu().numpy(), Yd.cpu().numpy(),
+                        st.ptiles_nonzero, st.ptiles_total)
+    P0, b0, g0, Z0, Y0s, nz0, tot = out[0]
+    P1, b1, g1, Z1, Y1s, nz1, tot1 = out[1]
+    for a, b in zip(chunk_blocks(P1, off), chunk_blocks(P0, off)):
+        assert p_error(a, b) <= P_TOL
+    assert np.abs(b1 - b0).max() <= 1e-4 * b0.max()
+    assert rel_max(g1, g0) <= GRAD_TOL
+    assert np.abs(Z1 - Z0).max() <= 1e-6 * Z0.max()
+    assert rel_max(Y1s - Y0, Y0s - Y0) <= 1e-3
+    assert tot1 == tot and nz0 <= tot and nz1 < 0.8 * tot, (nz0, nz1, tot)
