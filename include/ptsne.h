@@ -131,7 +131,8 @@ typedef struct {
     int64_t bisect_evals;         /* entropy evaluations (FP32 and FP64) of the last search, all rows */
     int64_t ptiles_total;         /* batched schedule: stored 32 x 32 tiles of the joint P */
     int64_t ptiles_nonzero;       /* of those, tiles with a nonzero entry in the last affinities
-                                     (the iteration kernel streams P only for these) */
+                                     (FP32 exponentials of far pairs underflow to exactly 0);
+                                     counted on the stats call's stream, not among kernel_launches */
 } ptsne_stats;
 
 /* Turn on (1) or off (0) per-stage timing of ptsne_run: CUDA events are

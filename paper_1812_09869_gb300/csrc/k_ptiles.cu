@@ -13,8 +13,7 @@ namespace ptsne {
 __global__ void __launch_bounds__(256)
 psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
                    const TileDesc2* __restrict__ tiles, int64_t t0, const float* __restrict__ beta,
-                   const float* __restrict__ mrow, const float* __restrict__ Srow, uint8_t* __restrict__ nz_out,
-                   unsigned long long* __restrict__ nz_count) {
+                   const float* __restrict__ mrow, const float* __restrict__ Srow, uint8_t* __restrict__ nz_out) {
     constexpr float kLog2e = 1.4426950408889634f;
     const TileDesc2 td = tiles[t0 + blockIdx.x];
     const int c = td.chunk;
@@ -77,8 +76,7 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
 #pragma unroll
     for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e, L.od)] = out[e];
     // a tile whose every entry is exactly zero (far pairs: the FP32
-    // exponentials underflow) is flagged, and the iteration kernel skips its
-    // P (the attractive terms p w (y_i - y_j) vanish exactly)
+    // exponentials underflow) is flagged (counted by ptsne_get_stats)
     const int nz = __syncthreads_or(out[0] != 0.f || out[1] != 0.f || out[2] != 0.f || out[3] != 0.f);
     const int64_t gt = ptile_off[c] + td.pos;
     float* dst = P2 + gt * kPTileStride;
@@ -86,7 +84,6 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
     if (tid == 0) {   // trailer: the tile's row and column blocks and its flag
         *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, nz, 0);
         nz_out[gt] = (uint8_t)nz;
-        if (nz) atomicAdd(nz_count, 1ull);
     }
 }
 
@@ -126,8 +123,7 @@ cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s) {
     for (int64_t b = 0; b < c->ntiles2; b += 2147483647LL, ++k) {
         const int64_t cnt = (c->ntiles2 - b) < 2147483647LL ? (c->ntiles2 - b) : 2147483647LL;
         psym_packed_kernel<<<(unsigned)cnt, 256, 0, s>>>(c->D, c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2, b,
-                                                         c->beta, c->mrow, c->Srow, c->ptile_nz,
-                                                         &c->dstats->ptiles_nonzero);
+                                                         c->beta, c->mrow, c->Srow, c->ptile_nz);
     }
     return launched(c, k);
 }
@@ -137,6 +133,25 @@ cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t 
                                                               c->d_dense_off, c->loc_active ? c->src_row : nullptr,
                                                               P_out);
     return launched(c, 1);
+}
+
+// Number of stored tiles flagged nonzero by the last joint-P assembly.
+__global__ void __launch_bounds__(256) count_nonzero_kernel(const uint8_t* __restrict__ nz, int64_t n,
+                                                            unsigned long long* __restrict__ out) {
+    unsigned long long cnt = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cnt += nz[i] != 0;
+    cnt = warp_sum((double)cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+cudaError_t launch_count_nonzero(const ptsne_ctx* c, unsigned long long* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || c->ntiles2 <= 0) return e;
+    int64_t g = (c->ntiles2 + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    count_nonzero_kernel<<<(unsigned)g, 256, 0, s>>>(c->ptile_nz, c->ntiles2, out);
+    return cudaGetLastError();   // a query: not counted among the context's kernel launches
 }
 
 }  // namespace ptsne

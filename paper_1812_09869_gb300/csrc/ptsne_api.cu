@@ -728,6 +728,7 @@ int ptsne_run_host(ptsne_ctx* c, const float* X_host, const int32_t* perms_host,
 int ptsne_get_stats(ptsne_ctx* c, ptsne_stats* out, void* stream) {
     if (!c || !out) return PTSNE_EINVAL;
     cudaStream_t s = as_stream(stream);
+    if (c->ptile_nz && c->have_P) CK(launch_count_nonzero(c, &c->dstats->ptiles_nonzero, s));
     DeviceStats h;
     CK(cudaMemcpyAsync(&h, c->dstats, sizeof h, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -307,6 +307,8 @@ cudaError_t launch_embedding_size(const ptsne_ctx* c, const float* Y, double* ou
 cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s);
 // (with the locality order active, rows and columns go back to the caller's order)
 cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t s);
+// stored tiles flagged nonzero by the last joint P (into *out, device)
+cudaError_t launch_count_nonzero(const ptsne_ctx* c, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc,
                            double* cost_chunk, cudaStream_t s);
 int iterate_ring(int od, int64_t zmax, int slots); // 0 if the map does not fit in shared memory

@@ -418,3 +418,14 @@ def test_locality_order_changes_no_result(dev, precision):
     assert np.abs(Z1 - Z0).max() <= 1e-6 * Z0.max()
     assert rel_max(Y1s - Y0, Y0s - Y0) <= 1e-3
     assert tot1 == tot and nz0 <= tot and nz1 < 0.8 * tot, (nz0, nz1, tot)
+    # without the locality order the stored tiles are the 32 x 32 blocks on and
+    # above the diagonal of each exported chunk block: the nonzero count is exact
+    want_tot = want_nz = 0
+    for blk in chunk_blocks(P0, off):
+        z = blk.shape[0]
+        t = (z + 31) // 32
+        for a in range(t):
+            for b in range(a, t):
+                want_tot += 1
+                want_nz += bool(np.any(blk[32 * a:32 * a + 32, 32 * b:32 * b + 32] != 0))
+    assert (tot, nz0) == (want_tot, want_nz)
