@@ -242,27 +242,41 @@ def compare_forms(w, Xd, perms, dev, stream, tuning):
     and the final KL compared."""
     import torch
     from paper_1812_09869_gb300 import ptsne
+    # "form": how the mixed-precision contexts pick each chunk's distance form
+    # ("auto": ptsne_autotune_form; "all_mixed": BF16 Gram + window for every chunk)
     kinds = {"plain_fp32": dict(precision="fp32", schedule="per_chunk", use_graph=0),
              "batched_fp32": dict(precision="fp32", schedule="batched", use_graph=1),
-             "batched_bf16_window": dict(precision="bf16_window", schedule="batched", use_graph=1),
+             "batched_bf16_window": dict(precision="bf16_window", schedule="batched", use_graph=1, form="auto"),
+             "batched_bf16_window_all_mixed": dict(precision="bf16_window", schedule="batched", use_graph=1,
+                                                   form="all_mixed"),
              # the paper's own update: adaptive learning rate of Eq. 13, no gains
              "batched_bf16_window_lr_eq13": dict(precision="bf16_window", schedule="batched", use_graph=1,
-                                                 lr_mode=ptsne.LR_PAPER, use_gains=0)}
+                                                 lr_mode=ptsne.LR_PAPER, use_gains=0, form="auto")}
     out = {}
     for name, kw in kinds.items():
+        kw = dict(kw)
+        form = kw.pop("form", None)
         cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
                            momentum=w.momentum, **kw)
         with ptsne.Context(cfg) as c:
             if kw["schedule"] == "batched":
                 c.set_tuning(*tuning)
+            if form == "auto":
+                c.autotune_form(Xd, perms[0])
+            frec = c.form_record() if form else None
             Y = torch.from_numpy(w.Y0.copy()).to(dev)
             _timed_epochs(c, Xd, [perms[0]], Y, stream)
             rec = []
             secs, kls = _timed_epochs(c, Xd, [perms[1]], Y, stream, record=rec)
+            if frec is not None:
+                frec["fp32_chunks_per_epoch"] = int(c.stats().fp32_chunks)
         out[name] = {"value": w.n * w.iters / secs, "unit": UNIT, "ms_per_epoch": secs * 1e3,
                      "final_kl_after_2_epochs": kls[-1], "window_pairs_per_epoch": rec[-1]["window_pairs"],
                      "fp64_rows_per_epoch": rec[-1]["fp64_rows"],
                      "max_abs_entropy_err": rec[-1]["max_abs_entropy_err"], **kw}
+        if form:
+            out[name]["form"] = form
+            out[name]["distance_form"] = frec
     base = out["plain_fp32"]
     for name, r in out.items():
         r["speedup_vs_plain"] = r["value"] / base["value"]
@@ -382,6 +396,8 @@ def eq13_study(w, Xd, dev, stream, tuning, ref_epochs=10, epochs=24):
                            momentum=w.momentum, precision=w.precision, schedule="batched", **kw)
         with ptsne.Context(cfg) as c:
             c.set_tuning(*tuning)
+            if w.precision == "bf16_window":
+                c.autotune_form(Xd, perms[0])
             Y = torch.from_numpy(Y0.copy()).to(dev)
             rec = []
             _timed_epochs(c, Xd, [perms[e] for e in range(epochs)], Y, stream, record=rec)
@@ -468,13 +484,17 @@ def bench_ours(args, rank, world, local_rank):
         """Partitions of steps k0 .. k0 + count - 1 (cycling through the pool), contiguous."""
         return torch.stack([perms[(k0 + k) % PERM_POOL] for k in range(count)]).contiguous()
 
-    # launch shape of the iteration kernel, chosen by the library's autotuner
+    # launch shape of the iteration kernel (and, under BF16_WINDOW, the form of
+    # the distances), chosen by the library's autotuner
     if args.tuning:
+        if precision == "bf16_window":
+            ctx.autotune_form(Xd, perms[0])
         ctx.set_tuning(*[int(v) for v in args.tuning.split(",")])
         trials = []
     else:
         trials = ctx.autotune(Xd, perms[0], Y, iters=3)
     tuning = ctx.tuning()
+    form = ctx.form_record() if precision == "bf16_window" else None
     # profiling marks are part of the captured epoch graph: turn them on before
     # the warm-up steps so that the timed steps replay the same graph
     ctx.set_profiling(True)
@@ -502,6 +522,8 @@ def bench_ours(args, rank, world, local_rank):
     stages = {name: (st.stage_ms[k] / st.stage_calls[k] if st.stage_calls[k] else None)
               for k, name in enumerate(ptsne.STAGES)}
     # search counters of the timed call, per epoch
+    if form is not None:
+        form["fp32_chunks_per_epoch"] = st.fp32_chunks / args.steps
     search = {"evals_per_row": st.bisect_evals / w.n / args.steps,
               "fp64_rows_per_epoch": st.bisect_fp64_rows / args.steps,
               "failed_rows": int(st.bisect_failed_rows), "window_pairs_per_epoch": st.window_pairs / args.steps,
@@ -561,7 +583,10 @@ def bench_ours(args, rank, world, local_rank):
                    "chunk_size_range": [int(sizes.min()), int(sizes.max())], "perplexity": w.perplexity,
                    "iters_per_epoch": w.iters, "out_dim": 2, "schedule": "batched persistent, graph-captured epoch",
                    "distances": {"fp32": "fp32 direct differences",
-                                 "bf16_window": "bf16 tcgen05 Gram + fp32 window recompute"}[precision],
+                                 "bf16_window": "bf16 tcgen05 Gram + fp32 window recompute, per-chunk form "
+                                                "autotuned (chunks whose window covers most of the chunk "
+                                                "computed in fp32 whole)"}[precision],
+                   "distance_form": form,
                    "step": "one epoch (the K timed epochs run as one ptsne_run call)", "parallelism": f"replicas{world}",
                    "tuning": {"cluster": tuning[0], "group": tuning[1], "consumer_warps": tuning[2]},
                    "autotune_ms_per_iter": {f"{t[0]}x{t[1]}x{t[2]}": round(ms, 4) for t, ms in trials},

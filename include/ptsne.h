@@ -120,7 +120,10 @@ typedef struct {
     int64_t bisect_rows;          /* rows searched by the last ptsne_affinities */
     int64_t bisect_fp64_rows;     /* rows whose FP32 search stalled and were redone in FP64 */
     int64_t bisect_failed_rows;   /* rows that missed the tolerance even in FP64 */
-    int64_t window_pairs;         /* BF16_WINDOW: distances recomputed in FP32 */
+    int64_t window_pairs;         /* BF16_WINDOW: distances recomputed in FP32 (the window
+                                     candidates of sparse rows, and every pair of the 64 x 64
+                                     tiles recomputed whole for dense rows; chunks computed in
+                                     FP32 whole are not counted) */
     int64_t nonfinite_inputs;     /* NaN/Inf entries seen in X by the last gather */
     int64_t bad_perm_entries;     /* permutation entries outside [0, n): skipped, never dereferenced */
     int64_t wait_timeouts;        /* bounded in-kernel waits that ran out (PTSNE_ETIMEOUT) */
@@ -133,6 +136,19 @@ typedef struct {
     int64_t ptiles_nonzero;       /* of those, tiles with a nonzero entry in the last affinities
                                      (FP32 exponentials of far pairs underflow to exactly 0);
                                      counted on the stats call's stream, not among kernel_launches */
+    int64_t fp32_chunks;          /* BF16_WINDOW: chunks computed in FP32 whole (see
+                                     ptsne_set_form_threshold), summed like window_pairs */
+    double form_threshold;        /* BF16_WINDOW: the window fraction at or above which a chunk
+                                     runs in FP32 whole (> 1: never) */
+    double window_fraction[8];    /* BF16_WINDOW: window fraction (window pairs / (z - 1) per
+                                     row) last measured in each of 8 equal chunk-size bins
+                                     over [zmin, zmax] */
+    double form_ms_mixed;         /* ptsne_autotune on BF16_WINDOW: affinities time with every
+                                     chunk in the mixed form, */
+    double form_ms_fp32;          /* ... with every chunk in FP32 whole, */
+    double form_ms_window;        /* ... and of the window recompute alone (0: not tuned) */
+    int64_t locality_order;       /* 1: the locality order is on (ptsne_set_locality_order, or
+                                     ptsne_autotune_form's choice) */
 } ptsne_stats;
 
 /* Turn on (1) or off (0) per-stage timing of ptsne_run: CUDA events are
@@ -173,6 +189,22 @@ int ptsne_set_tuning(ptsne_ctx* ctx, const ptsne_tuning* tuning);
  * ptsne_affinities_from_distances never reorders.  PTSNE_EINVAL on the
  * per-chunk schedule. */
 int ptsne_set_locality_order(ptsne_ctx* ctx, int on);
+
+/* Form of each chunk's distances under PTSNE_PREC_BF16_WINDOW.  A row's
+ * window (the pairs whose weight exp(-beta (d - m)) can reach e^-25 of the
+ * row's largest, the BF16 error bound included) is what the FP32 recompute
+ * must cover; when windows are most of a chunk, computing the chunk's
+ * distances in FP32 whole (direct differences, as PTSNE_PREC_FP32) costs less
+ * than the BF16 Gram matrix, the coarse search and the recompute.  Each
+ * affinities computation gives every chunk whose size bin's last measured
+ * window fraction (ptsne_stats.window_fraction) is >= threshold the FP32 form
+ * (no Gram tiles, no coarse search; the fine search and everything after it
+ * are the same).  Either form yields the same distances wherever they matter:
+ * results differ only by FP32 rounding.  Default 2 (never); ptsne_autotune
+ * measures both forms and sets it; a negative value puts every chunk in FP32.
+ * PTSNE_EINVAL unless the context is BF16_WINDOW, or for NaN.  Synchronous;
+ * a captured ptsne_run graph reads the threshold from device memory. */
+int ptsne_set_form_threshold(ptsne_ctx* ctx, double threshold);
 int ptsne_get_tuning(const ptsne_ctx* ctx, ptsne_tuning* tuning);
 
 typedef struct {
@@ -180,9 +212,23 @@ typedef struct {
     double ms_per_iter;           /* device time per gradient iteration (all chunks) */
 } ptsne_tune_trial;
 
+/* Form of the distances under BF16_WINDOW (A1 of the autotuner; no
+ * counterpart in the paper, which computes distances in double precision):
+ * the affinities of perm_dev are timed with every chunk in the mixed form and
+ * with every chunk in FP32 whole (each the faster of two runs after an
+ * untimed one), and the window recompute alone; the break-even window
+ * fraction goes to ptsne_set_form_threshold (times in ptsne_stats.form_ms_*).
+ * On the batched schedule the mixed form is timed with the locality order off
+ * and on (it gathers a dense window row's pairs on few tiles) and the faster
+ * setting is applied, unless every chunk goes to FP32 whole (then the
+ * caller's setting stays).  Leaves the affinities of perm_dev in ctx.
+ * Synchronous.  PTSNE_EINVAL unless the context is BF16_WINDOW. */
+int ptsne_autotune_form(ptsne_ctx* ctx, const float* X_dev, const int32_t* perm_dev, void* stream);
+
 /* Autotuner of the batched iteration kernel's launch shape (no counterpart in
- * the paper, whose kernels are CPU threads).  Computes the affinities of the
- * partition perm_dev, then times `iters` gradient iterations from the map
+ * the paper, whose kernels are CPU threads).  Under BF16_WINDOW it first runs
+ * ptsne_autotune_form (timed on every call, cache or not).  Then it computes
+ * the affinities of the partition perm_dev and times `iters` gradient iterations from the map
  * Y_dev (n x out_dim, not modified) for every candidate shape with CUDA
  * events (best of two), restoring the optimiser state between trials, and
  * applies the fastest to ctx.  cache_path (optional): a text file of one
@@ -352,8 +398,8 @@ int ptsne_knn_preservation(const float* X_dev, const float* Y_dev, int64_t n, in
  * memory, shared by every call on a device: calls that can overlap on the GPU
  * race on it; calls ordered on one stream are safe, and nothing needs
  * clearing between them.  The first call on each device looks up the array's
- * address (and the SM count) and may load the module: make it before any
- * stream capture.  The address is kept per device together with the CUDA
+ * address (and the SM count) and may load the module.  The address is kept
+ * per device together with the CUDA
  * context it was taken in, and looked up again after that context has been
  * destroyed and re-created (cudaDeviceReset).  Async. */
 int ptsne_gradient_static(const float* P_dev, int64_t ld, const float* Y_dev, int32_t z, int32_t out_dim,

@@ -1,10 +1,13 @@
 // Autotuner of the batched iteration kernel's launch shape: times every
 // candidate (blocks per chunk x consumer warps; one warp per tile) on the
 // caller's chunk layout and keeps the fastest; results persist in a small text
-// cache keyed by device and layout.
+// cache keyed by device and layout.  Under BF16_WINDOW it first chooses the
+// form of the distances (ptsne_set_form_threshold) by timing the affinities
+// with every chunk in each form on the caller's data.
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -72,6 +75,115 @@ void cache_append(const char* path, const std::string& key, const IterTune& t, d
 
 extern "C" int ptsne_affinities(ptsne_ctx* c, const float* X, const int32_t* perm, float* P_out, float* beta_out,
                                 void* stream);
+extern "C" int ptsne_set_form_threshold(ptsne_ctx* c, double threshold);
+
+namespace {
+
+// Mixed-precision form choice.  With every chunk in the mixed form the
+// affinities take Tm, of which Tw is the window recompute of a measured
+// window fraction f; with every chunk in FP32 whole they take Tf.  Taking the
+// recompute as proportional to the window fraction, a chunk of fraction f
+// costs (Tm - Tw) + Tw f / f_meas mixed and Tf in FP32 (per unit of z^2), so
+// the mixed form pays below f* = f_meas (Tf - Tm + Tw) / Tw.  Each time is
+// the faster of two runs after one untimed run.  On the batched schedule the
+// mixed form is timed with the locality order off and on (it gathers a dense
+// row's window pairs on few tiles), and the faster setting is kept.
+int tune_form(ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    auto timed = [&](double fstar, double* ms) {
+        int st = ptsne_set_form_threshold(c, fstar);
+        if (st == PTSNE_OK) st = ptsne_affinities(c, X, perm, nullptr, nullptr, s);   // untimed: fills the bins
+        float best = 1e30f;
+        for (int rep = 0; rep < 2 && st == PTSNE_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = ptsne_affinities(c, X, perm, nullptr, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (st == PTSNE_OK && cudaEventSynchronize(e1) != cudaSuccess) st = PTSNE_ECUDA;
+            float t = 0.f;
+            if (st == PTSNE_OK) cudaEventElapsedTime(&t, e0, e1);
+            best = t < best ? t : best;
+        }
+        *ms = best;
+        return st;
+    };
+    double tm = 0, tf = 0;
+    const bool user_loc = c->locality;
+    int st = PTSNE_OK;
+    if (c->p.schedule == PTSNE_SCHED_BATCHED) {
+        double tl[2] = {0, 0};
+        for (int loc = 0; loc < 2 && st == PTSNE_OK; ++loc) {
+            c->locality = loc != 0;
+            st = timed(2.0, &tl[loc]);
+        }
+        c->locality = tl[1] < tl[0];
+        tm = tl[1];
+        // the window recompute is timed below on the state of the last run: the kept setting's
+        if (st == PTSNE_OK && !c->locality) st = timed(2.0, &tm);
+    } else {
+        st = timed(2.0, &tm);
+    }
+    if (st != PTSNE_OK) {
+        c->locality = user_loc;
+        return st;
+    }
+    // the window fraction of the last (mixed) run, before the next one consumes it
+    unsigned long long acc[2 * kFormBins];
+    if (cudaMemcpy(acc, c->form_acc, sizeof acc, cudaMemcpyDeviceToHost) != cudaSuccess) return PTSNE_ECUDA;
+    double w = 0, nrow = 0, fmin = 2.0;
+    for (int b = 0; b < kFormBins; ++b) {
+        w += (double)acc[2 * b];
+        nrow += (double)acc[2 * b + 1];
+        if (acc[2 * b + 1]) fmin = std::min(fmin, (double)acc[2 * b] / (double)acc[2 * b + 1]);
+    }
+    const double fmeas = nrow > 0 ? w / nrow : 0.0;
+    // the window recompute alone, on the state the last run left
+    float tw = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        const cudaError_t e = launch_window_recompute(c, 0, c->p.n, s);
+        cudaEventRecord(e1, s);
+        if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return PTSNE_ECUDA;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        tw = t < tw ? t : tw;
+    }
+    const bool loc_mixed = c->locality;
+    c->locality = user_loc;   // FP32 whole gains nothing from the order
+    st = timed(-1.0, &tf);
+    if (st != PTSNE_OK) return st;
+    double fstar;
+    if (tf <= tm - tw) fstar = -1.0;                  // FP32 whole is faster even with no window at all
+    else if (tw <= 0.0 || fmeas <= 0.0) fstar = tf < tm ? -1.0 : 2.0;
+    else fstar = fmeas * (tf - tm + tw) / tw;
+    if (fstar > 1.0) fstar = 2.0;
+    // every measured size bin on the FP32 side: the plain FP32 path (no Gram
+    // matrix, coarse search or window launches at all)
+    if (fstar <= fmin) fstar = -1.0;
+    if (fstar > 0.0) c->locality = loc_mixed;   // some chunks may run mixed
+    c->form_ms[0] = tm;
+    c->form_ms[1] = tf;
+    c->form_ms[2] = tw;
+    return ptsne_set_form_threshold(c, fstar);
+}
+
+}  // namespace
+
+extern "C" int ptsne_autotune_form(ptsne_ctx* c, const float* X, const int32_t* perm, void* stream) {
+    if (!c) return PTSNE_EINVAL;
+    if (!X || !perm) {
+        c->err = "autotune_form: X and perm must be device pointers";
+        return PTSNE_EINVAL;
+    }
+    if (!c->form_fstar) {
+        c->err = "autotune_form: the distances' form needs PTSNE_PREC_BF16_WINDOW";
+        return PTSNE_EINVAL;
+    }
+    cudaEvent_t f0 = nullptr, f1 = nullptr;
+    int st = cudaEventCreate(&f0) == cudaSuccess && cudaEventCreate(&f1) == cudaSuccess ? PTSNE_OK : PTSNE_ECUDA;
+    if (st == PTSNE_OK) st = tune_form(c, X, perm, reinterpret_cast<cudaStream_t>(stream), f0, f1);
+    if (f0) cudaEventDestroy(f0);
+    if (f1) cudaEventDestroy(f1);
+    return st;
+}
 
 extern "C" int ptsne_autotune(ptsne_ctx* c, const float* X, const int32_t* perm, const float* Y, int32_t iters,
                               const char* cache_path, ptsne_tune_trial* trials, int32_t max_trials, int32_t* n_trials,
@@ -87,6 +199,10 @@ extern "C" int ptsne_autotune(ptsne_ctx* c, const float* X, const int32_t* perm,
         return PTSNE_EINVAL;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (c->form_fstar) {   // BF16_WINDOW: the distances' form first
+        const int st = ptsne_autotune_form(c, X, perm, stream);
+        if (st != PTSNE_OK) return st;
+    }
     const std::string key = tune_key(c);
     IterTune cached;
     if (cache_path && cache_lookup(cache_path, key, &cached)) {

@@ -36,6 +36,18 @@ constexpr int kMaxEval32 = 64;
 constexpr int kMaxEval64 = 200;
 }  // namespace
 
+// Mixed-precision bookkeeping of a search (all NULL: none): the chunks
+// computed in FP32 whole, the window tiles of the dense rows, and the window
+// pairs and (z - 1) summed per chunk-size bin.
+struct FormArgs {
+    const uint8_t* chunk_fp32 = nullptr;
+    uint8_t* tflag = nullptr;
+    const int64_t* tflag_off = nullptr;
+    unsigned long long* form_acc = nullptr;
+    int zmin = 0, zmax = 0;
+    bool fp32_warm = false;   // beta_init of the FP32 chunks' rows is a warm start (else unset)
+};
+
 // packed FP32 pairs (f32x2 arithmetic, round to nearest like the scalar ops)
 typedef unsigned long long f2;
 __device__ __forceinline__ f2 pk(float a, float b) {
@@ -224,14 +236,17 @@ __global__ void __launch_bounds__(kGroup, VPT >= 48 ? 3 : (VPT >= 16 ? 8 : 6))
 bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r1, double ln_perp_d,
                     float* __restrict__ beta_out, float* __restrict__ m_out, float* __restrict__ S_out,
                     DeviceStats* st, const float* beta_init, int coarse, const unsigned int* maxnorm,
-                    int32_t* __restrict__ dense_rows, int* __restrict__ dense_cnt, uint8_t* __restrict__ row_dense) {
+                    uint8_t* __restrict__ row_dense, FormArgs fa) {
     __shared__ float red[kGroup / 32];
+    __shared__ unsigned long long s_form[kFormBins][2];   // this block's window pairs and (z - 1) per size bin
     __shared__ float red5[kGroup / 32][5];
     __shared__ float s_bc[4];    // warp 0's decision: next beta, S, f, state
     __shared__ double redd3[kGroup / 32][3];
     __shared__ double s_bd[4];   // the same for the FP64 search
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float ln_perp = (float)ln_perp_d;
+    if (tid < 2 * kFormBins) s_form[tid >> 1][tid & 1] = 0ull;
+    __syncthreads();
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const int c = L.chunk_of_row[r];
         const int64_t off = L.off[c];
@@ -239,6 +254,14 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
         const int i = (int)(r - off);
         const int ld = L.ld[c];
         const float* src = D + L.moff[c] + (int64_t)i * ld;
+        const bool fp32_chunk = fa.chunk_fp32 && fa.chunk_fp32[c];
+        if (coarse && fp32_chunk) {
+            // computed in FP32 whole (the fine search alone): on to this
+            // block's first row past the chunk (block-uniform)
+            const int64_t end = L.off[c + 1];
+            r += (end - r - 1) / gridDim.x * gridDim.x;
+            continue;
+        }
 
         float t[VPT];
         float mn = FLT_MAX;
@@ -280,7 +303,9 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
             float lo = 0.f, hi = INFINITY;
             beta = (float)(z - 1) / tsum;
             float f = INFINITY;
-            if (beta_init) {   // warm start: expected near the root, so evaluate compensated at once
+            // warm start (a chunk computed in FP32 whole holds no coarse beta:
+            // its rows start from the previous epoch's, or from 1 / mean)
+            if (beta_init && (!fp32_chunk || fa.fp32_warm)) {   // expected near the root: compensated at once
                 const float b0 = beta_init[r];
                 if (b0 > 0.f && isfinite(b0)) { beta = b0; f = 0.f; }
             }
@@ -413,18 +438,39 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                 failed = herr > kTolFine;
             }
         }
-        if (coarse) {
-            // window placement for the mixed-precision recompute: rows whose
-            // window covers >= 1/16 of the chunk are listed for the tiled kernel
+        if (coarse || (fp32_chunk && (i & 7) == 0)) {
+            // the row's window (the pairs whose weight can reach e^-T of the
+            // largest; Eq. 1 with the BF16 error bound): its size feeds the
+            // form choice of the next affinities; in the coarse search, a row
+            // whose window covers >= 1/16 of the chunk flags the 64 x 64 tiles
+            // holding its window pairs, recomputed whole in FP32 (in a chunk
+            // computed in FP32 whole, every eighth row is counted)
             const float dmax = window_dmax(beta, mn, __uint_as_float(*maxnorm), L.dp);
             float ncand = 0.f;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) ncand += (t[k] < kBig && t[k] + mn <= dmax) ? 1.f : 0.f;
             ncand = group_sum(ncand, red);
+            const bool dense = coarse && ncand * 16.f >= (float)z;
+            if (dense) {   // block-uniform
+                const int T = (z + kTile - 1) / kTile;
+                uint8_t* fl = fa.tflag + fa.tflag_off[c] + (int64_t)(i / kTile) * T;
+#pragma unroll
+                for (int q = 0; q < VPT / 4; ++q) {
+                    if (4 * kGroup * q >= z) break;
+                    bool has = false;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) has |= t[4 * q + e] < kBig && t[4 * q + e] + mn <= dmax;
+                    // lanes 16h .. 16h + 15 hold the 64 entries of column block 2 warp + h + 8 q
+                    const unsigned m = __ballot_sync(0xffffffffu, has);
+                    if ((lane & 15) == 0 && ((m >> (lane & 16)) & 0xffffu) != 0u)
+                        fl[(4 * tid + 4 * kGroup * q) / kTile] = 1;
+                }
+            }
             if (tid == 0) {
-                const bool dense = ncand * 16.f >= (float)z;
-                if (dense) dense_rows[off + atomicAdd(&dense_cnt[c], 1)] = i;
-                row_dense[r] = dense ? 1 : 0;
+                if (coarse) row_dense[r] = dense ? 1 : 0;
+                const int b = min(kFormBins - 1, (int)((int64_t)(z - fa.zmin) * kFormBins / (fa.zmax - fa.zmin + 1)));
+                s_form[b][0] += (unsigned long long)ncand;
+                s_form[b][1] += (unsigned long long)(z - 1);
             }
         }
         if (tid == 0) {
@@ -437,6 +483,11 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
             if (!coarse) atomicMax(&st->max_herr_bits, __float_as_uint(herr));
         }
         __syncthreads();
+    }
+    __syncthreads();
+    if (fa.form_acc && tid < 2 * kFormBins) {
+        const unsigned long long v = s_form[tid >> 1][tid & 1];
+        if (v) atomicAdd(&fa.form_acc[tid], v);
     }
 }
 
@@ -518,32 +569,41 @@ psym_kernel(const float* __restrict__ D, float* __restrict__ P, Layout L, const 
 
 template <int VPT>
 static void launch_group(const ptsne_ctx* c, int64_t r0, int64_t r1, cudaStream_t s, const float* beta_init,
-                         int coarse) {
+                         int coarse, const FormArgs& fa) {
     int64_t blocks = r1 - r0;
     if (blocks > 152 * 32) blocks = 152 * 32;
     bisect_group_kernel<VPT><<<(unsigned)blocks, kGroup, 0, s>>>(c->D, make_layout(c), r0, r1,
                                                                    log(c->p.perplexity), c->beta, c->mrow, c->Srow,
                                                                    c->dstats, beta_init, coarse, c->maxnorm,
-                                                                   c->dense_rows, c->dense_cnt, c->row_dense);
+                                                                   c->row_dense, fa);
 }
 
 cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
-                          const float* beta_init, int coarse) {
+                          const float* beta_init, int coarse, int form) {
     if (row_end <= row_begin) return cudaSuccess;
-    if (coarse) {   // the coarse search lists the dense window rows of its chunks
-        if (!c->dense_cnt) return cudaErrorInvalidValue;
-        const int c0 = c->chunk_of(row_begin), c1 = c->chunk_of(row_end - 1);
-        const cudaError_t e = cudaMemsetAsync(c->dense_cnt + c0, 0, sizeof(int) * (size_t)(c1 - c0 + 1), s);
-        if (e != cudaSuccess) return e;
+    // mixed precision: the per-chunk form, the window tiles and the size-bin
+    // window fractions (the FP32 and the distance-input searches use none)
+    FormArgs fa;
+    if (form) {
+        if (!c->chunk_fp32 || !c->maxnorm) return cudaErrorInvalidValue;
+        fa.chunk_fp32 = c->chunk_fp32;
+        fa.tflag = c->tflag;
+        fa.tflag_off = c->d_tflag_off;
+        fa.form_acc = c->form_acc;
+        fa.zmin = (int)c->zmin;
+        fa.zmax = (int)c->zmax;
+        fa.fp32_warm = form == 2;
+    } else if (coarse) {
+        return cudaErrorInvalidValue;
     }
     const int64_t per = (c->zmax + 4 * kGroup - 1) / (4 * kGroup) * 4;   // values per thread
-    if (per <= 8) launch_group<8>(c, row_begin, row_end, s, beta_init, coarse);
-    else if (per <= 16) launch_group<16>(c, row_begin, row_end, s, beta_init, coarse);
-    else if (per <= 24) launch_group<24>(c, row_begin, row_end, s, beta_init, coarse);
-    else if (per <= 32) launch_group<32>(c, row_begin, row_end, s, beta_init, coarse);
-    else if (per <= 40) launch_group<40>(c, row_begin, row_end, s, beta_init, coarse);
-    else if (per <= 48) launch_group<48>(c, row_begin, row_end, s, beta_init, coarse);
-    else launch_group<64>(c, row_begin, row_end, s, beta_init, coarse);
+    if (per <= 8) launch_group<8>(c, row_begin, row_end, s, beta_init, coarse, fa);
+    else if (per <= 16) launch_group<16>(c, row_begin, row_end, s, beta_init, coarse, fa);
+    else if (per <= 24) launch_group<24>(c, row_begin, row_end, s, beta_init, coarse, fa);
+    else if (per <= 32) launch_group<32>(c, row_begin, row_end, s, beta_init, coarse, fa);
+    else if (per <= 40) launch_group<40>(c, row_begin, row_end, s, beta_init, coarse, fa);
+    else if (per <= 48) launch_group<48>(c, row_begin, row_end, s, beta_init, coarse, fa);
+    else launch_group<64>(c, row_begin, row_end, s, beta_init, coarse, fa);
     return launched(c, 1);
 }
 

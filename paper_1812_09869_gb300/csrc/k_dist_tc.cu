@@ -75,7 +75,7 @@ __global__ void gather_bf16_kernel(const float* __restrict__ Xg, int64_t n, int 
 __global__ void __launch_bounds__(128)
 dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D, Layout L,
                  const TileDesc* __restrict__ tiles, int64_t t0, const float* __restrict__ xnorm, int kblocks,
-                 unsigned int* timeouts) {
+                 unsigned int* timeouts, const uint8_t* __restrict__ skip) {
     extern __shared__ unsigned char dsmem[];
     __shared__ uint64_t full_bar[2], done_bar[2];
     __shared__ uint32_t tmem_base;
@@ -85,6 +85,7 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
     const uint32_t sbase = (tc::smem_addr(dsmem) + 1023u) & ~1023u;
     const TileDesc td = tiles[t0 + blockIdx.x];
     const int c = td.chunk;
+    if (skip && skip[c]) return;   // a chunk computed in FP32 whole (before any barrier or TMEM use)
     const int64_t off = L.off[c];
     const int z = (int)(L.off[c + 1] - off);
     const int ld = L.ld[c];
@@ -198,9 +199,10 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xi, const fl
     return s;
 }
 
-// Window recompute of the sparse rows (the coarse search has listed the rows
-// whose window covers >= 1/16 of the chunk for the tiled kernel below): one
-// warp per row.  The row of D is scanned 256 entries per step (two float4 per
+// Window recompute of the sparse rows (the coarse search has flagged the
+// 64 x 64 tiles holding the window pairs of the rows whose window covers
+// >= 1/16 of the chunk; those tiles are recomputed whole by the FP32 distance
+// kernel, which also computes the chunks run in FP32 whole): one warp per row.  The row of D is scanned 256 entries per step (two float4 per
 // lane, the next step's loads issued before this step's are used);
 // candidates d~_ij <= window_dmax(...) are compacted with ballots into a
 // per-warp list and recomputed 32 at a time, one per lane, by direct
@@ -212,7 +214,8 @@ template <int KR>
 __global__ void __launch_bounds__(256)
 window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int64_t r0, int64_t r1,
               const float* __restrict__ beta, const float* __restrict__ mrow, const unsigned int* maxnorm,
-              unsigned long long* pairs, const uint8_t* __restrict__ row_dense) {
+              unsigned long long* pairs, const uint8_t* __restrict__ row_dense,
+              const uint8_t* __restrict__ chunk_fp32) {
     extern __shared__ float wsm[];   // per warp: one staged row of Xg (dp floats) + kWinSlots candidate slots
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int dp = L.dp;
@@ -225,10 +228,12 @@ window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int
         const int c = L.chunk_of_row[r];
         const int64_t off = L.off[c];
         const int z = (int)(L.off[c + 1] - off);
-        if (row_dense[r]) {   // recomputed whole by window_dense_kernel
-            count += (lane == 0) ? (unsigned long long)(z - 1) : 0ull;
+        if (chunk_fp32[c]) {   // computed in FP32 whole: on to this warp's first row past the chunk
+            const int64_t G = (int64_t)gridDim.x * nw;
+            r += (L.off[c + 1] - r - 1) / G * G;
             continue;
         }
+        if (row_dense[r]) continue;   // a dense row: its window tiles are recomputed whole
         const int i = (int)(r - off);
         const int ld = L.ld[c];
         float* Drow = D + L.moff[c] + (int64_t)i * ld;
@@ -274,188 +279,6 @@ window_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, int
     if (lane == 0 && count) atomicAdd(pairs, count);
 }
 
-// Dense window rows, D <= KR (padded) dimensions: as window_dense_kernel, with
-// the block's column x_j held in registers and 8 dense rows staged k-major in
-// shared memory, two rows per packed f32x2 instruction (IEEE per lane, the
-// same operation order as exact_d2, so the results are identical).
-typedef unsigned long long f2x;
-__device__ __forceinline__ f2x pk2(float a, float b) {
-    f2x r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(f2x v, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2x fma2x(f2x a, f2x b, f2x c) {
-    f2x d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2x sub2x(f2x a, f2x b) {
-    f2x d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-template <int KR>
-__global__ void __launch_bounds__(128)
-window_dense_reg_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L,
-                        const TileDesc* __restrict__ colblk, const int32_t* __restrict__ dense_rows,
-                        const int* __restrict__ dense_cnt) {
-    __shared__ __align__(16) float xiT[2][KR][8];   // double-buffered groups of 8 dense rows
-    const TileDesc td = colblk[blockIdx.x];
-    const int c = td.chunk;
-    const int cnt = dense_cnt[c];
-    if (cnt == 0) return;
-    const int64_t off = L.off[c];
-    const int z = (int)(L.off[c + 1] - off);
-    const int ld = L.ld[c];
-    const int dp = L.dp;
-    const int tid = threadIdx.x;
-    const int j = td.J * 128 + tid;
-    const bool jv = j < z;
-    float xj[KR];
-    const float* xj_row = Xg + (off + (jv ? j : 0)) * dp;
-#pragma unroll
-    for (int k = 0; k < KR; k += 4) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jv && k < dp) v = *reinterpret_cast<const float4*>(xj_row + k);
-        xj[k] = v.x; xj[k + 1] = v.y; xj[k + 2] = v.z; xj[k + 3] = v.w;
-    }
-    float* Dc = D + L.moff[c];
-    // the next group's rows are loaded into registers while this group computes
-    constexpr int kPer = 8 * KR / 128;   // staged values per thread and group
-    float pre[kPer];
-    auto gather = [&](int rg) {
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int idx = tid + 128 * q, r = idx & 7, k = idx >> 3;
-            pre[q] = (rg + r < cnt && k < dp) ? Xg[(off + dense_rows[off + rg + r]) * dp + k] : 0.f;
-        }
-    };
-    gather(0);
-    int buf = 0;
-    for (int rg = 0; rg < cnt; rg += 8, buf ^= 1) {
-        const int R = min(8, cnt - rg);
-        // buffer `buf` was last read two groups ago, before every thread passed
-        // the previous group's barrier
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int idx = tid + 128 * q;
-            xiT[buf][idx >> 3][idx & 7] = pre[q];
-        }
-        __syncthreads();
-        if (rg + 8 < cnt) gather(rg + 8);
-        f2x acc[4] = {0ull, 0ull, 0ull, 0ull};
-#pragma unroll
-        for (int k = 0; k < KR; ++k) {
-            const float4 a = *reinterpret_cast<const float4*>(&xiT[buf][k][0]);
-            const float4 b = *reinterpret_cast<const float4*>(&xiT[buf][k][4]);
-            const f2x XJ = pk2(xj[k], xj[k]);
-            f2x t = sub2x(pk2(a.x, a.y), XJ);
-            acc[0] = fma2x(t, t, acc[0]);
-            t = sub2x(pk2(a.z, a.w), XJ);
-            acc[1] = fma2x(t, t, acc[1]);
-            t = sub2x(pk2(b.x, b.y), XJ);
-            acc[2] = fma2x(t, t, acc[2]);
-            t = sub2x(pk2(b.z, b.w), XJ);
-            acc[3] = fma2x(t, t, acc[3]);
-        }
-        if (jv) {
-            float v[8];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) upk2(acc[q], v[2 * q], v[2 * q + 1]);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                if (r < R) {
-                    const int i = dense_rows[off + rg + r];
-                    if (i != j) Dc[(int64_t)i * ld + j] = v[r];
-                }
-            }
-        }
-    }
-}
-
-// Dense window rows: one block per (chunk, 128-column block).  The block's
-// columns x_j are staged transposed in shared memory (all of K when it fits,
-// else 64 dimensions at a time) and every dense row of the chunk is run
-// against them, 8 rows at a time, by direct differences in the same order as
-// exact_d2.  Writes D[i][j] of the dense rows only.
-template <bool kFull>
-__global__ void __launch_bounds__(128)
-window_dense_kernel(float* __restrict__ D, const float* __restrict__ Xg, Layout L, const TileDesc* __restrict__ colblk,
-                    const int32_t* __restrict__ dense_rows, const int* __restrict__ dense_cnt) {
-    extern __shared__ float dsm[];
-    const TileDesc td = colblk[blockIdx.x];
-    const int c = td.chunk;
-    const int cnt = dense_cnt[c];
-    if (cnt == 0) return;
-    const int64_t off = L.off[c];
-    const int z = (int)(L.off[c + 1] - off);
-    const int ld = L.ld[c];
-    const int dp = L.dp;
-    const int tid = threadIdx.x;
-    const int j = td.J * 128 + tid;
-    const bool jv = j < z;
-    const int kc_max = kFull ? dp : 64;
-    float* xjT = dsm;                       // [kc_max][128]
-    float* xi = dsm + (size_t)kc_max * 128; // [8][kc_max]
-    const float* xj_row = Xg + (off + (jv ? j : 0)) * dp;
-    float* Dc = D + L.moff[c];
-    if (kFull) {
-        for (int k = 0; k < dp; k += 4) {
-            const float4 v = jv ? *reinterpret_cast<const float4*>(xj_row + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            xjT[(k + 0) * 128 + tid] = v.x;
-            xjT[(k + 1) * 128 + tid] = v.y;
-            xjT[(k + 2) * 128 + tid] = v.z;
-            xjT[(k + 3) * 128 + tid] = v.w;
-        }
-    }
-    for (int rg = 0; rg < cnt; rg += 8) {
-        const int R = min(8, cnt - rg);
-        float acc[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) acc[r] = 0.f;
-        for (int k0 = 0; k0 < dp; k0 += kc_max) {
-            const int kc = min(kc_max, dp - k0);
-            __syncthreads();   // previous users of xi / xjT are done
-            if (!kFull) {
-                for (int k = 0; k < kc; k += 4) {
-                    const float4 v =
-                        jv ? *reinterpret_cast<const float4*>(xj_row + k0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    xjT[(k + 0) * 128 + tid] = v.x;
-                    xjT[(k + 1) * 128 + tid] = v.y;
-                    xjT[(k + 2) * 128 + tid] = v.z;
-                    xjT[(k + 3) * 128 + tid] = v.w;
-                }
-            }
-            for (int idx = tid; idx < 8 * kc; idx += 128) {
-                const int r = idx / kc, k = idx % kc;
-                xi[r * kc_max + k] = r < R ? Xg[(off + dense_rows[off + rg + r]) * dp + k0 + k] : 0.f;
-            }
-            __syncthreads();
-            for (int k = 0; k < kc; ++k) {
-                const float xv = xjT[k * 128 + tid];
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const float t = xi[r * kc_max + k] - xv;
-                    acc[r] = fmaf(t, t, acc[r]);
-                }
-            }
-        }
-        if (jv) {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                if (r < R) {
-                    const int i = dense_rows[off + rg + r];
-                    if (i != j) Dc[(int64_t)i * ld + j] = acc[r];
-                }
-            }
-        }
-    }
-}
-
 cudaError_t launch_gather_bf16(const ptsne_ctx* c, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->maxnorm, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
@@ -465,7 +288,8 @@ cudaError_t launch_gather_bf16(const ptsne_ctx* c, cudaStream_t s) {
     return launched(c, 1);
 }
 
-cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s) {
+cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s,
+                             const uint8_t* skip) {
     const int64_t nt = tile_end - tile_begin;
     if (nt <= 0) return cudaSuccess;
     CUtensorMap tm;
@@ -478,44 +302,35 @@ cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t til
     cudaError_t e = cudaFuncSetAttribute(dist_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dist_bf16_kernel<<<(unsigned)nt, 128, smem, s>>>(tm, c->D, make_layout(c), c->d_tiles128, tile_begin, c->xnorm,
-                                                     kblocks, &c->dstats->timeouts);
+                                                     kblocks, &c->dstats->timeouts, skip);
     return launched(c, 1);
 }
 
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s) {
     const int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
-    // sparse rows (the coarse search has listed the dense ones)
+    // sparse rows: their candidates one by one
     const size_t smem = (size_t)8 * (c->dp + kWinSlots) * sizeof(float);
     void (*wk)(float*, const float*, Layout, int64_t, int64_t, const float*, const float*, const unsigned int*,
-               unsigned long long*, const uint8_t*) = c->dp <= 16   ? window_kernel<16>
-                                                      : c->dp <= 32 ? window_kernel<32>
-                                                      : c->dp <= 64 ? window_kernel<64>
-                                                                    : window_kernel<0>;
+               unsigned long long*, const uint8_t*, const uint8_t*) = c->dp <= 16   ? window_kernel<16>
+                                                                      : c->dp <= 32 ? window_kernel<32>
+                                                                      : c->dp <= 64 ? window_kernel<64>
+                                                                                    : window_kernel<0>;
     cudaError_t e = cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
     wk<<<(unsigned)blocks, 256, smem, s>>>(c->D, c->Xg, make_layout(c), row_begin, row_end, c->beta, c->mrow,
-                                           c->maxnorm, &c->dstats->window_pairs, c->row_dense);
-    // dense rows: the column blocks of the chunks these rows belong to
+                                           c->maxnorm, &c->dstats->window_pairs, c->row_dense, c->chunk_fp32);
+    e = launched(c, 1);
+    if (e != cudaSuccess) return e;
+    // dense rows' window tiles, and the chunks computed in FP32 whole
     const int c0 = c->chunk_of(row_begin), c1 = c->chunk_of(row_end - 1);
-    const int64_t b0 = c->colblk_start[c0], b1 = c->colblk_start[c1 + 1];
-    const unsigned nb = (unsigned)(b1 - b0);
-    const Layout L = make_layout(c);
-    if (c->dp <= 16) window_dense_reg_kernel<16><<<nb, 128, 0, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
-    else if (c->dp <= 32) window_dense_reg_kernel<32><<<nb, 128, 0, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
-    else if (c->dp <= 64) window_dense_reg_kernel<64><<<nb, 128, 0, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
-    else if (c->dp <= 256) {
-        const size_t dsm = (size_t)c->dp * (128 + 8) * sizeof(float);
-        e = cudaFuncSetAttribute(window_dense_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-        if (e != cudaSuccess) return e;
-        window_dense_kernel<true><<<nb, 128, dsm, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
-    } else {
-        const size_t dsm = (size_t)64 * (128 + 8) * sizeof(float);
-        window_dense_kernel<false><<<nb, 128, dsm, s>>>(c->D, c->Xg, L, c->d_colblk + b0, c->dense_rows, c->dense_cnt);
-    }
-    return launched(c, 2);
+    TileSel sel;
+    sel.chunk_fp32 = c->chunk_fp32;
+    sel.tflag = c->tflag;
+    sel.tflag_off = c->d_tflag_off;
+    return launch_dist_fp32_sel(c, c->tile_start[c0], c->tile_start[c1 + 1], sel, s);
 }
 
 }  // namespace ptsne

@@ -15,9 +15,8 @@
 //    (z doubles) followed by per-row accumulators A_i, R_i (z x 2 x out_dim
 //    floats), enough for PTSNE_STATIC_MAX_ROWS rows at out_dim 3.
 //  - Its device address is looked up with cudaGetSymbolAddress once per
-//    device, on the first call made while that device is current.  That first
-//    lookup may load the module, so make it before any stream capture begins.
-//    The address is cached together with the identity of the CUDA context it
+//    device, on the first call made while that device is current (that first
+//    lookup may load the module).  The address is cached together with the identity of the CUDA context it
 //    was taken in; when the device's context has been destroyed and created
 //    again (cudaDeviceReset), the module may load at another address, so the
 //    next call sees the new context and looks the address up again.

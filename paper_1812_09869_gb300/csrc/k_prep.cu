@@ -101,9 +101,10 @@ static int grid_for(int64_t work, int block) {
 // The order of a chunk's rows changes none of the method's results (P, the
 // gradient and the cost are equivariant under it; only FP32 summation order
 // moves).  Rows of nearby points placed next to each other concentrate the
-// joint P on few 32 x 32 tiles and leave the others exactly zero (the FP32
-// exponentials of far pairs underflow), which the iteration kernel then
-// streams no P for.  The chunk's first kLandmarks rows (a random sample, the
+// joint P on few 32 x 32 tiles (leaving the others exactly zero: the FP32
+// exponentials of far pairs underflow) and the window pairs of the
+// mixed-precision distances on few 64 x 64 tiles, which are then the only
+// ones recomputed in FP32.  The chunk's first kLandmarks rows (a random sample, the
 // partition being random) serve as landmarks: each row's key is its nearest
 // landmark (squared distance, ties to the smaller index); landmarks closer
 // to each other than twice the median nearest-landmark distance are joined
@@ -113,52 +114,66 @@ static int grid_for(int64_t work, int block) {
 constexpr int kLandmarks = 64;
 constexpr int kLandK = 32;          // dimensions staged per pass
 
-// Block (row tile of 256, chunk): the chunk's landmarks are staged kLandK
-// dimensions at a time in shared memory; each thread keeps its row's
-// distances to all landmarks in registers.
+// Block (row tile of 128, chunk): the chunk's landmarks are staged kLandK
+// dimensions at a time in shared memory; the two threads of a row (adjacent
+// lanes) keep its distances to landmarks 0..31 and 32..63 in registers and
+// combine their nearest at the end (ties to the smaller index).
 __global__ void __launch_bounds__(256)
 landmark_key_kernel(const float* __restrict__ Xg, Layout L, uint8_t* __restrict__ key) {
-    __shared__ float sl[kLandmarks][kLandK];
+    constexpr int kHalf = kLandmarks / 2;
+    constexpr int kStride = kLandK + 4;   // 16-byte rows; the two halves' rows start 4 banks apart
+    __shared__ __align__(16) float sl[kLandmarks][kStride];
     const int c = blockIdx.y;
     const int64_t off = L.off[c];
     const int z = (int)(L.off[c + 1] - off);
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    if (blockIdx.x * 256 >= z) return;   // block-uniform
+    const int half = threadIdx.x & 1;
+    const int i = blockIdx.x * 128 + (threadIdx.x >> 1);
+    if (blockIdx.x * 128 >= z) return;   // block-uniform
     const int nl = z < kLandmarks ? z : kLandmarks;
     const bool valid = i < z;
     const float* xr = Xg + (off + (valid ? i : 0)) * L.dp;
-    float acc[kLandmarks];
+    float acc[kHalf];
 #pragma unroll
-    for (int l = 0; l < kLandmarks; ++l) acc[l] = 0.f;
+    for (int l = 0; l < kHalf; ++l) acc[l] = 0.f;
     for (int k0 = 0; k0 < L.dp; k0 += kLandK) {
         const int kc = min(kLandK, L.dp - k0);
         __syncthreads();
+        // landmark h * 32 + l at row 2 l + h: the two halves read different banks
         for (int e = threadIdx.x; e < kLandmarks * kLandK; e += 256) {
             const int l = e / kLandK, k = e % kLandK;
-            sl[l][k] = (l < nl && k < kc) ? Xg[(off + l) * L.dp + k0 + k] : 0.f;
+            sl[2 * (l % kHalf) + l / kHalf][k] = (l < nl && k < kc) ? Xg[(off + l) * L.dp + k0 + k] : 0.f;
         }
         float xv[kLandK];
 #pragma unroll
         for (int k = 0; k < kLandK; ++k) xv[k] = k < kc ? xr[k0 + k] : 0.f;
         __syncthreads();
 #pragma unroll
-        for (int l = 0; l < kLandmarks; ++l) {
+        for (int l = 0; l < kHalf; ++l) {
+            const float4* lm = reinterpret_cast<const float4*>(sl[2 * l + half]);
             float d = 0.f;
 #pragma unroll
-            for (int k = 0; k < kLandK; ++k) {
-                const float t = xv[k] - sl[l][k];
+            for (int k4 = 0; k4 < kLandK / 4; ++k4) {
+                const float4 v = lm[k4];
+                float t = xv[4 * k4] - v.x;
+                d = fmaf(t, t, d);
+                t = xv[4 * k4 + 1] - v.y;
+                d = fmaf(t, t, d);
+                t = xv[4 * k4 + 2] - v.z;
+                d = fmaf(t, t, d);
+                t = xv[4 * k4 + 3] - v.w;
                 d = fmaf(t, t, d);
             }
             acc[l] += d;
         }
     }
-    if (!valid) return;
     float bd = FLT_MAX;
     int bl = 0;
 #pragma unroll
-    for (int l = 0; l < kLandmarks; ++l)
-        if (l < nl && acc[l] < bd) { bd = acc[l]; bl = l; }
-    key[off + i] = (uint8_t)bl;
+    for (int l = 0; l < kHalf; ++l)
+        if (half * kHalf + l < nl && acc[l] < bd) { bd = acc[l]; bl = half * kHalf + l; }
+    const float od = __shfl_xor_sync(0xffffffffu, bd, 1);
+    const int ol = __shfl_xor_sync(0xffffffffu, bl, 1);
+    if (half == 0 && valid) key[off + i] = (uint8_t)(od < bd ? ol : bl);
 }
 
 // One block of kLandmarks threads per chunk.  Thread l holds landmark l's
@@ -285,7 +300,7 @@ chunk_order_kernel(const float* __restrict__ Xg, const uint8_t* __restrict__ key
 cudaError_t launch_locality_order(ptsne_ctx* c, const float* X, const int32_t* perm, cudaStream_t s) {
     cudaError_t e = launch_gather(c, X, perm, s);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((c->zmax + 255) / 256), (unsigned)c->p.n_chunks);
+    const dim3 grid((unsigned)((c->zmax + 127) / 128), (unsigned)c->p.n_chunks);
     landmark_key_kernel<<<grid, 256, 0, s>>>(c->Xg, make_layout(c), c->lkey);
     chunk_order_kernel<<<(unsigned)c->p.n_chunks, kLandmarks, 0, s>>>(c->Xg, c->lkey, perm, make_layout(c),
                                                                         c->perm_loc, c->src_row);

@@ -82,9 +82,9 @@ void free_all(ptsne_ctx* c) {
                     c->acc,    c->gradp,   c->rowz,   c->Zc,             c->ystat,   c->cost_rows,
                     c->cost_chunk, c->cost_hist, c->queue, c->dstats, c->hX,   c->hperms,
                     c->hY,     c->P2,      c->d_ptile_off, c->d_tiles2, c->d_tiles128, c->maxnorm,
-                    c->perm_cur, c->cost_cur, c->dense_rows, c->dense_cnt, c->d_colblk, c->row_dense,
+                    c->perm_cur, c->cost_cur, c->chunk_fp32, c->tflag, c->d_tflag_off, c->row_dense,
                     c->beta_pt, c->d_vsrc, c->d_vbase, c->vperm, c->size_part, c->size_done, c->ycold,
-                    c->perm_loc, c->src_row, c->lkey, c->ptile_nz};
+                    c->perm_loc, c->src_row, c->lkey, c->ptile_nz, c->form_acc, c->form_frac, c->form_fstar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -168,6 +168,12 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     c->p = p;
     c->p.chunk_offsets = nullptr;
     c->npts = p.n;
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        c->num_sms = sms;
+    }
     c->layers = p.layers;
     c->n_elem = p.n_chunks;
     c->p.n = toff[p.n_chunks];   // rows: layers x points
@@ -225,16 +231,16 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         c->tile_start128[nc] = (int64_t)tiles128.size();
         c->ntiles128 = (int64_t)tiles128.size();
     }
-    // 128-column blocks of each chunk (dense window rows)
-    std::vector<TileDesc> colblk;
+    // 64-tile flags of each chunk (window tiles of the dense window rows)
+    std::vector<int64_t> tfoff(nc);
     if (p.precision == PTSNE_PREC_BF16_WINDOW) {
-        c->colblk_start.resize(nc + 1);
+        int64_t acc = 0;
         for (int k = 0; k < nc; ++k) {
-            c->colblk_start[k] = (int64_t)colblk.size();
-            const int nb = (int)((c->off[k + 1] - c->off[k] + 127) / 128);
-            for (int J = 0; J < nb; ++J) colblk.push_back(TileDesc{k, (int16_t)0, (int16_t)J});
+            const int64_t T = (c->off[k + 1] - c->off[k] + kTile - 1) / kTile;
+            tfoff[k] = acc;
+            acc += T * T;
         }
-        c->colblk_start[nc] = (int64_t)colblk.size();
+        c->tflag_total = acc;
     }
     // packed symmetric P: 32 x 32 tiles of each chunk in tournament order
     std::vector<TileDesc2> tiles2;
@@ -290,10 +296,13 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         AL(c->xnorm, n);
         AL(c->d_tiles128, c->ntiles128);
         AL(c->maxnorm, 1);
-        AL(c->dense_rows, n);
-        AL(c->dense_cnt, nc);
         AL(c->row_dense, n);
-        AL(c->d_colblk, (int64_t)colblk.size());
+        AL(c->chunk_fp32, nc);
+        AL(c->tflag, c->tflag_total);
+        AL(c->d_tflag_off, nc);
+        AL(c->form_acc, 2 * kFormBins);
+        AL(c->form_frac, kFormBins);
+        AL(c->form_fstar, 1);
     }
     AL(c->D, m);
     if (p.schedule == PTSNE_SCHED_BATCHED) {
@@ -347,7 +356,13 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
     if (e == cudaSuccess) e = up(c->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size());
     if (e == cudaSuccess && c->ntiles128)
         e = up(c->d_tiles128, tiles128.data(), sizeof(TileDesc) * tiles128.size());
-    if (e == cudaSuccess && !colblk.empty()) e = up(c->d_colblk, colblk.data(), sizeof(TileDesc) * colblk.size());
+    if (e == cudaSuccess && c->tflag) {
+        e = up(c->d_tflag_off, tfoff.data(), sizeof(int64_t) * nc);
+        if (e == cudaSuccess) e = cudaMemset(c->form_acc, 0, sizeof(unsigned long long) * 2 * kFormBins);
+        if (e == cudaSuccess) e = cudaMemset(c->form_frac, 0, sizeof(float) * kFormBins);
+        if (e == cudaSuccess) e = up(c->form_fstar, &c->form_fstar_host, sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(c->chunk_fp32, 0, (size_t)nc);
+    }
     if (e == cudaSuccess && p.layers > 1) {
         e = up(c->d_vsrc, vsrc.data(), sizeof(int32_t) * vsrc.size());
         if (e == cudaSuccess) e = up(c->d_vbase, vbase.data(), sizeof(int32_t) * vbase.size());
@@ -393,7 +408,10 @@ static void mark(ptsne_ctx* c, int k, cudaStream_t s) {
 static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t** perm_io, cudaStream_t s, bool reset_stats,
                            const float* Y_run) {
     if (reset_stats) CK(cudaMemsetAsync(c->dstats, 0, sizeof(DeviceStats), s));
-    const bool mixed = c->p.precision == PTSNE_PREC_BF16_WINDOW;
+    // BF16_WINDOW with a threshold <= 0 puts every chunk in FP32 whole: the
+    // plain FP32 path (the form choice still records its chunks)
+    const bool all_fp32 = c->p.precision == PTSNE_PREC_BF16_WINDOW && c->form_fstar_host <= 0.f;
+    const bool mixed = c->p.precision == PTSNE_PREC_BF16_WINDOW && !all_fp32;
     mark(c, PTSNE_STAGE_GATHER, s);
     c->loc_active = c->locality && c->p.schedule == PTSNE_SCHED_BATCHED;
     if (c->loc_active) {
@@ -414,27 +432,30 @@ static int affinities_impl(ptsne_ctx* c, const float* X, const int32_t** perm_io
         warm = c->beta;
     }
     mark(c, PTSNE_STAGE_DISTANCES, s);
+    // mixed precision: each chunk's form (BF16 Gram + window, or FP32 whole)
+    if (mixed || all_fp32) CK(launch_form_select(c, s));
     if (c->p.schedule == PTSNE_SCHED_BATCHED) {
-        if (mixed) CK(launch_dist_bf16(c, 0, c->ntiles128, s));
+        if (mixed) CK(launch_dist_bf16(c, 0, c->ntiles128, s, c->chunk_fp32));
         else CK(launch_dist_fp32(c, 0, c->ntiles, s));
         mark(c, PTSNE_STAGE_PERPLEXITY, s);
         // mixed precision: a coarse search on d~ only places the windows
-        CK(launch_bisect(c, 0, c->p.n, s, warm, mixed ? 1 : 0));
+        CK(launch_bisect(c, 0, c->p.n, s, warm, mixed ? 1 : 0, mixed ? 1 : 0));
         if (mixed) {
-            // FP32 distances inside each row's window, then the search again from beta~
+            // FP32 distances inside each row's window (and of the FP32 chunks),
+            // then the search again from beta~
             CK(launch_window_recompute(c, 0, c->p.n, s));
-            CK(launch_bisect(c, 0, c->p.n, s, c->beta));
+            CK(launch_bisect(c, 0, c->p.n, s, c->beta, 0, warm ? 2 : 1));
         }
         mark(c, PTSNE_STAGE_JOINT_P, s);
         CK(launch_psym_packed(c, s));
     } else {
         for (int k = 0; k < c->p.n_chunks; ++k) {
-            if (mixed) CK(launch_dist_bf16(c, c->tile_start128[k], c->tile_start128[k + 1], s));
+            if (mixed) CK(launch_dist_bf16(c, c->tile_start128[k], c->tile_start128[k + 1], s, c->chunk_fp32));
             else CK(launch_dist_fp32(c, c->tile_start[k], c->tile_start[k + 1], s));
-            CK(launch_bisect(c, c->off[k], c->off[k + 1], s, warm, mixed ? 1 : 0));
+            CK(launch_bisect(c, c->off[k], c->off[k + 1], s, warm, mixed ? 1 : 0, mixed ? 1 : 0));
             if (mixed) {
                 CK(launch_window_recompute(c, c->off[k], c->off[k + 1], s));
-                CK(launch_bisect(c, c->off[k], c->off[k + 1], s, c->beta));
+                CK(launch_bisect(c, c->off[k], c->off[k + 1], s, c->beta, 0, warm ? 2 : 1));
             }
             CK(launch_psym(c, c->tile_start[k], c->tile_start[k + 1], s));
         }
@@ -742,6 +763,22 @@ int ptsne_get_stats(ptsne_ctx* c, ptsne_stats* out, void* stream) {
     out->bisect_evals = (int64_t)h.bisect_evals;
     out->ptiles_total = c->ntiles2;
     out->ptiles_nonzero = (int64_t)h.ptiles_nonzero;
+    out->fp32_chunks = (int64_t)h.fp32_chunks;
+    out->form_threshold = c->form_fstar ? (double)c->form_fstar_host : 0.0;
+    for (int k = 0; k < 8; ++k) out->window_fraction[k] = 0.0;
+    if (c->form_frac) {   // the last measurement: sums not yet taken by a form choice, else the kept fraction
+        static_assert(kFormBins == 8, "ptsne_stats.window_fraction has 8 bins");
+        float fr[kFormBins];
+        unsigned long long acc[2 * kFormBins];
+        CK(cudaMemcpy(fr, c->form_frac, sizeof fr, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(acc, c->form_acc, sizeof acc, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < kFormBins; ++k)
+            out->window_fraction[k] = acc[2 * k + 1] ? (double)acc[2 * k] / (double)acc[2 * k + 1] : (double)fr[k];
+    }
+    out->form_ms_mixed = c->form_ms[0];
+    out->form_ms_fp32 = c->form_ms[1];
+    out->form_ms_window = c->form_ms[2];
+    out->locality_order = c->locality ? 1 : 0;
     float herr;
     memcpy(&herr, &h.max_herr_bits, sizeof herr);
     out->max_abs_entropy_err = herr;
@@ -750,6 +787,15 @@ int ptsne_get_stats(ptsne_ctx* c, ptsne_stats* out, void* stream) {
         out->stage_ms[k] = c->stage_ms[k];
         out->stage_calls[k] = c->stage_calls[k];
     }
+    return PTSNE_OK;
+}
+
+int ptsne_set_form_threshold(ptsne_ctx* c, double threshold) {
+    if (!c) return PTSNE_EINVAL;
+    if (!c->form_fstar) return fail(c, PTSNE_EINVAL, "the form threshold needs PTSNE_PREC_BF16_WINDOW%s%lld");
+    if (!(threshold == threshold)) return fail(c, PTSNE_EINVAL, "threshold must not be NaN%s%lld");
+    c->form_fstar_host = (float)threshold;
+    CK(cudaMemcpy(c->form_fstar, &c->form_fstar_host, sizeof(float), cudaMemcpyHostToDevice));
     return PTSNE_OK;
 }
 

@@ -30,6 +30,21 @@ struct TileDesc {
     int16_t I, J;
 };
 
+// Which 64 x 64 distance tiles an FP32 pass computes.  chunk_fp32 NULL: every
+// tile.  Otherwise every tile of a chunk with chunk_fp32[c] != 0, and of the
+// other chunks the tiles (I, J) whose flag (I, J) or (J, I) is set in that
+// chunk's T x T flags (T = ceil(z / 64)) at tflag + tflag_off[c].
+struct TileSel {
+    const uint8_t* chunk_fp32 = nullptr;
+    const uint8_t* tflag = nullptr;
+    const int64_t* tflag_off = nullptr;
+};
+
+// Mixed-precision form choice: chunk sizes are split into kFormBins equal
+// bins over [zmin, zmax]; each bin keeps the window fraction of the last
+// affinities (window pairs / (z - 1) per row, summed over its rows).
+constexpr int kFormBins = 8;
+
 // ---- packed symmetric P for the batched iteration kernel ---------------------
 // Each chunk's joint P is stored once per unordered pair of 32-row blocks as
 // 32 x 32 FP32 tiles (row block a <= column block b), in the order of a
@@ -133,7 +148,7 @@ struct DeviceStats {               // device-side counters, reset per affinities
     unsigned int max_herr_bits;    // float bits of max |H - ln perp| (non-negative floats order as ints)
     unsigned int bad_index;        // permutation entries outside [0, n) (skipped)
     unsigned int timeouts;         // bounded device waits that ran out
-    unsigned int pad;
+    unsigned int fp32_chunks;      // mixed precision: chunks whose distances were computed in FP32 whole
     unsigned long long ptiles_nonzero;  // stored P tiles with a nonzero entry (batched schedule)
 };
 
@@ -188,11 +203,18 @@ struct ptsne_ctx {
     unsigned int* maxnorm = nullptr;   // largest |x~| (float bits), for the window bound
     // window rows recomputed whole: per chunk, a list of rows and its length,
     // and the chunks' 128-column blocks (TileDesc{chunk, 0, block})
-    int32_t* dense_rows = nullptr;     // n (chunk c's list starts at off[c])
-    int* dense_cnt = nullptr;          // n_chunks
-    uint8_t* row_dense = nullptr;      // n: 1 = row listed in dense_rows (set by the coarse search)
-    ptsne::TileDesc* d_colblk = nullptr;
-    std::vector<int64_t> colblk_start; // n_chunks + 1
+    uint8_t* row_dense = nullptr;      // n: 1 = the row's window pairs are recomputed by whole tiles
+    // the form of each chunk's distances and the window tiles of the dense rows
+    int num_sms = 0;
+    uint8_t* chunk_fp32 = nullptr;     // n_chunks: 1 = this affinities computes the chunk in FP32 whole
+    uint8_t* tflag = nullptr;          // sum of T^2 over chunks: 64-tiles holding a dense row's window pairs
+    int64_t* d_tflag_off = nullptr;    // n_chunks
+    int64_t tflag_total = 0;
+    unsigned long long* form_acc = nullptr;  // kFormBins x 2: window pairs and (z - 1), summed over rows
+    float* form_frac = nullptr;        // kFormBins: window fraction of each size bin (last measured)
+    float* form_fstar = nullptr;       // 1: chunks whose bin fraction is >= this run in FP32 whole
+    float form_fstar_host = 2.0f;      // host copy (> 1: never)
+    double form_ms[3] = {0, 0, 0};     // autotuner: affinities ms all mixed, all FP32, and the window recompute
     int chunk_of(int64_t r) const {     // chunk holding row r (off is sorted)
         return (int)(std::upper_bound(off.begin(), off.end(), r) - off.begin()) - 1;
     }
@@ -279,7 +301,14 @@ cudaError_t launch_export_P(const ptsne_ctx* c, float* P_out, cudaStream_t s);
 cudaError_t launch_export_dense(const ptsne_ctx* c, const float* src, float* out, cudaStream_t s);
 
 cudaError_t launch_dist_fp32(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
-cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
+cudaError_t launch_dist_fp32_sel(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, const TileSel& sel,
+                                 cudaStream_t s);
+// mixed precision: each chunk's form for this affinities (c->chunk_fp32) from
+// its size bin's last window fraction; clears the tile flags
+cudaError_t launch_form_select(const ptsne_ctx* c, cudaStream_t s);
+// skip (optional, n_chunks): tiles of chunks with skip[c] != 0 are left alone
+cudaError_t launch_dist_bf16(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s,
+                             const uint8_t* skip = nullptr);
 cudaError_t launch_window_recompute(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s);
 // beta_init (optional): start each row's search from this beta instead of 1 / mean(d - m)
 // layers > 1: the caller's permutation (npts entries) -> the virtual one of
@@ -290,7 +319,11 @@ cudaError_t launch_gather_dist(const ptsne_ctx* c, const float* Dfull, int64_t l
 cudaError_t launch_beta_warm(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s);
 cudaError_t launch_beta_keep(const ptsne_ctx* c, const int32_t* perm, cudaStream_t s);
 cudaError_t launch_bisect(const ptsne_ctx* c, int64_t row_begin, int64_t row_end, cudaStream_t s,
-                          const float* beta_init = nullptr, int coarse = 0);
+                          const float* beta_init = nullptr, int coarse = 0, int form = 0);
+// (form 1: mixed precision bookkeeping — the coarse search skips the chunks
+// run in FP32 whole and flags its dense rows' window tiles; both searches add
+// their rows' window sizes to the size-bin fractions.  form 2: the same, and
+// the fine search's beta_init holds a warm start for the FP32 chunks' rows)
 cudaError_t launch_gather_bf16(const ptsne_ctx* c, cudaStream_t s);
 cudaError_t launch_psym(const ptsne_ctx* c, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 

@@ -69,6 +69,13 @@ class Stats(C.Structure):
         ("bisect_evals", C.c_int64),
         ("ptiles_total", C.c_int64),
         ("ptiles_nonzero", C.c_int64),
+        ("fp32_chunks", C.c_int64),
+        ("form_threshold", C.c_double),
+        ("window_fraction", C.c_double * 8),
+        ("form_ms_mixed", C.c_double),
+        ("form_ms_fp32", C.c_double),
+        ("form_ms_window", C.c_double),
+        ("locality_order", C.c_int64),
     ]
 
 
@@ -114,6 +121,8 @@ def lib():
         L.ptsne_reset_counters.argtypes = [vp]
         L.ptsne_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.ptsne_set_locality_order.argtypes = [vp, C.c_int]
+        L.ptsne_set_form_threshold.argtypes = [vp, C.c_double]
+        L.ptsne_autotune_form.argtypes = [vp, vp, vp, vp]
         L.ptsne_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.ptsne_autotune.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_char_p, C.POINTER(TuneTrial), C.c_int32,
                                      C.POINTER(C.c_int32), vp]
@@ -264,10 +273,27 @@ class Context:
     def set_locality_order(self, on: bool):
         return self._check(lib().ptsne_set_locality_order(self.h, int(bool(on))))
 
+    def set_form_threshold(self, threshold: float):
+        """BF16_WINDOW: chunks whose size bin's window fraction is >= threshold
+        are computed in FP32 whole (2: never, negative: always)."""
+        return self._check(lib().ptsne_set_form_threshold(self.h, C.c_double(threshold)))
+
     def tuning(self) -> tuple:
         t = Tuning()
         self._check(lib().ptsne_get_tuning(self.h, C.byref(t)))
         return (t.cluster, t.group, t.consumer_warps)
+
+    def autotune_form(self, X, perm, stream=None):
+        """BF16_WINDOW: time both forms of the distances (and the locality
+        order) on this partition and set the form threshold."""
+        return self._check(lib().ptsne_autotune_form(self.h, _ptr(X), _ptr(perm), _stream(stream)))
+
+    def form_record(self) -> dict:
+        """The form choice of a BF16_WINDOW context, for reports."""
+        st = self.stats()
+        return {"threshold": st.form_threshold, "ms_all_mixed": st.form_ms_mixed, "ms_all_fp32": st.form_ms_fp32,
+                "ms_window": st.form_ms_window, "locality_order": bool(st.locality_order),
+                "window_fraction_by_size_bin": [round(v, 4) for v in st.window_fraction]}
 
     def autotune(self, X, perm, Y, iters=3, cache_path=None, stream=None):
         """Returns [((cluster, group, consumer_warps), ms_per_iter), ...] of the timed trials."""

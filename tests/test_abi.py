@@ -74,6 +74,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.ptsne_affinities(None, None, None, None, None, None) == -1
     assert lib.ptsne_step(None, None, None, None, None, None) == -1
     assert lib.ptsne_run(None, None, None, 1, None, None, None) == -1
+    assert lib.ptsne_set_form_threshold(None, 0.5) == -1
+    assert lib.ptsne_autotune_form(None, None, None, None) == -1
     lib.ptsne_destroy(None)
 
 
