@@ -27,7 +27,11 @@ def dev():
     return torch.device("cuda:0")
 
 
-def test_full_size_bench_configuration(dev):
+@pytest.mark.parametrize("form", ["autotuned", "all_mixed"])
+def test_full_size_bench_configuration(dev, form):
+    """form "autotuned": the distance form ptsne_autotune picks (as the bench
+    runs it); "all_mixed": every chunk through the BF16 Gram matrix, the
+    coarse search and the window recompute."""
     from paper_1812_09869_gb300 import ptsne
     w = synth.workload("uneven-1m-d64", epochs=1)
     sizes = np.diff(w.offsets)
@@ -38,7 +42,10 @@ def test_full_size_bench_configuration(dev):
         Xd = torch.from_numpy(w.X).to(dev)
         pd = torch.from_numpy(perm).to(dev)
         Yd = torch.from_numpy(w.Y0.copy()).to(dev)
-        ctx.autotune(Xd, pd, Yd, iters=3)                      # the bench's launch shape
+        ctx.autotune(Xd, pd, Yd, iters=3)                      # the bench's launch shape and form
+        if form == "all_mixed":
+            ctx.set_form_threshold(2.0)
+            ctx.set_locality_order(False)
         Pd = torch.zeros(int((sizes.astype(np.int64) ** 2).sum()), dtype=torch.float32, device=dev)
         bd = torch.zeros(w.n, dtype=torch.float32, device=dev)
         ctx.affinities(Xd, pd, P_out=Pd, beta_out=bd)
@@ -74,24 +81,28 @@ def test_full_size_bench_configuration(dev):
             assert abs(Z[c] - Zr) <= 1e-6 * Zr
 
 
-@pytest.mark.parametrize("precision", ["bf16_window", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16_window", "bf16_window_autotuned", "fp32"])
 def test_full_size_precision_stress(dev, precision):
     """The precision-stress workload at full size: 200,000 sparse image-like
     vectors (D = 784, ~80% zeros, values in [0, 1]) in 64 chunks of 3125, with
     the BF16 tensor-core Gram matrix, FP32 window recompute and FP64 redo of
-    stalled rows (and, for comparison, FP32 distances throughout).  Three
-    chunks (first, middle, last) against the FP64 oracle element by element;
-    the errors are printed for the record."""
+    stalled rows ("bf16_window": every chunk mixed in the caller's row order;
+    "bf16_window_autotuned": the form and locality order ptsne_autotune_form
+    picks, as the bench runs it), and for comparison FP32 distances
+    throughout.  Three chunks (first, middle, last) against the FP64 oracle
+    element by element; the errors are printed for the record."""
     from paper_1812_09869_gb300 import ptsne
     w = synth.workload("sparse-200k-d784", epochs=1)
     sizes = np.diff(w.offsets)
     cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
-                       momentum=w.momentum, precision=precision, schedule="batched")
+                       momentum=w.momentum, precision=precision.replace("_autotuned", ""), schedule="batched")
     perm = w.perms[0]
     with ptsne.Context(cfg) as ctx:
         Xd = torch.from_numpy(w.X).to(dev)
         pd = torch.from_numpy(perm).to(dev)
         Yd = torch.from_numpy(w.Y0.copy()).to(dev)
+        if precision.endswith("_autotuned"):
+            ctx.autotune_form(Xd, pd)
         Pd = torch.zeros(int((sizes.astype(np.int64) ** 2).sum()), dtype=torch.float32, device=dev)
         bd = torch.zeros(w.n, dtype=torch.float32, device=dev)
         ctx.affinities(Xd, pd, P_out=Pd, beta_out=bd)
@@ -117,5 +128,6 @@ def test_full_size_precision_stress(dev, precision):
         print(f"\n[precision stress {precision}] max over chunks 0, 32, 63: P {errs['P']:.2e} (of row max / "
               f"relative), beta {errs['beta']:.2e}, gradient {errs['grad']:.2e}, Z {errs['Z']:.2e}; "
               f"max |H - ln perp| {st.max_abs_entropy_err:.2e} nats; FP64 rows {st.bisect_fp64_rows}, "
-              f"window pairs {st.window_pairs}")
+              f"window pairs {st.window_pairs}, FP32-whole chunks {st.fp32_chunks}, locality order "
+              f"{st.locality_order}")
         assert errs["P"] <= P_TOL and errs["beta"] <= 1e-4 and errs["grad"] <= GRAD_TOL and errs["Z"] <= 1e-6, errs
