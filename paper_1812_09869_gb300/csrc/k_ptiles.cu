@@ -9,8 +9,11 @@ namespace ptsne {
 // Joint P (Eq. 3) of one stored 32 x 32 tile, written in the packed order:
 //   p_ij = (exp(-beta_i (d_ij - m_i)) / S_i + exp(-beta_j (d_ji - m_j)) / S_j) / (2z),
 // zero on the diagonal and outside the chunk.  D need not be symmetric: after
-// the window recompute each row holds its own exact entries.
-__global__ void __launch_bounds__(256)
+// the window recompute each row holds its own exact entries.  128 threads per
+// tile (thread: rows r and r + 16, four columns), so that 16 tiles' chains of
+// dependent loads are in flight per SM.
+constexpr int kPsymThreads = 128;
+__global__ void __launch_bounds__(kPsymThreads, 16)
 psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L, const int64_t* __restrict__ ptile_off,
                    const TileDesc2* __restrict__ tiles, int64_t t0, const float* __restrict__ beta,
                    const float* __restrict__ mrow, const float* __restrict__ Srow, uint8_t* __restrict__ nz_out) {
@@ -20,8 +23,7 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
     const int64_t off = L.off[c];
     const int z = (int)(L.off[c + 1] - off);
     const int ld = L.ld[c];
-    const int tid = threadIdx.x, r = tid >> 3, c4 = tid & 7;
-    const int i = td.a * kPT + r;
+    const int tid = threadIdx.x, r0 = tid >> 3, c4 = tid & 7;
     const int j0 = td.b * kPT + c4 * 4;
     // the (b, a) block of D, transposed: dT[jj][ii] = d_{j i}, so that each
     // conditional of Eq. 3 is taken from its own row of D
@@ -41,46 +43,59 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
         pm[side][k] = m;
         ps[side][k] = si;
     }
-    // both 16-byte loads of D are issued before the barrier
+    // all four 16-byte loads of D are issued before the barrier
     const float* Dc = D + L.moff[c];
-    float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < z) dv = *reinterpret_cast<const float4*>(Dc + (int64_t)i * ld + j0);
-    {
-        const int jr = td.b * kPT + r;
+    float4 dv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = td.a * kPT + r0 + 16 * h;
+        dv[h] = i < z ? *reinterpret_cast<const float4*>(Dc + (int64_t)i * ld + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int rr = r0 + 16 * h, jr = td.b * kPT + rr;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (jr < z) v = *reinterpret_cast<const float4*>(Dc + (int64_t)jr * ld + td.a * kPT + c4 * 4);
-        dT[r][c4 * 4 + 0] = v.x; dT[r][c4 * 4 + 1] = v.y; dT[r][c4 * 4 + 2] = v.z; dT[r][c4 * 4 + 3] = v.w;
+        dT[rr][c4 * 4 + 0] = v.x; dT[rr][c4 * 4 + 1] = v.y; dT[rr][c4 * 4 + 2] = v.z; dT[rr][c4 * 4 + 3] = v.w;
     }
     __syncthreads();
-    float out[4] = {0.f, 0.f, 0.f, 0.f};
-    if (i < z) {
-        const float d4[4] = {dv.x, dv.y, dv.z, dv.w};
-        const float bi = pb[0][r], mi = pm[0][r], si = ps[0][r];
-        const float inv2z = 1.0f / (2.0f * (float)z);
+    __shared__ __align__(16) float ot[kPTileFloats];
+    const float inv2z = 1.0f / (2.0f * (float)z);
+    bool any = false;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = j0 + e;
-            if (j < z && j != i) {
-                const int jj = c4 * 4 + e;
-                const float bj = pb[1][jj], mj = pm[1][jj], sj = ps[1][jj];
-                // explicitly rounded: the two halves of a diagonal tile round identically
-                const float cij = __fmul_rn(hw_ex2(-bi * (d4[e] - mi)), si);
-                const float cji = __fmul_rn(hw_ex2(-bj * (dT[c4 * 4 + e][r] - mj)), sj);
-                out[e] = __fmul_rn(__fadd_rn(cij, cji), inv2z);
+    for (int h = 0; h < 2; ++h) {
+        const int r = r0 + 16 * h, i = td.a * kPT + r;
+        float out[4] = {0.f, 0.f, 0.f, 0.f};
+        if (i < z) {
+            const float d4[4] = {dv[h].x, dv[h].y, dv[h].z, dv[h].w};
+            const float bi = pb[0][r], mi = pm[0][r], si = ps[0][r];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = j0 + e;
+                if (j < z && j != i) {
+                    const int jj = c4 * 4 + e;
+                    const float bj = pb[1][jj], mj = pm[1][jj], sj = ps[1][jj];
+                    // explicitly rounded: the two halves of a diagonal tile round identically
+                    const float cij = __fmul_rn(hw_ex2(-bi * (d4[e] - mi)), si);
+                    const float cji = __fmul_rn(hw_ex2(-bj * (dT[jj][r] - mj)), sj);
+                    out[e] = __fmul_rn(__fadd_rn(cij, cji), inv2z);
+                }
             }
         }
-    }
-    // reorder through shared memory into the stored order, then write the
-    // tile with coalesced 16-byte stores
-    __shared__ __align__(16) float ot[kPTileFloats];
+        // reorder through shared memory into the stored order
 #pragma unroll
-    for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e, L.od)] = out[e];
+        for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e, L.od)] = out[e];
+        any = any || out[0] != 0.f || out[1] != 0.f || out[2] != 0.f || out[3] != 0.f;
+    }
     // a tile whose every entry is exactly zero (far pairs: the FP32
     // exponentials underflow) is flagged (counted by ptsne_get_stats)
-    const int nz = __syncthreads_or(out[0] != 0.f || out[1] != 0.f || out[2] != 0.f || out[3] != 0.f);
+    const int nz = __syncthreads_or(any);
     const int64_t gt = ptile_off[c] + td.pos;
     float* dst = P2 + gt * kPTileStride;
-    reinterpret_cast<float4*>(dst)[tid] = reinterpret_cast<const float4*>(ot)[tid];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)   // coalesced 16-byte stores of the tile
+        reinterpret_cast<float4*>(dst)[tid + kPsymThreads * h] =
+            reinterpret_cast<const float4*>(ot)[tid + kPsymThreads * h];
     if (tid == 0) {   // trailer: the tile's row and column blocks and its flag
         *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, nz, 0);
         nz_out[gt] = (uint8_t)nz;
@@ -122,7 +137,7 @@ cudaError_t launch_psym_packed(const ptsne_ctx* c, cudaStream_t s) {
     int k = 0;
     for (int64_t b = 0; b < c->ntiles2; b += 2147483647LL, ++k) {
         const int64_t cnt = (c->ntiles2 - b) < 2147483647LL ? (c->ntiles2 - b) : 2147483647LL;
-        psym_packed_kernel<<<(unsigned)cnt, 256, 0, s>>>(c->D, c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2, b,
+        psym_packed_kernel<<<(unsigned)cnt, kPsymThreads, 0, s>>>(c->D, c->P2, make_layout(c), c->d_ptile_off, c->d_tiles2, b,
                                                          c->beta, c->mrow, c->Srow, c->ptile_nz);
     }
     return launched(c, k);

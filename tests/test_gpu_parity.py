@@ -239,6 +239,42 @@ def test_multi_epoch_run_matches_oracle_cost(dev):
     assert np.all(kl2 >= lo * (1 - KL_TOL)) and np.all(kl2 <= hi * (1 + KL_TOL)), (cost, ens)
 
 
+def test_run_resumes_from_a_saved_map(dev):
+    """Checkpoint and resume: the state a run carries between epochs is the
+    map (and, within a context, each point's last beta as the next search's
+    start).  A call's first epoch equals the first epoch of a longer call,
+    and the epoch after a checkpoint is the same whether the run continues in
+    its context or resumes in a fresh one from the saved map (whose searches
+    start cold).  Only FP32 rounding differs (the iteration kernel's atomic
+    order, the searches' starting points); the chaotic trajectory amplifies
+    it to ~1% within two epochs here, so each comparison spans one epoch
+    from the same map."""
+    X, _ = synth.gaussian_mixture(4000, 20, 8, seed=45, anisotropic=True)
+    off = synth.equal_chunk_offsets(4000, 4)
+    perms = synth.permutations(4000, 4, seed=46)
+    Y0 = synth.init_gaussian(4000, 2, 1e-4, seed=47)
+    Xd, Pd = torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev)
+    ctx = _ctx(X, off, perplexity=30.0, iters=60)
+    Yd = torch.from_numpy(Y0.copy()).to(dev)
+    c4 = np.zeros((4, 3))
+    ctx.run(Xd, Pd, 4, Yd, cost_out=c4)
+    ctx.close()
+    ctx = _ctx(X, off, perplexity=30.0, iters=60)
+    Yd = torch.from_numpy(Y0.copy()).to(dev)
+    a, b = np.zeros((2, 3)), np.zeros((1, 3))
+    ctx.run(Xd, Pd[0:2], 2, Yd, cost_out=a)
+    saved = Yd.cpu().numpy().copy()                      # the checkpoint
+    ctx.run(Xd, Pd[2:3], 1, Yd, cost_out=b)             # continued in its context
+    ctx.close()
+    ctx = _ctx(X, off, perplexity=30.0, iters=60)
+    Yr = torch.from_numpy(saved).to(dev)
+    r = np.zeros((1, 3))
+    ctx.run(Xd, Pd[2:3], 1, Yr, cost_out=r)             # resumed in a fresh context
+    ctx.close()
+    assert np.allclose(a[0], c4[0], rtol=1e-3, atol=0), (a, c4)   # the map's extent moves ~1e-4
+    assert np.allclose(r, b, rtol=1e-3, atol=0), (r, b)
+
+
 def test_batched_iterations_equal_plain_per_chunk_form(dev):
     """The batched kernel (packed symmetric P, one launch for all iterations)
     and the plain per-chunk kernels (dense P, three launches per iteration)
