@@ -34,6 +34,13 @@ constexpr float kTolBeta = 3e-6f;
 constexpr double kTol64 = 1e-9;        // FP64 fallback tolerance
 constexpr int kMaxEval32 = 64;
 constexpr int kMaxEval64 = 200;
+// FP64 redo: an entry with b t > 40 weighs e^-40 < 2^-57 of the row's largest
+// (t = 0), so the sums cannot see it; the entries with b0 t <= 60 at the
+// redo's starting beta b0 are compacted once and stand for the row while
+// b >= (2/3) b0 (then every entry with b t <= 40 is among them).
+constexpr double kNear64 = 60.0;
+constexpr double kNearKeep = 2.0 / 3.0;
+constexpr int kNearMax = 1024;
 }  // namespace
 
 // Mixed-precision bookkeeping of a search (all NULL: none): the chunks
@@ -243,6 +250,8 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
     __shared__ float s_bc[4];    // warp 0's decision: next beta, S, f, state
     __shared__ double redd3[kGroup / 32][3];
     __shared__ double s_bd[4];   // the same for the FP64 search
+    __shared__ float s_near[kNearMax];   // FP64 redo: the row's entries that can matter
+    __shared__ int s_wcnt[kGroup / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float ln_perp = (float)ln_perp_d;
     if (tid < 2 * kFormBins) s_form[tid >> 1][tid & 1] = 0ull;
@@ -378,14 +387,50 @@ bisect_group_kernel(const float* __restrict__ D, Layout L, int64_t r0, int64_t r
                 // takes the step
                 fp64 = true;
                 double b = beta, blo = 0.0, bhi = INFINITY, fd = INFINITY, Sd = 0.0;
+                // compact the entries that can matter (in thread order: deterministic)
+                const double b0 = b;
+                int mine = 0;
+#pragma unroll
+                for (int k = 0; k < VPT; ++k)
+                    mine += (t[k] < kBig && b0 * (double)t[k] <= kNear64) ? 1 : 0;
+                int incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                if (lane == 31) s_wcnt[warp] = incl;
+                __syncthreads();
+                int nnear = 0, wbase = 0;
+#pragma unroll
+                for (int w = 0; w < kGroup / 32; ++w) {
+                    wbase += w < warp ? s_wcnt[w] : 0;
+                    nnear += s_wcnt[w];
+                }
+                const bool compact = nnear <= kNearMax;
+                if (compact) {
+                    int pos = wbase + incl - mine;
+#pragma unroll
+                    for (int k = 0; k < VPT; ++k)
+                        if (t[k] < kBig && b0 * (double)t[k] <= kNear64) s_near[pos++] = t[k];
+                }
+                __syncthreads();
                 for (int it = 0; it < kMaxEval64; ++it) {
                     double sS = 0.0, sT1 = 0.0, sT2 = 0.0;
+                    if (compact && b >= kNearKeep * b0) {   // block-uniform
+                        for (int k = tid; k < nnear; k += kGroup) {
+                            const double tk = (double)s_near[k];
+                            const double e = exp(-b * tk);
+                            sS += e; sT1 += tk * e; sT2 += tk * tk * e;
+                        }
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < VPT; ++k) {
-                        if (4 * kGroup * (k / 4) >= z) break;
-                        if (t[k] >= kBig) continue;
-                        const double e = exp(-b * (double)t[k]);
-                        sS += e; sT1 += (double)t[k] * e; sT2 += (double)t[k] * t[k] * e;
+                        for (int k = 0; k < VPT; ++k) {
+                            if (4 * kGroup * (k / 4) >= z) break;
+                            if (t[k] >= kBig) continue;
+                            const double e = exp(-b * (double)t[k]);
+                            sS += e; sT1 += (double)t[k] * e; sT2 += (double)t[k] * t[k] * e;
+                        }
                     }
                     sS = warp_sum(sS);
                     sT1 = warp_sum(sT1);
