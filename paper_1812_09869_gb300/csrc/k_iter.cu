@@ -3,8 +3,9 @@
 //
 // One persistent launch runs every iteration of every chunk of an epoch.  A
 // chunk is owned by a cluster of K blocks (K = 1, 2 or 4); the chunk's map
-// lives in every block's shared memory and each block takes every K-th tile
-// of the chunk's stored tiles.  Within a block:
+// lives in every block's shared memory and each block takes a contiguous
+// K-th of the chunk's stored tiles (stored row block by row block).  Within
+// a block:
 //   - one producer warp streams the block's P tiles (4 KB each, stored once
 //     per unordered pair of 32-row blocks) from HBM into a ring of shared
 //     buffers with cp.async.bulk, one tile per lane in batches of 8 (at most
@@ -17,6 +18,9 @@
 //     A and w^2 (y_i - y_j) of R go to row i and, negated, to row j (column
 //     sums travel around rings of lanes, see the tile evaluation below), and
 //     2 w to Z; a diagonal tile holds both orders and is evaluated row-wise.
+//     For 2-D maps a warp keeps the row sums of its current row block in
+//     registers across its tiles and adds them to the accumulators when the
+//     row block changes;
 //     So P is read once per unordered pair (2 bytes per ordered pair) and w is
 //     computed once per unordered pair.  Packed f32x2 arithmetic for 2-D
 //     maps; the sums are merged into shared-memory accumulators with atomic
@@ -257,81 +261,42 @@ __device__ __forceinline__ float keep_row(float mine0, float mine1, int h) {
     return keep + __shfl_xor_sync(0xffffffffu, give, 16);
 }
 
-// Gradient sums of one tile, 2-D maps (packed f32x2 over the two columns of a
-// step).  Lane L = 8 q + g holds rows 4g .. 4g+3 of block a (the map's column
+// Gradient sums of 2-D maps (packed f32x2 over the two columns of a step).
+// Lane L = 8 q + g holds rows 4g .. 4g+3 of row block a (the map's column
 // pairs 2g and 2g + 1) and meets the 8 columns of ring q of block b as the
 // natural column pairs (g / 2 + s) & 3, s = 0..3, each read as one float4
-// (x, x', y, y').  Off-diagonal tile: the column packet of a step (the sums of
-// its two columns over the lane's four rows) moves two lanes down the ring
-// after each step (lane g receives from lane g + 2), so it meets the four
-// lanes of one parity; lanes g and g ^ 1 end with the two partial packets of
-// pair (g / 2 - 1) & 3 and each keeps one column.  The row sums of the four
-// rings are reduced over lanes g, g + 8, g + 16, g + 24, each keeping one row.
-// Adds A and R into acc, returns the lane's sum of w (both orders of each pair
-// of an off-diagonal tile).
-template <bool SYM>
-__device__ __forceinline__ float tile_grad_2d(const float* map, int zcap, int a, int b, int lane,
-                                              const float4 (&pv)[8], float* acc) {
+// (x, x', y, y').  A warp keeps the row sums of its current row block across
+// the tiles it takes in a row (the stored tiles come row block by row block,
+// so consecutive tiles of a warp often share a) and adds them to acc when the
+// row block changes or the pass ends (rows2_flush).
+struct Rows2 {
+    f2 OX[4], OY[4];                     // the lane's four rows, duplicated into both halves
+    f2 AX[4], AY[4], RX[4], RY[4];       // their partial sums over the columns met so far
+};
+
+__device__ __forceinline__ void rows2_begin(Rows2& R, const float* map, int a, int lane) {
     const float4* mp = reinterpret_cast<const float4*>(map);
-    const int g = lane & 7, q = lane >> 3, u = g >> 1;
+    const int g = lane & 7;
     const float4 o0 = mp[a * 16 + 2 * g], o1 = mp[a * 16 + 2 * g + 1];
-    const f2 OX[4] = {pk(o0.x, o0.x), pk(o0.y, o0.y), pk(o1.x, o1.x), pk(o1.y, o1.y)};
-    const f2 OY[4] = {pk(o0.z, o0.z), pk(o0.w, o0.w), pk(o1.z, o1.z), pk(o1.w, o1.w)};
-    const f2 ONE = pk(1.f, 1.f);
-    f2 AX[4] = {0, 0, 0, 0}, AY[4] = {0, 0, 0, 0}, RX[4] = {0, 0, 0, 0}, RY[4] = {0, 0, 0, 0}, Z = 0;
-    f2 CAX = 0, CAY = 0, CRX = 0, CRY = 0;   // column packet (SYM)
-    const int nxt = (lane & 24) | ((g + 2) & 7);
-    const float4* cbase = mp + b * 16 + 4 * q;
+    R.OX[0] = pk(o0.x, o0.x); R.OX[1] = pk(o0.y, o0.y); R.OX[2] = pk(o1.x, o1.x); R.OX[3] = pk(o1.y, o1.y);
+    R.OY[0] = pk(o0.z, o0.z); R.OY[1] = pk(o0.w, o0.w); R.OY[2] = pk(o1.z, o1.z); R.OY[3] = pk(o1.w, o1.w);
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const float4 cv = cbase[(u + s) & 3];
-        const f2 XC = pk(cv.x, cv.y), YC = pk(cv.z, cv.w);
-        const f2 P[4] = {pk(pv[2 * s].x, pv[2 * s].y), pk(pv[2 * s].z, pv[2 * s].w),
-                         pk(pv[2 * s + 1].x, pv[2 * s + 1].y), pk(pv[2 * s + 1].z, pv[2 * s + 1].w)};
-        f2 DX[4], DY[4], W[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            DX[r] = sub2(OX[r], XC);   // own - other
-            DY[r] = sub2(OY[r], YC);
-            f2 Q = fma2(DX[r], DX[r], ONE);
-            Q = fma2(DY[r], DY[r], Q);
-            float q0, q1;
-            upk(Q, q0, q1);
-            W[r] = pk(hw_rcp(q0), hw_rcp(q1));
-        }
-        Z = add2(Z, add2(add2(W[0], W[1]), add2(W[2], W[3])));
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const f2 PW = mul2(P[r], W[r]), WW = mul2(W[r], W[r]);
-            AX[r] = fma2(PW, DX[r], AX[r]);
-            AY[r] = fma2(PW, DY[r], AY[r]);
-            RX[r] = fma2(WW, DX[r], RX[r]);
-            RY[r] = fma2(WW, DY[r], RY[r]);
-            if constexpr (SYM) {
-                CAX = fma2(PW, DX[r], CAX);
-                CAY = fma2(PW, DY[r], CAY);
-                CRX = fma2(WW, DX[r], CRX);
-                CRY = fma2(WW, DY[r], CRY);
-            }
-        }
-        if constexpr (SYM) {
-            if (s < 3) {
-                CAX = shfl_f2(CAX, nxt);
-                CAY = shfl_f2(CAY, nxt);
-                CRX = shfl_f2(CRX, nxt);
-                CRY = shfl_f2(CRY, nxt);
-            }
-        }
-    }
-    // rows: ring q keeps row 4g + 2 (q >> 1) + (q & 1) of the four rings' sums
+    for (int r = 0; r < 4; ++r) R.AX[r] = R.AY[r] = R.RX[r] = R.RY[r] = 0ull;
+}
+
+// The row sums of the four rings are reduced over lanes g, g + 8, g + 16,
+// g + 24, each keeping one row, and added to acc.
+__device__ __forceinline__ void rows2_flush(const Rows2& R, int zcap, int a, int lane, float* acc) {
+    const int g = lane & 7, q = lane >> 3;
     float v[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        v[r][0] = hsum2(AX[r]);
-        v[r][1] = hsum2(AY[r]);
-        v[r][2] = hsum2(RX[r]);
-        v[r][3] = hsum2(RY[r]);
+        v[r][0] = hsum2(R.AX[r]);
+        v[r][1] = hsum2(R.AY[r]);
+        v[r][2] = hsum2(R.RX[r]);
+        v[r][3] = hsum2(R.RY[r]);
     }
+    // ring q keeps row 4g + 2 (q >> 1) + (q & 1) of the four rings' sums
     const bool hi = q >= 2, odd = q & 1;
     float w2[2][4];
 #pragma unroll
@@ -348,6 +313,67 @@ __device__ __forceinline__ float tile_grad_2d(const float* map, int zcap, int a,
         const float keep = odd ? w2[1][k] : w2[0][k];
         const float give = odd ? w2[0][k] : w2[1][k];
         atomicAdd(acc + k * zcap + row, keep + __shfl_xor_sync(0xffffffffu, give, 8));
+    }
+}
+
+// One tile (rows of R's block, columns of block b).  Off-diagonal tile: the
+// column packet of a step (the sums of its two columns over the lane's four
+// rows) moves two lanes down the ring after each step (lane g receives from
+// lane g + 2), so it meets the four lanes of one parity; lanes g and g ^ 1
+// end with the two partial packets of pair (g / 2 - 1) & 3, each keeps one
+// column and adds it to acc.  Diagonal tile: both orders are stored, rows
+// only.  Returns the lane's sum of w (both orders of each pair of an
+// off-diagonal tile).
+template <bool SYM>
+__device__ __forceinline__ float tile_grad_2d(Rows2& R, const float* map, int zcap, int b, int lane,
+                                              const float4 (&pv)[8], float* acc) {
+    const float4* mp = reinterpret_cast<const float4*>(map);
+    const int g = lane & 7, q = lane >> 3, u = g >> 1;
+    const f2 ONE = pk(1.f, 1.f);
+    f2 Z = 0;
+    f2 CAX = 0, CAY = 0, CRX = 0, CRY = 0;   // column packet (SYM)
+    const int nxt = (lane & 24) | ((g + 2) & 7);
+    const float4* cbase = mp + b * 16 + 4 * q;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float4 cv = cbase[(u + s) & 3];
+        const f2 XC = pk(cv.x, cv.y), YC = pk(cv.z, cv.w);
+        const f2 P[4] = {pk(pv[2 * s].x, pv[2 * s].y), pk(pv[2 * s].z, pv[2 * s].w),
+                         pk(pv[2 * s + 1].x, pv[2 * s + 1].y), pk(pv[2 * s + 1].z, pv[2 * s + 1].w)};
+        f2 DX[4], DY[4], W[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            DX[r] = sub2(R.OX[r], XC);   // own - other
+            DY[r] = sub2(R.OY[r], YC);
+            f2 Q = fma2(DX[r], DX[r], ONE);
+            Q = fma2(DY[r], DY[r], Q);
+            float q0, q1;
+            upk(Q, q0, q1);
+            W[r] = pk(hw_rcp(q0), hw_rcp(q1));
+        }
+        Z = add2(Z, add2(add2(W[0], W[1]), add2(W[2], W[3])));
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const f2 PW = mul2(P[r], W[r]), WW = mul2(W[r], W[r]);
+            R.AX[r] = fma2(PW, DX[r], R.AX[r]);
+            R.AY[r] = fma2(PW, DY[r], R.AY[r]);
+            R.RX[r] = fma2(WW, DX[r], R.RX[r]);
+            R.RY[r] = fma2(WW, DY[r], R.RY[r]);
+            if constexpr (SYM) {
+                CAX = fma2(PW, DX[r], CAX);
+                CAY = fma2(PW, DY[r], CAY);
+                CRX = fma2(WW, DX[r], CRX);
+                CRY = fma2(WW, DY[r], CRY);
+            }
+        }
+        if constexpr (SYM) {
+            if (s < 3) {
+                CAX = shfl_f2(CAX, nxt);
+                CAY = shfl_f2(CAY, nxt);
+                CRX = shfl_f2(CRX, nxt);
+                CRY = shfl_f2(CRY, nxt);
+            }
+        }
     }
     if constexpr (SYM) {
         const int oddg = g & 1;
@@ -526,10 +552,13 @@ __device__ __forceinline__ void tile_cost(const float* map, int zcap, int a, int
 // so consecutive tiles of a stream mostly lie in one round and touch disjoint
 // row blocks); the K streams differ in length by at most one tile.
 struct Stream {
-    int nq;      // tiles per pass
+    int first, nq;   // this block's tiles of the chunk: stored tiles first .. first + nq - 1, per pass
     __device__ Stream(int nb, uint32_t rank, uint32_t K) {
-        const int total = nb * (nb + 1) / 2;
-        nq = total > (int)rank ? (total - 1 - (int)rank) / (int)K + 1 : 0;
+        // contiguous shares (counts differ by at most one tile), so that a
+        // warp's consecutive tiles share their row block as often as possible
+        const long long total = (long long)nb * (nb + 1) / 2;
+        first = (int)(total * rank / K);
+        nq = (int)(total * (rank + 1) / K) - first;
     }
 };
 
@@ -572,6 +601,8 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
     const float w_ii = hw_rcp(1.0f);
     const bool diag_lane = OD == 2 ? (lane >> 3) == ((lane & 7) >> 1) : (lane >> 4) == ((lane & 15) >> 3);
     constexpr float kDiagPairs = OD == 2 ? 4.0f : 2.0f;
+    Rows2 R;          // 2-D gradient pass: the row sums of row block cur_a
+    int cur_a = -1;
     for (; cur.q < qend; cur.advance_ring(nslots, ring_n)) {
         // The ring holds a whole number of consumer slots, so tile q - ring
         // (this buffer's previous use) belonged to this same slot and was
@@ -599,10 +630,18 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
         const float drop = diag && diag_lane ? kDiagPairs * w_ii : 0.0f;
         if constexpr (!COST) {
             float zl;
-            if constexpr (OD == 2) zl = diag ? tile_grad_2d<false>(map, zcap, a, b, lane, pv, acc)
-                                             : tile_grad_2d<true>(map, zcap, a, b, lane, pv, acc);
-            else zl = diag ? tile_grad_3d<false>(map, zcap, a, b, lane, pv, acc)
-                           : tile_grad_3d<true>(map, zcap, a, b, lane, pv, acc);
+            if constexpr (OD == 2) {
+                if (a != cur_a) {   // warp-uniform: a new row block
+                    if (cur_a >= 0) rows2_flush(R, zcap, cur_a, lane, acc);
+                    rows2_begin(R, map, a, lane);
+                    cur_a = a;
+                }
+                zl = diag ? tile_grad_2d<false>(R, map, zcap, b, lane, pv, acc)
+                          : tile_grad_2d<true>(R, map, zcap, b, lane, pv, acc);
+            } else {
+                zl = diag ? tile_grad_3d<false>(map, zcap, a, b, lane, pv, acc)
+                          : tile_grad_3d<true>(map, zcap, a, b, lane, pv, acc);
+            }
             part[0].add(zl - drop);
         } else {
             float cs[4];
@@ -618,6 +657,9 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
             part[2].add(cs[1]);
             part[3].add(cs[2]);
         }
+    }
+    if constexpr (OD == 2 && !COST) {
+        if (cur_a >= 0) rows2_flush(R, zcap, cur_a, lane, acc);
     }
 }
 
@@ -743,7 +785,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                         const uint32_t buf = t % ring_n, ph = q0ph ^ ((t / ring_n) & 1u);
                         // a copy is issued only into a buffer known to be released
                         if (mbar_wait(empty_a + 8 * buf, ph ^ 1u, A.timeouts, &s_fail)) {
-                            const float* src = P2c + ((int64_t)rank + (int64_t)K * s) * kPTileStride;
+                            const float* src = P2c + ((int64_t)S.first + s) * kPTileStride;
                             mbar_expect_tx(full_a + 8 * buf, kTileBytes);
                             bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
                             issued = true;
@@ -752,7 +794,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                             // now, so that its copy, issued once this one is consumed,
                             // is served from L2 rather than from HBM
                             const int sn = (s + A.ring) % S.nq;
-                            bulk_prefetch_l2(P2c + ((int64_t)rank + (int64_t)K * sn) * kPTileStride, kTileBytes);
+                            bulk_prefetch_l2(P2c + ((int64_t)S.first + sn) * kPTileStride, kTileBytes);
                         } else {
                             atomicAdd(A.timeouts, 1u);
                         }

@@ -242,22 +242,19 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         }
         c->tflag_total = acc;
     }
-    // packed symmetric P: 32 x 32 tiles of each chunk in tournament order
+    // packed symmetric P: the 32 x 32 tiles (a <= b) of each chunk, row block
+    // by row block
     std::vector<TileDesc2> tiles2;
     std::vector<int64_t> ptoff(nc);
     if (p.schedule == PTSNE_SCHED_BATCHED) {
         int64_t acc2 = 0;
         for (int k = 0; k < nc; ++k) {
             const int nb = (int)((c->off[k + 1] - c->off[k] + kPT - 1) / kPT);
-            const TourSched T(nb);
             ptoff[k] = acc2;
-            for (int r = 0; r < T.rounds(); ++r)
-                for (int q = 0; q < T.tiles_in_round(r); ++q) {
-                    int a, b;
-                    T.pair(r, q, a, b);
-                    tiles2.push_back(TileDesc2{k, (int16_t)a, (int16_t)b, (int32_t)(T.round_base(r) + q)});
-                }
-            acc2 += T.total_tiles();
+            int32_t pos = 0;
+            for (int a = 0; a < nb; ++a)
+                for (int b = a; b < nb; ++b) tiles2.push_back(TileDesc2{k, (int16_t)a, (int16_t)b, pos++});
+            acc2 += (int64_t)nb * (nb + 1) / 2;
         }
         c->ntiles2 = acc2;
     }

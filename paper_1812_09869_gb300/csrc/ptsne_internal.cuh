@@ -47,13 +47,12 @@ constexpr int kFormBins = 8;
 
 // ---- packed symmetric P for the batched iteration kernel ---------------------
 // Each chunk's joint P is stored once per unordered pair of 32-row blocks as
-// 32 x 32 FP32 tiles (row block a <= column block b), in the order of a
-// round-robin tournament over the chunk's nb row blocks: in every round each
-// block meets exactly one partner (or its own diagonal tile), so one pass over
-// the tiles in storage order touches every block once per round.  Inside a
-// tile the 1024 values are ordered for the warp that evaluates it (see
-// packed_index, which depends on the map's dimension): lane L owns 32
-// consecutive floats, read as 8 float4.
+// 32 x 32 FP32 tiles (row block a <= column block b), row block by row block
+// (a = 0: b = 0, 1, ..., then a = 1: b = 1, 2, ...), so that the tiles a warp
+// takes from the stream often share their row block.  Inside a tile the 1024
+// values are ordered for the warp that evaluates it (see packed_index, which
+// depends on the map's dimension): lane L owns 32 consecutive floats, read as
+// 8 float4.
 constexpr int kPT = 32;                      // packed tile edge
 constexpr int kPTileFloats = kPT * kPT;      // 1024 floats = 4 KB of P
 // Stored tile: the 4 KB of P followed by a 16-byte trailer {a, b, 0, 0} (int
@@ -65,33 +64,6 @@ struct TileDesc2 {
     int32_t chunk;
     int16_t a, b;      // row block a <= column block b
     int32_t pos;       // tile index inside the chunk's packed block
-};
-
-// Tournament schedule of nb row blocks (circle method).  For odd nb a dummy
-// player makes nb + 1 players: nb rounds of (nb + 1) / 2 tiles, the block
-// paired with the dummy taking its diagonal tile.  For even nb: nb - 1 pair
-// rounds of nb / 2 tiles, then one round of the nb diagonal tiles.
-struct TourSched {
-    int nb, M, tpr;    // M = pair rounds' modulus (odd), tpr = tiles per pair round
-    __host__ __device__ explicit TourSched(int nb_) : nb(nb_) {
-        M = (nb & 1) ? nb : nb - 1;
-        tpr = (nb + 1) / 2;
-    }
-    __host__ __device__ int rounds() const { return nb; }
-    __host__ __device__ bool diag_round(int r) const { return !(nb & 1) && r == nb - 1; }
-    __host__ __device__ int tiles_in_round(int r) const { return diag_round(r) ? nb : tpr; }
-    __host__ __device__ long long round_base(int r) const { return (long long)r * tpr; }
-    __host__ __device__ long long total_tiles() const { return (long long)nb * (nb + 1) / 2; }
-    // blocks (a <= b) of tile p of round r; a == b for a diagonal tile
-    __host__ __device__ void pair(int r, int p, int& a, int& b) const {
-        if (diag_round(r)) { a = b = p; return; }
-        int u, v;
-        if (p == 0) { u = M; v = r; }
-        else { u = (r + p) % M; v = (r - p + M) % M; }
-        if ((nb & 1) && u == M) { a = b = v; return; }   // bye: the diagonal tile
-        a = u < v ? u : v;
-        b = u < v ? v : u;
-    }
 };
 
 // Position of element (r, c) of a stored tile, in the order of the warp that
