@@ -246,12 +246,11 @@ __device__ __forceinline__ float hsum2(f2 v) {
     return lo + hi;
 }
 
-// A lane's 32 P values: float4 s holds rows (2g, 2g + 1) x steps (2s, 2s + 1).
+// A lane's 32 P values: its float4 f = 0..7 (see packed_index).
 __device__ __forceinline__ void tile_lane_values(const float* tile, int lane, float4 (&pv)[8]) {
-    const float* base = tile + lane * kPT;
-    const int l7 = lane & 7;
+    const float4* base = reinterpret_cast<const float4*>(tile) + lane;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) pv[s] = *reinterpret_cast<const float4*>(base + ((s ^ l7) << 2));
+    for (int s = 0; s < 8; ++s) pv[s] = base[s * kPT];
 }
 
 // Row sums of 2 rows kept by one lane of the pair (h, h ^ 1): lane h keeps row

@@ -82,9 +82,14 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
                 }
             }
         }
-        // reorder through shared memory into the stored order
+        // reorder through shared memory into the stored order (float4 F of
+        // the tile staged at F ^ ((F >> 5) & 7): few bank conflicts on
+        // these writes, none on the contiguous reads below)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) ot[packed_index(r, c4 * 4 + e, L.od)] = out[e];
+        for (int e = 0; e < 4; ++e) {
+            const int pi = packed_index(r, c4 * 4 + e, L.od);
+            ot[(((pi >> 2) ^ ((pi >> 7) & 7)) << 2) | (pi & 3)] = out[e];
+        }
         any = any || out[0] != 0.f || out[1] != 0.f || out[2] != 0.f || out[3] != 0.f;
     }
     // a tile whose every entry is exactly zero (far pairs: the FP32
@@ -93,9 +98,10 @@ psym_packed_kernel(const float* __restrict__ D, float* __restrict__ P2, Layout L
     const int64_t gt = ptile_off[c] + td.pos;
     float* dst = P2 + gt * kPTileStride;
 #pragma unroll
-    for (int h = 0; h < 2; ++h)   // coalesced 16-byte stores of the tile
-        reinterpret_cast<float4*>(dst)[tid + kPsymThreads * h] =
-            reinterpret_cast<const float4*>(ot)[tid + kPsymThreads * h];
+    for (int h = 0; h < 2; ++h) {   // coalesced 16-byte stores of the tile
+        const int F = tid + kPsymThreads * h;
+        reinterpret_cast<float4*>(dst)[F] = reinterpret_cast<const float4*>(ot)[F ^ ((F >> 5) & 7)];
+    }
     if (tid == 0) {   // trailer: the tile's row and column blocks and its flag
         *reinterpret_cast<int4*>(dst + kPTileFloats) = make_int4(td.a, td.b, nz, 0);
         nz_out[gt] = (uint8_t)nz;

@@ -51,8 +51,7 @@ constexpr int kFormBins = 8;
 // (a = 0: b = 0, 1, ..., then a = 1: b = 1, 2, ...), so that the tiles a warp
 // takes from the stream often share their row block.  Inside a tile the 1024
 // values are ordered for the warp that evaluates it (see packed_index, which
-// depends on the map's dimension): lane L owns 32 consecutive floats, read as
-// 8 float4.
+// depends on the map's dimension): lane L owns 32 floats, read as 8 float4.
 constexpr int kPT = 32;                      // packed tile edge
 constexpr int kPTileFloats = kPT * kPT;      // 1024 floats = 4 KB of P
 // Stored tile: the 4 KB of P followed by a 16-byte trailer {a, b, 0, 0} (int
@@ -67,14 +66,15 @@ struct TileDesc2 {
 };
 
 // Position of element (r, c) of a stored tile, in the order of the warp that
-// evaluates it: lane L owns 32 consecutive floats, read as 8 float4 whose
-// index is XOR-swizzled by L & 7 so that a warp-wide float4 read is free of
-// bank conflicts.  Two lane layouts:
+// evaluates it: lane L owns 32 values, read as 8 float4; float4 f of lane L
+// sits at float4 index 32 f + L, so that a warp-wide read of float4 f is 512
+// contiguous bytes (no bank conflict, compile-time offsets).  Two lane
+// layouts:
 //
 // 3-D maps (packed_index_ring16): lane L = 16 h + g owns rows 2g and 2g + 1
 // and the ring h of columns 16h..16h+15, which it meets in the order
-// (g + t) & 15, t = 0..15; float4 s = t / 2 holds {(2g, 2s), (2g, 2s+1),
-// (2g+1, 2s), (2g+1, 2s+1)} in (row, step) terms.
+// (g + t) & 15, t = 0..15; float4 f = t / 2 holds {(2g, 2f), (2g, 2f+1),
+// (2g+1, 2f), (2g+1, 2f+1)} in (row, step) terms.
 //
 // 2-D maps (packed_index_ring8): lane L = 8 q + g owns rows 4g .. 4g+3 and
 // the ring q of columns 8q..8q+7, which it meets as natural column pairs:
@@ -83,13 +83,13 @@ struct TileDesc2 {
 __host__ __device__ inline int packed_index_ring16(int r, int c) {
     const int g = r >> 1, L = (c & 16) | g;
     const int t = ((c & 15) - g) & 15;
-    return L * kPT + ((((t >> 1) ^ (L & 7)) << 2) | ((r & 1) << 1) | (t & 1));
+    return (((t >> 1) * kPT + L) << 2) | ((r & 1) << 1) | (t & 1);
 }
 __host__ __device__ inline int packed_index_ring8(int r, int c) {
     const int g = r >> 2, q = c >> 3, L = 8 * q + g;
     const int s = (((c & 7) >> 1) - (g >> 1)) & 3;
     const int f = 2 * s + ((r >> 1) & 1);
-    return L * kPT + (((f ^ (L & 7)) << 2) | ((r & 1) << 1) | (c & 1));
+    return ((f * kPT + L) << 2) | ((r & 1) << 1) | (c & 1);
 }
 __host__ __device__ inline int packed_index(int r, int c, int od) {
     return od == 2 ? packed_index_ring8(r, c) : packed_index_ring16(r, c);
