@@ -162,12 +162,13 @@ int ptsne_reset_counters(ptsne_ctx* ctx);
 
 /* Launch shape of the batched iteration kernel (no effect on results beyond
  * FP32 summation order).  cluster: thread blocks sharing one chunk through
- * distributed shared memory (1, 2 or 4); group: consumer warps per P tile,
- * 1 (each consumer warp evaluates whole tiles; other values are rejected);
- * consumer_warps: per block, 1 .. 20 (16 or fewer run a build of the kernel
- * with more registers per thread; 2-D maps use at most 15, the four rows per
- * lane of their evaluation need 128 registers).  Defaults {2, 1, 20};
- * ptsne_autotune picks by timing. */
+ * distributed shared memory (1, 2 or 4); group: warps per P tile, 1 (each
+ * warp evaluates whole tiles; other values are rejected); consumer_warps:
+ * warps per block, each evaluating tiles and copying its own, 1 .. 21 (2-D
+ * maps use at most 16, the four rows per lane of their evaluation need 128
+ * registers; 3-D maps at most 21; the largest chunks leave shared memory for
+ * fewer warps' tile buffers).  Defaults {2, 1, 20}; ptsne_autotune picks by
+ * timing. */
 typedef struct {
     int32_t cluster;
     int32_t group;

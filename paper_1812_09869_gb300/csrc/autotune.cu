@@ -1,5 +1,5 @@
 // Autotuner of the batched iteration kernel's launch shape: times every
-// candidate (blocks per chunk x consumer warps; one warp per tile) on the
+// candidate (blocks per chunk x warps per block; one warp per tile) on the
 // caller's chunk layout and keeps the fastest; results persist in a small text
 // cache keyed by device and layout.  Under BF16_WINDOW it first chooses the
 // form of the distances (ptsne_set_form_threshold) by timing the affinities
@@ -251,9 +251,9 @@ extern "C" int ptsne_autotune(ptsne_ctx* c, const float* X, const int32_t* perm,
     IterTune best = keep;
     double best_ms = 1e300;
     int nt = 0;
-    // consumer warps per block: the 2-D evaluation runs with at most 15
+    // warps per block: the 2-D evaluation runs with at most 16
     const int clusters[] = {1, 2, 4}, groups[] = {1};
-    const int warps2[] = {8, 12, 15}, warps3[] = {12, 16, 19, 20};
+    const int warps2[] = {8, 12, 16}, warps3[] = {12, 17, 20, 21};
     const bool two_d = c->p.out_dim == 2;
     const int nwarps = two_d ? 3 : 4;
     for (int cl : clusters)

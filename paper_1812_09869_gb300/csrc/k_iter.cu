@@ -5,14 +5,15 @@
 // chunk is owned by a cluster of K blocks (K = 1, 2 or 4); the chunk's map
 // lives in every block's shared memory and each block takes a contiguous
 // K-th of the chunk's stored tiles (stored row block by row block).  Within
-// a block:
-//   - one producer warp streams the block's P tiles (4 KB each, stored once
-//     per unordered pair of 32-row blocks) from HBM into a ring of shared
-//     buffers with cp.async.bulk, one tile per lane in batches of 8 (at most
-//     the ring size), completion tracked by mbarriers;
-//   - consumer warps take whole tiles in stream order (warp w: tiles q with
-//     q = w mod the warp count); a warp copies its tile into registers and
-//     releases the buffer before computing;
+// a block every warp evaluates whole tiles: warp w of W takes a contiguous
+// W-th of the block's share (P tiles of 4 KB, stored once per unordered pair
+// of 32-row blocks), the same piece in every pass, and owns one shared tile
+// buffer.  For each tile it waits for its own copy (cp.async, each lane
+// copying the eight 16-byte pieces of P it will read back), reads the tile
+// into registers, starts the copy of its next tile into the buffer and asks
+// L2 for the one after, and then evaluates the tile from registers: the next
+// copy has a whole tile's arithmetic to land and is served from L2.  No
+// producer warp, no barrier between warps and no spin-wait in the tile loop.
 //   - an off-diagonal tile (rows a, columns b) is evaluated once per unordered
 //     pair: w = 1 / (1 + |y_i - y_j|^2) and the terms p_ij w (y_i - y_j) of
 //     A and w^2 (y_i - y_j) of R go to row i and, negated, to row j (column
@@ -28,19 +29,6 @@
 //   - then Z = sum_i Z_i (FP64, over the cluster through distributed shared
 //     memory), dC/dy_i = 4 (A_i - R_i / Z) (Eq. 6), and the update of each
 //     block's slice of rows, broadcast to every block's copy of the map.
-// Every mbarrier wait is bounded in time; a wait that runs out is counted in
-// DeviceStats::timeouts (the host then reports PTSNE_ETIMEOUT) and the kernel
-// runs to completion without blocking.  A failed wait sets the block's
-// freeze flag, so that every wait not yet satisfied then fails at once; a
-// consumer warp whose wait failed skips that tile and every later one (no
-// read, no release), and after a batch with a failed wait the producer
-// issues no further copy.  A ring buffer belongs to one consumer warp, so a
-// phase of it can be left incomplete only by that warp's own failure or by a
-// copy the producer skipped: a ready barrier is therefore never a stale phase,
-// and the fast path (the barrier already complete) reads no flag.  A copy
-// never lands in a buffer that is being read or that still has one in
-// flight.  Before the block exits, the producer waits (bounded) for the last
-// copy it issued into each buffer.
 #include <float.h>
 
 #include "ptsne_internal.cuh"
@@ -53,9 +41,8 @@ namespace {
 // square overflows) and p = 0, and padding rows can be processed like real
 // ones without changing A, R or Z (their own updates are never written).
 constexpr float kPad = 1e18f;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
 constexpr float kLn2f = 0.69314718055994531f;
-constexpr int kTileBytes = kPTileStride * 4;    // P tile + trailer, one bulk copy
+constexpr int kStaticSmem = 2048;               // bound on the kernel's static shared memory
 }  // namespace
 
 struct IterArgs {
@@ -72,65 +59,26 @@ struct IterArgs {
     int cost_pass;              // 1: one cost pass after the gradient passes
     Optim opt;
     int* queue;                 // chunk work queue (zeroed before launch)
-    unsigned int* timeouts;
     int zcap;                   // rows of the shared map / accumulators (multiple of 32)
-    int ring;                   // ring buffers: a multiple of the consumer warps (see below)
 };
 
 // ---------------------------------------------------------------- PTX helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+// 16-byte copy global -> shared, completed by cp.async.wait_group; cached in
+// L2 only (P is read once per pass).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase of the given parity; false if it did not complete within
-// kWaitNs, or at once (while not complete) when the block's freeze flag
-// `fail` or the launch's timeout count is set.  A failed wait sets `fail`.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const unsigned int* timeouts,
-                                          volatile int* fail) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try(bar, parity)) {
-        if (*fail || *(volatile const unsigned int*)timeouts != 0u || global_ns() - t0 > kWaitNs) {
-            *fail = 1;
-            return false;
-        }
-    }
-    return true;
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-// Bring `bytes` at src into L2 ahead of their copy to shared memory (no
-// completion to wait for; a hint the hardware may drop).
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Ask L2 for a stored tile (4 KB of P and its trailer): lane l takes the
+// 128-byte line at byte 128 l, lanes 0 and 1 the trailer's one or two lines.
+__device__ __forceinline__ void prefetch_tile_l2(const float* tile, int lane) {
+    const char* t = reinterpret_cast<const char*>(tile);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(t + 128 * lane));
+    if (lane < 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(t + 4096 + 15 * lane));
 }
 __device__ __forceinline__ uint32_t cl_rank() {
     uint32_t r;
@@ -214,7 +162,7 @@ __device__ __forceinline__ int map_idx(int zcap, int i, int k) {
     else return k * zcap + i;
 }
 //
-// One consumer warp evaluates a whole 32 x 32 tile (rows of block a, columns
+// One warp evaluates a whole 32 x 32 tile (rows of block a, columns
 // of block b).  Lane L = 16 h + g owns rows 2g and 2g + 1 of a and the ring h
 // of b's columns 16h..16h+15, met in the order (g + t) & 15, two columns per
 // double step s (t = 2s, 2s + 1).  Per pair: w = 1 / (1 + |y_i - y_j|^2) and
@@ -246,11 +194,22 @@ __device__ __forceinline__ float hsum2(f2 v) {
     return lo + hi;
 }
 
-// A lane's 32 P values: its float4 f = 0..7 (see packed_index).
+// A lane's 32 P values: its float4 f = 0..7 (see packed_index), float4
+// f * 32 + lane of the tile, so that each of the eight accesses of a warp
+// touches 512 contiguous bytes.
 __device__ __forceinline__ void tile_lane_values(const float* tile, int lane, float4 (&pv)[8]) {
     const float4* base = reinterpret_cast<const float4*>(tile) + lane;
 #pragma unroll
     for (int s = 0; s < 8; ++s) pv[s] = base[s * kPT];
+}
+// Copy a stored tile from HBM into the warp's shared buffer: lane l copies its
+// own eight float4 (the ones it reads back), lane 0 the trailer too.
+__device__ __forceinline__ void tile_copy_async(uint32_t buf_a, const float* tile, int lane) {
+    const float4* src = reinterpret_cast<const float4*>(tile) + lane;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) cp_async16(buf_a + (uint32_t)(s * kPT + lane) * 16u, src + s * kPT);
+    if (lane == 0) cp_async16(buf_a + (uint32_t)kPTileFloats * 4u, tile + kPTileFloats);
+    cp_async_commit();
 }
 
 // Row sums of 2 rows kept by one lane of the pair (h, h ^ 1): lane h keeps row
@@ -546,30 +505,16 @@ __device__ __forceinline__ void tile_cost(const float* map, int zcap, int a, int
     }
 }
 
-// Tile stream of one block of the cluster: the chunk's stored tiles
-// g = rank, rank + K, rank + 2K, ... (storage follows the tournament rounds,
-// so consecutive tiles of a stream mostly lie in one round and touch disjoint
-// row blocks); the K streams differ in length by at most one tile.
+// Stored tiles of one block of the cluster: a contiguous share of the
+// chunk's stored tiles (stored row block by row block), so that a warp's
+// consecutive tiles share their row block as often as possible; the K shares
+// differ in length by at most one tile.
 struct Stream {
     int first, nq;   // this block's tiles of the chunk: stored tiles first .. first + nq - 1, per pass
     __device__ Stream(int nb, uint32_t rank, uint32_t K) {
-        // contiguous shares (counts differ by at most one tile), so that a
-        // warp's consecutive tiles share their row block as often as possible
         const long long total = (long long)nb * (nb + 1) / 2;
         first = (int)(total * rank / K);
         nq = (int)(total * (rank + 1) / K) - first;
-    }
-};
-
-// Position of a consumer warp in the ring: stream index q, its buffer and the
-// buffer's phase parity.
-struct Cursor {
-    unsigned long long q;
-    uint32_t buf, ph;
-    __device__ __forceinline__ void advance_ring(uint32_t delta, uint32_t ring) {
-        q += delta;
-        buf += delta;
-        if (buf >= ring) { buf -= ring; ph ^= 1u; }   // delta <= ring: at most one wrap
     }
 };
 
@@ -585,14 +530,18 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// A consumer warp's tiles of one pass: tiles q = slot, slot + nslots, ...
-// below qend, each waited for, copied into registers, released and evaluated
-// (COST: the cost sums instead of the gradient sums).
+// A warp's n_w tiles of one pass: tile j is stored at P2w + j * step (the
+// block's tile w + j W).  The warp owns one shared buffer: on entry it holds
+// (or is receiving) tile 0; for each tile the warp waits for its copy, reads
+// it into registers, starts the copy of the next tile into the buffer (after
+// the pass's last tile, the next pass's first when `more`; nothing after the
+// chunk's last) and asks L2 for the tile after that, then evaluates (COST:
+// the cost sums instead of the gradient sums).  The copy of the next tile
+// thus has a whole tile's arithmetic to land, and its source is in L2.
 template <int OD, bool COST>
-__device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qend, uint32_t nslots, uint32_t ring_n,
-                                             const float* ring, uint32_t full_a, uint32_t empty_a,
-                                             unsigned int* timeouts, volatile int* fail, bool& wfail, int nb,
-                                             const float* map, int zcap, float* acc, int lane, KSum (&part)[4]) {
+__device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int n_w, bool more, int nb,
+                                             const float* buf, const float* map, int zcap, float* acc, int lane,
+                                             KSum (&part)[4]) {
     // w of the pair (i, i), which a diagonal tile's row-wise pass counts in
     // its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own columns)
     // (ring-8 layout: lanes with q == g / 2 meet their own four rows;
@@ -600,31 +549,30 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
     const float w_ii = hw_rcp(1.0f);
     const bool diag_lane = OD == 2 ? (lane >> 3) == ((lane & 7) >> 1) : (lane >> 4) == ((lane & 15) >> 3);
     constexpr float kDiagPairs = OD == 2 ? 4.0f : 2.0f;
+    const uint32_t buf_a = smem_u32(buf);
     Rows2 R;          // 2-D gradient pass: the row sums of row block cur_a
     int cur_a = -1;
-    for (; cur.q < qend; cur.advance_ring(nslots, ring_n)) {
-        // The ring holds a whole number of consumer slots, so tile q - ring
-        // (this buffer's previous use) belonged to this same slot and was
-        // waited for before: the barrier is at most one phase behind, and
-        // the parity test cannot mistake an older phase for this one.
-        // After a failed wait this warp skips its tiles whole: no wait, no
-        // read, no release (a buffer may still receive its copy), no arithmetic.
-        if (wfail) continue;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(full_a + 8 * cur.buf, cur.ph, timeouts, fail));
-        if (!ok) {
-            wfail = true;
-            if (lane == 0) atomicAdd(timeouts, 1u);
-            continue;
+    for (int j = 0; j < n_w; ++j) {
+        cp_async_wait_all();   // this lane's part of the tile (and lane 0's trailer) ...
+        __syncwarp();          // ... and every lane's, visible to the warp
+        const int2 ab = *reinterpret_cast<const int2*>(buf + kPTileFloats);
+        float4 pv[8];
+        tile_lane_values(buf, lane, pv);
+        // the reads have returned (their registers are used here) before the
+        // next copy may overwrite the buffer
+        asm volatile("" ::"f"(pv[0].x), "f"(pv[1].x), "f"(pv[2].x), "f"(pv[3].x), "f"(pv[4].x), "f"(pv[5].x),
+                     "f"(pv[6].x), "f"(pv[7].x), "r"(ab.x), "r"(ab.y)
+                     : "memory");
+        __syncwarp();
+        if (j + 1 < n_w || more) {
+            const int jn = j + 1 < n_w ? j + 1 : 0;
+            const int jq = jn + 1 < n_w ? jn + 1 : 0;
+            tile_copy_async(buf_a, P2w + jn * step, lane);
+            prefetch_tile_l2(P2w + jq * step, lane);
         }
-        const float* tile = ring + (size_t)cur.buf * kPTileStride;
-        const int2 ab = *reinterpret_cast<const int2*>(tile + kPTileFloats);
         // the trailer is written by the joint-P kernel; clamp it anyway so
         // that no shared-memory index can leave the chunk's rows
         const int a = (int)min((unsigned)ab.x, (unsigned)(nb - 1)), b = (int)min((unsigned)ab.y, (unsigned)(nb - 1));
-        float4 pv[8];
-        tile_lane_values(tile, lane, pv);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty_a + 8 * cur.buf);   // the buffer is free again
         const bool diag = a == b;
         const float drop = diag && diag_lane ? kDiagPairs * w_ii : 0.0f;
         if constexpr (!COST) {
@@ -662,59 +610,31 @@ __device__ __forceinline__ void consume_pass(Cursor& cur, unsigned long long qen
     }
 }
 
-// Compiled for at most MAXT threads.  2-D maps: 512 (15 consumer warps + the
-// producer) or 416 (12 + 1), both 128 registers per thread.  3-D maps: 672
-// (20 + 1, 80 registers) or 544 (16 + 1, 96 registers).  Registers are granted
-// per 4 warps, so 21 warps get 80, 17 to 20 warps 96 and 16 or fewer 128.
+// Compiled for at most MAXT threads.  2-D maps: 512 (16 warps) or 384 (12),
+// both 128 registers per thread.  3-D maps: 672 (21 warps, 80 registers) or
+// 544 (17, 96 registers).  Registers are granted per 4 warps, so 21 warps
+// get 80, 17 to 20 warps 96 and 16 or fewer 128.
 template <int OD, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = blockDim.x;
-    const int Wc = (nthreads >> 5) - 1;            // consumer warps; the last warp produces
-    const bool is_producer = warp == Wc;
-    const int slot = warp, nslots = Wc;             // consumer warp: tiles q with q % nslots == slot
-    const uint32_t ring_n = (uint32_t)A.ring;
+    const int W = nthreads >> 5;                    // warps, each evaluating tiles
     const int zcap = A.zcap;
 
-    float* ring = reinterpret_cast<float*>(smem_raw);
-    uint64_t* fullb = reinterpret_cast<uint64_t*>(smem_raw + (size_t)A.ring * kTileBytes);
-    uint64_t* emptyb = fullb + A.ring;
-    float* map = reinterpret_cast<float*>(emptyb + A.ring);   // OD arrays of zcap floats
-    float* acc = map + (size_t)OD * zcap;                     // 2*OD arrays: A_0.., R_0..
+    // one tile buffer per warp (4112 bytes: P and trailer), then the map and
+    // the accumulators
+    float* wbuf = reinterpret_cast<float*>(smem_raw) + (size_t)warp * kPTileStride;
+    float* map = reinterpret_cast<float*>(smem_raw) + (size_t)W * kPTileStride;   // OD arrays of zcap floats
+    float* acc = map + (size_t)OD * zcap;                                         // 2*OD arrays: A_0.., R_0..
 
     __shared__ double s_red[32][4];
     __shared__ double s_part[4];                    // this block's Z (and cost) partial sums
     __shared__ int s_item;
     __shared__ float s_mn[32], s_mx[32];
     __shared__ float s_eta;
-    __shared__ int s_fail;                          // the block's freeze flag (see mbar_wait)
-    // the producer's first batch with a failed wait (it issues nothing after
-    // it): its stream position and the lanes that did issue (rare path, kept
-    // out of the registers of the hot loop)
-    __shared__ unsigned long long s_fail_base;
-    __shared__ unsigned int s_fail_issued;
 
     const uint32_t K = cl_size(), rank = cl_rank();
-    const uint32_t ring_a = smem_u32(ring), full_a = smem_u32(fullb), empty_a = smem_u32(emptyb);
-    if (tid == 0) {
-        s_fail = 0;
-        for (int b = 0; b < A.ring; ++b) {
-            mbar_init(full_a + 8 * b, 1);
-            mbar_init(empty_a + 8 * b, 1u);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-
-    // stream cursors: the producer visits every q, a consumer slot q = slot + k * nslots
-    Cursor cur;
-    cur.q = is_producer ? 0ull : (unsigned long long)slot;
-    cur.buf = is_producer ? 0u : (uint32_t)slot;   // slot < nslots <= ring
-    cur.ph = 0u;
-    unsigned long long q0 = 0;  // first stream index of the current pass (same in every thread)
-    bool wfail = false;         // this warp had a failed wait (warp-uniform)
     for (;;) {
         if (rank == 0 && tid == 0) s_item = atomicAdd(A.queue, 1);
         sync_owner(K);
@@ -728,9 +648,23 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         const int nb = (z + kPT - 1) / kPT;
         const int zr = nb * kPT;
         const Stream S(nb, rank, K);
-        const float* P2c = A.P2 + A.ptile_off[c] * kPTileStride;
         const int slice = (z + (int)K - 1) / (int)K;           // rows updated by this block
         const int ulo = (int)rank * slice, uhi = min(z, ulo + slice);
+        const int npass = A.iters + (A.cost_pass ? 1 : 0);
+
+        // this warp's tiles of the chunk: a contiguous W-th of the block's
+        // share (so that its consecutive tiles share their row block: its row
+        // sums are added to the accumulators once per row block); the copy of
+        // the first starts (and the second is asked of L2) before the map is
+        // even loaded
+        const int w0 = (int)((long long)S.nq * warp / W);
+        const int n_w = (int)((long long)S.nq * (warp + 1) / W) - w0;
+        const int64_t step = kPTileStride;
+        const float* P2w = A.P2 + (A.ptile_off[c] + S.first + w0) * kPTileStride;
+        if (n_w > 0) {
+            tile_copy_async(smem_u32(wbuf), P2w, lane);
+            if (n_w > 1) prefetch_tile_l2(P2w + step, lane);
+        }
 
         for (int i = tid; i < zr; i += nthreads) {
 #pragma unroll
@@ -739,7 +673,6 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         for (int i = tid; i < 2 * OD * zcap; i += nthreads) acc[i] = 0.f;
         __syncthreads();
 
-        const int npass = A.iters + (A.cost_pass ? 1 : 0);
         for (int it = 0; it < npass; ++it) {
             const bool cost = it == A.iters;
             if (!cost && A.opt.lr_mode == PTSNE_LR_PAPER) {
@@ -756,7 +689,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 __syncthreads();
                 if (tid == 0) {
                     float a = FLT_MAX, b = -FLT_MAX;
-                    for (int w = 0; w < (nthreads >> 5); ++w) { a = fminf(a, s_mn[w]); b = fmaxf(b, s_mx[w]); }
+                    for (int w = 0; w < W; ++w) { a = fminf(a, s_mn[w]); b = fmaxf(b, s_mx[w]); }
                     s_eta = step_eta(A.opt, z, a, b);
                 }
             }
@@ -764,56 +697,9 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             KSum part[4];                              // Z, sum p ln p, sum p ln w, sum p
 #pragma unroll
             for (int k = 0; k < 4; ++k) part[k].clear();
-            const unsigned long long qend = q0 + (unsigned long long)S.nq;
-            if (is_producer) {
-                // Lane l issues tile s = base + l of each batch.  A batch spans at most
-                // `ring` tiles, so it uses every buffer at most once, and the warp ends
-                // batch k before starting batch k + 1: each buffer's uses stay in
-                // stream order, one phase at a time.  Batches of 8: a batch waits for
-                // the slowest of its buffers to be released, so long batches hold
-                // back copies whose buffers are already free (batches of 19 measured
-                // 3.5% slower), while batches of 3 or fewer cannot keep the ring fed.
-                const int batch = A.ring < 8 ? A.ring : 8;
-                const uint32_t q0r = (uint32_t)(q0 % ring_n), q0ph = (uint32_t)(q0 / ring_n) & 1u;
-                for (int base = 0; base < S.nq && !wfail; base += batch) {
-                    const int s = base + lane;
-                    const bool active = lane < batch && s < S.nq;
-                    bool issued = false;
-                    if (active) {
-                        const uint32_t t = q0r + (uint32_t)s;
-                        const uint32_t buf = t % ring_n, ph = q0ph ^ ((t / ring_n) & 1u);
-                        // a copy is issued only into a buffer known to be released
-                        if (mbar_wait(empty_a + 8 * buf, ph ^ 1u, A.timeouts, &s_fail)) {
-                            const float* src = P2c + ((int64_t)S.first + s) * kPTileStride;
-                            mbar_expect_tx(full_a + 8 * buf, kTileBytes);
-                            bulk_load(ring_a + buf * kTileBytes, src, kTileBytes, full_a + 8 * buf);
-                            issued = true;
-                            // the tile this buffer takes next (a ring later; past the
-                            // end of the pass, the next pass's tile) is read into L2
-                            // now, so that its copy, issued once this one is consumed,
-                            // is served from L2 rather than from HBM
-                            const int sn = (s + A.ring) % S.nq;
-                            bulk_prefetch_l2(P2c + ((int64_t)S.first + sn) * kPTileStride, kTileBytes);
-                        } else {
-                            atomicAdd(A.timeouts, 1u);
-                        }
-                    }
-                    // after a batch with a failed wait the producer issues nothing more
-                    const unsigned int got = __ballot_sync(0xffffffffu, issued);
-                    if (got != __ballot_sync(0xffffffffu, active)) {
-                        wfail = true;
-                        if (lane == 0) {
-                            s_fail_base = q0 + (unsigned long long)base;
-                            s_fail_issued = got;
-                        }
-                    }
-                }
-            } else {
-                if (!cost) consume_pass<OD, false>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts,
-                                                   &s_fail, wfail, nb, map, zcap, acc, lane, part);
-                else consume_pass<OD, true>(cur, qend, (uint32_t)nslots, ring_n, ring, full_a, empty_a, A.timeouts,
-                                            &s_fail, wfail, nb, map, zcap, acc, lane, part);
-            }
+            const bool more = it + 1 < npass;
+            if (!cost) consume_pass<OD, false>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
+            else consume_pass<OD, true>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
             // block partials (fixed order), then the cluster total; a gradient pass
             // has only Z (the cost sums are zero there)
             const int nsum = cost ? 4 : 1;
@@ -824,7 +710,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             __syncthreads();
             if (tid < nsum) {
                 double v = 0.0;
-                for (int w = 0; w < Wc; ++w) v += s_red[w][tid];
+                for (int w = 0; w < W; ++w) v += s_red[w][tid];
                 s_part[tid] = v;
             }
             sync_owner(K);
@@ -873,67 +759,28 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             for (int i = tid; i < OD * zcap / 2; i += nthreads)   // 2 OD zcap floats, zcap a multiple of 32
                 reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             __syncthreads();
-            q0 = qend;
         }
         for (int i = ulo + tid; i < uhi; i += nthreads)
 #pragma unroll
             for (int k = 0; k < OD; ++k) A.Yc[(off + i) * OD + k] = map[map_idx<OD>(zcap, i, k)];
         __syncthreads();
     }
-    // Normally every issued copy has been waited for by a consumer.  After a
-    // failed wait some may still be in flight: before the block exits, wait
-    // (bounded, whatever the freeze flag says) for the phase of the last copy
-    // issued into each buffer.  Copies into one buffer are issued one at a
-    // time (each after the release of the previous one), so that phase is the
-    // only one a buffer can still owe.  Stream position G went to buffer
-    // G mod ring with parity (G / ring) mod 2; the producer issued every
-    // position below `end` (its whole stream, or the start of its failed
-    // batch) and, of the failed batch, the lanes in fail_issued.
-    if (is_producer && lane == 0 && *(volatile int*)&s_fail != 0) {
-        const unsigned long long end = wfail ? s_fail_base : q0;
-        const unsigned int issued_lanes = wfail ? s_fail_issued : 0u;
-        for (int b = 0; b < A.ring; ++b) {
-            long long last = -1;   // last issued stream position of buffer b
-            if (end > (unsigned long long)b) last = (long long)(end - 1 - ((end - 1 - (unsigned long long)b) % ring_n));
-            for (int l = 0; l < 32; ++l)
-                if ((issued_lanes >> l) & 1u) {
-                    const unsigned long long g = end + (unsigned long long)l;
-                    if (g % ring_n == (unsigned long long)b && (long long)g > last) last = (long long)g;
-                }
-            if (last < 0) continue;
-            {
-                const uint32_t bar = full_a + 8 * b, ph = (uint32_t)(((unsigned long long)last / ring_n) & 1u);
-                const unsigned long long t0 = global_ns();
-                while (!mbar_try(bar, ph)) {
-                    if (global_ns() - t0 > kWaitNs) {
-                        atomicAdd(A.timeouts, 1u);
-                        break;
-                    }
-                }
-            }
-        }
-    }
 }
 
 // ---------------------------------------------------------------- launchers
 
-int iterate_smem_bytes(int od, int64_t zmax, int ring) {
+int iterate_smem_bytes(int od, int64_t zmax, int warps) {
     const int zcap = (int)((zmax + kPT - 1) / kPT * kPT);
-    const int per_row = 3 * od * 4;   // map + A + R, structure-of-arrays
-    // tiles (with trailers), full + empty barriers, map and accumulators
-    return ring * (kTileBytes + 16) + zcap * per_row;
+    // a tile buffer per warp, map + A + R (structure-of-arrays; a 2-D map as column pairs)
+    return warps * kPTileStride * 4 + zcap * 3 * od * 4;
 }
 
-// Ring size for `slots` consumer slots: a whole number of buffers per slot
-// (at most 4, at most 48 buffers) next to the map in 227 KB; 0 if not even
-// one buffer per slot fits.
-int iterate_ring(int od, int64_t zmax, int slots) {
-    const int avail = 227 * 1024 - 2048 - iterate_smem_bytes(od, zmax, 0);
-    const int fit = avail > 0 ? avail / (kTileBytes + 16) : 0;
-    int m = fit / slots;
-    if (m > 4) m = 4;
-    if (m * slots > 48) m = 48 / slots;
-    return m >= 1 ? m * slots : 0;
+// Warps (at most `want`) whose tile buffers fit beside the map and the
+// accumulators in 227 KB of shared memory; 0 if not even one fits.
+int iterate_warps(int od, int64_t zmax, int want) {
+    int w = want;
+    while (w > 0 && iterate_smem_bytes(od, zmax, w) > 227 * 1024 - kStaticSmem) --w;
+    return w;
 }
 
 cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc, double* cost_chunk,
@@ -941,17 +788,15 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     if (iters <= 0 && !cost_pass) return cudaSuccess;
     const int K = c->tune.cluster;
     if (c->tune.group != 1) return cudaErrorInvalidValue;
-    int Wc = c->tune.consumer_warps;
+    int Wc = c->tune.consumer_warps;   // warps per block, each evaluating tiles
     // the 2-D evaluation (four rows per lane) needs 128 registers per thread,
-    // which a block of at most 16 warps gets: at most 15 consumer warps
-    if (c->p.out_dim == 2 && Wc > 15) Wc = 15;
-    int ring = iterate_ring(c->p.out_dim, c->zmax, Wc);
-    while (ring == 0 && Wc > 1) {   // very large chunks: fewer consumer warps
-        --Wc;
-        ring = iterate_ring(c->p.out_dim, c->zmax, Wc);
-    }
-    if (ring == 0) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, ring);
+    // which a block of at most 16 warps gets; 3-D maps run at most 21 warps;
+    // very large chunks leave room for fewer tile buffers
+    if (c->p.out_dim == 2 && Wc > 16) Wc = 16;
+    if (c->p.out_dim == 3 && Wc > 21) Wc = 21;
+    Wc = iterate_warps(c->p.out_dim, c->zmax, Wc);
+    if (Wc < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, Wc);
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     IterArgs a;
@@ -968,14 +813,12 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     a.cost_pass = cost_pass;
     a.opt = Optim{c->p.lr, c->p.momentum, c->p.lr_mode, c->p.use_gains};
     a.queue = c->queue;
-    a.timeouts = &c->dstats->timeouts;
     a.zcap = (int)((c->zmax + kPT - 1) / kPT * kPT);
-    a.ring = ring;
 
     // the build for the fewest threads that hold the block: more registers per thread
     void (*kern)(IterArgs);
-    if (c->p.out_dim == 2) kern = Wc > 12 ? iterate_kernel<2, 512> : iterate_kernel<2, 416>;
-    else kern = Wc > 16 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>;
+    if (c->p.out_dim == 2) kern = Wc > 12 ? iterate_kernel<2, 512> : iterate_kernel<2, 384>;
+    else kern = Wc > 17 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -983,7 +826,7 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.blockDim = dim3((unsigned)((Wc + 1) * 32), 1, 1);
+    cfg.blockDim = dim3((unsigned)(Wc * 32), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     int clusters = sms / K;

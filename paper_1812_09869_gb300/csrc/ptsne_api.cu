@@ -162,7 +162,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         return bad("precision", p.precision);
     if (p.schedule != PTSNE_SCHED_BATCHED && p.schedule != PTSNE_SCHED_PER_CHUNK) return bad("schedule", p.schedule);
     if (p.use_graph != 0 && p.use_graph != 1) return bad("use_graph must be 0 or 1", p.use_graph);
-    if (p.schedule == PTSNE_SCHED_BATCHED && iterate_ring(p.out_dim, zmax, 1) < 1)
+    if (p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(p.out_dim, zmax, 1) < 1)
         return bad("largest chunk too large for the batched schedule at this out_dim", zmax);
 
     c->p = p;
@@ -808,7 +808,7 @@ int ptsne_set_profiling(ptsne_ctx* c, int on) {
 int ptsne_set_tuning(ptsne_ctx* c, const ptsne_tuning* t) {
     if (!c || !t) return PTSNE_EINVAL;
     const bool ok_k = t->cluster == 1 || t->cluster == 2 || t->cluster == 4;
-    if (!ok_k || t->group != 1 || t->consumer_warps < 1 || t->consumer_warps > 20)
+    if (!ok_k || t->group != 1 || t->consumer_warps < 1 || t->consumer_warps > 21)
         return fail(c, PTSNE_EINVAL, "invalid tuning%s (cluster %lld)", "", t->cluster);
     c->tune.cluster = t->cluster;
     c->tune.group = t->group;

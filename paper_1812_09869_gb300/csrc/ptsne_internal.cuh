@@ -132,8 +132,8 @@ struct Optim {                     // optimiser settings
 // Launch shape of the batched iteration kernel (chosen by the autotuner).
 struct IterTune {
     int cluster = 2;               // blocks sharing one chunk (1, 2 or 4)
-    int group = 1;                 // consumer warps per tile (1: each warp evaluates whole tiles)
-    int consumer_warps = 20;       // consumer warps per block (1 .. 20)
+    int group = 1;                 // warps per tile (1: each warp evaluates whole tiles)
+    int consumer_warps = 20;       // warps per block (1 .. 21)
 };
 
 }  // namespace ptsne
@@ -316,8 +316,8 @@ cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t 
 cudaError_t launch_count_nonzero(const ptsne_ctx* c, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc,
                            double* cost_chunk, cudaStream_t s);
-int iterate_ring(int od, int64_t zmax, int slots); // 0 if the map does not fit in shared memory
-int iterate_smem_bytes(int od, int64_t zmax, int ring);
+int iterate_warps(int od, int64_t zmax, int want);   // 0 if the map does not fit in shared memory
+int iterate_smem_bytes(int od, int64_t zmax, int warps);
 
 Layout make_layout(const ptsne_ctx* c);
 

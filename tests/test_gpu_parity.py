@@ -140,7 +140,7 @@ def test_step_three_dims_paper_lr_no_gains(dev, schedule):
 @pytest.mark.parametrize("tuning", [(2, 1, 20), (1, 1, 12)])
 def test_three_dims_every_build_gradient_and_cost(dev, tuning):
     """3-D maps through both builds of the batched kernel for 3-D (more and
-    fewer than 16 consumer warps): one step's gradient and Z, and the cost
+    fewer than 18 warps): one step's gradient and Z, and the cost
     (Eq. 5, Eq. 9), against the oracle; two chunks with ragged last blocks."""
     X, _ = synth.gaussian_mixture(1300, 10, 4, seed=60)
     off = np.array([0, 610, 1300])     # 20 and 22 row blocks, both ragged
@@ -295,21 +295,21 @@ def test_batched_iterations_equal_plain_per_chunk_form(dev):
     assert rel_max(out[0] - Y0, out[1] - Y0) <= 1e-4
 
 
-# launch shapes of the batched kernel: blocks per chunk (cluster) x consumer warps,
-# every build (12, 16, 19 and 20 consumer warps at most), one warp and a ring of 17 slots
+# launch shapes of the batched kernel: blocks per chunk (cluster) x warps per block,
+# both 2-D builds (at most 12 and 16 warps; more are run as 16), a single warp, and odd counts
 TUNINGS = [(1, 1, 16), (2, 1, 16), (4, 1, 12), (4, 1, 8), (1, 1, 4), (1, 1, 1), (2, 1, 17), (1, 1, 19), (2, 1, 20),
            (1, 1, 20), (4, 1, 20)]
 
 
 def test_invalid_launch_shapes_are_rejected(dev):
     """ptsne_set_tuning refuses shapes the kernel has no build for (a cluster
-    of 3, more than one warp per tile, 0 or 21 consumer warps) and keeps the
+    of 3, more than one warp per tile, 0 or 22 warps) and keeps the
     previous shape."""
     from paper_1812_09869_gb300 import ptsne
     X, _ = synth.gaussian_mixture(300, 6, 3, seed=57)
     ctx = _ctx(X, np.array([0, 150, 300]), perplexity=5.0)
     ctx.set_tuning(1, 1, 12)
-    for bad in [(3, 1, 16), (2, 2, 16), (2, 4, 16), (2, 1, 0), (2, 1, 21), (0, 1, 8)]:
+    for bad in [(3, 1, 16), (2, 2, 16), (2, 4, 16), (2, 1, 0), (2, 1, 22), (0, 1, 8)]:
         with pytest.raises(ptsne.PtsneError):
             ctx.set_tuning(*bad)
         assert ctx.tuning() == (1, 1, 12), bad
@@ -387,7 +387,7 @@ def test_errors_nonfinite_input_and_call_order(dev):
 @pytest.mark.parametrize("precision", ["fp32", "bf16_window"])
 def test_maximum_chunk_size(dev, precision):
     """z = 8192, the largest chunk: the batched kernel's map and accumulators
-    take 196 KB of shared memory, so it runs with fewer consumer slots; P, β,
+    take 196 KB of shared memory, so it runs with fewer warps; P, β,
     the gradient and Z after one step still match the oracle."""
     z = 8192
     X, _ = synth.gaussian_mixture(z + 700, 16, 12, seed=80, anisotropic=True)
