@@ -10,10 +10,10 @@
 // of 32-row blocks), the same piece in every pass, and owns one shared tile
 // buffer.  For each tile it waits for its own copy (cp.async, each lane
 // copying the eight 16-byte pieces of P it will read back), reads the tile
-// into registers, starts the copy of its next tile into the buffer and asks
-// L2 for the one after, and then evaluates the tile from registers: the next
-// copy has a whole tile's arithmetic to land and is served from L2.  No
-// producer warp, no barrier between warps and no spin-wait in the tile loop.
+// into registers, starts the copy of its next tile into the buffer, and then
+// evaluates the tile from registers: the next copy has a whole tile's
+// arithmetic to land.  No producer warp, no barrier between warps and no
+// spin-wait in the tile loop.
 //   - an off-diagonal tile (rows a, columns b) is evaluated once per unordered
 //     pair: w = 1 / (1 + |y_i - y_j|^2) and the terms p_ij w (y_i - y_j) of
 //     A and w^2 (y_i - y_j) of R go to row i and, negated, to row j (column
@@ -73,13 +73,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-// Ask L2 for a stored tile (4 KB of P and its trailer): lane l takes the
-// 128-byte line at byte 128 l, lanes 0 and 1 the trailer's one or two lines.
-__device__ __forceinline__ void prefetch_tile_l2(const float* tile, int lane) {
-    const char* t = reinterpret_cast<const char*>(tile);
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(t + 128 * lane));
-    if (lane < 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(t + 4096 + 15 * lane));
-}
 __device__ __forceinline__ uint32_t cl_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -105,12 +98,12 @@ __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
 }
 __device__ __forceinline__ float ld_cl_f32(uint32_t a) {
     float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ double ld_cl_f64(uint32_t a) {
     double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ int ld_cl_s32(uint32_t a) {
@@ -119,7 +112,7 @@ __device__ __forceinline__ int ld_cl_s32(uint32_t a) {
     return v;
 }
 __device__ __forceinline__ void st_cl_f32(uint32_t a, float v) {
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v));
 }
 
 // packed FP32 pairs (f32x2 arithmetic, round to nearest like the scalar ops)
@@ -535,9 +528,10 @@ struct KSum {
 // (or is receiving) tile 0; for each tile the warp waits for its copy, reads
 // it into registers, starts the copy of the next tile into the buffer (after
 // the pass's last tile, the next pass's first when `more`; nothing after the
-// chunk's last) and asks L2 for the tile after that, then evaluates (COST:
-// the cost sums instead of the gradient sums).  The copy of the next tile
-// thus has a whole tile's arithmetic to land, and its source is in L2.
+// chunk's last), then evaluates (COST: the cost sums instead of the gradient
+// sums).  The copy of the next tile thus has a whole tile's arithmetic to
+// land (an L2 prefetch of the tile after that measured slower: its
+// instructions cost more than the latency they hide).
 template <int OD, bool COST>
 __device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int n_w, bool more, int nb,
                                              const float* buf, const float* map, int zcap, float* acc, int lane,
@@ -566,9 +560,7 @@ __device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int
         __syncwarp();
         if (j + 1 < n_w || more) {
             const int jn = j + 1 < n_w ? j + 1 : 0;
-            const int jq = jn + 1 < n_w ? jn + 1 : 0;
             tile_copy_async(buf_a, P2w + jn * step, lane);
-            prefetch_tile_l2(P2w + jq * step, lane);
         }
         // the trailer is written by the joint-P kernel; clamp it anyway so
         // that no shared-memory index can leave the chunk's rows
@@ -655,16 +647,12 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         // this warp's tiles of the chunk: a contiguous W-th of the block's
         // share (so that its consecutive tiles share their row block: its row
         // sums are added to the accumulators once per row block); the copy of
-        // the first starts (and the second is asked of L2) before the map is
-        // even loaded
+        // the first starts before the map is even loaded
         const int w0 = (int)((long long)S.nq * warp / W);
         const int n_w = (int)((long long)S.nq * (warp + 1) / W) - w0;
         const int64_t step = kPTileStride;
         const float* P2w = A.P2 + (A.ptile_off[c] + S.first + w0) * kPTileStride;
-        if (n_w > 0) {
-            tile_copy_async(smem_u32(wbuf), P2w, lane);
-            if (n_w > 1) prefetch_tile_l2(P2w + step, lane);
-        }
+        if (n_w > 0) tile_copy_async(smem_u32(wbuf), P2w, lane);
 
         for (int i = tid; i < zr; i += nthreads) {
 #pragma unroll
@@ -728,10 +716,21 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 if (rank == 0 && tid == 0 && A.Zc) A.Zc[c] = tot[0];
                 const float invZ = (float)(1.0 / tot[0]);
                 const float eta = A.opt.lr_mode == PTSNE_LR_PAPER ? s_eta : A.opt.lr;
+                // each thread's rows: every load of a row (the accumulators of
+                // the cluster's blocks, the velocity and gains in HBM) is issued
+                // before any of its arithmetic (two rows at a time measured
+                // slower: the registers they take spill elsewhere)
                 for (int i = ulo + tid; i < uhi; i += nthreads) {
-                    float Av[OD], Rv[OD], y[OD];
+                    const int64_t gi = (off + i) * OD;
+                    float Av[OD], Rv[OD], y[OD], vel[OD], gn[OD];
 #pragma unroll
-                    for (int k = 0; k < OD; ++k) { Av[k] = 0.f; Rv[k] = 0.f; y[k] = map[map_idx<OD>(zcap, i, k)]; }
+                    for (int k = 0; k < OD; ++k) {
+                        y[k] = map[map_idx<OD>(zcap, i, k)];
+                        vel[k] = A.vel[gi + k];
+                        gn[k] = A.gains[gi + k];
+                        Av[k] = 0.f;
+                        Rv[k] = 0.f;
+                    }
                     for (uint32_t rr = 0; rr < K; ++rr) {
 #pragma unroll
                         for (int k = 0; k < OD; ++k) {
@@ -744,9 +743,12 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                             }
                         }
                     }
-                    const int64_t gi = (off + i) * OD;
-                    update_point<OD>(y, A.vel + gi, A.gains + gi, Av, Rv, invZ, eta, A.opt,
-                                     A.gradp ? A.gradp + gi : nullptr);
+                    update_point<OD>(y, vel, gn, Av, Rv, invZ, eta, A.opt, A.gradp ? A.gradp + gi : nullptr);
+#pragma unroll
+                    for (int k = 0; k < OD; ++k) {
+                        A.vel[gi + k] = vel[k];
+                        if (A.opt.use_gains) A.gains[gi + k] = gn[k];
+                    }
                     for (uint32_t rr = 0; rr < K; ++rr)
 #pragma unroll
                         for (int k = 0; k < OD; ++k) {
