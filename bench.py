@@ -246,6 +246,8 @@ def compare_forms(w, Xd, perms, dev, stream, tuning):
     # ("auto": ptsne_autotune_form; "all_mixed": BF16 Gram + window for every chunk)
     kinds = {"plain_fp32": dict(precision="fp32", schedule="per_chunk", use_graph=0),
              "batched_fp32": dict(precision="fp32", schedule="batched", use_graph=1),
+             # fixed-point accumulators: bitwise repeatable (fewer warps on the largest chunks)
+             "batched_fp32_deterministic": dict(precision="fp32", schedule="batched", use_graph=1, det=True),
              "batched_bf16_window": dict(precision="bf16_window", schedule="batched", use_graph=1, form="auto"),
              "batched_bf16_window_all_mixed": dict(precision="bf16_window", schedule="batched", use_graph=1,
                                                    form="all_mixed"),
@@ -256,11 +258,14 @@ def compare_forms(w, Xd, perms, dev, stream, tuning):
     for name, kw in kinds.items():
         kw = dict(kw)
         form = kw.pop("form", None)
+        det = kw.pop("det", False)
         cfg = ptsne.Config(n=w.n, d=w.d, offsets=w.offsets, perplexity=w.perplexity, iters=w.iters, lr=w.lr,
                            momentum=w.momentum, **kw)
         with ptsne.Context(cfg) as c:
             if kw["schedule"] == "batched":
                 c.set_tuning(*tuning)
+            if det:
+                c.set_deterministic(True)
             if form == "auto":
                 c.autotune_form(Xd, perms[0])
             frec = c.form_record() if form else None
@@ -277,6 +282,8 @@ def compare_forms(w, Xd, perms, dev, stream, tuning):
         if form:
             out[name]["form"] = form
             out[name]["distance_form"] = frec
+        if det:
+            out[name]["deterministic"] = True
     base = out["plain_fp32"]
     for name, r in out.items():
         r["speedup_vs_plain"] = r["value"] / base["value"]

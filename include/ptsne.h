@@ -191,6 +191,19 @@ int ptsne_set_tuning(ptsne_ctx* ctx, const ptsne_tuning* tuning);
  * per-chunk schedule. */
 int ptsne_set_locality_order(ptsne_ctx* ctx, int on);
 
+/* Summation order of the batched iteration kernel (Eq. 6 sums A_i and R_i).
+ * 0 (default): FP32 atomic adds in shared memory, whose order varies from
+ * run to run, so that two identical runs agree to about 1e-7 relative per
+ * iteration, not bit for bit.  1: the sums are kept in 64-bit fixed point
+ * (A at 2^-61, R at 2^-48; integer adds do not depend on their order), so
+ * that identical runs on one GPU give bitwise identical maps and costs; it
+ * doubles the accumulators' shared memory, so the largest chunks run with
+ * fewer warps (slower).  The per-chunk schedule sums in a fixed order in
+ * either mode.  PTSNE_EINVAL if the largest chunk does not fit the
+ * deterministic kernel (2-D maps: z up to about 5600, with all 16 warps up
+ * to about 4100; 3-D maps: up to about 3700). */
+int ptsne_set_deterministic(ptsne_ctx* ctx, int on);
+
 /* Form of each chunk's distances under PTSNE_PREC_BF16_WINDOW.  A row's
  * window (the pairs whose weight exp(-beta (d - m)) can reach e^-25 of the
  * row's largest, the BF16 error bound included) is what the FP32 recompute

@@ -106,6 +106,11 @@ __device__ __forceinline__ double ld_cl_f64(uint32_t a) {
     asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
     return v;
 }
+__device__ __forceinline__ long long ld_cl_s64(uint32_t a) {
+    long long v;
+    asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(a));
+    return v;
+}
 __device__ __forceinline__ int ld_cl_s32(uint32_t a) {
     int v;
     asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
@@ -142,6 +147,26 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
     f2 d;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
+}
+
+// ---------------------------------------------------------------- accumulators
+// A and R of a pass are summed in shared memory with atomic adds: FP32 (the
+// order of the adds, and so the last bits of the sums, varies from run to
+// run), or, in the deterministic build, 64-bit fixed point, whose integer adds
+// do not depend on their order.  Fixed point: A_i has |A_i| <= 1/2 (sum_j
+// P_ij <= 1 and |w d| <= 1/2), kept at 2^-61; R_i has |R_i| <= 0.33 (z - 1)
+// < 2700 (|w^2 d| <= 0.33), kept at 2^-48; both stay below 2^62.  The layout
+// (quantity k of row i at k zcap + i) is the same; a deterministic entry is
+// 8 bytes.
+constexpr float kFixA = 2305843009213693952.0f;   // 2^61
+constexpr float kFixR = 281474976710656.0f;       // 2^48
+template <bool DET>
+__device__ __forceinline__ void acc_add(float* acc, int idx, float v, bool isR) {
+    if constexpr (DET)
+        atomicAdd(reinterpret_cast<unsigned long long*>(acc) + idx,
+                  (unsigned long long)__float2ll_rn(v * (isR ? kFixR : kFixA)));
+    else
+        atomicAdd(acc + idx, v);
 }
 
 // ---------------------------------------------------------------- tile evaluation
@@ -237,6 +262,7 @@ __device__ __forceinline__ void rows2_begin(Rows2& R, const float* map, int a, i
 
 // The row sums of the four rings are reduced over lanes g, g + 8, g + 16,
 // g + 24, each keeping one row, and added to acc.
+template <bool DET>
 __device__ __forceinline__ void rows2_flush(const Rows2& R, int zcap, int a, int lane, float* acc) {
     const int g = lane & 7, q = lane >> 3;
     float v[4][4];
@@ -263,7 +289,7 @@ __device__ __forceinline__ void rows2_flush(const Rows2& R, int zcap, int a, int
     for (int k = 0; k < 4; ++k) {
         const float keep = odd ? w2[1][k] : w2[0][k];
         const float give = odd ? w2[0][k] : w2[1][k];
-        atomicAdd(acc + k * zcap + row, keep + __shfl_xor_sync(0xffffffffu, give, 8));
+        acc_add<DET>(acc, k * zcap + row, keep + __shfl_xor_sync(0xffffffffu, give, 8), k >= 2);
     }
 }
 
@@ -276,7 +302,7 @@ __device__ __forceinline__ void rows2_flush(const Rows2& R, int zcap, int a, int
 // only.  Returns the lane's sum of w (both orders of each pair of an
 // off-diagonal tile).  After the first step it starts the copy of the
 // warp's next tile nsrc (if any) into the warp's buffer at buf_a.
-template <bool SYM>
+template <bool SYM, bool DET>
 __device__ __forceinline__ float tile_grad_2d(Rows2& R, const float* map, int zcap, int b, int lane,
                                               const float4 (&pv)[8], float* acc, const float* nsrc, uint32_t buf_a) {
     const float4* mp = reinterpret_cast<const float4*>(map);
@@ -341,20 +367,20 @@ __device__ __forceinline__ float tile_grad_2d(Rows2& R, const float* map, int zc
         const int col = b * kPT + 8 * q + 2 * ((u + 3) & 3) + oddg;
         float lo, hv;
         upk(CAX, lo, hv);
-        atomicAdd(acc + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
+        acc_add<DET>(acc, col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), false);
         upk(CAY, lo, hv);
-        atomicAdd(acc + zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
+        acc_add<DET>(acc, zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), false);
         upk(CRX, lo, hv);
-        atomicAdd(acc + 2 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
+        acc_add<DET>(acc, 2 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), true);
         upk(CRY, lo, hv);
-        atomicAdd(acc + 3 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)));
+        acc_add<DET>(acc, 3 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), true);
         return 2.0f * hsum2(Z);
     }
     return hsum2(Z);
 }
 
 // Same sums for 3-D maps (scalar arithmetic, same lane order and packets).
-template <bool SYM>
+template <bool SYM, bool DET>
 __device__ __forceinline__ float tile_grad_3d(const float* map, int zcap, int a, int b, int lane,
                                               const float4 (&pv)[8], float* acc) {
     const int g = lane & 15, h = lane >> 4;
@@ -418,16 +444,16 @@ __device__ __forceinline__ float tile_grad_3d(const float* map, int zcap, int a,
     const int row = ra + h;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        atomicAdd(acc + k * zcap + row, keep_row(ra_[0][k], ra_[1][k], h));
-        atomicAdd(acc + (3 + k) * zcap + row, keep_row(rr_[0][k], rr_[1][k], h));
+        acc_add<DET>(acc, k * zcap + row, keep_row(ra_[0][k], ra_[1][k], h), false);
+        acc_add<DET>(acc, (3 + k) * zcap + row, keep_row(rr_[0][k], rr_[1][k], h), true);
     }
     if constexpr (SYM) {
         const int prv = (lane & 16) | ((g + 15) & 15);
         const int col = cb + ((g + 14) & 15);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            atomicAdd(acc + k * zcap + col, -(ca[0][k] + __shfl_sync(0xffffffffu, ca[1][k], prv)));
-            atomicAdd(acc + (3 + k) * zcap + col, -(cr[0][k] + __shfl_sync(0xffffffffu, cr[1][k], prv)));
+            acc_add<DET>(acc, k * zcap + col, -(ca[0][k] + __shfl_sync(0xffffffffu, ca[1][k], prv)), false);
+            acc_add<DET>(acc, (3 + k) * zcap + col, -(cr[0][k] + __shfl_sync(0xffffffffu, cr[1][k], prv)), true);
         }
         return 2.0f * z;
     }
@@ -545,7 +571,7 @@ struct KSum {
 // pass the copy starts after the tile's first step, by when the warp's
 // reads of the buffer have long returned (measured 1.5% faster than
 // waiting for them before the first step).
-template <int OD, bool COST>
+template <int OD, bool COST, bool DET>
 __device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int n_w, bool more, int nb,
                                              const float* buf, const float* map, int zcap, float* acc, int lane,
                                              KSum (&part)[4]) {
@@ -586,15 +612,15 @@ __device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int
             float zl;
             if constexpr (OD == 2) {
                 if (a != cur_a) {   // warp-uniform: a new row block
-                    if (cur_a >= 0) rows2_flush(R, zcap, cur_a, lane, acc);
+                    if (cur_a >= 0) rows2_flush<DET>(R, zcap, cur_a, lane, acc);
                     rows2_begin(R, map, a, lane);
                     cur_a = a;
                 }
-                zl = diag ? tile_grad_2d<false>(R, map, zcap, b, lane, pv, acc, nsrc, buf_a)
-                          : tile_grad_2d<true>(R, map, zcap, b, lane, pv, acc, nsrc, buf_a);
+                zl = diag ? tile_grad_2d<false, DET>(R, map, zcap, b, lane, pv, acc, nsrc, buf_a)
+                          : tile_grad_2d<true, DET>(R, map, zcap, b, lane, pv, acc, nsrc, buf_a);
             } else {
-                zl = diag ? tile_grad_3d<false>(map, zcap, a, b, lane, pv, acc)
-                          : tile_grad_3d<true>(map, zcap, a, b, lane, pv, acc);
+                zl = diag ? tile_grad_3d<false, DET>(map, zcap, a, b, lane, pv, acc)
+                          : tile_grad_3d<true, DET>(map, zcap, a, b, lane, pv, acc);
             }
             part[0].add(zl - drop);
         } else {
@@ -613,7 +639,7 @@ __device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int
         }
     }
     if constexpr (OD == 2 && !COST) {
-        if (cur_a >= 0) rows2_flush(R, zcap, cur_a, lane, acc);
+        if (cur_a >= 0) rows2_flush<DET>(R, zcap, cur_a, lane, acc);
     }
 }
 
@@ -621,7 +647,7 @@ __device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int
 // both 128 registers per thread.  3-D maps: 672 (21 warps, 80 registers) or
 // 544 (17, 96 registers).  Registers are granted per 4 warps, so 21 warps
 // get 80, 17 to 20 warps 96 and 16 or fewer 128.
-template <int OD, int MAXT>
+template <int OD, int MAXT, bool DET>
 __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -673,7 +699,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
 #pragma unroll
             for (int k = 0; k < OD; ++k) map[map_idx<OD>(zcap, i, k)] = i < z ? A.Yc[(off + i) * OD + k] : kPad * (float)(i - z + 1);
         }
-        for (int i = tid; i < 2 * OD * zcap; i += nthreads) acc[i] = 0.f;
+        for (int i = tid; i < (DET ? 4 : 2) * OD * zcap; i += nthreads) acc[i] = 0.f;
         __syncthreads();
 
         for (int it = 0; it < npass; ++it) {
@@ -701,8 +727,8 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) part[k].clear();
             const bool more = it + 1 < npass;
-            if (!cost) consume_pass<OD, false>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
-            else consume_pass<OD, true>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
+            if (!cost) consume_pass<OD, false, DET>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
+            else consume_pass<OD, true, DET>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
             // block partials (fixed order), then the cluster total; a gradient pass
             // has only Z (the cost sums are zero there)
             const int nsum = cost ? 4 : 1;
@@ -746,15 +772,39 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                         Av[k] = 0.f;
                         Rv[k] = 0.f;
                     }
-                    for (uint32_t rr = 0; rr < K; ++rr) {
+                    if constexpr (DET) {   // integer sums over the cluster, then to float
+                        const long long* acc64 = reinterpret_cast<const long long*>(acc);
+                        long long sa[OD], sr[OD];
+#pragma unroll
+                        for (int k = 0; k < OD; ++k) sa[k] = sr[k] = 0;
+                        for (uint32_t rr = 0; rr < K; ++rr) {
+#pragma unroll
+                            for (int k = 0; k < OD; ++k) {
+                                if (K > 1) {
+                                    sa[k] += ld_cl_s64(map_rank(smem_u32(acc64 + k * zcap + i), rr));
+                                    sr[k] += ld_cl_s64(map_rank(smem_u32(acc64 + (OD + k) * zcap + i), rr));
+                                } else {
+                                    sa[k] += acc64[k * zcap + i];
+                                    sr[k] += acc64[(OD + k) * zcap + i];
+                                }
+                            }
+                        }
 #pragma unroll
                         for (int k = 0; k < OD; ++k) {
-                            if (K > 1) {
-                                Av[k] += ld_cl_f32(map_rank(smem_u32(acc + k * zcap + i), rr));
-                                Rv[k] += ld_cl_f32(map_rank(smem_u32(acc + (OD + k) * zcap + i), rr));
-                            } else {
-                                Av[k] += acc[k * zcap + i];
-                                Rv[k] += acc[(OD + k) * zcap + i];
+                            Av[k] = (float)((double)sa[k] * (1.0 / (double)kFixA));
+                            Rv[k] = (float)((double)sr[k] * (1.0 / (double)kFixR));
+                        }
+                    } else {
+                        for (uint32_t rr = 0; rr < K; ++rr) {
+#pragma unroll
+                            for (int k = 0; k < OD; ++k) {
+                                if (K > 1) {
+                                    Av[k] += ld_cl_f32(map_rank(smem_u32(acc + k * zcap + i), rr));
+                                    Rv[k] += ld_cl_f32(map_rank(smem_u32(acc + (OD + k) * zcap + i), rr));
+                                } else {
+                                    Av[k] += acc[k * zcap + i];
+                                    Rv[k] += acc[(OD + k) * zcap + i];
+                                }
                             }
                         }
                     }
@@ -773,7 +823,8 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 }
             }
             sync_owner(K);   // new map everywhere; remote reads of acc are done
-            for (int i = tid; i < OD * zcap / 2; i += nthreads)   // 2 OD zcap floats, zcap a multiple of 32
+            // 2 OD zcap entries of 4 (8 if DET) bytes, zcap a multiple of 32
+            for (int i = tid; i < (DET ? 2 : 1) * OD * zcap / 2; i += nthreads)
                 reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             __syncthreads();
         }
@@ -786,17 +837,18 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
 
 // ---------------------------------------------------------------- launchers
 
-int iterate_smem_bytes(int od, int64_t zmax, int warps) {
+int iterate_smem_bytes(int od, int64_t zmax, int warps, bool det) {
     const int zcap = (int)((zmax + kPT - 1) / kPT * kPT);
-    // a tile buffer per warp, map + A + R (structure-of-arrays; a 2-D map as column pairs)
-    return warps * kPTileStride * 4 + zcap * 3 * od * 4;
+    // a tile buffer per warp, the map (a 2-D map as column pairs), A and R
+    // (structure-of-arrays; 8-byte fixed point when deterministic)
+    return warps * kPTileStride * 4 + zcap * od * 4 + zcap * 2 * od * (det ? 8 : 4);
 }
 
 // Warps (at most `want`) whose tile buffers fit beside the map and the
 // accumulators in 227 KB of shared memory; 0 if not even one fits.
-int iterate_warps(int od, int64_t zmax, int want) {
+int iterate_warps(int od, int64_t zmax, int want, bool det) {
     int w = want;
-    while (w > 0 && iterate_smem_bytes(od, zmax, w) > 227 * 1024 - kStaticSmem) --w;
+    while (w > 0 && iterate_smem_bytes(od, zmax, w, det) > 227 * 1024 - kStaticSmem) --w;
     return w;
 }
 
@@ -811,9 +863,10 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     // very large chunks leave room for fewer tile buffers
     if (c->p.out_dim == 2 && Wc > 16) Wc = 16;
     if (c->p.out_dim == 3 && Wc > 21) Wc = 21;
-    Wc = iterate_warps(c->p.out_dim, c->zmax, Wc);
+    const bool det = c->deterministic;
+    Wc = iterate_warps(c->p.out_dim, c->zmax, Wc, det);
     if (Wc < 1) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, Wc);
+    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, Wc, det);
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     IterArgs a;
@@ -834,8 +887,13 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
 
     // the build for the fewest threads that hold the block: more registers per thread
     void (*kern)(IterArgs);
-    if (c->p.out_dim == 2) kern = Wc > 12 ? iterate_kernel<2, 512> : iterate_kernel<2, 384>;
-    else kern = Wc > 17 ? iterate_kernel<3, 672> : iterate_kernel<3, 544>;
+    if (c->p.out_dim == 2) {
+        if (det) kern = Wc > 12 ? iterate_kernel<2, 512, true> : iterate_kernel<2, 384, true>;
+        else kern = Wc > 12 ? iterate_kernel<2, 512, false> : iterate_kernel<2, 384, false>;
+    } else {
+        if (det) kern = Wc > 17 ? iterate_kernel<3, 672, true> : iterate_kernel<3, 544, true>;
+        else kern = Wc > 17 ? iterate_kernel<3, 672, false> : iterate_kernel<3, 544, false>;
+    }
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;

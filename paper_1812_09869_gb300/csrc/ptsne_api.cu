@@ -162,7 +162,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         return bad("precision", p.precision);
     if (p.schedule != PTSNE_SCHED_BATCHED && p.schedule != PTSNE_SCHED_PER_CHUNK) return bad("schedule", p.schedule);
     if (p.use_graph != 0 && p.use_graph != 1) return bad("use_graph must be 0 or 1", p.use_graph);
-    if (p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(p.out_dim, zmax, 1) < 1)
+    if (p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(p.out_dim, zmax, 1, false) < 1)
         return bad("largest chunk too large for the batched schedule at this out_dim", zmax);
 
     c->p = p;
@@ -821,6 +821,15 @@ int ptsne_set_locality_order(ptsne_ctx* c, int on) {
     if (c->p.schedule != PTSNE_SCHED_BATCHED)
         return fail(c, PTSNE_EINVAL, "the locality order needs the batched schedule%s%lld");
     c->locality = on != 0;
+    return PTSNE_OK;
+}
+
+int ptsne_set_deterministic(ptsne_ctx* c, int on) {
+    if (!c) return PTSNE_EINVAL;
+    if (on && c->p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(c->p.out_dim, c->zmax, 1, true) < 1)
+        return fail(c, PTSNE_EINVAL, "largest chunk too large for the deterministic batched kernel%s (%lld)", "",
+                    (long long)c->zmax);
+    c->deterministic = on != 0;
     return PTSNE_OK;
 }
 

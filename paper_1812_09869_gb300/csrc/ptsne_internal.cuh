@@ -225,6 +225,7 @@ struct ptsne_ctx {
     float* ycold = nullptr;            // ptsne_mlp_warm_start: the cold start's map (lazily allocated)
     // locality order of the rows within each chunk (batched schedule)
     bool locality = false;             // on: each affinities call orders the chunks' rows (ptsne_set_locality_order)
+    bool deterministic = false;        // on: fixed-point accumulators in the batched kernel (ptsne_set_deterministic)
     bool loc_active = false;           // the kept affinities were computed in locality order
     int32_t* perm_loc = nullptr;       // n: the partition in locality order
     int32_t* src_row = nullptr;        // n: position in the caller's partition of each row of perm_loc
@@ -316,8 +317,8 @@ cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t 
 cudaError_t launch_count_nonzero(const ptsne_ctx* c, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc,
                            double* cost_chunk, cudaStream_t s);
-int iterate_warps(int od, int64_t zmax, int want);   // 0 if the map does not fit in shared memory
-int iterate_smem_bytes(int od, int64_t zmax, int warps);
+int iterate_warps(int od, int64_t zmax, int want, bool det);   // 0 if the map does not fit in shared memory
+int iterate_smem_bytes(int od, int64_t zmax, int warps, bool det);
 
 Layout make_layout(const ptsne_ctx* c);
 

@@ -121,6 +121,7 @@ def lib():
         L.ptsne_reset_counters.argtypes = [vp]
         L.ptsne_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.ptsne_set_locality_order.argtypes = [vp, C.c_int]
+        L.ptsne_set_deterministic.argtypes = [vp, C.c_int]
         L.ptsne_set_form_threshold.argtypes = [vp, C.c_double]
         L.ptsne_autotune_form.argtypes = [vp, vp, vp, vp]
         L.ptsne_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
@@ -272,6 +273,10 @@ class Context:
 
     def set_locality_order(self, on: bool):
         return self._check(lib().ptsne_set_locality_order(self.h, int(bool(on))))
+
+    def set_deterministic(self, on: bool):
+        """Fixed-point accumulation in the batched kernel: bitwise repeatable runs."""
+        return self._check(lib().ptsne_set_deterministic(self.h, int(bool(on))))
 
     def set_form_threshold(self, threshold: float):
         """BF16_WINDOW: chunks whose size bin's window fraction is >= threshold

@@ -116,3 +116,45 @@ def test_identical_runs_give_identical_maps(dev):
             assert st.bisect_failed_rows == 0
     assert rel_max(outs[0][0] - Y0, outs[1][0] - Y0) <= 1e-5
     assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-6 * np.abs(outs[0][1]).max()
+
+
+@pytest.mark.parametrize("tuning", [(2, 1, 16), (1, 1, 12)])
+def test_deterministic_runs_are_bitwise_identical(dev, tuning):
+    """With fixed-point accumulation (ptsne_set_deterministic) two identical
+    multi-epoch runs give the same map and costs bit for bit, in either
+    launch shape, and agree with the FP32-atomic kernel to its tolerance."""
+    from paper_1812_09869_gb300 import ptsne
+    X, off, perms, Y0 = _setup(epochs=3)
+    cfg = ptsne.Config(n=X.shape[0], d=X.shape[1], offsets=off, perplexity=30.0, iters=5,
+                       precision="bf16_window")
+    Xd, Pd = torch.from_numpy(X).to(dev), torch.from_numpy(perms).to(dev)
+    outs = []
+    with ptsne.Context(cfg) as ctx:
+        ctx.set_tuning(*tuning)
+        for det in (True, True, False):
+            ctx.set_deterministic(det)
+            Yd = torch.from_numpy(Y0.copy()).to(dev)
+            cost = np.zeros((3, 3))
+            ctx.run(Xd, Pd, 3, Yd, cost_out=cost)
+            torch.cuda.synchronize()
+            outs.append((Yd.cpu().numpy(), cost.copy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert rel_max(outs[0][0] - Y0, outs[2][0] - Y0) <= 1e-4
+    assert np.abs(outs[0][1] - outs[2][1]).max() <= 1e-5 * np.abs(outs[2][1]).max()
+
+
+def test_deterministic_mode_limits():
+    """ptsne_set_deterministic refuses a chunk too large for the fixed-point
+    accumulators of the batched kernel and accepts it on the per-chunk
+    schedule (no GPU work is done)."""
+    from paper_1812_09869_gb300 import ptsne
+    for schedule, ok in (("batched", False), ("per_chunk", True)):
+        cfg = ptsne.Config(n=6000, d=4, offsets=np.array([0, 6000]), perplexity=30.0, iters=1, schedule=schedule)
+        with ptsne.Context(cfg) as ctx:
+            if ok:
+                ctx.set_deterministic(True)
+            else:
+                with pytest.raises(ptsne.PtsneError):
+                    ctx.set_deterministic(True)
+            ctx.set_deterministic(False)

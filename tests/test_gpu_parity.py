@@ -137,8 +137,8 @@ def test_step_three_dims_paper_lr_no_gains(dev, schedule):
         assert rel_max(Y1[idx] - Y0[idx], Yr - Y0[idx]) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("tuning", [(2, 1, 20), (1, 1, 12)])
-def test_three_dims_every_build_gradient_and_cost(dev, tuning):
+@pytest.mark.parametrize("tuning,det", [((2, 1, 20), False), ((1, 1, 12), False), ((2, 1, 20), True)])
+def test_three_dims_every_build_gradient_and_cost(dev, tuning, det):
     """3-D maps through both builds of the batched kernel for 3-D (more and
     fewer than 18 warps): one step's gradient and Z, and the cost
     (Eq. 5, Eq. 9), against the oracle; two chunks with ragged last blocks."""
@@ -148,6 +148,7 @@ def test_three_dims_every_build_gradient_and_cost(dev, tuning):
     Y0 = synth.init_gaussian(1300, 3, 2.0, seed=62)
     ctx, Xd, pd, _, _ = _gpu_affinities(dev, X, perm, off, perplexity=12.0, out_dim=3)
     ctx.set_tuning(*tuning)
+    ctx.set_deterministic(det)
     Yd = torch.from_numpy(Y0.copy()).to(dev)
     cost = torch.zeros(2, dtype=torch.float64, device=dev)
     ctx.cost(pd, Yd, cost)
@@ -316,9 +317,10 @@ def test_invalid_launch_shapes_are_rejected(dev):
     ctx.close()
 
 
-@pytest.mark.parametrize("tuning", TUNINGS)
-def test_gradient_for_every_launch_shape(dev, tuning):
-    """Gradient, Z, updated map and cost of one step for each launch shape,
+@pytest.mark.parametrize("tuning,det", [(t, False) for t in TUNINGS] + [((2, 1, 16), True), ((1, 1, 5), True)])
+def test_gradient_for_every_launch_shape(dev, tuning, det):
+    """Gradient, Z, updated map and cost of one step for each launch shape
+    (and, det, with the fixed-point accumulators of ptsne_set_deterministic),
     on uneven chunks (an odd and an even number of 32-row blocks, a ragged
     tail, and a chunk smaller than one block) against the oracle."""
     X, _ = synth.gaussian_mixture(2100, 9, 5, seed=50, anisotropic=True)
@@ -327,6 +329,7 @@ def test_gradient_for_every_launch_shape(dev, tuning):
     Y0 = synth.init_gaussian(2100, 2, 2.0, seed=52)
     ctx = _ctx(X, off, perplexity=5.0)
     ctx.set_tuning(*tuning)
+    ctx.set_deterministic(det)
     assert ctx.tuning() == tuning
     Xd, pd = torch.from_numpy(X).to(dev), torch.from_numpy(perm).to(dev)
     ctx.affinities(Xd, pd)
