@@ -43,6 +43,7 @@ namespace {
 constexpr float kPad = 1e18f;
 constexpr float kLn2f = 0.69314718055994531f;
 constexpr int kStaticSmem = 2048;               // bound on the kernel's static shared memory
+constexpr int kMaxWarps = 24;                   // warps per block (the builds run at most 21)
 }  // namespace
 
 struct IterArgs {
@@ -572,9 +573,8 @@ struct KSum {
 // reads of the buffer have long returned (measured 1.5% faster than
 // waiting for them before the first step).
 template <int OD, bool COST, bool DET>
-__device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int n_w, bool more, int nb,
-                                             const float* buf, const float* map, int zcap, float* acc, int lane,
-                                             KSum (&part)[4]) {
+__device__ __forceinline__ void consume_pass(const float* P2b, int w0, int n_w, int next0, int nb, const float* buf,
+                                             const float* map, int zcap, float* acc, int lane, KSum (&part)[4]) {
     // w of the pair (i, i), which a diagonal tile's row-wise pass counts in
     // its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own columns)
     // (ring-8 layout: lanes with q == g / 2 meet their own four rows;
@@ -591,7 +591,8 @@ __device__ __forceinline__ void consume_pass(const float* P2w, int64_t step, int
         const int2 ab = *reinterpret_cast<const int2*>(buf + kPTileFloats);
         float4 pv[8];
         tile_lane_values(buf, lane, pv);
-        const float* nsrc = (j + 1 < n_w || more) ? P2w + (j + 1 < n_w ? j + 1 : 0) * step : nullptr;
+        const int qn = j + 1 < n_w ? w0 + j + 1 : next0;
+        const float* nsrc = qn >= 0 ? P2b + (int64_t)qn * kPTileStride : nullptr;
         if (OD != 2 || COST) {
             // the reads have returned (their registers are used here) before the
             // next copy may overwrite the buffer
@@ -666,6 +667,8 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     __shared__ int s_item;
     __shared__ float s_mn[32], s_mx[32];
     __shared__ float s_eta;
+    __shared__ int s_cut[2][kMaxWarps + 1];        // warp pieces of the block's share: passes 0-1, passes 2+
+    __shared__ long long s_cyc[kMaxWarps];          // each warp's cycles in the chunk's first pass
 
     const uint32_t K = cl_size(), rank = cl_rank();
     for (;;) {
@@ -685,15 +688,22 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         const int ulo = (int)rank * slice, uhi = min(z, ulo + slice);
         const int npass = A.iters + (A.cost_pass ? 1 : 0);
 
-        // this warp's tiles of the chunk: a contiguous W-th of the block's
+        // this warp's tiles of the chunk: a contiguous piece of the block's
         // share (so that its consecutive tiles share their row block: its row
-        // sums are added to the accumulators once per row block); the copy of
-        // the first starts before the map is even loaded
-        const int w0 = (int)((long long)S.nq * warp / W);
-        const int n_w = (int)((long long)S.nq * (warp + 1) / W) - w0;
-        const int64_t step = kPTileStride;
-        const float* P2w = A.P2 + (A.ptile_off[c] + S.first + w0) * kPTileStride;
-        if (n_w > 0) tile_copy_async(smem_u32(wbuf), P2w, lane);
+        // sums are added to the accumulators once per row block), equal
+        // pieces in the first two passes and, from the third, pieces sized to
+        // each warp's measured rate in the first (the warps of a block do not
+        // run at quite the same speed, and a pass waits for the slowest; the
+        // deterministic build keeps equal pieces, whose FP32 partial sums do
+        // not depend on timing); the copy of the first tile starts before the
+        // map is even loaded
+        const float* P2b = A.P2 + (A.ptile_off[c] + S.first) * kPTileStride;
+        if (tid <= W) s_cut[0][tid] = s_cut[1][tid] = (int)((long long)S.nq * tid / W);
+        {
+            const int w0 = (int)((long long)S.nq * warp / W);
+            if ((int)((long long)S.nq * (warp + 1) / W) > w0)
+                tile_copy_async(smem_u32(wbuf), P2b + (int64_t)w0 * kPTileStride, lane);
+        }
 
         for (int i = tid; i < zr; i += nthreads) {
 #pragma unroll
@@ -726,9 +736,16 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             KSum part[4];                              // Z, sum p ln p, sum p ln w, sum p
 #pragma unroll
             for (int k = 0; k < 4; ++k) part[k].clear();
-            const bool more = it + 1 < npass;
-            if (!cost) consume_pass<OD, false, DET>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
-            else consume_pass<OD, true, DET>(P2w, step, n_w, more, nb, wbuf, map, zcap, acc, lane, part);
+            const int* cut = s_cut[it >= 2 ? 1 : 0];
+            const int* cut_n = s_cut[it + 1 >= 2 ? 1 : 0];
+            const int w0 = cut[warp], n_w = cut[warp + 1] - w0;
+            // the next pass's first tile of this warp (none after the chunk's
+            // last pass, or if its next piece is empty)
+            const int next0 = it + 1 < npass && cut_n[warp + 1] > cut_n[warp] ? cut_n[warp] : -1;
+            const long long t_pass = clock64();
+            if (!cost) consume_pass<OD, false, DET>(P2b, w0, n_w, next0, nb, wbuf, map, zcap, acc, lane, part);
+            else consume_pass<OD, true, DET>(P2b, w0, n_w, next0, nb, wbuf, map, zcap, acc, lane, part);
+            if (it == 0 && lane == 0) s_cyc[warp] = clock64() - t_pass;
             // block partials (fixed order), then the cluster total; a gradient pass
             // has only Z (the cost sums are zero there)
             const int nsum = cost ? 4 : 1;
@@ -737,6 +754,19 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 if (lane == 0) s_red[warp][k] = v;
             }
             __syncthreads();
+            if (!DET && it == 0 && tid == 0 && S.nq >= 16 * W) {   // (deterministic: the pieces stay fixed)
+                // pieces from the third pass on: proportional to each warp's
+                // rate (tiles per cycle) in the first pass
+                float tot = 0.f;
+                for (int w = 0; w < W; ++w) tot += (float)(s_cut[0][w + 1] - s_cut[0][w]) / (float)max(s_cyc[w], 1ll);
+                float acc_r = 0.f;
+                for (int w = 0; w < W; ++w) {
+                    const float rate = (float)(s_cut[0][w + 1] - s_cut[0][w]) / (float)max(s_cyc[w], 1ll);
+                    s_cut[1][w] = min(S.nq, (int)((float)S.nq * (acc_r / tot) + 0.5f));
+                    acc_r += rate;
+                }
+                s_cut[1][W] = S.nq;
+            }
             if (tid < nsum) {
                 double v = 0.0;
                 for (int w = 0; w < W; ++w) v += s_red[w][tid];
