@@ -560,6 +560,27 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// s + v with the rounding error carried in c (error-free two-sum)
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v, float cv) {
+    const float t = s + v;
+    const float bb = t - s;
+    const float e = (s - (t - bb)) + (v - bb);
+    s = t;
+    c = c + cv + e;
+}
+// Sum over the warp of the lanes' compensated sums, exact to the FP32 sum of
+// the rounding errors (error-free two-sums on the shuffles; FP64 arithmetic,
+// slow on this GPU, only for lane 0's final conversion); lane 0 holds it.
+__device__ __forceinline__ double warp_sum_ksum(const KSum& k) {
+    float hi = k.s, lo = -k.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        two_sum_add(hi, lo, h2, l2);
+    }
+    return (double)hi + (double)lo;
+}
+
 // A warp's n_w tiles of one pass: tile j is stored at P2w + j * step (the
 // block's tile w + j W).  The warp owns one shared buffer: on entry it holds
 // (or is receiving) tile 0; for each tile the warp waits for its copy, reads
@@ -667,6 +688,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
     __shared__ int s_item;
     __shared__ float s_mn[32], s_mx[32];
     __shared__ float s_eta;
+    __shared__ float s_invZ;                        // 1 / Z of the pass
     __shared__ int s_cut[2][kMaxWarps + 1];        // warp pieces of the block's share: passes 0-1, passes 2+
     __shared__ long long s_cyc[kMaxWarps];          // each warp's cycles in the chunk's first pass
 
@@ -750,7 +772,7 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             // has only Z (the cost sums are zero there)
             const int nsum = cost ? 4 : 1;
             for (int k = 0; k < nsum; ++k) {
-                const double v = warp_sum(part[k].value());
+                const double v = warp_sum_ksum(part[k]);
                 if (lane == 0) s_red[warp][k] = v;
             }
             __syncthreads();
@@ -773,19 +795,28 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                 s_part[tid] = v;
             }
             sync_owner(K);
-            double tot[4] = {0.0, 0.0, 0.0, 0.0};
-            for (uint32_t rr = 0; rr < K; ++rr)
-                for (int k = 0; k < nsum; ++k)
-                    tot[k] += K > 1 ? ld_cl_f64(map_rank(smem_u32(&s_part[k]), rr)) : s_part[k];
-            if (cost) {
-                if (rank == 0 && tid == 0) {
-                    const double lnZ = log(tot[0]);
-                    A.cost_chunk[2 * c] = tot[1] - tot[2] + tot[3] * lnZ;
-                    A.cost_chunk[2 * c + 1] = (-tot[2] + tot[3] * lnZ) / (log((double)z) + log((double)(z - 1)));
+            // the cluster totals (FP64, in rank order), by one thread: FP64
+            // arithmetic is slow on this GPU, so the block's other threads
+            // take 1 / Z from shared memory
+            if (tid == 0) {
+                double tot[4] = {0.0, 0.0, 0.0, 0.0};
+                for (uint32_t rr = 0; rr < K; ++rr)
+                    for (int k = 0; k < nsum; ++k)
+                        tot[k] += K > 1 ? ld_cl_f64(map_rank(smem_u32(&s_part[k]), rr)) : s_part[k];
+                if (cost) {
+                    if (rank == 0) {
+                        const double lnZ = log(tot[0]);
+                        A.cost_chunk[2 * c] = tot[1] - tot[2] + tot[3] * lnZ;
+                        A.cost_chunk[2 * c + 1] = (-tot[2] + tot[3] * lnZ) / (log((double)z) + log((double)(z - 1)));
+                    }
+                } else {
+                    if (rank == 0 && A.Zc) A.Zc[c] = tot[0];
+                    s_invZ = (float)(1.0 / tot[0]);
                 }
-            } else {
-                if (rank == 0 && tid == 0 && A.Zc) A.Zc[c] = tot[0];
-                const float invZ = (float)(1.0 / tot[0]);
+            }
+            __syncthreads();
+            if (!cost) {
+                const float invZ = s_invZ;
                 const float eta = A.opt.lr_mode == PTSNE_LR_PAPER ? s_eta : A.opt.lr;
                 // each thread's rows: every load of a row (the accumulators of
                 // the cluster's blocks, the velocity and gains in HBM) is issued
