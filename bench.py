@@ -56,6 +56,10 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shape 'cluster,group,warps' of the iteration kernel, group 1 (skips the autotuner)")
+    ap.add_argument("--form", default=None, metavar="THRESHOLD[,LOCALITY]",
+                    help="BF16_WINDOW: fixed distance-form threshold (a chunk whose window fraction is >= it runs in "
+                         "FP32 whole; 2 = every chunk mixed) and locality order 0/1, instead of ptsne_autotune_form "
+                         "(for profiling runs, whose timings the profiler distorts)")
     return ap.parse_args(argv)
 
 
@@ -495,7 +499,12 @@ def bench_ours(args, rank, world, local_rank):
     # the distances), chosen by the library's autotuner
     if args.tuning:
         if precision == "bf16_window":
-            ctx.autotune_form(Xd, perms[0])
+            if args.form:
+                f = args.form.split(",")
+                ctx.set_form_threshold(float(f[0]))
+                ctx.set_locality_order(len(f) > 1 and f[1] == "1")
+            else:
+                ctx.autotune_form(Xd, perms[0])
         ctx.set_tuning(*[int(v) for v in args.tuning.split(",")])
         trials = []
     else:
