@@ -433,6 +433,272 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     if (warp == 0) tc::tmem_dealloc(tmem, NT < 32 ? 32 : NT);
 }
 
+// ---------------------------------------------------------------- fused inference
+// Inference of 128-row tiles in one persistent, warp-specialised kernel.
+// Layer 1 (X W1^T + b1, GELU) goes from tensor memory into shared memory as
+// the A operand of layer 2 (BF16, in the 128-byte-swizzled K-major layout
+// that TMA writes: row r, 16-byte chunk c of a 64-column K block at
+// r * 128 + ((c ^ (r mod 8)) * 16)), so the hidden activations never leave
+// the SM; layer 2 (+ b2, GELU) ends in the output head (y = W3 h + b3,
+// de-standardised).  Warp 0 (one thread) issues the TMA loads and the MMAs;
+// warps 1..16 are the epilogue (warp w reads tensor-memory lanes
+// 32 (w mod 4) .. + 31, one row per thread, and column group (w - 1) / 4 of
+// four 64-column groups, which is one K block of the layer-2 operand).  Two
+// accumulators (2 x 256 tensor-memory columns) let the tensor cores run
+// layer 2 of tile j and layer 1 of tile j + 1 while the epilogue warps take
+// layer 1 of tile j + 1 and layer 2 of tile j.  W1 stays in shared memory;
+// W2 streams from L2 in 128-row x 64-column boxes, four in flight.
+// Mbarrier waits are bounded; the first that runs out stops every role
+// (the epilogue warps still meet at their named barrier).
+constexpr int kInferEpiWarps = 16;
+constexpr int kInferThreads = 32 * (1 + kInferEpiWarps);
+constexpr int kW2Stages = 4;
+constexpr uint32_t kBox = 16384;                      // one 128-row x 64-column BF16 box
+constexpr uint32_t kOffW1 = 0;                        // W1: 2 boxes (256 rows)
+constexpr uint32_t kOffX = kOffW1 + 2 * kBox;         // X: 2 stages
+constexpr uint32_t kOffH1 = kOffX + 2 * kBox;         // layer-2 A operand: 4 K blocks
+constexpr uint32_t kOffW2 = kOffH1 + 4 * kBox;        // W2: kW2Stages boxes
+constexpr size_t kInferSmem = kOffW2 + kW2Stages * kBox + 1024;   // + 1024-byte alignment slack
+
+struct InferArgs {
+    int M;                  // valid rows of the slab
+    int mtiles;             // 128-row tiles of the slab
+    const float* b1;
+    const float* b2;
+    const bf16* W3;         // [OD][256]
+    const float* b3;
+    const double* scaler;   // mean[OD], std[OD]
+    float* Y;               // [M][OD]
+    unsigned int* timeouts;
+};
+
+// bounded wait that fails at once after any role's wait has failed
+__device__ __forceinline__ bool iwait(uint32_t bar, uint32_t parity, volatile int* fail) {
+    if (tc::mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = tc::now_ns();
+    while (!tc::mbar_try(bar, parity)) {
+        if (*fail || tc::now_ns() - t0 > tc::kWaitNs) {
+            *fail = 1;
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive1(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kInferEpiWarps) : "memory"); }
+
+template <int OD>
+__global__ void __launch_bounds__(kInferThreads, 1)
+mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
+                 const __grid_constant__ CUtensorMap tmW2, const InferArgs a) {
+    extern __shared__ unsigned char dsmem[];
+    // 0: W1 loaded; 1-2: X stage full; 3-6: W2 stage full; 7-10: W2 stage free;
+    // 11-12: layer 1 done (per accumulator); 13-14: layer 2 done; 15: H1
+    // written; 16-17: accumulator read by the layer-2 epilogue
+    __shared__ uint64_t bars[18];
+    __shared__ uint32_t tmem_base;
+    __shared__ float sb1[kH], sb2[kH];
+    __shared__ float sw3[OD][kH];
+    __shared__ float s_y[2][4][128][OD];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t sbase = (tc::smem_addr(dsmem) + 1023u) & ~1023u;
+    auto B = [&](int i) { return tc::smem_addr(&bars[i]); };
+    const int ntl = ((int)blockIdx.x < a.mtiles) ? (a.mtiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    auto tile_row = [&](int j) { return ((int)blockIdx.x + j * (int)gridDim.x) * 128; };
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem_base), 512);
+    if (tid == 0) {
+        s_fail = 0;
+        for (int i = 0; i < 18; ++i) tc::mbar_init(B(i), (i == 15 || i >= 16) ? (uint32_t)kInferEpiWarps : 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int n = tid; n < kH; n += kInferThreads) {
+        sb1[n] = a.b1[n];
+        sb2[n] = a.b2[n];
+    }
+    for (int idx = tid; idx < OD * kH; idx += kInferThreads) sw3[idx / kH][idx % kH] = __bfloat162float(a.W3[idx]);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int* fail = &s_fail;
+
+    if (warp == 0) {
+        if (lane == 0 && ntl > 0) {
+            const uint32_t id1 = tc::idesc_bf16_f32(128, 256), id2 = tc::idesc_bf16_f32(128, 128);
+            const int nuse = 8 * ntl;   // W2 boxes: 2 halves x 4 K blocks per tile
+            int x_issued = 0, w2_issued = 0, mma1_tiles = 0, mma2_tiles = 0;
+            auto load_x = [&](int j) {
+                const uint32_t bar = B(1 + (j & 1));
+                tc::mbar_expect_tx(bar, kBox);
+                tc::tma_load_2d(sbase + kOffX + (uint32_t)(j & 1) * kBox, &tmX, 0, tile_row(j), bar);
+                x_issued = j + 1;
+            };
+            auto load_w2 = [&](int u) {
+                const int s = u % kW2Stages, h = (u >> 2) & 1, kb = u & 3;
+                const uint32_t bar = B(3 + s);
+                tc::mbar_expect_tx(bar, kBox);
+                tc::tma_load_2d(sbase + kOffW2 + (uint32_t)s * kBox, &tmW2, kb * 64, h * 128, bar);
+                w2_issued = u + 1;
+            };
+            tc::mbar_expect_tx(B(0), 2 * kBox);
+            tc::tma_load_2d(sbase + kOffW1, &tmW1, 0, 0, B(0));
+            tc::tma_load_2d(sbase + kOffW1 + kBox, &tmW1, 0, 128, B(0));
+            for (int j = 0; j < 2 && j < ntl; ++j) load_x(j);
+            for (int u = 0; u < kW2Stages && u < nuse; ++u) load_w2(u);
+            for (int j = 0; j < ntl; ++j) {
+                const int b = j & 1;
+                const uint32_t acc = tmem + (uint32_t)(b * 256);
+                if (!iwait(B(1 + b), (uint32_t)(j >> 1) & 1u, fail)) break;
+                if (!iwait(B(16 + b), ((uint32_t)(j >> 1) & 1u) ^ 1u, fail)) break;   // layer 2 of tile j - 2 read
+                if (j == 0 && !iwait(B(0), 0u, fail)) break;
+                tc::tc_fence_after();
+                const uint64_t dx = tc::sw128_desc(sbase + kOffX + (uint32_t)b * kBox), dw1 = tc::sw128_desc(sbase + kOffW1);
+#pragma unroll
+                for (int k16 = 0; k16 < 4; ++k16) tc::mma_bf16(acc, dx + 2 * k16, dw1 + 2 * k16, id1, k16 > 0 ? 1u : 0u);
+                tc::mma_commit(B(11 + b));
+                mma1_tiles = j + 1;
+                if (j + 2 < ntl) {   // the X stage is free once layer 1 has read it
+                    if (!iwait(B(11 + b), (uint32_t)(j >> 1) & 1u, fail)) break;
+                    load_x(j + 2);
+                }
+                if (!iwait(B(15), (uint32_t)j & 1u, fail)) break;   // layer-1 activations of tile j written
+                tc::tc_fence_after();
+                bool ok = true;
+                for (int h = 0; h < 2 && ok; ++h)
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const int u = 8 * j + 4 * h + kb, s = u % kW2Stages;
+                        if (!iwait(B(3 + s), (uint32_t)(u / kW2Stages) & 1u, fail)) { ok = false; break; }
+                        tc::tc_fence_after();
+                        const uint64_t dh = tc::sw128_desc(sbase + kOffH1 + (uint32_t)kb * kBox),
+                                       dw = tc::sw128_desc(sbase + kOffW2 + (uint32_t)s * kBox);
+#pragma unroll
+                        for (int k16 = 0; k16 < 4; ++k16)
+                            tc::mma_bf16(acc + (uint32_t)(128 * h), dh + 2 * k16, dw + 2 * k16, id2,
+                                         (kb > 0 || k16 > 0) ? 1u : 0u);
+                        tc::mma_commit(B(7 + s));
+                        // the stage of the previous box (its MMAs queued ahead of these) takes box u + 3
+                        if (u >= 1 && u + kW2Stages - 1 < nuse) {
+                            const int v = u - 1, sv = v % kW2Stages;
+                            if (!iwait(B(7 + sv), (uint32_t)(v / kW2Stages) & 1u, fail)) { ok = false; break; }
+                            load_w2(u + kW2Stages - 1);
+                        }
+                    }
+                if (!ok) break;
+                tc::mma_commit(B(13 + b));
+                mma2_tiles = j + 1;
+            }
+            if (*fail) {
+                // a wait ran out: wait (bounded) for the copies and MMAs this
+                // thread issued, so that none is in flight when the CTA exits
+                atomicAdd(a.timeouts, 1u);
+                tc::mbar_wait(B(0), 0u);
+                for (int j = x_issued > 2 ? x_issued - 2 : 0; j < x_issued; ++j)
+                    tc::mbar_wait(B(1 + (j & 1)), (uint32_t)(j >> 1) & 1u);
+                for (int u = w2_issued > kW2Stages ? w2_issued - kW2Stages : 0; u < w2_issued; ++u)
+                    tc::mbar_wait(B(3 + u % kW2Stages), (uint32_t)(u / kW2Stages) & 1u);
+                if (mma1_tiles > 0) tc::mbar_wait(B(11 + ((mma1_tiles - 1) & 1)), (uint32_t)((mma1_tiles - 1) >> 1) & 1u);
+                if (mma2_tiles > 0) tc::mbar_wait(B(13 + ((mma2_tiles - 1) & 1)), (uint32_t)((mma2_tiles - 1) >> 1) & 1u);
+            }
+        }
+    } else {
+        const int q = warp & 3, cg = (warp - 1) >> 2;
+        const int row = 32 * q + lane;
+        const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        const uint32_t h1row = sbase + kOffH1 + (uint32_t)cg * kBox + (uint32_t)row * 128u;
+        for (int j = 0; j <= ntl; ++j) {
+            if (j < ntl) {   // layer 1 of tile j -> the layer-2 operand
+                const int b = j & 1;
+                bool ok = iwait(B(11 + b), (uint32_t)(j >> 1) & 1u, fail);
+                if (ok && j >= 1) ok = iwait(B(13 + ((j - 1) & 1)), (uint32_t)((j - 1) >> 1) & 1u, fail);   // H1 read
+                tc::tc_fence_after();
+                if (ok) {
+                    const uint32_t tb = tmem + (uint32_t)(b * 256) + lanes;
+#pragma unroll
+                    for (int c16 = 0; c16 < 4; ++c16) {
+                        const int col = 64 * cg + 16 * c16;
+                        float v[16];
+                        tc::tmem_ld16(tb + (uint32_t)col, v);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] += sb1[col + e];
+#pragma unroll
+                        for (int e = 0; e < 16; e += 2) gelu2(v[e], v[e + 1]);
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const __nv_bfloat162 p = __floats2bfloat162_rn(v[8 * half + 2 * e], v[8 * half + 2 * e + 1]);
+                                w[e] = *reinterpret_cast<const uint32_t*>(&p);
+                            }
+                            const int ch = 2 * c16 + half;
+                            const uint32_t dst = h1row + ((uint32_t)(ch ^ (row & 7)) << 4);
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]),
+                                         "r"(w[2]), "r"(w[3])
+                                         : "memory");
+                        }
+                    }
+                }
+                // the writes are seen by the tensor cores' (async-proxy) reads
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive1(B(15));
+            }
+            if (j >= 1) {   // layer 2 of tile j - 1 and the head
+                const int t = j - 1, b = t & 1;
+                const bool ok = iwait(B(13 + b), (uint32_t)(t >> 1) & 1u, fail);
+                tc::tc_fence_after();
+                float y[OD];
+#pragma unroll
+                for (int k = 0; k < OD; ++k) y[k] = 0.f;
+                if (ok) {
+                    const uint32_t tb = tmem + (uint32_t)(b * 256) + lanes;
+#pragma unroll
+                    for (int c16 = 0; c16 < 4; ++c16) {
+                        const int col = 64 * cg + 16 * c16;
+                        float v[16];
+                        tc::tmem_ld16(tb + (uint32_t)col, v);
+#pragma unroll
+                        for (int e = 0; e < 16; e += 2) {
+                            float h0 = v[e] + sb2[col + e], h1 = v[e + 1] + sb2[col + e + 1];
+                            gelu2(h0, h1);
+#pragma unroll
+                            for (int k = 0; k < OD; ++k)
+                                y[k] = fmaf(h1, sw3[k][col + e + 1], fmaf(h0, sw3[k][col + e], y[k]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < OD; ++k) s_y[t & 1][cg][row][k] = y[k];
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive1(B(16 + b));   // the accumulator is free for layer 1 of tile t + 2
+                epi_bar();
+                if (ok && cg == 0) {
+                    const int m = tile_row(t) + row;
+                    if (m < a.M) {
+#pragma unroll
+                        for (int k = 0; k < OD; ++k) {
+                            float s = a.b3[k];
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) s += s_y[t & 1][g][row][k];
+                            a.Y[(int64_t)m * OD + k] = (float)((double)s * a.scaler[OD + k] + a.scaler[k]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 // Batch gather: rows of X (FP32, n x din) -> Xb (B x 64 BF16, zero-padded) and
 // Xb^T (64 x B), targets -> standardised t (B x OD).  64 rows per block.
 __global__ void __launch_bounds__(256)
@@ -751,6 +1017,34 @@ cudaError_t run_adamw(ptsne_mlp* m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// One slab of inference through the fused kernel (persistent: one CTA per
+// SM, each taking every gridDim.x-th row tile).
+template <int OD>
+cudaError_t launch_infer(ptsne_mlp* m, int M, float* Y, cudaStream_t s) {
+    auto kern = mlp_infer_kernel<OD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
+    if (e != cudaSuccess) return e;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    }
+    InferArgs a;
+    a.M = M;
+    a.mtiles = (M + 127) / 128;
+    a.b1 = m->W + m->off.b1;
+    a.b2 = m->W + m->off.b2;
+    a.W3 = m->cp.W3b;
+    a.b3 = m->W + m->off.b3;
+    a.scaler = m->scaler;
+    a.Y = Y;
+    a.timeouts = m->dflags;
+    const int grid = a.mtiles < sms ? a.mtiles : sms;
+    kern<<<(unsigned)grid, kInferThreads, kInferSmem, s>>>(m->tmXs, m->tmW1b, m->tmW2b, a);
+    return cudaGetLastError();
+}
+
 template <int OD>
 cudaError_t run_infer_od(ptsne_mlp* m, const float* X, int64_t n, float* Y, cudaStream_t s) {
     for (int64_t r0 = 0; r0 < n; r0 += m->slab) {
@@ -758,25 +1052,7 @@ cudaError_t run_infer_od(ptsne_mlp* m, const float* X, int64_t n, float* Y, cuda
         int64_t g = ((int64_t)M * kKin + 255) / 256;
         if (g > 152 * 16) g = 152 * 16;
         convert_rows_kernel<<<(unsigned)g, 256, 0, s>>>(X, r0, M, m->din, m->Xs);
-        const int mt = (M + 127) / 128;
-        GemmArgs a = base_args(m);
-        a.M = M;
-        a.kblocks = 1;
-        a.kb_per_split = 1;
-        a.bias = m->W + m->off.b1;
-        a.H = m->H1s;
-        cudaError_t e = launch_gemm<kH, EPI_FWD, OD>(m->tmXs, m->tmW1b, a, mt, 1, s);
-        if (e != cudaSuccess) return e;
-        a = base_args(m);
-        a.M = M;
-        a.kblocks = kH / 64;
-        a.kb_per_split = a.kblocks;
-        a.bias = m->W + m->off.b2;
-        a.W3 = m->cp.W3b;
-        a.b3 = m->W + m->off.b3;
-        a.scaler = m->scaler;
-        a.Y = Y + r0 * OD;
-        e = launch_gemm<kH, EPI_HEAD_INFER, OD>(m->tmH1s, m->tmW2b, a, mt, 1, s);
+        const cudaError_t e = launch_infer<OD>(m, M, Y + r0 * OD, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
