@@ -50,7 +50,7 @@ typedef struct {
     int32_t d_in;            /* input features, 1 .. 64 */
     int32_t out_dim;         /* 2 or 3 */
     int32_t batch;           /* training rows per step, a multiple of 128, <= 65536 */
-    int64_t infer_rows;      /* rows per inference slab (workspace size), multiple of 128 */
+    int64_t infer_rows;      /* rows per inference launch, multiple of 128, <= 2^24 */
     float lr;                /* AdamW step size (e.g. 1e-3) */
     float beta1, beta2, eps; /* AdamW moments (0.9, 0.999, 1e-8) */
     float weight_decay;      /* decoupled decay on W1, W2, W3 (e.g. 1e-4) */
@@ -103,7 +103,8 @@ int ptsne_mlp_autotune(ptsne_mlp* m, const float* X_dev, const float* T_dev, int
                        const char* cache_path, int32_t* split_out, void* stream);
 
 /* Map n points: X_dev (n x d_in) -> Y_out_dev (n x out_dim), de-standardised
- * by the scaler.  Runs in slabs of infer_rows rows.  Async. */
+ * by the scaler.  One fused kernel launch per infer_rows rows (X is read
+ * in place, FP32, rounded to BF16 on chip).  Async. */
 int ptsne_mlp_infer(ptsne_mlp* m, const float* X_dev, int64_t n, float* Y_out_dev, void* stream);
 
 struct ptsne_ctx;

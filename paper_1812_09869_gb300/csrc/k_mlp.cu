@@ -130,9 +130,11 @@ __device__ __forceinline__ f2m mul2m(f2m a, f2m b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ void gelu2(float& x, float& y) {
+__device__ __forceinline__ f2m gelu2p(f2m u) {
     constexpr float kB1 = 0.0705230784f, kB2 = 0.0422820123f, kB3 = 0.0092705272f, kB4 = 0.0001520143f,
                     kB5 = 0.0002765672f, kB6 = 0.0000430638f, kRsqrt2 = 0.70710678118654752f;
+    float x, y;
+    upkm(u, x, y);
     const f2m A = pkm(fabsf(x) * kRsqrt2, fabsf(y) * kRsqrt2);
     f2m P = fma2m(A, pkm(kB6, kB6), pkm(kB5, kB5));
     P = fma2m(A, P, pkm(kB4, kB4));
@@ -149,9 +151,9 @@ __device__ __forceinline__ void gelu2(float& x, float& y) {
     const float qx = hw_rcp(px), qy = hw_rcp(py);   // erfc(|u| / sqrt 2)
     const float fx = x >= 0.f ? fmaf(-0.5f, qx, 1.0f) : 0.5f * qx;
     const float fy = y >= 0.f ? fmaf(-0.5f, qy, 1.0f) : 0.5f * qy;
-    const f2m G = mul2m(pkm(x, y), pkm(fx, fy));
-    upkm(G, x, y);
+    return mul2m(u, pkm(fx, fy));
 }
+__device__ __forceinline__ void gelu2(float& x, float& y) { upkm(gelu2p(pkm(x, y)), x, y); }
 __device__ __forceinline__ float gelu(float u) { return u * normal_parts(u).Phi; }
 __device__ __forceinline__ float gelu_grad(float u) {
     const NormalParts n = normal_parts(u);
@@ -435,23 +437,28 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
 // ---------------------------------------------------------------- fused inference
 // Inference of 128-row tiles in one persistent, warp-specialised kernel.
-// Layer 1 (X W1^T + b1, GELU) goes from tensor memory into shared memory as
-// the A operand of layer 2 (BF16, in the 128-byte-swizzled K-major layout
-// that TMA writes: row r, 16-byte chunk c of a 64-column K block at
-// r * 128 + ((c ^ (r mod 8)) * 16)), so the hidden activations never leave
-// the SM; layer 2 (+ b2, GELU) ends in the output head (y = W3 h + b3,
-// de-standardised).  Warp 0 (one thread) issues the TMA loads and the MMAs;
-// warps 1..16 are the epilogue (warp w reads tensor-memory lanes
-// 32 (w mod 4) .. + 31, one row per thread, and column group (w - 1) / 4 of
-// four 64-column groups, which is one K block of the layer-2 operand).  Two
-// accumulators (2 x 256 tensor-memory columns) let the tensor cores run
-// layer 2 of tile j and layer 1 of tile j + 1 while the epilogue warps take
-// layer 1 of tile j + 1 and layer 2 of tile j.  W1 stays in shared memory;
-// W2 streams from L2 in 128-row x 64-column boxes, four in flight.
-// Mbarrier waits are bounded; the first that runs out stops every role
-// (the epilogue warps still meet at their named barrier).
+// Two loader warps read the tile's FP32 rows of X straight from global
+// memory (a warp per row, two columns per lane), round them to BF16 and
+// write the layer-1 A operand (zero-padded to 64 columns) into shared memory
+// in the 128-byte-swizzled K-major layout that TMA writes (row r, 16-byte
+// chunk c of a 64-column K block at r * 128 + ((c ^ (r mod 8)) * 16)).
+// Layer 1 (X W1^T + b1, GELU) goes from tensor memory into shared memory in
+// the same layout as the A operand of layer 2, so the hidden activations
+// never leave the SM; layer 2 (+ b2, GELU) ends in the output head
+// (y = W3 h + b3, de-standardised).  Warp 0 (one thread) issues the TMA
+// loads of the weights and the MMAs; warps 1..16 are the epilogue (warp w
+// reads tensor-memory lanes 32 (w mod 4) .. + 31, one row per thread, and
+// column group (w - 1) / 4 of four 64-column groups, which is one K block of
+// the layer-2 operand); warps 17 and 18 load X.  Two accumulators (2 x 256
+// tensor-memory columns) let the tensor cores run layer 2 of tile j and
+// layer 1 of tile j + 1 while the epilogue warps take layer 1 of tile j + 1
+// and layer 2 of tile j.  W1 stays in shared memory; W2 streams from L2 in
+// 128-row x 64-column boxes, four in flight.  Mbarrier waits are bounded;
+// the first that runs out stops every role (the epilogue warps still meet at
+// their named barrier).
 constexpr int kInferEpiWarps = 16;
-constexpr int kInferThreads = 32 * (1 + kInferEpiWarps);
+constexpr int kInferLoadWarps = 2;
+constexpr int kInferThreads = 32 * (1 + kInferEpiWarps + kInferLoadWarps);
 constexpr int kW2Stages = 4;
 constexpr uint32_t kBox = 16384;                      // one 128-row x 64-column BF16 box
 constexpr uint32_t kOffW1 = 0;                        // W1: 2 boxes (256 rows)
@@ -461,8 +468,11 @@ constexpr uint32_t kOffW2 = kOffH1 + 4 * kBox;        // W2: kW2Stages boxes
 constexpr size_t kInferSmem = kOffW2 + kW2Stages * kBox + 1024;   // + 1024-byte alignment slack
 
 struct InferArgs {
-    int M;                  // valid rows of the slab
-    int mtiles;             // 128-row tiles of the slab
+    const float* X;         // the launch's rows of X [M][din], FP32
+    int M;                  // rows of the launch
+    int mtiles;             // 128-row tiles of the launch
+    int din;
+    int pairs;              // 1: din even and X 8-byte aligned (two columns per load)
     const float* b1;
     const float* b2;
     const bf16* W3;         // [OD][256]
@@ -488,19 +498,28 @@ __device__ __forceinline__ void mbar_arrive1(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kInferEpiWarps) : "memory"); }
+__device__ __forceinline__ f2m add2m(f2m a, f2m b) {
+    f2m d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&p);
+}
 
 template <int OD>
 __global__ void __launch_bounds__(kInferThreads, 1)
-mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
-                 const __grid_constant__ CUtensorMap tmW2, const InferArgs a) {
+mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant__ CUtensorMap tmW2, const InferArgs a) {
     extern __shared__ unsigned char dsmem[];
-    // 0: W1 loaded; 1-2: X stage full; 3-6: W2 stage full; 7-10: W2 stage free;
-    // 11-12: layer 1 done (per accumulator); 13-14: layer 2 done; 15: H1
-    // written; 16-17: accumulator read by the layer-2 epilogue
+    // 0: W1 loaded; 1-2: X stage written; 3-6: W2 stage full; 7-10: W2 stage
+    // free; 11-12: layer 1 done (per accumulator and X stage); 13-14: layer 2
+    // done; 15: H1 written; 16-17: accumulator read by the layer-2 epilogue
     __shared__ uint64_t bars[18];
     __shared__ uint32_t tmem_base;
-    __shared__ float sb1[kH], sb2[kH];
-    __shared__ float sw3[OD][kH];
+    __shared__ __align__(16) float sb1[kH];
+    __shared__ __align__(16) float sb2[kH];
+    __shared__ __align__(16) float sw3[OD][kH];
     __shared__ float s_y[2][4][128][OD];
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -512,7 +531,11 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem_base), 512);
     if (tid == 0) {
         s_fail = 0;
-        for (int i = 0; i < 18; ++i) tc::mbar_init(B(i), (i == 15 || i >= 16) ? (uint32_t)kInferEpiWarps : 1u);
+        for (int i = 0; i < 18; ++i) {
+            const uint32_t count = (i == 1 || i == 2) ? (uint32_t)kInferLoadWarps
+                                 : (i >= 15) ? (uint32_t)kInferEpiWarps : 1u;
+            tc::mbar_init(B(i), count);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -531,13 +554,7 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         if (lane == 0 && ntl > 0) {
             const uint32_t id1 = tc::idesc_bf16_f32(128, 256), id2 = tc::idesc_bf16_f32(128, 128);
             const int nuse = 8 * ntl;   // W2 boxes: 2 halves x 4 K blocks per tile
-            int x_issued = 0, w2_issued = 0, mma1_tiles = 0, mma2_tiles = 0;
-            auto load_x = [&](int j) {
-                const uint32_t bar = B(1 + (j & 1));
-                tc::mbar_expect_tx(bar, kBox);
-                tc::tma_load_2d(sbase + kOffX + (uint32_t)(j & 1) * kBox, &tmX, 0, tile_row(j), bar);
-                x_issued = j + 1;
-            };
+            int w2_issued = 0, mma1_tiles = 0, mma2_tiles = 0;
             auto load_w2 = [&](int u) {
                 const int s = u % kW2Stages, h = (u >> 2) & 1, kb = u & 3;
                 const uint32_t bar = B(3 + s);
@@ -548,12 +565,11 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
             tc::mbar_expect_tx(B(0), 2 * kBox);
             tc::tma_load_2d(sbase + kOffW1, &tmW1, 0, 0, B(0));
             tc::tma_load_2d(sbase + kOffW1 + kBox, &tmW1, 0, 128, B(0));
-            for (int j = 0; j < 2 && j < ntl; ++j) load_x(j);
             for (int u = 0; u < kW2Stages && u < nuse; ++u) load_w2(u);
             for (int j = 0; j < ntl; ++j) {
                 const int b = j & 1;
                 const uint32_t acc = tmem + (uint32_t)(b * 256);
-                if (!iwait(B(1 + b), (uint32_t)(j >> 1) & 1u, fail)) break;
+                if (!iwait(B(1 + b), (uint32_t)(j >> 1) & 1u, fail)) break;                  // X of tile j written
                 if (!iwait(B(16 + b), ((uint32_t)(j >> 1) & 1u) ^ 1u, fail)) break;   // layer 2 of tile j - 2 read
                 if (j == 0 && !iwait(B(0), 0u, fail)) break;
                 tc::tc_fence_after();
@@ -562,10 +578,6 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                 for (int k16 = 0; k16 < 4; ++k16) tc::mma_bf16(acc, dx + 2 * k16, dw1 + 2 * k16, id1, k16 > 0 ? 1u : 0u);
                 tc::mma_commit(B(11 + b));
                 mma1_tiles = j + 1;
-                if (j + 2 < ntl) {   // the X stage is free once layer 1 has read it
-                    if (!iwait(B(11 + b), (uint32_t)(j >> 1) & 1u, fail)) break;
-                    load_x(j + 2);
-                }
                 if (!iwait(B(15), (uint32_t)j & 1u, fail)) break;   // layer-1 activations of tile j written
                 tc::tc_fence_after();
                 bool ok = true;
@@ -597,19 +609,64 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                 // thread issued, so that none is in flight when the CTA exits
                 atomicAdd(a.timeouts, 1u);
                 tc::mbar_wait(B(0), 0u);
-                for (int j = x_issued > 2 ? x_issued - 2 : 0; j < x_issued; ++j)
-                    tc::mbar_wait(B(1 + (j & 1)), (uint32_t)(j >> 1) & 1u);
                 for (int u = w2_issued > kW2Stages ? w2_issued - kW2Stages : 0; u < w2_issued; ++u)
                     tc::mbar_wait(B(3 + u % kW2Stages), (uint32_t)(u / kW2Stages) & 1u);
                 if (mma1_tiles > 0) tc::mbar_wait(B(11 + ((mma1_tiles - 1) & 1)), (uint32_t)((mma1_tiles - 1) >> 1) & 1u);
                 if (mma2_tiles > 0) tc::mbar_wait(B(13 + ((mma2_tiles - 1) & 1)), (uint32_t)((mma2_tiles - 1) >> 1) & 1u);
             }
         }
+    } else if (warp > kInferEpiWarps) {
+        // X loaders: warp lw takes rows lw, lw + 2, ... of the tile; lane l
+        // columns 2l and 2l + 1 (one 4-byte word of 16-byte chunk l / 4).
+        constexpr int kRows = 128 / kInferLoadWarps, kU = 16;
+        const int lw = warp - 1 - kInferEpiWarps, c0 = 2 * lane;
+        const bool in0 = c0 < a.din, in1 = c0 + 1 < a.din;
+        for (int j = 0; j < ntl; ++j) {
+            const int b = j & 1;
+            if (j >= 2 && !iwait(B(11 + b), ((uint32_t)(j >> 1) & 1u) ^ 1u, fail)) break;   // layer 1 of tile j - 2 read it
+            const uint32_t stage = sbase + kOffX + (uint32_t)b * kBox + (uint32_t)(lane & 3) * 4u;
+            const int m0 = tile_row(j);
+            for (int r0 = 0; r0 < kRows; r0 += kU) {
+                float2 v[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int m = m0 + lw + kInferLoadWarps * (r0 + u);
+                    v[u] = make_float2(0.f, 0.f);
+                    if (m < a.M) {
+                        const float* src = a.X + (int64_t)m * a.din + c0;
+                        if (a.pairs) {
+                            if (in0) v[u] = __ldcs(reinterpret_cast<const float2*>(src));
+                        } else {
+                            if (in0) v[u].x = __ldcs(src);
+                            if (in1) v[u].y = __ldcs(src + 1);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t r = (uint32_t)(lw + kInferLoadWarps * (r0 + u));
+                    const uint32_t dst = stage + r * 128u + ((((uint32_t)lane >> 2) ^ (r & 7u)) << 4);
+                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst), "r"(bf16x2_bits(v[u].x, v[u].y)) : "memory");
+                }
+            }
+            // the writes are seen by the tensor cores' (async-proxy) reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(B(1 + b));
+        }
     } else {
         const int q = warp & 3, cg = (warp - 1) >> 2;
         const int row = 32 * q + lane;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
         const uint32_t h1row = sbase + kOffH1 + (uint32_t)cg * kBox + (uint32_t)row * 128u;
+        float b3r[OD];
+        double mean[OD], sd[OD];
+#pragma unroll
+        for (int k = 0; k < OD; ++k) {
+            b3r[k] = a.b3[k];
+            mean[k] = a.scaler[k];
+            sd[k] = a.scaler[OD + k];
+        }
         for (int j = 0; j <= ntl; ++j) {
             if (j < ntl) {   // layer 1 of tile j -> the layer-2 operand
                 const int b = j & 1;
@@ -617,30 +674,37 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                 if (ok && j >= 1) ok = iwait(B(13 + ((j - 1) & 1)), (uint32_t)((j - 1) >> 1) & 1u, fail);   // H1 read
                 tc::tc_fence_after();
                 if (ok) {
-                    const uint32_t tb = tmem + (uint32_t)(b * 256) + lanes;
+                    const uint32_t tb = tmem + (uint32_t)(b * 256 + 64 * cg) + lanes;
+                    uint32_t ra[16], rb[16];
+                    tc::tmem_ld16_issue(tb, ra);
+                    tc::tmem_wait_ld16(ra);
 #pragma unroll
                     for (int c16 = 0; c16 < 4; ++c16) {
-                        const int col = 64 * cg + 16 * c16;
-                        float v[16];
-                        tc::tmem_ld16(tb + (uint32_t)col, v);
+                        uint32_t(&cur)[16] = (c16 & 1) ? rb : ra;
+                        uint32_t(&nxt)[16] = (c16 & 1) ? ra : rb;
+                        if (c16 < 3) tc::tmem_ld16_issue(tb + (uint32_t)(16 * (c16 + 1)), nxt);   // in flight during this block
+                        const float4* bp = reinterpret_cast<const float4*>(&sb1[64 * cg + 16 * c16]);
+                        uint32_t w[8];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) v[e] += sb1[col + e];
-#pragma unroll
-                        for (int e = 0; e < 16; e += 2) gelu2(v[e], v[e + 1]);
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            const float4 bb = bp[q4];
+                            const f2m g0 = gelu2p(add2m(pkm(__uint_as_float(cur[4 * q4]), __uint_as_float(cur[4 * q4 + 1])), pkm(bb.x, bb.y)));
+                            const f2m g1 = gelu2p(add2m(pkm(__uint_as_float(cur[4 * q4 + 2]), __uint_as_float(cur[4 * q4 + 3])), pkm(bb.z, bb.w)));
+                            float x0, x1, x2, x3;
+                            upkm(g0, x0, x1);
+                            upkm(g1, x2, x3);
+                            w[2 * q4] = bf16x2_bits(x0, x1);
+                            w[2 * q4 + 1] = bf16x2_bits(x2, x3);
+                        }
 #pragma unroll
                         for (int half = 0; half < 2; ++half) {
-                            uint32_t w[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const __nv_bfloat162 p = __floats2bfloat162_rn(v[8 * half + 2 * e], v[8 * half + 2 * e + 1]);
-                                w[e] = *reinterpret_cast<const uint32_t*>(&p);
-                            }
-                            const int ch = 2 * c16 + half;
-                            const uint32_t dst = h1row + ((uint32_t)(ch ^ (row & 7)) << 4);
-                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]),
-                                         "r"(w[2]), "r"(w[3])
+                            const uint32_t ch = (uint32_t)(2 * c16 + half);
+                            const uint32_t dst = h1row + ((ch ^ (uint32_t)(row & 7)) << 4);
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[4 * half]),
+                                         "r"(w[4 * half + 1]), "r"(w[4 * half + 2]), "r"(w[4 * half + 3])
                                          : "memory");
                         }
+                        if (c16 < 3) tc::tmem_wait_ld16(nxt);
                     }
                 }
                 // the writes are seen by the tensor cores' (async-proxy) reads
@@ -653,28 +717,42 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                 const int t = j - 1, b = t & 1;
                 const bool ok = iwait(B(13 + b), (uint32_t)(t >> 1) & 1u, fail);
                 tc::tc_fence_after();
-                float y[OD];
+                f2m y2[OD];
 #pragma unroll
-                for (int k = 0; k < OD; ++k) y[k] = 0.f;
+                for (int k = 0; k < OD; ++k) y2[k] = pkm(0.f, 0.f);
                 if (ok) {
-                    const uint32_t tb = tmem + (uint32_t)(b * 256) + lanes;
+                    const uint32_t tb = tmem + (uint32_t)(b * 256 + 64 * cg) + lanes;
+                    uint32_t ra[16], rb[16];
+                    tc::tmem_ld16_issue(tb, ra);
+                    tc::tmem_wait_ld16(ra);
 #pragma unroll
                     for (int c16 = 0; c16 < 4; ++c16) {
+                        uint32_t(&cur)[16] = (c16 & 1) ? rb : ra;
+                        uint32_t(&nxt)[16] = (c16 & 1) ? ra : rb;
+                        if (c16 < 3) tc::tmem_ld16_issue(tb + (uint32_t)(16 * (c16 + 1)), nxt);
                         const int col = 64 * cg + 16 * c16;
-                        float v[16];
-                        tc::tmem_ld16(tb + (uint32_t)col, v);
+                        const float4* bp = reinterpret_cast<const float4*>(&sb2[col]);
 #pragma unroll
-                        for (int e = 0; e < 16; e += 2) {
-                            float h0 = v[e] + sb2[col + e], h1 = v[e + 1] + sb2[col + e + 1];
-                            gelu2(h0, h1);
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            const float4 bb = bp[q4];
+                            const f2m g0 = gelu2p(add2m(pkm(__uint_as_float(cur[4 * q4]), __uint_as_float(cur[4 * q4 + 1])), pkm(bb.x, bb.y)));
+                            const f2m g1 = gelu2p(add2m(pkm(__uint_as_float(cur[4 * q4 + 2]), __uint_as_float(cur[4 * q4 + 3])), pkm(bb.z, bb.w)));
 #pragma unroll
-                            for (int k = 0; k < OD; ++k)
-                                y[k] = fmaf(h1, sw3[k][col + e + 1], fmaf(h0, sw3[k][col + e], y[k]));
+                            for (int k = 0; k < OD; ++k) {
+                                const float4 ww = reinterpret_cast<const float4*>(&sw3[k][col])[q4];
+                                y2[k] = fma2m(g0, pkm(ww.x, ww.y), y2[k]);
+                                y2[k] = fma2m(g1, pkm(ww.z, ww.w), y2[k]);
+                            }
                         }
+                        if (c16 < 3) tc::tmem_wait_ld16(nxt);
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < OD; ++k) s_y[t & 1][cg][row][k] = y[k];
+                for (int k = 0; k < OD; ++k) {
+                    float lo, hi;
+                    upkm(y2[k], lo, hi);
+                    s_y[t & 1][cg][row][k] = lo + hi;
+                }
                 tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive1(B(16 + b));   // the accumulator is free for layer 1 of tile t + 2
@@ -684,10 +762,10 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                     if (m < a.M) {
 #pragma unroll
                         for (int k = 0; k < OD; ++k) {
-                            float s = a.b3[k];
+                            float s = b3r[k];
 #pragma unroll
                             for (int g = 0; g < 4; ++g) s += s_y[t & 1][g][row][k];
-                            a.Y[(int64_t)m * OD + k] = (float)((double)s * a.scaler[OD + k] + a.scaler[k]);
+                            a.Y[(int64_t)m * OD + k] = (float)((double)s * sd[k] + mean[k]);
                         }
                     }
                 }
@@ -727,17 +805,6 @@ gather_batch_kernel(const float* __restrict__ X, const float* __restrict__ T, in
         const int32_t r = rows[b0 + s];
         const double v = (r >= 0 && r < n) ? (double)T[(int64_t)r * od + k] : scaler[k];
         t[(int64_t)(b0 + s) * od + k] = (float)((v - scaler[k]) / scaler[od + k]);
-    }
-}
-
-// Inference input: X rows [r0, r0 + M) -> Xs (M x 64 BF16, zero-padded).
-__global__ void convert_rows_kernel(const float* __restrict__ X, int64_t r0, int M, int din, bf16* __restrict__ Xs) {
-    const int64_t total = (int64_t)M * kKin;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = idx / kKin;
-        const int k = (int)(idx % kKin);
-        Xs[idx] = __float2bfloat16_rn(k < din ? X[(r0 + s) * din + k] : 0.f);
     }
 }
 
@@ -850,10 +917,9 @@ struct ptsne_mlp {
     float *U1 = nullptr, *tb = nullptr;
     double* loss = nullptr;       // [1 + max epochs tracked per train call]
     int loss_cap = 0;
-    bf16 *Xs = nullptr, *H1s = nullptr;
     unsigned int* dflags = nullptr;   // [0] timeouts, [1] bad rows
     int split = 0;                    // CTAs along K of the weight-gradient GEMMs (0: heuristic)
-    CUtensorMap tmXb, tmW1b, tmH1, tmW2b, tmdA2T, tmH1T, tmdA2, tmW2Tb, tmdA1T, tmXbT, tmXs, tmH1s;
+    CUtensorMap tmXb, tmW1b, tmH1, tmW2b, tmdA2T, tmH1T, tmdA2, tmW2Tb, tmdA1T, tmXbT;
     std::string err;
 };
 
@@ -885,7 +951,7 @@ cudaError_t malloc_zero(T** p, size_t count) {
 void free_mlp(ptsne_mlp* m) {
     void* ptrs[] = {m->W,   m->m1,  m->m2,   m->grad, m->cp.W1b, m->cp.W2b, m->cp.W2Tb, m->cp.W3b,
                     m->scaler, m->sacc, m->Xb, m->XbT, m->H1, m->H1T, m->dA2, m->dA2T, m->dA1T,
-                    m->U1,  m->tb,  m->loss, m->Xs, m->H1s, m->dflags};
+                    m->U1,  m->tb,  m->loss, m->dflags};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -1017,10 +1083,10 @@ cudaError_t run_adamw(ptsne_mlp* m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One slab of inference through the fused kernel (persistent: one CTA per
-// SM, each taking every gridDim.x-th row tile).
+// Rows [0, M) of X through the fused kernel (persistent: one CTA per SM,
+// each taking every gridDim.x-th row tile).
 template <int OD>
-cudaError_t launch_infer(ptsne_mlp* m, int M, float* Y, cudaStream_t s) {
+cudaError_t launch_infer(ptsne_mlp* m, const float* X, int M, float* Y, cudaStream_t s) {
     auto kern = mlp_infer_kernel<OD>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
     if (e != cudaSuccess) return e;
@@ -1031,8 +1097,11 @@ cudaError_t launch_infer(ptsne_mlp* m, int M, float* Y, cudaStream_t s) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     }
     InferArgs a;
+    a.X = X;
     a.M = M;
     a.mtiles = (M + 127) / 128;
+    a.din = m->din;
+    a.pairs = (m->din % 2 == 0 && ((uintptr_t)X & 7u) == 0) ? 1 : 0;
     a.b1 = m->W + m->off.b1;
     a.b2 = m->W + m->off.b2;
     a.W3 = m->cp.W3b;
@@ -1041,7 +1110,7 @@ cudaError_t launch_infer(ptsne_mlp* m, int M, float* Y, cudaStream_t s) {
     a.Y = Y;
     a.timeouts = m->dflags;
     const int grid = a.mtiles < sms ? a.mtiles : sms;
-    kern<<<(unsigned)grid, kInferThreads, kInferSmem, s>>>(m->tmXs, m->tmW1b, m->tmW2b, a);
+    kern<<<(unsigned)grid, kInferThreads, kInferSmem, s>>>(m->tmW1b, m->tmW2b, a);
     return cudaGetLastError();
 }
 
@@ -1049,10 +1118,7 @@ template <int OD>
 cudaError_t run_infer_od(ptsne_mlp* m, const float* X, int64_t n, float* Y, cudaStream_t s) {
     for (int64_t r0 = 0; r0 < n; r0 += m->slab) {
         const int M = (int)((n - r0) < m->slab ? (n - r0) : m->slab);
-        int64_t g = ((int64_t)M * kKin + 255) / 256;
-        if (g > 152 * 16) g = 152 * 16;
-        convert_rows_kernel<<<(unsigned)g, 256, 0, s>>>(X, r0, M, m->din, m->Xs);
-        const cudaError_t e = launch_infer<OD>(m, M, Y + r0 * OD, s);
+        const cudaError_t e = launch_infer<OD>(m, X + r0 * m->din, M, Y + r0 * OD, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -1095,7 +1161,7 @@ int ptsne_mlp_create(ptsne_mlp** out, const ptsne_mlp_params* prm, const float* 
     m->B = prm->batch;
     m->slab = prm->infer_rows;
     m->off = param_offsets(m->din, m->od);
-    const int64_t B = m->B, S = m->slab;
+    const int64_t B = m->B;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) {
         if (e == cudaSuccess) e = r;
@@ -1121,8 +1187,6 @@ int ptsne_mlp_create(ptsne_mlp** out, const ptsne_mlp_params* prm, const float* 
     A(malloc_zero(&m->tb, (size_t)B * m->od));
     m->loss_cap = 1024;
     A(malloc_zero(&m->loss, (size_t)m->loss_cap + 1));
-    A(malloc_zero(&m->Xs, (size_t)S * kKin));
-    A(malloc_zero(&m->H1s, (size_t)S * kH));
     A(malloc_zero(&m->dflags, 2));
     if (e == cudaSuccess) e = cudaMemcpy(m->W, init_host, sizeof(float) * m->off.n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -1145,8 +1209,7 @@ int ptsne_mlp_create(ptsne_mlp** out, const ptsne_mlp_params* prm, const float* 
               tc::make_bf16_tmap(&m->tmH1, m->H1, B, kH) && tc::make_bf16_tmap(&m->tmW2b, m->cp.W2b, kH, kH) &&
               tc::make_bf16_tmap(&m->tmdA2T, m->dA2T, kH, B) && tc::make_bf16_tmap(&m->tmH1T, m->H1T, kH, B) &&
               tc::make_bf16_tmap(&m->tmdA2, m->dA2, B, kH) && tc::make_bf16_tmap(&m->tmW2Tb, m->cp.W2Tb, kH, kH) &&
-              tc::make_bf16_tmap(&m->tmdA1T, m->dA1T, kH, B) && tc::make_bf16_tmap(&m->tmXbT, m->XbT, 128, B) &&
-              tc::make_bf16_tmap(&m->tmXs, m->Xs, S, kKin) && tc::make_bf16_tmap(&m->tmH1s, m->H1s, S, kH);
+              tc::make_bf16_tmap(&m->tmdA1T, m->dA1T, kH, B) && tc::make_bf16_tmap(&m->tmXbT, m->XbT, 128, B);
     if (!ok) {
         g_mlp_create_err = "the driver refused a TMA tensor map";
         free_mlp(m);

@@ -85,7 +85,7 @@ _stream = ptsne._stream
 class Mapper:
     """Owns one ptsne_mlp handle (parameters, AdamW state, workspace)."""
 
-    def __init__(self, d_in, init, out_dim=2, batch=4096, infer_rows=1 << 18, lr=1e-3, betas=(0.9, 0.999),
+    def __init__(self, d_in, init, out_dim=2, batch=4096, infer_rows=1 << 24, lr=1e-3, betas=(0.9, 0.999),
                  eps=1e-8, weight_decay=1e-4):
         self.d_in, self.out_dim, self.batch = int(d_in), int(out_dim), int(batch)
         flat = pack(init) if isinstance(init, dict) else np.ascontiguousarray(np.asarray(init, np.float32))

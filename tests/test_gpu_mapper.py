@@ -68,6 +68,34 @@ def test_forward_with_scaler_matches_oracle(dev):
     assert rel_max((y - mean) / std, y_ref) <= FWD_TOL
 
 
+@pytest.mark.parametrize("d_in,od,n,offset,rows", [
+    (33, 2, 700, 0, 256),      # odd d_in: one column per load
+    (64, 3, 1000, 0, 384),     # full K block, 3-D output
+    (50, 2, 389, 1, 1 << 24),  # X one float off 8-byte alignment: one column per load; 3 full tiles + 5 rows
+    (1, 3, 129, 0, 128),       # a single feature; one full tile per launch and a 1-row launch
+])
+def test_inference_input_forms_match_oracle(dev, d_in, od, n, offset, rows):
+    """The fused inference kernel reads FP32 X in place (two columns per load
+    when d_in is even and X 8-byte aligned, else one) and rounds it to BF16
+    on chip: odd and full widths, an unaligned view, ragged tails and
+    several launches all match the oracle on the BF16-rounded input."""
+    from paper_1812_09869_gb300.mapper import Mapper
+    X, _ = synth.gaussian_mixture(n, d_in, 4, seed=130 + d_in)
+    W = _weights(d_in, od, 131)
+    flat = torch.zeros(n * d_in + offset, dtype=torch.float32)
+    flat[offset:] = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).reshape(-1)
+    with Mapper(d_in, W, out_dim=od, infer_rows=rows) as m:
+        Xd = flat.to(dev)[offset:].view(n, d_in)
+        assert (Xd.data_ptr() % 8 != 0) == (offset % 2 == 1)
+        Yd = torch.full((n, od), float("nan"), dtype=torch.float32, device=dev)
+        m.infer(Xd, Yd)
+        torch.cuda.synchronize()
+        y = Yd.cpu().numpy().astype(np.float64)
+    y_ref, _ = O.mlp_forward(_f64(W), _bf16(X).astype(np.float64))
+    assert np.all(np.isfinite(y))
+    assert rel_max(y, y_ref) <= FWD_TOL
+
+
 @pytest.mark.parametrize("batch", [128, 512])
 def test_gradient_matches_oracle(dev, batch):
     from paper_1812_09869_gb300 import mapper as M
