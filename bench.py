@@ -50,7 +50,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-learned", action="store_true", help="skip the learned (mapper) form")
     ap.add_argument("--no-eq13", action="store_true", help="skip the Eq. 13 study (adaptive vs fixed learning rate)")
     ap.add_argument("--mapper-kernels", type=int, default=0, metavar="ROWS",
-                    help="only time the mapper's kernels: inference of ROWS points (one slab) and training "
+                    help="only time the mapper's kernels: inference of ROWS points (one launch) and training "
                          "epochs over them (batch 4096); prints one JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
@@ -433,7 +433,7 @@ def eq13_study(w, Xd, dev, stream, tuning, ref_epochs=10, epochs=24):
 
 def mapper_kernels(rows: int, dev, stream, reps: int = 5, train_epochs: int = 2) -> dict:
     """The learned mapper's kernels alone (MLP 50-256-256-2): inference of
-    `rows` points of the D = 50 mixture in one slab, timed over `reps` calls
+    `rows` points of the D = 50 mixture in one launch, timed over `reps` calls
     after one warm-up call, and `train_epochs` training epochs over them."""
     import torch
     from paper_1812_09869_gb300 import mapper as M

@@ -16,9 +16,9 @@
 // stages): one CTA's loads and MMAs run under the other's epilogue.
 //
 //   FWD        u = acc + b; U = u (FP32), H = g(u) (BF16), H^T (BF16)
-//   HEAD_INFER h = g(acc + b2); y = W3 h + b3 per row (the whole hidden row is
-//              in the thread's accumulator lane); Y = y * std + mean
-//   HEAD_TRAIN as HEAD_INFER, then r = (y - t) / B, loss += |y - t|^2 / (2B),
+//   HEAD_TRAIN h = g(acc + b2); y = W3 h + b3 per row (each column group's
+//              partial sums of the row, added in group order); then
+//              r = (y - t) / B, loss += |y - t|^2 / (2B),
 //              dL/dW3 += r h^T, dL/db3 += r, and, re-reading the accumulator,
 //              dA2 = (W3^T r) * g'(u2) (BF16, and transposed), dL/db2 += dA2
 //   DGELU      dA1 = acc * g'(U1) (transposed, BF16), dL/db1 += dA1
@@ -54,13 +54,13 @@ constexpr int kKin = 64;               // input features padded to one K block
 constexpr int kStages = 3;              // at most; a CTA uses min(kStages, its K blocks)
 constexpr int kMaxStagesPair = 2;       // stages when K needs more: two CTAs per SM fit
 
-enum Epi { EPI_FWD = 0, EPI_HEAD_INFER = 1, EPI_HEAD_TRAIN = 2, EPI_DGELU = 3, EPI_ATOMIC = 4 };
+enum Epi { EPI_FWD = 0, EPI_HEAD_TRAIN = 2, EPI_DGELU = 3, EPI_ATOMIC = 4 };
 
 struct GemmArgs {
     int M;               // valid rows of A (rows >= M are computed but not stored)
     int kblocks;         // K / 64
     int kb_per_split;    // K blocks per CTA along gridDim.y
-    const float* bias;   // FWD, HEAD_*: [NT]
+    const float* bias;   // FWD, HEAD_TRAIN, DGELU: [NT]
     float* U;            // FWD: pre-activation [M][NT] (optional)
     bf16* H;             // FWD: activation [M][NT] (optional); HEAD_TRAIN: dA2 [M][NT]
     bf16* HT;            // FWD: activation^T; HEAD_TRAIN: dA2^T; DGELU: dA1^T  ([NT][ldT])
@@ -69,16 +69,14 @@ struct GemmArgs {
     float* colsum;       // DGELU: db1; HEAD_TRAIN: db2  ([NT])
     float* C;            // ATOMIC: [M][ldc]
     int ldc, ncols;
-    const bf16* W3;      // HEAD_*: [OD][NT]
-    const float* b3;     // HEAD_*: [OD]
+    const bf16* W3;      // HEAD_TRAIN: [OD][NT]
+    const float* b3;     // HEAD_TRAIN: [OD]
     const float* T;      // HEAD_TRAIN: standardised targets [M][OD]
     float invB;          // HEAD_TRAIN
     int stages;          // ring stages (1 .. kStages)
     double* loss;        // HEAD_TRAIN: accumulates sum |y - t|^2 / (2B)
     float* gW3;          // HEAD_TRAIN: [OD][NT]
     float* gb3;          // HEAD_TRAIN: [OD]
-    const double* scaler;   // HEAD_INFER: mean[OD], std[OD]
-    float* Y;            // HEAD_INFER: [M][OD]
     unsigned int* timeouts;
 };
 
@@ -212,7 +210,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     constexpr uint32_t kABytes = tc::kTileBytes;
     constexpr uint32_t kBBytes = (uint32_t)kBRows * 128u;
     constexpr uint32_t kStageBytes = kABytes + kBBytes;
-    constexpr bool kHead = EPI == EPI_HEAD_INFER || EPI == EPI_HEAD_TRAIN;
+    constexpr bool kHead = EPI == EPI_HEAD_TRAIN;
     extern __shared__ unsigned char dsmem[];
     __shared__ uint64_t full_bar[kStages], done_bar[kStages];
     __shared__ uint32_t tmem_base;
@@ -337,62 +335,54 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             for (int g = 0; g < CG; ++g) t += s_y[g][row][k];
             y[k] = t + a.b3[k];
         }
-        if constexpr (EPI == EPI_HEAD_INFER) {
-            if (valid && grp == 0) {
+        float r[OD];
+        float l2 = 0.f;
 #pragma unroll
-                for (int k = 0; k < OD; ++k)
-                    a.Y[(int64_t)m * OD + k] = (float)((double)y[k] * a.scaler[OD + k] + a.scaler[k]);
-            }
-        } else {
-            float r[OD];
-            float l2 = 0.f;
+        for (int k = 0; k < OD; ++k) {
+            const float diff = valid ? y[k] - a.T[(int64_t)m * OD + k] : 0.f;
+            l2 = fmaf(diff, diff, l2);
+            r[k] = diff * a.invB;
+        }
+        if (grp == 0) {   // every group holds the same r; group 0 reports it
+            const double lw = warp_sum((double)l2);
+            if (lane == 0) atomicAdd(a.loss, lw * 0.5 * (double)a.invB);
 #pragma unroll
             for (int k = 0; k < OD; ++k) {
-                const float diff = valid ? y[k] - a.T[(int64_t)m * OD + k] : 0.f;
-                l2 = fmaf(diff, diff, l2);
-                r[k] = diff * a.invB;
+                const float rs = warp_sum(r[k]);
+                if (lane == 0) atomicAdd(&a.gb3[k], rs);
             }
-            if (grp == 0) {   // every group holds the same r; group 0 reports it
-                const double lw = warp_sum((double)l2);
-                if (lane == 0) atomicAdd(a.loss, lw * 0.5 * (double)a.invB);
+        }
+        // second pass over the group's accumulator columns: dW3, dA2 and db2
+        for (int c = c0; c < c0 + kChunks; ++c) {
+            float v[32], g[32], t[32];
+            tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
 #pragma unroll
-                for (int k = 0; k < OD; ++k) {
-                    const float rs = warp_sum(r[k]);
-                    if (lane == 0) atomicAdd(&a.gb3[k], rs);
-                }
+            for (int e = 0; e < 32; ++e) {
+                const float u = v[e] + sb[c * 32 + e];
+                g[e] = gelu(u);
+                v[e] = gelu_grad(u);
             }
-            // second pass over the group's accumulator columns: dW3, dA2 and db2
-            for (int c = c0; c < c0 + kChunks; ++c) {
-                float v[32], g[32], t[32];
-                tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const float u = v[e] + sb[c * 32 + e];
-                    g[e] = gelu(u);
-                    v[e] = gelu_grad(u);
-                }
+            for (int k = 0; k < OD; ++k) {
 #pragma unroll
-                for (int k = 0; k < OD; ++k) {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) t[e] = r[k] * g[e];
-                    const float s = warp_transpose_sum(t, lane);
-                    atomicAdd(&a.gW3[k * NT + c * 32 + lane], s);
-                }
-#pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    float dh = 0.f;
-#pragma unroll
-                    for (int k = 0; k < OD; ++k) dh = fmaf(r[k], sw3[k][c * 32 + e], dh);
-                    t[e] = dh * v[e];
-                }
-                if (valid) {
-                    store_bf16x32(a.H + (int64_t)m * NT + c * 32, t);
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) a.HT[(int64_t)(c * 32 + e) * a.ldT + m] = __float2bfloat16_rn(t[e]);
-                }
+                for (int e = 0; e < 32; ++e) t[e] = r[k] * g[e];
                 const float s = warp_transpose_sum(t, lane);
-                atomicAdd(&a.colsum[c * 32 + lane], s);
+                atomicAdd(&a.gW3[k * NT + c * 32 + lane], s);
             }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                float dh = 0.f;
+#pragma unroll
+                for (int k = 0; k < OD; ++k) dh = fmaf(r[k], sw3[k][c * 32 + e], dh);
+                t[e] = dh * v[e];
+            }
+            if (valid) {
+                store_bf16x32(a.H + (int64_t)m * NT + c * 32, t);
+#pragma unroll
+                for (int e = 0; e < 32; ++e) a.HT[(int64_t)(c * 32 + e) * a.ldT + m] = __float2bfloat16_rn(t[e]);
+            }
+            const float s = warp_transpose_sum(t, lane);
+            atomicAdd(&a.colsum[c * 32 + lane], s);
         }
     } else if constexpr (EPI == EPI_DGELU) {
         for (int c = c0; c < c0 + kChunks; ++c) {
