@@ -77,7 +77,7 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
                  const TileDesc* __restrict__ tiles, int64_t t0, const float* __restrict__ xnorm, int kblocks,
                  unsigned int* timeouts, const uint8_t* __restrict__ skip) {
     extern __shared__ unsigned char dsmem[];
-    __shared__ uint64_t full_bar[2], done_bar[2];
+    __shared__ uint64_t full_bar[2], done_bar[2], drain_bar;
     __shared__ uint32_t tmem_base;
     __shared__ float nj[tc::kTileRows];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -97,6 +97,7 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
             tc::mbar_init(tc::smem_addr(&full_bar[s]), 1);
             tc::mbar_init(tc::smem_addr(&done_bar[s]), 1);
         }
+        tc::mbar_init(tc::smem_addr(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -112,15 +113,17 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
     if (tid == 0) {
         const uint32_t idesc = tc::idesc_bf16_f32(tc::kTileRows, tc::kTileRows);
         bool ok = true;
+        int issued = 0;   // K blocks whose loads were issued
         for (int kb = 0; kb < kblocks; ++kb) {
             const int s = kb & 1;
             const uint32_t fb = tc::smem_addr(&full_bar[s]), db = tc::smem_addr(&done_bar[s]);
-            if (kb >= 2) ok = tc::mbar_wait(db, (uint32_t)((kb - 2) >> 1) & 1u) && ok;   // stage free again
+            if (kb >= 2 && !(ok = tc::mbar_wait(db, (uint32_t)((kb - 2) >> 1) & 1u))) break;   // stage free again
             const uint32_t sa = sbase + (uint32_t)s * 2u * tc::kTileBytes, sb = sa + tc::kTileBytes;
             tc::mbar_expect_tx(fb, 2u * tc::kTileBytes);
             tc::tma_load_2d(sa, &tmX, kb * tc::kTileK, (int)(off + i0), fb);
             tc::tma_load_2d(sb, &tmX, kb * tc::kTileK, (int)(off + j0), fb);
-            ok = tc::mbar_wait(fb, (uint32_t)(kb >> 1) & 1u) && ok;
+            issued = kb + 1;
+            if (!(ok = tc::mbar_wait(fb, (uint32_t)(kb >> 1) & 1u))) break;
             tc::tc_fence_after();
             const uint64_t da = tc::sw128_desc(sa), dbd = tc::sw128_desc(sb);
 #pragma unroll
@@ -129,8 +132,11 @@ dist_bf16_kernel(const __grid_constant__ CUtensorMap tmX, float* __restrict__ D,
             tc::mma_commit(db);
         }
         const int last = kblocks - 1;
-        ok = tc::mbar_wait(tc::smem_addr(&done_bar[last & 1]), (uint32_t)(last >> 1) & 1u) && ok;
-        if (!ok) atomicAdd(timeouts, 1u);
+        if (ok) ok = tc::mbar_wait(tc::smem_addr(&done_bar[last & 1]), (uint32_t)(last >> 1) & 1u);
+        if (!ok) {   // the host reports the count; nothing issued stays in flight
+            atomicAdd(timeouts, 1u);
+            tc::drain_issued(tc::smem_addr(&full_bar[0]), 2, issued, tc::smem_addr(&drain_bar));
+        }
     }
     __syncthreads();
     tc::tc_fence_after();

@@ -212,7 +212,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     constexpr uint32_t kStageBytes = kABytes + kBBytes;
     constexpr bool kHead = EPI == EPI_HEAD_TRAIN;
     extern __shared__ unsigned char dsmem[];
-    __shared__ uint64_t full_bar[kStages], done_bar[kStages];
+    __shared__ uint64_t full_bar[kStages], done_bar[kStages], drain_bar;
     __shared__ uint32_t tmem_base;
     __shared__ float sb[NT];
     __shared__ float sw3[kHead ? OD : 1][NT];
@@ -234,6 +234,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             tc::mbar_init(tc::smem_addr(&full_bar[s]), 1);
             tc::mbar_init(tc::smem_addr(&done_bar[s]), 1);
         }
+        tc::mbar_init(tc::smem_addr(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -249,6 +250,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     if (tid == 0) {
         const uint32_t idesc = tc::idesc_bf16_f32(128, NT);
         bool ok = true;
+        int issued = 0;   // K blocks whose loads were issued
         auto issue = [&](int i) {
             const int s = i % nst;
             const uint32_t fb = tc::smem_addr(&full_bar[s]);
@@ -258,12 +260,13 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             tc::tma_load_2d(sa, &tmA, col, m0, fb);
 #pragma unroll
             for (int r = 0; r < kBRows / 128; ++r) tc::tma_load_2d(sbb + (uint32_t)r * tc::kTileBytes, &tmB, col, r * 128, fb);
+            issued = i + 1;
         };
         for (int i = 0; i < nst && i < nkb; ++i) issue(i);
         for (int i = 0; i < nkb; ++i) {
             const int s = i % nst;
             const uint32_t par = (uint32_t)(i / nst) & 1u;
-            ok = tc::mbar_wait(tc::smem_addr(&full_bar[s]), par) && ok;
+            if (!(ok = tc::mbar_wait(tc::smem_addr(&full_bar[s]), par))) break;
             tc::tc_fence_after();
             const uint32_t sa = sbase + (uint32_t)s * kStageBytes, sbb = sa + kABytes;
             const uint64_t da = tc::sw128_desc(sa), db = tc::sw128_desc(sbb);
@@ -272,13 +275,16 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 tc::mma_bf16(tmem, da + 2 * k16, db + 2 * k16, idesc, (i > 0 || k16 > 0) ? 1u : 0u);
             tc::mma_commit(tc::smem_addr(&done_bar[s]));
             if (i + nst < nkb) {   // stage s is free once these MMAs are done
-                ok = tc::mbar_wait(tc::smem_addr(&done_bar[s]), par) && ok;
+                if (!(ok = tc::mbar_wait(tc::smem_addr(&done_bar[s]), par))) break;
                 issue(i + nst);
             }
         }
         const int last = nkb - 1;
-        ok = tc::mbar_wait(tc::smem_addr(&done_bar[last % nst]), (uint32_t)(last / nst) & 1u) && ok;
-        if (!ok) atomicAdd(a.timeouts, 1u);
+        if (ok) ok = tc::mbar_wait(tc::smem_addr(&done_bar[last % nst]), (uint32_t)(last / nst) & 1u);
+        if (!ok) {   // the host reports the count; nothing issued stays in flight
+            atomicAdd(a.timeouts, 1u);
+            tc::drain_issued(tc::smem_addr(&full_bar[0]), nst, issued, tc::smem_addr(&drain_bar));
+        }
     }
     __syncthreads();
     tc::tc_fence_after();
@@ -504,8 +510,9 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
     extern __shared__ unsigned char dsmem[];
     // 0: W1 loaded; 1-2: X stage written; 3-6: W2 stage full; 7-10: W2 stage
     // free; 11-12: layer 1 done (per accumulator and X stage); 13-14: layer 2
-    // done; 15: H1 written; 16-17: accumulator read by the layer-2 epilogue
-    __shared__ uint64_t bars[18];
+    // done; 15: H1 written; 16-17: accumulator read by the layer-2 epilogue;
+    // 18: every MMA issued (the exit drain)
+    __shared__ uint64_t bars[19];
     __shared__ uint32_t tmem_base;
     __shared__ __align__(16) float sb1[kH];
     __shared__ __align__(16) float sb2[kH];
@@ -521,9 +528,9 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem_base), 512);
     if (tid == 0) {
         s_fail = 0;
-        for (int i = 0; i < 18; ++i) {
+        for (int i = 0; i < 19; ++i) {
             const uint32_t count = (i == 1 || i == 2) ? (uint32_t)kInferLoadWarps
-                                 : (i >= 15) ? (uint32_t)kInferEpiWarps : 1u;
+                                 : (i >= 15 && i <= 17) ? (uint32_t)kInferEpiWarps : 1u;
             tc::mbar_init(B(i), count);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -544,7 +551,7 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
         if (lane == 0 && ntl > 0) {
             const uint32_t id1 = tc::idesc_bf16_f32(128, 256), id2 = tc::idesc_bf16_f32(128, 128);
             const int nuse = 8 * ntl;   // W2 boxes: 2 halves x 4 K blocks per tile
-            int w2_issued = 0, mma1_tiles = 0, mma2_tiles = 0;
+            int w2_issued = 0;
             auto load_w2 = [&](int u) {
                 const int s = u % kW2Stages, h = (u >> 2) & 1, kb = u & 3;
                 const uint32_t bar = B(3 + s);
@@ -567,7 +574,6 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
 #pragma unroll
                 for (int k16 = 0; k16 < 4; ++k16) tc::mma_bf16(acc, dx + 2 * k16, dw1 + 2 * k16, id1, k16 > 0 ? 1u : 0u);
                 tc::mma_commit(B(11 + b));
-                mma1_tiles = j + 1;
                 if (!iwait(B(15), (uint32_t)j & 1u, fail)) break;   // layer-1 activations of tile j written
                 tc::tc_fence_after();
                 bool ok = true;
@@ -592,18 +598,14 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
                     }
                 if (!ok) break;
                 tc::mma_commit(B(13 + b));
-                mma2_tiles = j + 1;
             }
-            if (*fail) {
-                // a wait ran out: wait (bounded) for the copies and MMAs this
-                // thread issued, so that none is in flight when the CTA exits
-                atomicAdd(a.timeouts, 1u);
-                tc::mbar_wait(B(0), 0u);
-                for (int u = w2_issued > kW2Stages ? w2_issued - kW2Stages : 0; u < w2_issued; ++u)
-                    tc::mbar_wait(B(3 + u % kW2Stages), (uint32_t)(u / kW2Stages) & 1u);
-                if (mma1_tiles > 0) tc::mbar_wait(B(11 + ((mma1_tiles - 1) & 1)), (uint32_t)((mma1_tiles - 1) >> 1) & 1u);
-                if (mma2_tiles > 0) tc::mbar_wait(B(13 + ((mma2_tiles - 1) & 1)), (uint32_t)((mma2_tiles - 1) >> 1) & 1u);
-            }
+            // Whether or not a wait ran out (in this role or another, also
+            // after this thread's last tile): wait (bounded) for W1, the W2
+            // loads and every MMA this thread issued, so that none is in
+            // flight when the CTA frees tensor memory and exits.  Without a
+            // timeout all of them are done by now.
+            tc::mbar_wait(B(0), 0u);
+            tc::drain_issued(B(3), kW2Stages, w2_issued, B(18));
         }
     } else if (warp > kInferEpiWarps) {
         // X loaders: warp lw takes rows lw, lw + 2, ... of the tile; lane l
@@ -764,6 +766,7 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
     }
     tc::tc_fence_before();
     __syncthreads();
+    if (tid == 0 && *fail) atomicAdd(a.timeouts, 1u);   // the host reports PTSNE_ETIMEOUT
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 

@@ -157,6 +157,20 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
+// Wait (bounded) for the TMA loads still in flight (loads 0 .. issued - 1
+// of a ring of `stages` stages, load i on stage i mod stages in phase
+// i / stages, the full barriers 8 bytes apart from full0; only the last
+// `stages` can be in flight) and, through one more commit onto drain_bar
+// (count 1, otherwise unused), for every MMA the calling thread issued, so
+// that neither is in flight when the CTA frees its tensor memory and exits.
+// The issuing thread calls it after one of its bounded waits ran out (it
+// issues nothing more after that).
+__device__ __forceinline__ void drain_issued(uint32_t full0, int stages, int issued, uint32_t drain_bar) {
+    for (int i = issued > stages ? issued - stages : 0; i < issued; ++i)
+        mbar_wait(full0 + 8u * (uint32_t)(i % stages), (uint32_t)(i / stages) & 1u);
+    mma_commit(drain_bar);
+    mbar_wait(drain_bar, 0u);
+}
 #endif
 
 }  // namespace tc
