@@ -4,7 +4,7 @@
 // network is trained on ptSNE's own maps and used to place held-out points
 // and to warm-start ptsne_run.
 //
-// One GEMM kernel serves every contraction: C = A B^T with A (M x K) and
+// Training: one GEMM kernel serves every contraction, C = A B^T with A (M x K) and
 // B (N x K) BF16, both K-major, staged by TMA (128-byte swizzle, a ring of
 // up to 3 stages, as many as the CTA's K blocks need), one elected thread
 // issuing tcgen05.mma (M = 128, N = NT, K = 16) into an FP32 accumulator of
@@ -32,6 +32,10 @@
 //   DGELU     dA2 x W2^T    -> dA1^T, db1                   (K = 256)
 //   ATOMIC    dA1^T x Xb^T  -> dW1 (256 x d_in)             (K = B, split)
 //   AdamW on the FP32 master parameters, rewriting the BF16 copies.
+//
+// Inference runs in one fused, warp-specialised kernel (mlp_infer_kernel,
+// below): FP32 X read in place, both layers and the head per 128-row tile,
+// the hidden activations kept in shared memory.
 #include <float.h>
 #include <math.h>
 #include <stdio.h>

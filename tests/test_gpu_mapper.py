@@ -50,7 +50,7 @@ def _f64(W):
 
 def test_forward_with_scaler_matches_oracle(dev):
     from paper_1812_09869_gb300.mapper import Mapper
-    n, d_in = 1000, 50                     # 3 inference slabs of 256 rows and a ragged one of 232
+    n, d_in = 1000, 50                     # 3 inference launches of 256 rows and a ragged one of 232
     X, _ = synth.gaussian_mixture(n, d_in, 5, seed=70)
     X = _bf16(X)
     W = _weights(d_in, 2, 71)
