@@ -741,7 +741,19 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
                             }
                         }
                         if (c16 < 3) tc::tmem_wait_ld16(nxt);
+                        if (c16 == 2) {
+                            // the last block's columns are in registers: the
+                            // accumulator is free for layer 1 of tile t + 2
+                            // while this warp finishes the arithmetic
+                            tc::tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive1(B(16 + b));
+                        }
                     }
+                } else {
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive1(B(16 + b));
                 }
 #pragma unroll
                 for (int k = 0; k < OD; ++k) {
@@ -749,9 +761,6 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
                     upkm(y2[k], lo, hi);
                     s_y[t & 1][cg][row][k] = lo + hi;
                 }
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive1(B(16 + b));   // the accumulator is free for layer 1 of tile t + 2
                 epi_bar();
                 if (ok && cg == 0) {
                     const int m = tile_row(t) + row;
