@@ -13,7 +13,11 @@
 //
 // Thread (ty, tx) of 16 x 16 owns rows 4ty..4ty+3 and columns 4tx..4tx+3.
 // Each step of k stages 32 dimensions of both row blocks k-major in shared
-// memory (8 lanes per row: coalesced 128-byte loads); the products run two
+// memory (8 lanes per row: coalesced 128-byte loads; the 4-row groups of
+// dimension k sit at group g ^ ((k / 4) mod 8), so that the eight lanes of a
+// row, which store dimensions 4m .. 4m + 3 for m = 0..7, and the warp's four
+// rows hit 32 different banks, while the reads of four consecutive rows stay
+// one aligned 16-byte load); the products run two
 // rows per packed f32x2 instruction against a column value duplicated into
 // both halves (IEEE round-to-nearest per lane, so every distance is the same
 // sequence of roundings as the scalar sum over k in order).  The next step's
@@ -25,6 +29,8 @@ namespace ptsne {
 namespace {
 constexpr int KC = 32;            // dims staged per step
 constexpr int SROW = kTile + 4;   // shared-memory row stride (floats) of the k-major blocks
+// column of row `row` in the k-major block's line for dimension k (4-row groups swizzled)
+__device__ __forceinline__ int swz(int k, int row) { return row ^ (((k >> 2) & 7) << 2); }
 
 typedef unsigned long long f2;
 __device__ __forceinline__ f2 pk(float a, float b) {
@@ -93,19 +99,19 @@ dist_fp32_kernel(const float* __restrict__ Xg, float* __restrict__ D, Layout L, 
         for (int k0 = 0; k0 < dp; k0 += KC) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int e = tid + 256 * h, row = e >> 3, kk = 4 * (e & 7);
-                sI[kk + 0][row] = ra[h].x; sI[kk + 1][row] = ra[h].y;
-                sI[kk + 2][row] = ra[h].z; sI[kk + 3][row] = ra[h].w;
-                sJ[kk + 0][row] = rb[h].x; sJ[kk + 1][row] = rb[h].y;
-                sJ[kk + 2][row] = rb[h].z; sJ[kk + 3][row] = rb[h].w;
+                const int e = tid + 256 * h, kk = 4 * (e & 7), col = swz(kk, e >> 3);
+                sI[kk + 0][col] = ra[h].x; sI[kk + 1][col] = ra[h].y;
+                sI[kk + 2][col] = ra[h].z; sI[kk + 3][col] = ra[h].w;
+                sJ[kk + 0][col] = rb[h].x; sJ[kk + 1][col] = rb[h].y;
+                sJ[kk + 2][col] = rb[h].z; sJ[kk + 3][col] = rb[h].w;
             }
             __syncthreads();
             if (k0 + KC < dp) load(k0 + KC);
             // (dimensions beyond dp are staged as zeros: fma(0, 0, acc) == acc exactly)
 #pragma unroll 8
             for (int k = 0; k < KC; ++k) {
-                const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(&sI[k][4 * ty]);   // rows in pairs
-                const float4 b = *reinterpret_cast<const float4*>(&sJ[k][4 * tx]);
+                const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(&sI[k][swz(k, 4 * ty)]);   // rows in pairs
+                const float4 b = *reinterpret_cast<const float4*>(&sJ[k][swz(k, 4 * tx)]);
                 const f2 bq[4] = {pk(b.x, b.x), pk(b.y, b.y), pk(b.z, b.z), pk(b.w, b.w)};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
