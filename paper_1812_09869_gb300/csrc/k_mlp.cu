@@ -784,20 +784,30 @@ mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW1, const __grid_constant
 }
 
 // Batch gather: rows of X (FP32, n x din) -> Xb (B x 64 BF16, zero-padded) and
-// Xb^T (64 x B), targets -> standardised t (B x OD).  64 rows per block.
+// Xb^T (64 x B), targets -> standardised t (B x OD).  64 rows per block; a
+// thread has all 16 of its (random-row) loads in flight before it uses any.
 __global__ void __launch_bounds__(256)
 gather_batch_kernel(const float* __restrict__ X, const float* __restrict__ T, int64_t n, int din, int od,
                     const int32_t* __restrict__ rows, int B, const double* __restrict__ scaler, bf16* __restrict__ Xb,
                     bf16* __restrict__ XbT, float* __restrict__ t, unsigned int* bad) {
+    constexpr int kPer = 64 * kKin / 256;   // elements per thread
     __shared__ bf16 tile[64][kKin + 8];
+    __shared__ int32_t s_rows[64];
     const int b0 = blockIdx.x * 64;
-    for (int idx = threadIdx.x; idx < 64 * kKin; idx += 256) {
-        const int s = idx / kKin, k = idx % kKin;
-        const int32_t r = rows[b0 + s];
-        const bool ok = r >= 0 && r < n;
-        if (!ok && k == 0) atomicAdd(bad, 1u);
-        const float v = (ok && k < din) ? X[(int64_t)r * din + k] : 0.f;
-        const bf16 bv = __float2bfloat16_rn(v);
+    if (threadIdx.x < 64) s_rows[threadIdx.x] = rows[b0 + threadIdx.x];
+    __syncthreads();
+    float v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int idx = threadIdx.x + 256 * q, s = idx / kKin, k = idx % kKin;
+        const int32_t r = s_rows[s];
+        v[q] = (r >= 0 && r < n && k < din) ? X[(int64_t)r * din + k] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int idx = threadIdx.x + 256 * q, s = idx / kKin, k = idx % kKin;
+        if (k == 0 && !(s_rows[s] >= 0 && s_rows[s] < n)) atomicAdd(bad, 1u);
+        const bf16 bv = __float2bfloat16_rn(v[q]);
         Xb[(int64_t)(b0 + s) * kKin + k] = bv;
         tile[s][k] = bv;
     }
@@ -808,9 +818,9 @@ gather_batch_kernel(const float* __restrict__ X, const float* __restrict__ T, in
     }
     for (int idx = threadIdx.x; idx < 64 * od; idx += 256) {
         const int s = idx / od, k = idx % od;
-        const int32_t r = rows[b0 + s];
-        const double v = (r >= 0 && r < n) ? (double)T[(int64_t)r * od + k] : scaler[k];
-        t[(int64_t)(b0 + s) * od + k] = (float)((v - scaler[k]) / scaler[od + k]);
+        const int32_t r = s_rows[s];
+        const double tv = (r >= 0 && r < n) ? (double)T[(int64_t)r * od + k] : scaler[k];
+        t[(int64_t)(b0 + s) * od + k] = (float)((tv - scaler[k]) / scaler[od + k]);
     }
 }
 
