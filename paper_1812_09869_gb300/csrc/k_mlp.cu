@@ -73,6 +73,7 @@ struct GemmArgs {
     float* colsum;       // DGELU: db1; HEAD_TRAIN: db2  ([NT])
     float* C;            // ATOMIC: [M][ldc]
     int ldc, ncols;
+    int red_width;       // ATOMIC: floats per vector reduction (4, 2 or 1), from C's and ldc's alignment
     const bf16* W3;      // HEAD_TRAIN: [OD][NT]
     const float* b3;     // HEAD_TRAIN: [OD]
     const float* T;      // HEAD_TRAIN: standardised targets [M][OD]
@@ -204,6 +205,15 @@ __device__ __forceinline__ void store_bf16x16(bf16* dst, const float (&v)[16]) {
         }
         reinterpret_cast<uint4*>(dst)[q] = pk;
     }
+}
+
+// FP32 vector reductions into global memory (relaxed, GPU scope): 4
+// consecutive floats at a 16-byte-aligned address, or 2 at an 8-byte one.
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+__device__ __forceinline__ void red_add2(float* p, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
 template <int NT, int EPI, int OD, int CG>
@@ -418,14 +428,32 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             atomicAdd(&a.colsum[c * 32 + lane], s);
         }
     } else {   // EPI_ATOMIC
+        // a thread's row of 32 columns goes out as vector reductions of 4 (or
+        // 2) consecutive floats where the row's alignment allows
+        const int vw = a.red_width;
         for (int c = c0; c < c0 + kChunks; ++c) {
             float v[32];
             tc::tmem_ld32(tb + (uint32_t)(c * 32), v);
-            if (valid) {
+            const int lim = min(32, a.ncols - c * 32);   // columns of this chunk inside C
+            if (valid && lim > 0) {
+                float* rowp = a.C + (int64_t)m * a.ldc + c * 32;
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int n = c * 32 + e;
-                    if (n < a.ncols) atomicAdd(&a.C[(int64_t)m * a.ldc + n], v[e]);
+                for (int q = 0; q < 8; ++q) {
+                    const int e = 4 * q;
+                    if (vw == 4 && e + 4 <= lim) {
+                        red_add4(rowp + e, v[e], v[e + 1], v[e + 2], v[e + 3]);
+                        continue;
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int f = e + 2 * h;
+                        if (vw >= 2 && f + 2 <= lim) {
+                            red_add2(rowp + f, v[f], v[f + 1]);
+                        } else {
+                            if (f < lim) atomicAdd(rowp + f, v[f]);
+                            if (f + 1 < lim) atomicAdd(rowp + f + 1, v[f + 1]);
+                        }
+                    }
                 }
             }
         }
@@ -999,6 +1027,14 @@ cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, GemmArgs a, 
     return cudaGetLastError();
 }
 
+// floats per vector reduction of the split-K epilogue into C (row stride ldc)
+int red_width(const float* C, int ldc) {
+    const uintptr_t p = (uintptr_t)C;
+    if (p % 16 == 0 && ldc % 4 == 0) return 4;
+    if (p % 8 == 0 && ldc % 2 == 0) return 2;
+    return 1;
+}
+
 GemmArgs base_args(ptsne_mlp* m) {
     GemmArgs a{};
     a.timeouts = m->dflags;
@@ -1061,6 +1097,7 @@ cudaError_t run_grad_od(ptsne_mlp* m, const float* X, const float* T, int64_t n,
     a.C = m->grad + m->off.W2;
     a.ldc = kH;
     a.ncols = kH;
+    a.red_width = red_width(a.C, a.ldc);
     if ((e = launch_gemm<kH, EPI_ATOMIC, OD>(m->tmdA2T, m->tmH1T, a, kH / 128, sp, s)) != cudaSuccess) return e;
     // dA1 = (dA2 W2) * g'(U1)
     a = base_args(m);
@@ -1080,6 +1117,7 @@ cudaError_t run_grad_od(ptsne_mlp* m, const float* X, const float* T, int64_t n,
     a.C = m->grad + m->off.W1;
     a.ldc = m->din;
     a.ncols = m->din;
+    a.red_width = red_width(a.C, a.ldc);
     if ((e = launch_gemm<64, EPI_ATOMIC, OD>(m->tmdA1T, m->tmXbT, a, kH / 128, sp, s)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
