@@ -11,9 +11,10 @@
 // NT columns in tensor memory, and CG groups of four warps reading it back
 // (tcgen05.ld; warp w reads accumulator rows 32 (w mod 4) .. + 31, one row per
 // thread, and group w / 4 takes NT / CG of the columns) for a fused epilogue.
-// The epilogue (exact GELU per element) is the heavy part, so a CTA carries 8
-// warps and two CTAs share an SM (2 x 256 TMEM columns, <= 2 x 96 KB of
-// stages): one CTA's loads and MMAs run under the other's epilogue.
+// The epilogue (exact GELU per element) is the heavy part: the 256-column
+// GELU epilogues carry 16 warps (four column groups, one CTA per SM), the
+// others 8 warps with two CTAs per SM (2 x 256 TMEM columns, <= 2 x 96 KB of
+// stages), one CTA's loads and MMAs under the other's epilogue.
 //
 //   FWD        u = acc + b; U = u (FP32), H = g(u) (BF16), H^T (BF16)
 //   HEAD_TRAIN h = g(acc + b2); y = W3 h + b3 per row (each column group's
@@ -217,7 +218,7 @@ __device__ __forceinline__ void red_add2(float* p, float a, float b) {
 }
 
 template <int NT, int EPI, int OD, int CG>
-__global__ void __launch_bounds__(128 * CG, 2)
+__global__ void __launch_bounds__(128 * CG, CG >= 4 ? 1 : 2)
 mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a) {
     static_assert((NT / 32) % CG == 0, "column groups must split the accumulator's 32-column chunks");
     constexpr int kBRows = NT < 128 ? 128 : NT;
@@ -1009,15 +1010,19 @@ size_t gemm_smem(int nt, int stages) {
     return (size_t)stages * (tc::kTileBytes + brows * 128) + 1024;
 }
 
-// Column groups of the epilogue: 2 (8 warps) where the accumulator has 64 or
-// more columns per group.
-template <int NT>
-constexpr int gemm_groups() { return NT >= 64 ? 2 : 1; }
+// Column groups of the epilogue: 4 (16 warps, one CTA per SM) for the
+// 256-column GELU epilogues (forward, head, GELU backward), whose 32 row
+// tiles per batch leave most SMs idle, so that each thread takes 64 columns;
+// else 2 (8 warps) where the accumulator has 64 or more columns.
+template <int NT, int EPI>
+constexpr int gemm_groups() {
+    return (NT == 256 && (EPI == EPI_FWD || EPI == EPI_HEAD_TRAIN || EPI == EPI_DGELU)) ? 4 : (NT >= 64 ? 2 : 1);
+}
 
 template <int NT, int EPI, int OD>
 cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, GemmArgs a, int mtiles, int splits,
                         cudaStream_t s) {
-    constexpr int CG = gemm_groups<NT>();
+    constexpr int CG = gemm_groups<NT, EPI>();
     auto kern = mlp_gemm_kernel<NT, EPI, OD, CG>;
     a.stages = gemm_stages(a.kb_per_split);
     const size_t smem = gemm_smem(NT, a.stages);
