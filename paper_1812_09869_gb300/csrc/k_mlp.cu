@@ -467,7 +467,8 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // ---------------------------------------------------------------- fused inference
 // Inference of 128-row tiles in one persistent, warp-specialised kernel.
 // Two loader warps read the tile's FP32 rows of X straight from global
-// memory (a warp per row, two columns per lane), round them to BF16 and
+// memory (alternate rows; one row per load instruction, lane l taking
+// columns 2l and 2l + 1), round them to BF16 and
 // write the layer-1 A operand (zero-padded to 64 columns) into shared memory
 // in the 128-byte-swizzled K-major layout that TMA writes (row r, 16-byte
 // chunk c of a 64-column K block at r * 128 + ((c ^ (r mod 8)) * 16)).
@@ -479,12 +480,14 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // reads tensor-memory lanes 32 (w mod 4) .. + 31, one row per thread, and
 // column group (w - 1) / 4 of four 64-column groups, which is one K block of
 // the layer-2 operand); warps 17 and 18 load X.  Two accumulators (2 x 256
-// tensor-memory columns) let the tensor cores run layer 2 of tile j and
-// layer 1 of tile j + 1 while the epilogue warps take layer 1 of tile j + 1
-// and layer 2 of tile j.  W1 stays in shared memory; W2 streams from L2 in
-// 128-row x 64-column boxes, four in flight.  Mbarrier waits are bounded;
-// the first that runs out stops every role (the epilogue warps still meet at
-// their named barrier).
+// tensor-memory columns, tile j in accumulator j mod 2, layer 2 overwriting
+// layer 1 once its activations are in shared memory) let the tensor cores
+// run layer 2 of tile j while the epilogue warps take layer 2 of tile j - 1,
+// and layer 1 of tile j + 1 as soon as that accumulator has been read.  W1
+// stays in shared memory; W2 streams from L2 in 128-row x 64-column boxes,
+// four in flight.  Mbarrier waits are bounded; the first that runs out stops
+// every role (the epilogue warps still meet at their named barrier), and the
+// issuing thread waits for its copies and MMAs before tensor memory is freed.
 constexpr int kInferEpiWarps = 16;
 constexpr int kInferLoadWarps = 2;
 constexpr int kInferThreads = 32 * (1 + kInferEpiWarps + kInferLoadWarps);
