@@ -196,12 +196,18 @@ int ptsne_set_locality_order(ptsne_ctx* ctx, int on);
  * run to run, so that two identical runs agree to about 1e-7 relative per
  * iteration, not bit for bit.  1: the sums are kept in 64-bit fixed point
  * (A at 2^-61, R at 2^-48; integer adds do not depend on their order), so
- * that identical runs on one GPU give bitwise identical maps and costs; it
- * doubles the accumulators' shared memory, so the largest chunks run with
- * fewer warps (slower).  The per-chunk schedule sums in a fixed order in
- * either mode.  PTSNE_EINVAL if the largest chunk does not fit the
- * deterministic kernel (2-D maps: z up to about 5600, with all 16 warps up
- * to about 4100; 3-D maps: up to about 3700). */
+ * that identical runs on one GPU give bitwise identical maps and costs.  The
+ * 8-byte sums need twice the shared memory; on clusters of 2 or 4 blocks
+ * (ptsne_set_tuning) each block holds only the sums of the rows it updates
+ * and adds to the other rows' sums in their block's shared memory, so the
+ * footprint is that of the FP32 sums on 2 blocks and less on 4.  The
+ * per-chunk schedule sums in a fixed order in either mode.  PTSNE_EINVAL if
+ * the largest chunk does not fit the deterministic kernel for the current
+ * cluster size (on 1 block per chunk: 2-D maps up to z of about 5600, 3-D
+ * about 3700; on 2 or 4 blocks every chunk the batched schedule takes; all
+ * 16 warps of a 2-D block up to about 4100, 6800 and 10200 on 1, 2 and 4
+ * blocks), and ptsne_set_tuning refuses a cluster size that would not fit
+ * while the mode is on. */
 int ptsne_set_deterministic(ptsne_ctx* ctx, int on);
 
 /* Form of each chunk's distances under PTSNE_PREC_BF16_WINDOW.  A row's

@@ -61,6 +61,9 @@ struct IterArgs {
     Optim opt;
     int* queue;                 // chunk work queue (zeroed before launch)
     int zcap;                   // rows of the shared map / accumulators (multiple of 32)
+    int acc_rows;               // rows of one block's accumulators: zcap, or in the deterministic
+                                // build with a cluster of K > 1 blocks ceil(zcap / K) rounded up
+                                // to 32 (each block holds the sums of the rows it updates)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -161,13 +164,35 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
 // 8 bytes.
 constexpr float kFixA = 2305843009213693952.0f;   // 2^61
 constexpr float kFixR = 281474976710656.0f;       // 2^48
+// One block's view of the accumulators.  The FP32 build and the
+// deterministic build on one block: every block holds all rows (quantity q
+// of row i at q * stride + i, stride = zcap).  The deterministic build on a
+// cluster of K > 1 blocks: block r holds rows [r slice, (r + 1) slice) only
+// (quantity q of its local row l at q * stride + l), and an add to another
+// block's row goes to that block's shared memory (a cluster-scope reduction),
+// so that each block's 8-byte sums take 1 / K of the space.
+struct AccRef {
+    float* p;
+    int stride;
+    int slice;
+    uint32_t rank, K;
+};
+__device__ __forceinline__ void red_cl_add_u64(uint32_t a, unsigned long long v) {
+    asm volatile("red.shared::cluster.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
 template <bool DET>
-__device__ __forceinline__ void acc_add(float* acc, int idx, float v, bool isR) {
-    if constexpr (DET)
-        atomicAdd(reinterpret_cast<unsigned long long*>(acc) + idx,
-                  (unsigned long long)__float2ll_rn(v * (isR ? kFixR : kFixA)));
-    else
-        atomicAdd(acc + idx, v);
+__device__ __forceinline__ void acc_add(const AccRef& A, int q, int i, float v, bool isR) {
+    if constexpr (DET) {
+        const unsigned long long x = (unsigned long long)__float2ll_rn(v * (isR ? kFixR : kFixA));
+        uint32_t owner = 0;
+        if (A.K > 1)
+            owner = (uint32_t)(i >= A.slice) + (A.K > 2 ? (uint32_t)(i >= 2 * A.slice) + (uint32_t)(i >= 3 * A.slice) : 0u);
+        unsigned long long* a = reinterpret_cast<unsigned long long*>(A.p) + (q * A.stride + i - (int)owner * A.slice);
+        if (owner == A.rank) atomicAdd(a, x);
+        else red_cl_add_u64(map_rank(smem_u32(a), owner), x);
+    } else {
+        atomicAdd(A.p + q * A.stride + i, v);
+    }
 }
 
 // ---------------------------------------------------------------- tile evaluation
@@ -264,7 +289,7 @@ __device__ __forceinline__ void rows2_begin(Rows2& R, const float* map, int a, i
 // The row sums of the four rings are reduced over lanes g, g + 8, g + 16,
 // g + 24, each keeping one row, and added to acc.
 template <bool DET>
-__device__ __forceinline__ void rows2_flush(const Rows2& R, int zcap, int a, int lane, float* acc) {
+__device__ __forceinline__ void rows2_flush(const Rows2& R, int a, int lane, const AccRef& acc) {
     const int g = lane & 7, q = lane >> 3;
     float v[4][4];
 #pragma unroll
@@ -290,7 +315,7 @@ __device__ __forceinline__ void rows2_flush(const Rows2& R, int zcap, int a, int
     for (int k = 0; k < 4; ++k) {
         const float keep = odd ? w2[1][k] : w2[0][k];
         const float give = odd ? w2[0][k] : w2[1][k];
-        acc_add<DET>(acc, k * zcap + row, keep + __shfl_xor_sync(0xffffffffu, give, 8), k >= 2);
+        acc_add<DET>(acc, k, row, keep + __shfl_xor_sync(0xffffffffu, give, 8), k >= 2);
     }
 }
 
@@ -305,7 +330,7 @@ __device__ __forceinline__ void rows2_flush(const Rows2& R, int zcap, int a, int
 // warp's next tile nsrc (if any) into the warp's buffer at buf_a.
 template <bool SYM, bool DET>
 __device__ __forceinline__ float tile_grad_2d(Rows2& R, const float* map, int zcap, int b, int lane,
-                                              const float4 (&pv)[8], float* acc, const float* nsrc, uint32_t buf_a) {
+                                              const float4 (&pv)[8], const AccRef& acc, const float* nsrc, uint32_t buf_a) {
     const float4* mp = reinterpret_cast<const float4*>(map);
     const int g = lane & 7, q = lane >> 3, u = g >> 1;
     const f2 ONE = pk(1.f, 1.f);
@@ -368,13 +393,13 @@ __device__ __forceinline__ float tile_grad_2d(Rows2& R, const float* map, int zc
         const int col = b * kPT + 8 * q + 2 * ((u + 3) & 3) + oddg;
         float lo, hv;
         upk(CAX, lo, hv);
-        acc_add<DET>(acc, col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), false);
+        acc_add<DET>(acc, 0, col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), false);
         upk(CAY, lo, hv);
-        acc_add<DET>(acc, zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), false);
+        acc_add<DET>(acc, 1, col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), false);
         upk(CRX, lo, hv);
-        acc_add<DET>(acc, 2 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), true);
+        acc_add<DET>(acc, 2, col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), true);
         upk(CRY, lo, hv);
-        acc_add<DET>(acc, 3 * zcap + col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), true);
+        acc_add<DET>(acc, 3, col, -((oddg ? hv : lo) + __shfl_xor_sync(0xffffffffu, oddg ? lo : hv, 1)), true);
         return 2.0f * hsum2(Z);
     }
     return hsum2(Z);
@@ -383,7 +408,7 @@ __device__ __forceinline__ float tile_grad_2d(Rows2& R, const float* map, int zc
 // Same sums for 3-D maps (scalar arithmetic, same lane order and packets).
 template <bool SYM, bool DET>
 __device__ __forceinline__ float tile_grad_3d(const float* map, int zcap, int a, int b, int lane,
-                                              const float4 (&pv)[8], float* acc) {
+                                              const float4 (&pv)[8], const AccRef& acc) {
     const int g = lane & 15, h = lane >> 4;
     const int ra = a * kPT + 2 * g, cb = b * kPT + 16 * h;
     const float* pf = reinterpret_cast<const float*>(pv);
@@ -445,16 +470,16 @@ __device__ __forceinline__ float tile_grad_3d(const float* map, int zcap, int a,
     const int row = ra + h;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        acc_add<DET>(acc, k * zcap + row, keep_row(ra_[0][k], ra_[1][k], h), false);
-        acc_add<DET>(acc, (3 + k) * zcap + row, keep_row(rr_[0][k], rr_[1][k], h), true);
+        acc_add<DET>(acc, k, row, keep_row(ra_[0][k], ra_[1][k], h), false);
+        acc_add<DET>(acc, 3 + k, row, keep_row(rr_[0][k], rr_[1][k], h), true);
     }
     if constexpr (SYM) {
         const int prv = (lane & 16) | ((g + 15) & 15);
         const int col = cb + ((g + 14) & 15);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            acc_add<DET>(acc, k * zcap + col, -(ca[0][k] + __shfl_sync(0xffffffffu, ca[1][k], prv)), false);
-            acc_add<DET>(acc, (3 + k) * zcap + col, -(cr[0][k] + __shfl_sync(0xffffffffu, cr[1][k], prv)), true);
+            acc_add<DET>(acc, k, col, -(ca[0][k] + __shfl_sync(0xffffffffu, ca[1][k], prv)), false);
+            acc_add<DET>(acc, 3 + k, col, -(cr[0][k] + __shfl_sync(0xffffffffu, cr[1][k], prv)), true);
         }
         return 2.0f * z;
     }
@@ -595,7 +620,7 @@ __device__ __forceinline__ double warp_sum_ksum(const KSum& k) {
 // waiting for them before the first step).
 template <int OD, bool COST, bool DET>
 __device__ __forceinline__ void consume_pass(const float* P2b, int w0, int n_w, int next0, int nb, const float* buf,
-                                             const float* map, int zcap, float* acc, int lane, KSum (&part)[4]) {
+                                             const float* map, int zcap, const AccRef& acc, int lane, KSum (&part)[4]) {
     // w of the pair (i, i), which a diagonal tile's row-wise pass counts in
     // its lanes with h == g / 8 (rows 2g, 2g + 1 meet their own columns)
     // (ring-8 layout: lanes with q == g / 2 meet their own four rows;
@@ -634,7 +659,7 @@ __device__ __forceinline__ void consume_pass(const float* P2b, int w0, int n_w, 
             float zl;
             if constexpr (OD == 2) {
                 if (a != cur_a) {   // warp-uniform: a new row block
-                    if (cur_a >= 0) rows2_flush<DET>(R, zcap, cur_a, lane, acc);
+                    if (cur_a >= 0) rows2_flush<DET>(R, cur_a, lane, acc);
                     rows2_begin(R, map, a, lane);
                     cur_a = a;
                 }
@@ -661,7 +686,7 @@ __device__ __forceinline__ void consume_pass(const float* P2b, int w0, int n_w, 
         }
     }
     if constexpr (OD == 2 && !COST) {
-        if (cur_a >= 0) rows2_flush<DET>(R, zcap, cur_a, lane, acc);
+        if (cur_a >= 0) rows2_flush<DET>(R, cur_a, lane, acc);
     }
 }
 
@@ -706,8 +731,13 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         const int nb = (z + kPT - 1) / kPT;
         const int zr = nb * kPT;
         const Stream S(nb, rank, K);
-        const int slice = (z + (int)K - 1) / (int)K;           // rows updated by this block
+        // rows updated by this block; the deterministic build on a cluster
+        // splits the accumulators the same way (over the zr padded rows, which
+        // all receive sums), each block holding its own rows' sums
+        const bool split = DET && K > 1;
+        const int slice = split ? (zr + (int)K - 1) / (int)K : (z + (int)K - 1) / (int)K;
         const int ulo = (int)rank * slice, uhi = min(z, ulo + slice);
+        const AccRef accr{acc, split ? A.acc_rows : zcap, slice, rank, split ? K : 1u};
         const int npass = A.iters + (A.cost_pass ? 1 : 0);
 
         // this warp's tiles of the chunk: a contiguous piece of the block's
@@ -731,8 +761,9 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
 #pragma unroll
             for (int k = 0; k < OD; ++k) map[map_idx<OD>(zcap, i, k)] = i < z ? A.Yc[(off + i) * OD + k] : kPad * (float)(i - z + 1);
         }
-        for (int i = tid; i < (DET ? 4 : 2) * OD * zcap; i += nthreads) acc[i] = 0.f;
+        for (int i = tid; i < (DET ? 4 : 2) * OD * accr.stride; i += nthreads) acc[i] = 0.f;
         __syncthreads();
+        if (split) cl_barrier();   // every block's sums are zero before any block adds to them
 
         for (int it = 0; it < npass; ++it) {
             const bool cost = it == A.iters;
@@ -765,8 +796,8 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
             // last pass, or if its next piece is empty)
             const int next0 = it + 1 < npass && cut_n[warp + 1] > cut_n[warp] ? cut_n[warp] : -1;
             const long long t_pass = clock64();
-            if (!cost) consume_pass<OD, false, DET>(P2b, w0, n_w, next0, nb, wbuf, map, zcap, acc, lane, part);
-            else consume_pass<OD, true, DET>(P2b, w0, n_w, next0, nb, wbuf, map, zcap, acc, lane, part);
+            if (!cost) consume_pass<OD, false, DET>(P2b, w0, n_w, next0, nb, wbuf, map, zcap, accr, lane, part);
+            else consume_pass<OD, true, DET>(P2b, w0, n_w, next0, nb, wbuf, map, zcap, accr, lane, part);
             if (it == 0 && lane == 0) s_cyc[warp] = clock64() - t_pass;
             // block partials (fixed order), then the cluster total; a gradient pass
             // has only Z (the cost sums are zero there)
@@ -833,12 +864,22 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                         Av[k] = 0.f;
                         Rv[k] = 0.f;
                     }
-                    if constexpr (DET) {   // integer sums over the cluster, then to float
-                        const long long* acc64 = reinterpret_cast<const long long*>(acc);
+                    if constexpr (DET) {   // integer sums (over the cluster), then to float
+                        long long* acc64 = reinterpret_cast<long long*>(acc);
                         long long sa[OD], sr[OD];
 #pragma unroll
                         for (int k = 0; k < OD; ++k) sa[k] = sr[k] = 0;
-                        for (uint32_t rr = 0; rr < K; ++rr) {
+                        if (split) {   // this block holds the row's sums: read and clear them
+                            const int l = i - ulo, st = accr.stride;
+#pragma unroll
+                            for (int k = 0; k < OD; ++k) {
+                                sa[k] = acc64[k * st + l];
+                                sr[k] = acc64[(OD + k) * st + l];
+                                acc64[k * st + l] = 0;
+                                acc64[(OD + k) * st + l] = 0;
+                            }
+                        }
+                        for (uint32_t rr = 0; rr < (split ? 0u : K); ++rr) {
 #pragma unroll
                             for (int k = 0; k < OD; ++k) {
                                 if (K > 1) {
@@ -883,10 +924,22 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
                         }
                 }
             }
+            if (split && !cost) {
+                // the rest of this block's sums (padded rows, or a block with
+                // no rows of this chunk): clear before the barrier below, after
+                // which the other blocks add the next pass's sums
+                long long* acc64 = reinterpret_cast<long long*>(acc);
+                const int l0 = max(0, uhi - ulo), st = accr.stride;
+                for (int l = l0 + tid; l < st; l += nthreads)
+#pragma unroll
+                    for (int q = 0; q < 2 * OD; ++q) acc64[q * st + l] = 0;
+            }
             sync_owner(K);   // new map everywhere; remote reads of acc are done
-            // 2 OD zcap entries of 4 (8 if DET) bytes, zcap a multiple of 32
-            for (int i = tid; i < (DET ? 2 : 1) * OD * zcap / 2; i += nthreads)
-                reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!split) {
+                // 2 OD zcap entries of 4 (8 if DET) bytes, zcap a multiple of 32
+                for (int i = tid; i < (DET ? 2 : 1) * OD * zcap / 2; i += nthreads)
+                    reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             __syncthreads();
         }
         for (int i = ulo + tid; i < uhi; i += nthreads)
@@ -898,18 +951,26 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
 
 // ---------------------------------------------------------------- launchers
 
-int iterate_smem_bytes(int od, int64_t zmax, int warps, bool det) {
+// Rows of one block's accumulators: all zcap, or, in the deterministic build
+// on a cluster of K > 1 blocks, the block's own share (rounded up to 32).
+int iterate_acc_rows(int64_t zmax, bool det, int K) {
+    const int zcap = (int)((zmax + kPT - 1) / kPT * kPT);
+    if (!det || K <= 1) return zcap;
+    return ((zcap + K - 1) / K + kPT - 1) / kPT * kPT;
+}
+
+int iterate_smem_bytes(int od, int64_t zmax, int warps, bool det, int K) {
     const int zcap = (int)((zmax + kPT - 1) / kPT * kPT);
     // a tile buffer per warp, the map (a 2-D map as column pairs), A and R
     // (structure-of-arrays; 8-byte fixed point when deterministic)
-    return warps * kPTileStride * 4 + zcap * od * 4 + zcap * 2 * od * (det ? 8 : 4);
+    return warps * kPTileStride * 4 + zcap * od * 4 + iterate_acc_rows(zmax, det, K) * 2 * od * (det ? 8 : 4);
 }
 
 // Warps (at most `want`) whose tile buffers fit beside the map and the
 // accumulators in 227 KB of shared memory; 0 if not even one fits.
-int iterate_warps(int od, int64_t zmax, int want, bool det) {
+int iterate_warps(int od, int64_t zmax, int want, bool det, int K) {
     int w = want;
-    while (w > 0 && iterate_smem_bytes(od, zmax, w, det) > 227 * 1024 - kStaticSmem) --w;
+    while (w > 0 && iterate_smem_bytes(od, zmax, w, det, K) > 227 * 1024 - kStaticSmem) --w;
     return w;
 }
 
@@ -925,9 +986,9 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     if (c->p.out_dim == 2 && Wc > 16) Wc = 16;
     if (c->p.out_dim == 3 && Wc > 21) Wc = 21;
     const bool det = c->deterministic;
-    Wc = iterate_warps(c->p.out_dim, c->zmax, Wc, det);
+    Wc = iterate_warps(c->p.out_dim, c->zmax, Wc, det, K);
     if (Wc < 1) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, Wc, det);
+    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, Wc, det, K);
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     IterArgs a;
@@ -945,6 +1006,7 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     a.opt = Optim{c->p.lr, c->p.momentum, c->p.lr_mode, c->p.use_gains};
     a.queue = c->queue;
     a.zcap = (int)((c->zmax + kPT - 1) / kPT * kPT);
+    a.acc_rows = iterate_acc_rows(c->zmax, det, K);
 
     // the build for the fewest threads that hold the block: more registers per thread
     void (*kern)(IterArgs);

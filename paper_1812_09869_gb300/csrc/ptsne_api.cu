@@ -162,7 +162,7 @@ int ptsne_create(ptsne_ctx** out, const ptsne_params* prm) {
         return bad("precision", p.precision);
     if (p.schedule != PTSNE_SCHED_BATCHED && p.schedule != PTSNE_SCHED_PER_CHUNK) return bad("schedule", p.schedule);
     if (p.use_graph != 0 && p.use_graph != 1) return bad("use_graph must be 0 or 1", p.use_graph);
-    if (p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(p.out_dim, zmax, 1, false) < 1)
+    if (p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(p.out_dim, zmax, 1, false, 1) < 1)
         return bad("largest chunk too large for the batched schedule at this out_dim", zmax);
 
     c->p = p;
@@ -810,6 +810,10 @@ int ptsne_set_tuning(ptsne_ctx* c, const ptsne_tuning* t) {
     const bool ok_k = t->cluster == 1 || t->cluster == 2 || t->cluster == 4;
     if (!ok_k || t->group != 1 || t->consumer_warps < 1 || t->consumer_warps > 21)
         return fail(c, PTSNE_EINVAL, "invalid tuning%s (cluster %lld)", "", t->cluster);
+    if (c->deterministic && c->p.schedule == PTSNE_SCHED_BATCHED &&
+        iterate_warps(c->p.out_dim, c->zmax, 1, true, t->cluster) < 1)
+        return fail(c, PTSNE_EINVAL, "largest chunk too large for the deterministic kernel on clusters of%s %lld",
+                    "", t->cluster);
     c->tune.cluster = t->cluster;
     c->tune.group = t->group;
     c->tune.consumer_warps = t->consumer_warps;
@@ -826,7 +830,7 @@ int ptsne_set_locality_order(ptsne_ctx* c, int on) {
 
 int ptsne_set_deterministic(ptsne_ctx* c, int on) {
     if (!c) return PTSNE_EINVAL;
-    if (on && c->p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(c->p.out_dim, c->zmax, 1, true) < 1)
+    if (on && c->p.schedule == PTSNE_SCHED_BATCHED && iterate_warps(c->p.out_dim, c->zmax, 1, true, c->tune.cluster) < 1)
         return fail(c, PTSNE_EINVAL, "largest chunk too large for the deterministic batched kernel%s (%lld)", "",
                     (long long)c->zmax);
     c->deterministic = on != 0;

@@ -317,8 +317,11 @@ cudaError_t launch_export_packed(const ptsne_ctx* c, float* P_out, cudaStream_t 
 cudaError_t launch_count_nonzero(const ptsne_ctx* c, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* gradp, double* Zc,
                            double* cost_chunk, cudaStream_t s);
-int iterate_warps(int od, int64_t zmax, int want, bool det);   // 0 if the map does not fit in shared memory
-int iterate_smem_bytes(int od, int64_t zmax, int warps, bool det);
+// Warps of the batched iteration kernel that fit its shared memory for the
+// largest chunk zmax (0: not even one), deterministic or not, on clusters of
+// K blocks (the deterministic build splits its accumulators over the cluster).
+int iterate_warps(int od, int64_t zmax, int want, bool det, int K);
+int iterate_smem_bytes(int od, int64_t zmax, int warps, bool det, int K);
 
 Layout make_layout(const ptsne_ctx* c);
 

@@ -118,7 +118,7 @@ def test_identical_runs_give_identical_maps(dev):
     assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-6 * np.abs(outs[0][1]).max()
 
 
-@pytest.mark.parametrize("tuning", [(2, 1, 16), (1, 1, 12)])
+@pytest.mark.parametrize("tuning", [(2, 1, 16), (1, 1, 12), (4, 1, 16)])
 def test_deterministic_runs_are_bitwise_identical(dev, tuning):
     """With fixed-point accumulation (ptsne_set_deterministic) two identical
     multi-epoch runs give the same map and costs bit for bit, in either
@@ -146,15 +146,30 @@ def test_deterministic_runs_are_bitwise_identical(dev, tuning):
 
 def test_deterministic_mode_limits():
     """ptsne_set_deterministic refuses a chunk too large for the fixed-point
-    accumulators of the batched kernel and accepts it on the per-chunk
-    schedule (no GPU work is done)."""
+    accumulators of the batched kernel: on one block per chunk a 6000-point
+    chunk does not fit; on a cluster of 2 or 4 blocks each block holds only
+    its own rows' sums, and it does.  A tuning change that would no longer
+    fit is refused while the mode is on; the per-chunk schedule takes any
+    chunk.  (No GPU work is done.)"""
     from paper_1812_09869_gb300 import ptsne
-    for schedule, ok in (("batched", False), ("per_chunk", True)):
-        cfg = ptsne.Config(n=6000, d=4, offsets=np.array([0, 6000]), perplexity=30.0, iters=1, schedule=schedule)
-        with ptsne.Context(cfg) as ctx:
+    cfg = ptsne.Config(n=6000, d=4, offsets=np.array([0, 6000]), perplexity=30.0, iters=1, schedule="batched")
+    with ptsne.Context(cfg) as ctx:
+        for cluster, ok in ((1, False), (2, True), (4, True)):
+            ctx.set_deterministic(False)
+            ctx.set_tuning(cluster, 1, 16)
             if ok:
                 ctx.set_deterministic(True)
             else:
                 with pytest.raises(ptsne.PtsneError):
                     ctx.set_deterministic(True)
-            ctx.set_deterministic(False)
+        ctx.set_deterministic(False)
+        ctx.set_tuning(2, 1, 16)
+        ctx.set_deterministic(True)
+        with pytest.raises(ptsne.PtsneError):
+            ctx.set_tuning(1, 1, 16)
+        assert ctx.tuning()[0] == 2
+        ctx.set_deterministic(False)
+    cfg = ptsne.Config(n=6000, d=4, offsets=np.array([0, 6000]), perplexity=30.0, iters=1, schedule="per_chunk")
+    with ptsne.Context(cfg) as ctx:
+        ctx.set_deterministic(True)
+        ctx.set_deterministic(False)

@@ -137,7 +137,8 @@ def test_step_three_dims_paper_lr_no_gains(dev, schedule):
         assert rel_max(Y1[idx] - Y0[idx], Yr - Y0[idx]) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("tuning,det", [((2, 1, 20), False), ((1, 1, 12), False), ((2, 1, 20), True)])
+@pytest.mark.parametrize("tuning,det", [((2, 1, 20), False), ((1, 1, 12), False), ((2, 1, 20), True),
+                                        ((4, 1, 20), True), ((1, 1, 12), True)])
 def test_three_dims_every_build_gradient_and_cost(dev, tuning, det):
     """3-D maps through both builds of the batched kernel for 3-D (more and
     fewer than 18 warps): one step's gradient and Z, and the cost
@@ -317,7 +318,8 @@ def test_invalid_launch_shapes_are_rejected(dev):
     ctx.close()
 
 
-@pytest.mark.parametrize("tuning,det", [(t, False) for t in TUNINGS] + [((2, 1, 16), True), ((1, 1, 5), True)])
+@pytest.mark.parametrize("tuning,det", [(t, False) for t in TUNINGS] + [((2, 1, 16), True), ((1, 1, 5), True),
+                                                                   ((4, 1, 12), True)])
 def test_gradient_for_every_launch_shape(dev, tuning, det):
     """Gradient, Z, updated map and cost of one step for each launch shape
     (and, det, with the fixed-point accumulators of ptsne_set_deterministic),
