@@ -197,7 +197,8 @@ int ptsne_set_locality_order(ptsne_ctx* ctx, int on);
  * iteration, not bit for bit.  1: the sums are kept in 64-bit fixed point
  * (A at 2^-61, R at 2^-48; integer adds do not depend on their order), so
  * that identical runs on one GPU give bitwise identical maps and costs.  The
- * 8-byte sums need twice the shared memory; on clusters of 2 or 4 blocks
+ * 8-byte sums need twice the shared memory; where that would leave a block
+ * fewer warps than the tuning asks for, on clusters of 2 or 4 blocks
  * (ptsne_set_tuning) each block holds only the sums of the rows it updates
  * and adds to the other rows' sums in their block's shared memory, so the
  * footprint is that of the FP32 sums on 2 blocks and less on 4.  The

@@ -61,9 +61,9 @@ struct IterArgs {
     Optim opt;
     int* queue;                 // chunk work queue (zeroed before launch)
     int zcap;                   // rows of the shared map / accumulators (multiple of 32)
-    int acc_rows;               // rows of one block's accumulators: zcap, or in the deterministic
-                                // build with a cluster of K > 1 blocks ceil(zcap / K) rounded up
-                                // to 32 (each block holds the sums of the rows it updates)
+    int acc_rows;               // rows of one block's accumulators: zcap, or, when the deterministic
+                                // build splits its sums over a cluster of K > 1 blocks, ceil(zcap / K)
+                                // rounded up to 32 (each block holds the sums of the rows it updates)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -164,13 +164,14 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
 // 8 bytes.
 constexpr float kFixA = 2305843009213693952.0f;   // 2^61
 constexpr float kFixR = 281474976710656.0f;       // 2^48
-// One block's view of the accumulators.  The FP32 build and the
-// deterministic build on one block: every block holds all rows (quantity q
-// of row i at q * stride + i, stride = zcap).  The deterministic build on a
-// cluster of K > 1 blocks: block r holds rows [r slice, (r + 1) slice) only
-// (quantity q of its local row l at q * stride + l), and an add to another
-// block's row goes to that block's shared memory (a cluster-scope reduction),
-// so that each block's 8-byte sums take 1 / K of the space.
+// One block's view of the accumulators.  Whole sums (the FP32 build, and the
+// deterministic build where they leave the block the warps asked for): every
+// block holds all rows (quantity q of row i at q * stride + i, stride = zcap).
+// Split sums (the deterministic build on a cluster of K > 1 blocks
+// otherwise): block r holds rows [r slice, (r + 1) slice) only (quantity q
+// of its local row l at q * stride + l), and an add to another block's row
+// goes to that block's shared memory (a cluster-scope reduction), so that
+// each block's 8-byte sums take 1 / K of the space.
 struct AccRef {
     float* p;
     int stride;
@@ -734,10 +735,11 @@ __global__ void __launch_bounds__(MAXT, 1) iterate_kernel(IterArgs A) {
         // rows updated by this block; the deterministic build on a cluster
         // splits the accumulators the same way (over the zr padded rows, which
         // all receive sums), each block holding its own rows' sums
-        const bool split = DET && K > 1;
+        const bool split = DET && K > 1 && A.acc_rows < zcap;   // chosen by the launcher
         const int slice = split ? (zr + (int)K - 1) / (int)K : (z + (int)K - 1) / (int)K;
         const int ulo = (int)rank * slice, uhi = min(z, ulo + slice);
-        const AccRef accr{acc, split ? A.acc_rows : zcap, slice, rank, split ? K : 1u};
+        // (whole sums: every add is local, owner 0 of a one-block view)
+        const AccRef accr{acc, split ? A.acc_rows : zcap, slice, split ? rank : 0u, split ? K : 1u};
         const int npass = A.iters + (A.cost_pass ? 1 : 0);
 
         // this warp's tiles of the chunk: a contiguous piece of the block's
@@ -986,9 +988,13 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     if (c->p.out_dim == 2 && Wc > 16) Wc = 16;
     if (c->p.out_dim == 3 && Wc > 21) Wc = 21;
     const bool det = c->deterministic;
-    Wc = iterate_warps(c->p.out_dim, c->zmax, Wc, det, K);
+    // deterministic sums: whole in every block, unless that leaves fewer
+    // warps than asked for and the cluster can split them
+    const int Wwhole = iterate_warps(c->p.out_dim, c->zmax, Wc, det, 1);
+    const bool split = det && K > 1 && Wwhole < Wc;
+    Wc = split ? iterate_warps(c->p.out_dim, c->zmax, Wc, det, K) : Wwhole;
     if (Wc < 1) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, Wc, det, K);
+    const size_t smem = (size_t)iterate_smem_bytes(c->p.out_dim, c->zmax, Wc, det, split ? K : 1);
     cudaError_t e = cudaMemsetAsync(c->queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     IterArgs a;
@@ -1006,7 +1012,7 @@ cudaError_t launch_iterate(const ptsne_ctx* c, int iters, int cost_pass, float* 
     a.opt = Optim{c->p.lr, c->p.momentum, c->p.lr_mode, c->p.use_gains};
     a.queue = c->queue;
     a.zcap = (int)((c->zmax + kPT - 1) / kPT * kPT);
-    a.acc_rows = iterate_acc_rows(c->zmax, det, K);
+    a.acc_rows = iterate_acc_rows(c->zmax, det, split ? K : 1);
 
     // the build for the fewest threads that hold the block: more registers per thread
     void (*kern)(IterArgs);
