@@ -383,7 +383,7 @@ size_t ptsne_workspace_bytes(const ptsne_ctx* ctx);
 int ptsne_kde_grid(const float* Y_dev, const float* beta_dev, int64_t n, int32_t gx, int32_t gy,
                    const float* box_host, float* density_dev, int64_t* dropped_dev, void* stream);
 
-/* k-nearest-neighbour preservation of a map (the judge of a map's local
+/* k-nearest-neighbour preservation of a map (the measure of a map's local
  * structure, used on the learned mapper's placements): for each query q (an
  * index into the n points), the k nearest neighbours of q among the rows of
  * X_dev (n x d) and among the rows of Y_dev (n x od), by squared Euclidean

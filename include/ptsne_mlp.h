@@ -4,7 +4,7 @@
  * The paper maps new points only by re-running ptSNE.  This library adds a
  * small network trained on the maps that ptSNE itself produces: it places
  * held-out points directly, and its output warm-starts ptsne_run (pass it as
- * the start map Y).  Plain ptSNE stays the fallback and the judge of the
+ * the start map Y).  Plain ptSNE stays the fallback and the measure of the
  * mapper's quality (KL of Eq. 5 and k-nearest-neighbour preservation).
  *
  * Network: y = W3 g(W2 g(W1 x + b1) + b2) + b3 with g the exact GELU
@@ -109,7 +109,7 @@ int ptsne_mlp_infer(ptsne_mlp* m, const float* X_dev, int64_t n, float* Y_out_de
 
 struct ptsne_ctx;
 
-/* Warm start with plain ptSNE as the fallback and the judge.  The mapper
+/* Warm start with plain ptSNE as the fallback and the arbiter.  The mapper
  * places the n points of X_dev (n x d_in, d_in = the context's d) into Y_dev
  * (n x out_dim); then one ptSNE epoch on the partition perm_dev runs from
  * that placement and one from the cold start Y_random_dev (n x out_dim, not
